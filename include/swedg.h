@@ -1,0 +1,175 @@
+/*
+ * swedg.h -- C ABI of libswedg, a GB300 (sm_103a) solver for the quadrature-free,
+ * p-adaptive discontinuous Galerkin discretisation of the 2D shallow water
+ * equations of Faghih-Naini, Aizinger, Kuckuk, Angersbach and Koestler,
+ * "p-adaptive discontinuous Galerkin method for the shallow water equations on
+ * heterogeneous computing architectures" (2023).
+ *
+ * The problem statement the calls follow is Sect. 2: a triangulation with
+ * bathymetry h_b, initial elevation xi and momentum q = (U, V), land
+ * (q.n = 0) and open-sea (xi = xi_hat) boundaries, per-element polynomial
+ * orders, and the semi-discrete system of Eqs. (8)-(9) advanced by an SSP
+ * Runge-Kutta method.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns 0 on success or one of the negative SWE_E* codes; the
+ *    text of the last failure is available from swe_last_error().
+ *  - The library owns all device memory.  Host buffers passed in are copied
+ *    before the call returns; nothing the caller passes is retained.
+ *  - Pointers marked "host or device" may point to host memory or to device
+ *    memory of the context's device (detected with cudaPointerGetAttributes).
+ *  - State arrays use the layout c[3][15][ne]: field (0 = xi, 1 = U, 2 = V),
+ *    modal index i of the orthonormal Dubiner basis (hierarchical: degree 0,
+ *    then degree 1, ... ; K(p) = 1, 3, 6, 10, 15 modes for p = 0..4, Sect. 2
+ *    Eqs. (11)-(12)), element in the caller's order.  Rows i >= K(p_e) are
+ *    ignored on input and written as zero on output.
+ *  - Coefficients are those of the basis orthonormal on each physical element
+ *    Omega_e, phi_{e,i} = phihat_i o F_e^{-1} / sqrt|det J_e|, so the element
+ *    mean of a field is c_1 / sqrt|Omega_e|.
+ *  - A context is not thread safe; calls on one context are serialised on its
+ *    CUDA stream.
+ */
+#ifndef SWEDG_H
+#define SWEDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define SWE_OK 0
+#define SWE_EINVAL (-1)   /* invalid argument or call order                        */
+#define SWE_EMESH (-2)    /* degenerate triangle, non-manifold edge, bad vertex id   */
+#define SWE_EDEPTH (-3)   /* an element mean of H = h_b + xi fell to or below h_min  */
+#define SWE_ENONFINITE (-4) /* a non-finite value appeared in the state or the rhs  */
+#define SWE_ECUDA (-5)    /* a CUDA runtime call failed                             */
+#define SWE_ETIMEOUT (-6) /* a bounded device-side wait gave up                     */
+
+/* precision modes of the higher-order correction (Sect. 3 order separation):
+ * the base part (modes of degree <= 1, the CFL reduction, the RK update of the
+ * base modes) is FP64 in every mode. */
+#define SWE_PREC_FP64 0       /* correction in FP64 as well                          */
+#define SWE_PREC_MIXED_FP32 1 /* correction arithmetic and storage in FP32           */
+
+typedef struct swe_ctx swe_ctx; /* opaque */
+
+typedef struct {
+  double g;           /* gravitational acceleration (Eq. 2)                          */
+  double cfl;         /* CFL factor of the automatic time step                       */
+  double h_min;       /* depth floor: an element mean H <= h_min is an error (-3)    */
+  int rk_order;       /* 2: two-stage SSP-RK (Heun), 3: three-stage SSP-RK            */
+  int precision;      /* SWE_PREC_*                                                  */
+  double tide_amp;    /* open-sea elevation xi_hat(t) = amp * sin(2 pi t / period    */
+  double tide_period; /*   + phase); period <= 0 gives the constant xi_hat = amp     */
+  double tide_phase;
+  void* cuda_stream;  /* cudaStream_t to run on; NULL = a stream the library creates */
+} swe_params;
+
+/* Fill *p with defaults: g = 9.81, cfl = 0.1, h_min = 1e-8, rk_order = 2,
+ * FP64, no tide, library stream. */
+void swe_default_params(swe_params* p);
+
+/* Create a context on the current CUDA device.  *out is set on success. */
+int swe_create(swe_ctx** out, const swe_params* params);
+
+/* Release every resource of the context (NULL is accepted). */
+void swe_destroy(swe_ctx* ctx);
+
+/* Text of the last error of the context (or of swe_create when ctx is NULL). */
+const char* swe_last_error(const swe_ctx* ctx);
+
+/* Triangulation (Sect. 2: Omega = union of triangles Omega_e).
+ *   xy[nv][2]   vertex coordinates (host)
+ *   tri[ne][3]  vertex indices (host); clockwise triangles are re-oriented
+ *               internally, which keeps "edge k is opposite vertex k"
+ *   bc_tag      host [ne][3] or NULL; entry k describes the edge opposite
+ *               vertex k: 0 = interior, or land if no neighbour matches;
+ *               1 = land (q.n = 0); 2 = open sea (xi = xi_hat).  NULL = every
+ *               edge without a neighbour is land.
+ * Errors: SWE_EMESH for a zero-area triangle, an out-of-range vertex index or
+ * an edge shared by more than two triangles.  Resets orders to p = 1, the
+ * bathymetry to zero and the state to zero. */
+int swe_set_mesh(swe_ctx* ctx, int64_t nv, const double* xy, int64_t ne, const int32_t* tri,
+                 const int8_t* bc_tag);
+
+/* Bathymetry h_b (Eq. 2: H = h_b + xi), depths > 0 below the datum, given at
+ * the vertices (host [nv]); the library uses its continuous piecewise-linear
+ * interpolant. */
+int swe_set_bathymetry(swe_ctx* ctx, const double* hb_vertex);
+
+/* Per-element polynomial orders p_e in 0..4 (host [ne], caller's element
+ * order).  The basis is hierarchical (Sect. 2), so the current state is kept:
+ * modes beyond the new K(p_e) are dropped, new modes start at zero. */
+int swe_set_orders(swe_ctx* ctx, const int8_t* p);
+
+/* Modal state c[3][15][ne] (host or device) and its time t. */
+int swe_set_state(swe_ctx* ctx, const double* c, double t);
+
+/* Copy the modal state out (host or device c_out[3][15][ne]); t_out may be NULL. */
+int swe_get_state(swe_ctx* ctx, double* c_out, double* t_out);
+
+/* Modal coefficients of the continuous piecewise-linear interpolant of vertex
+ * values (host vals[nv]) -> host or device modes_out[3][ne] (modes 1..3).
+ * This is how the bathymetry enters the scheme; it also gives P1 initial
+ * states. */
+int swe_p1_modes(swe_ctx* ctx, const double* vals, double* modes_out);
+
+/* Semi-discrete right-hand side dc/dt of Eq. (8) (orthonormal basis, so the
+ * mass matrix is the identity) for the state c_in at the context's time:
+ * rhs_out[3][15][ne].  c_in and rhs_out may be host or device.  The
+ * context's own state is not changed. */
+int swe_rhs(swe_ctx* ctx, const double* c_in, double* rhs_out);
+
+/* The two parts of the order separation (Sect. 3, Eq. 13 and the text after
+ * it): base_out holds every term whose test index and coefficient indices are
+ * all modes of degree <= 1; corr_out holds the rest.  base + corr = rhs. */
+int swe_rhs_parts(swe_ctx* ctx, const double* c_in, double* base_out, double* corr_out);
+
+/* One SSP Runge-Kutta step of the context state (Sect. 2).  dt > 0 is used as
+ * given; dt <= 0 takes the CFL step
+ *   dt = cfl * min_e d_e / ((|u_bar_e| + sqrt(g H_bar_e)) (2 p_e + 1)),
+ * d_e the inscribed diameter, u_bar and H_bar element means.  dt_used may be
+ * NULL.  Returns SWE_EDEPTH / SWE_ENONFINITE when the step produced such a
+ * state (the state is then left as computed). */
+int swe_rk_step(swe_ctx* ctx, double dt, double* dt_used);
+
+/* nsteps CFL steps (dt_fixed <= 0) or fixed steps of dt_fixed; t_out (may be
+ * NULL) receives the final time.  Checks the status word once at the end. */
+int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out);
+
+/* Diagnostics of the context state:
+ *   mass   = int xi dx = sum_e sqrt|Omega_e| xi_e1
+ *   energy = 1/2 g int xi^2 + 1/2 int q.u  (u from the auxiliary system) */
+int swe_mass(swe_ctx* ctx, double* m);
+int swe_energy(swe_ctx* ctx, double* e);
+
+/* Reference tensors the library generated (by its own Gauss quadrature) for
+ * the contractions of Eq. (13):
+ *   D[2][15][15]      D_k[q][i]    = int_T phihat_i d_k phihat_q
+ *   G[2][15][15][15]  G_k[q][i][j] = int_T phihat_i phihat_j d_k phihat_q
+ *   T[15][15][15]     T[n][i][j]   = int_T phihat_n phihat_i phihat_j
+ * on the reference triangle T = {x, y >= 0, x + y <= 1}.  Host pointers, any
+ * may be NULL.  Needs no device. */
+int swe_reference_tensors(double* D, double* G, double* T);
+
+/* Trace table of the factored edge integrals: npts Gauss-Legendre points
+ * s_g in (0,1) with weights w_g (summing to 1) and
+ *   B[k][i][g] = phihat_i(gamma_k(s_g)),
+ * gamma_0(s) = (1-s, s), gamma_1(s) = (0, 1-s), gamma_2(s) = (s, 0), i.e.
+ * local edge k is opposite reference vertex k and runs counter-clockwise.
+ * npts in 1..8; host pointers.  Needs no device. */
+int swe_edge_table(int npts, double* s, double* w, double* B);
+
+/* Timing of the last swe_run / swe_rk_step split by kernel family (ms, CUDA
+ * events on the context stream), when enabled with swe_profile(ctx, 1).
+ * names receives up to n entries; returns the number of entries. */
+int swe_profile(swe_ctx* ctx, int enable);
+int swe_profile_read(swe_ctx* ctx, int n, const char** names, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

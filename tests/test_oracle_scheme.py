@@ -1,0 +1,313 @@
+"""Pins of the oracle's scheme (no GPU): the right-hand side of Eq. (8) with
+the Lax-Friedrichs flux and Eq. (10), the truncated auxiliary system of
+Sect. 3, the order separation of Sect. 3 and the SSP-RK time stepping.
+
+Every check compares the oracle with something other than itself:
+brute-force quadrature of the pointwise weak form, a separate finite-volume
+code, exact invariants (mass, lake at rest, free stream, rotation) and the
+order of accuracy in time.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import dgref
+import oracle as O
+from paper_2311_11348_gb300 import inputs
+
+K_OF_P = dgref.K_OF_P
+
+
+def tiny_meshes():
+    one = (np.array([[0.1, 0.0], [1.3, 0.2], [0.4, 0.9]]), np.array([[0, 1, 2]]))
+    two = (np.array([[0.0, 0.0], [1.0, 0.1], [1.1, 1.0], [-0.1, 0.9]]), np.array([[0, 1, 2], [0, 2, 3]]))
+    xy, tri = inputs.split_square_mesh(2, 1.0, jitter=0.2, seed=11)
+    tri = tri.copy()
+    tri[3] = tri[3][[0, 2, 1]]  # one clockwise triangle: must be re-oriented
+    return [one, two, (xy, tri)]
+
+
+def random_state(ne, orders, rng, mean_xi=0.3, amp=0.05):
+    c = np.zeros((3, 15, ne))
+    for e in range(ne):
+        K = K_OF_P[orders[e]]
+        c[0, 0, e] = mean_xi
+        c[0, 1:K, e] = amp * rng.standard_normal(K - 1) * 0.5 ** dgref.DEG[1:K]
+        c[1, :K, e] = amp * rng.standard_normal(K) * 0.5 ** dgref.DEG[:K]
+        c[2, :K, e] = amp * rng.standard_normal(K) * 0.5 ** dgref.DEG[:K]
+    return c
+
+
+def scale_state_means(c, area):
+    c = c.copy()
+    c[:, 0, :] *= np.sqrt(area)  # coefficient of a constant = value * sqrt|Omega|
+    return c
+
+
+@pytest.mark.parametrize("case", range(3))
+@pytest.mark.parametrize("seed", [0, 1])
+def test_rhs_equals_brute_force_weak_form(case, seed):
+    xy, tri = tiny_meshes()[case]
+    rng = np.random.default_rng(100 * case + seed)
+    ne = len(tri)
+    orders = rng.integers(0, 5, size=ne).astype(np.int8)
+    hv = 1.0 + 0.3 * rng.uniform(size=len(xy))
+    bc = None
+    opened = []
+    if case == 1 and seed == 1:
+        # the edge opposite vertex 1 of triangle 0 is (2,0): interior; make a boundary one open
+        bc = np.zeros((ne, 3), np.int8)
+        bc[0, 2] = 2  # edge opposite vertex 2: (0,1), on the boundary
+        opened = [(0, 2)]
+    g = 9.81
+    m = O.Mesh(xy, tri, hv, orders, bc_tag=bc)
+    geo = m.geometry()
+    c = scale_state_means(random_state(ne, orders, rng), geo["area"])
+    P = O.Params(g=g, tide_amp=0.05, tide_period=0.0)
+    r, u = m.rhs(P, c, t=0.0, with_u=True)
+    msh = dgref.Tri(xy, tri)
+    u_ref = dgref.solve_u(msh, hv, orders, c)
+    assert np.abs(u - u_ref).max() <= 1e-13 * max(1.0, np.abs(u_ref).max())
+    # the brute-force side orients triangles itself; element order is the same
+    rb = dgref.brute_force_rhs(msh, hv, orders, c, u, g, bc_open=opened, xi_hat=0.05)
+    assert np.abs(r - rb).max() <= 1e-12 * max(1.0, np.abs(rb).max())
+
+
+def fv_rhs(xy, tri, hv, means, g):
+    """First-order finite volumes with the paper's LF flux (lambda of Eq. 10
+    from cell means), pressure g xi (xi/2 + h_b(x_E)) |E| and source
+    g xi grad h_b |Omega| -- the p = 0 case of the scheme written out."""
+    ne = len(tri)
+    xi, U, V = means
+    area = np.zeros(ne); grad = np.zeros((ne, 2)); hmean = np.zeros(ne)
+    edges = {}
+    for e in range(ne):
+        a, b, c = xy[tri[e]]
+        area[e] = 0.5 * abs((b[0] - a[0]) * (c[1] - a[1]) - (c[0] - a[0]) * (b[1] - a[1]))
+        A = np.array([[b[0] - a[0], b[1] - a[1]], [c[0] - a[0], c[1] - a[1]]])
+        h = hv[tri[e]]
+        grad[e] = np.linalg.solve(A, [h[1] - h[0], h[2] - h[0]])
+        hmean[e] = h.mean()
+        for k in range(3):
+            i, j = tri[e, (k + 1) % 3], tri[e, (k + 2) % 3]
+            edges.setdefault((min(i, j), max(i, j)), []).append(e)
+    H = xi + hmean
+    uu, vv = U / H, V / H
+    d = np.zeros((3, ne))
+    cen = np.array([xy[t].mean(axis=0) for t in tri])
+    for (i, j), els in edges.items():
+        pa, pb = xy[i], xy[j]
+        L = np.hypot(*(pb - pa))
+        hm = 0.5 * (hv[i] + hv[j])
+        e = els[0]
+        n = np.array([pb[1] - pa[1], -(pb[0] - pa[0])]) / L
+        if n @ (0.5 * (pa + pb) - cen[e]) < 0:
+            n = -n
+        ca = np.array([xi[e], U[e], V[e]])
+        wa = np.array([uu[e], vv[e]])
+        if len(els) == 2:
+            f = els[1]
+            cb = np.array([xi[f], U[f], V[f]]); wb = np.array([uu[f], vv[f]])
+        else:
+            qn = ca[1] * n[0] + ca[2] * n[1]
+            cb = np.array([ca[0], ca[1] - 2 * qn * n[0], ca[2] - 2 * qn * n[1]])
+            wb = wa - 2 * (wa @ n) * n
+        lam = max(abs(wa @ n), abs(wb @ n)) + max(math.sqrt(g * (ca[0] + hm)), math.sqrt(g * (cb[0] + hm)))
+
+        def flux(c_, w_):
+            P = g * c_[0] * (0.5 * c_[0] + hm)
+            un = w_ @ n
+            return np.array([c_[1] * n[0] + c_[2] * n[1], c_[1] * un + P * n[0], c_[2] * un + P * n[1]])
+
+        F = 0.5 * (flux(ca, wa) + flux(cb, wb) + lam * (ca - cb)) * L
+        d[:, e] -= F
+        if len(els) == 2:
+            d[:, els[1]] += F
+    d[1] += g * xi * grad[:, 0] * area
+    d[2] += g * xi * grad[:, 1] * area
+    return d / area
+
+
+def test_p0_is_first_order_finite_volumes():
+    xy, tri = inputs.split_square_mesh(6, 2.0, jitter=0.2, seed=3)
+    ne = len(tri)
+    rng = np.random.default_rng(7)
+    hv = 2.0 + 0.5 * rng.uniform(size=len(xy))
+    m = O.Mesh(xy, tri, hv, np.zeros(ne, np.int8))
+    area = m.geometry()["area"]
+    means = np.stack([0.2 * rng.standard_normal(ne), 0.3 * rng.standard_normal(ne), 0.3 * rng.standard_normal(ne)])
+    c = np.zeros((3, 15, ne))
+    c[:, 0, :] = means * np.sqrt(area)
+    r = m.rhs(O.Params(g=9.81), c)
+    dg = r[:, 0, :] / np.sqrt(area)
+    fv = fv_rhs(xy, tri, hv, means, 9.81)
+    assert np.abs(dg - fv).max() <= 1e-13 * np.abs(fv).max()
+    assert np.all(r[:, 1:, :] == 0.0)
+
+
+def jittered_mixed(n=6, seed=4, pmin=0, pmax=4):
+    xy, tri = inputs.split_square_mesh(n, 1.0, jitter=0.2, seed=seed)
+    rng = np.random.default_rng(seed)
+    orders = rng.integers(pmin, pmax + 1, size=len(tri)).astype(np.int8)
+    hv = 1.0 + 0.2 * np.sin(3 * xy[:, 0]) * np.cos(2 * xy[:, 1])
+    return xy, tri, hv, orders
+
+
+@pytest.mark.parametrize("xi0", [0.0, 0.37])
+def test_lake_at_rest(xi0):
+    xy, tri, hv, orders = jittered_mixed()
+    m = O.Mesh(xy, tri, hv, orders)
+    area = m.geometry()["area"]
+    c = np.zeros((3, 15, len(tri)))
+    c[0, 0, :] = xi0 * np.sqrt(area)
+    P = O.Params(g=9.81, rk_order=3, cfl=0.2)
+    r = m.rhs(P, c)
+    scale = 9.81 * max(xi0, 1.0) * hv.max()
+    if xi0 == 0.0:
+        assert np.all(r == 0.0)
+    else:
+        assert np.abs(r).max() <= 1e-12 * scale
+    c1, t = m.run(P, c, 0.0, 100)
+    assert np.abs(c1 - c).max() <= 1e-12 * max(xi0, 1.0)
+
+
+def test_free_stream_flat_bottom():
+    xy, tri, hv, orders = jittered_mixed(seed=5)
+    hv = np.full(len(xy), 3.0)
+    m = O.Mesh(xy, tri, hv, orders)
+    area = m.geometry()["area"]
+    ne = len(tri)
+    c = np.zeros((3, 15, ne))
+    c[0, 0] = 0.2 * np.sqrt(area); c[1, 0] = 0.5 * np.sqrt(area); c[2, 0] = -0.3 * np.sqrt(area)
+    r, u = m.rhs(O.Params(g=9.81), c, with_u=True)
+    # constant H: u = U / H exactly (P10)
+    assert np.allclose(u[0, 0] / np.sqrt(area), 0.5 / 3.2, rtol=1e-14, atol=0)
+    assert np.abs(u[:, 1:]).max() < 1e-15
+    nb = m.neighbours()["bc"]
+    inner = np.all(nb == 0, axis=1)
+    assert inner.sum() > 10
+    assert np.abs(r[:, :, inner]).max() < 1e-12
+
+
+def test_usolve_constant_depth_any_momentum():
+    xy, tri, hv, orders = jittered_mixed(seed=6, pmin=1)
+    hv = np.full(len(xy), 2.5)
+    m = O.Mesh(xy, tri, hv, orders)
+    area = m.geometry()["area"]
+    rng = np.random.default_rng(1)
+    c = random_state(len(tri), orders, rng, mean_xi=0.0)
+    c[0] = 0.0
+    c[0, 0] = 0.5 * np.sqrt(area)
+    u, st = m.usolve(O.Params(), c)
+    assert st == 0
+    assert np.abs(u - c[1:] / 3.0).max() < 1e-14 * np.abs(c[1:]).max()
+
+
+def test_separation_identity():
+    xy, tri, hv, orders = jittered_mixed(seed=8, pmin=1)
+    m = O.Mesh(xy, tri, hv, orders)
+    area = m.geometry()["area"]
+    rng = np.random.default_rng(3)
+    c = scale_state_means(random_state(len(tri), orders, rng), area)
+    P = O.Params(g=9.81)
+    full = m.rhs(P, c, part=0)
+    base = m.rhs(P, c, part=1)
+    corr = m.rhs(P, c, part=2)
+    assert np.abs(base + corr - full).max() <= 1e-14 * np.abs(full).max()
+    nb = m.neighbours()["nb"]
+    lo = np.array([orders[e] <= 1 and all(n < 0 or orders[n] <= 1 for n in nb[e]) for e in range(len(tri))])
+    assert lo.sum() > 0
+    assert np.all(corr[:, :, lo] == 0.0)
+    # base only ever touches modes of degree <= 1
+    assert np.all(base[:, 3:, :] == 0.0)
+
+
+def test_rotation_equivariance():
+    xy, tri, hv, orders = jittered_mixed(seed=9)
+    rng = np.random.default_rng(4)
+    m = O.Mesh(xy, tri, hv, orders)
+    area = m.geometry()["area"]
+    c = scale_state_means(random_state(len(tri), orders, rng), area)
+    r = m.rhs(O.Params(g=9.81), c)
+    xy2 = np.stack([-xy[:, 1], xy[:, 0]], axis=1)
+    m2 = O.Mesh(xy2, tri, hv, orders)
+    c2 = np.stack([c[0], -c[2], c[1]])
+    r2 = m2.rhs(O.Params(g=9.81), c2)
+    expect = np.stack([r[0], -r[2], r[1]])
+    assert np.abs(r2 - expect).max() <= 1e-13 * np.abs(r).max()
+
+
+def test_mass_conservation_walls():
+    xy, tri, hv, orders = jittered_mixed(n=8, seed=10)
+    m = O.Mesh(xy, tri, hv, orders)
+    c = m.project_state(lambda x, y: (0.05 * np.exp(-((x - 0.4) ** 2 + (y - 0.6) ** 2) / 0.02), 0.0 * x, 0.0 * x))
+    P = O.Params(g=9.81, rk_order=3, cfl=0.2)
+    M0 = m.mass(c)
+    area = m.geometry()["area"]
+    Mref = M0 + np.sum(m.geometry()["hb"][:, 0] * np.sqrt(area))  # total water volume int H
+    steps = 200
+    c1, t = m.run(P, c, 0.0, steps)
+    assert t > 0
+    assert abs(m.mass(c1) - M0) / Mref <= 1e-13 * math.sqrt(steps)
+    assert np.abs(c1 - c).max() > 1e-6  # the state did evolve
+
+
+def test_energy_matches_quadrature():
+    xy, tri = tiny_meshes()[2]
+    rng = np.random.default_rng(5)
+    orders = rng.integers(0, 5, size=len(tri)).astype(np.int8)
+    hv = 1.0 + 0.3 * rng.uniform(size=len(xy))
+    m = O.Mesh(xy, tri, hv, orders)
+    c = scale_state_means(random_state(len(tri), orders, rng), m.geometry()["area"])
+    P = O.Params(g=2.0)
+    E = m.energy(P, c)
+    u, _ = m.usolve(P, c)
+    msh = dgref.Tri(xy, tri)
+    x, y, w = dgref.tri_rule(10)
+    Eq = 0.0
+    for e in range(len(tri)):
+        K = K_OF_P[orders[e]]
+        X, Y = msh.to_phys(e, x, y)
+        ph, _, _ = msh.phys_basis(e, X, Y)
+        f = lambda a: np.tensordot(a[:K], ph[:K], 1)  # noqa: E731
+        Eq += np.sum(w * msh.det[e] * (0.5 * 2.0 * f(c[0, :, e]) ** 2 + 0.5 * (f(c[1, :, e]) * f(u[0, :, e]) + f(c[2, :, e]) * f(u[1, :, e]))))
+    assert abs(E - Eq) <= 1e-13 * abs(Eq)
+
+
+@pytest.mark.parametrize("rk,order", [(2, 2), (3, 3)])
+def test_ssp_rk_temporal_order(rk, order):
+    """Self-convergence in dt of the SSP-RK schemes (Sect. 2 time stepping)."""
+    xy, tri = inputs.split_square_mesh(4, 1.0)
+    hv = np.full(len(xy), 1.0)
+    orders = np.full(len(tri), 2, np.int8)
+    m = O.Mesh(xy, tri, hv, orders)
+    c0 = m.project_state(lambda x, y: (0.05 * np.cos(math.pi * x) * np.cos(math.pi * y), 0.0 * x, 0.0 * x))
+    P = O.Params(g=1.0, rk_order=rk)
+    T_end = 0.08
+    sols = []
+    for nsteps in (8, 16, 32, 64):
+        c, _ = m.run(P, c0, 0.0, nsteps, dt=T_end / nsteps)
+        sols.append(c)
+    e1 = np.abs(sols[0] - sols[3]).max()
+    e2 = np.abs(sols[1] - sols[3]).max()
+    e3 = np.abs(sols[2] - sols[3]).max()
+    # errors against the finest run: e_k ~ C dt^order (1 - 2^-order(...)) -> ratio 2^order
+    rate = math.log2((e1 - e2) / (e2 - e3))
+    assert abs(rate - order) < 0.3, rate
+
+
+def test_cfl_step_definition():
+    # one right isosceles triangle with legs 2: inscribed diameter 4|T|/perimeter
+    xy = np.array([[0.0, 0.0], [2.0, 0.0], [0.0, 2.0]])
+    tri = np.array([[0, 1, 2]])
+    m = O.Mesh(xy, tri, np.full(3, 4.0), np.array([1], np.int8))
+    c = np.zeros((3, 15, 1))
+    area = 2.0
+    c[0, 0, 0] = 0.9 * math.sqrt(area)      # mean xi 0.9 -> H = 4.9
+    c[1, 0, 0] = 4.9 * 3.0 * math.sqrt(area)  # u = 3
+    c[2, 0, 0] = 4.9 * 4.0 * math.sqrt(area)  # v = 4
+    P = O.Params(g=10.0, cfl=0.5)
+    d = 4 * area / (4 + 2 * math.sqrt(2))
+    expect = 0.5 * d / ((5.0 + math.sqrt(49.0)) * 3)
+    assert abs(m.dt(P, c) - expect) <= 1e-15 * expect
