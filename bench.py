@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark: DOF-stage updates/s of the SSP-RK3 step of the quadrature-free DG
+shallow water scheme on the 131,072-triangle p-adaptive ocean workload
+(256x256 split squares, +-20 % jitter, Fourier bathymetry 50..4000 m, orders
+p in {1,2,3} at 70/20/10 %, CFL steps), FP64 and mixed precision, each with its
+relative L2 error against the FP64 oracle.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one SSP-RK3 step (3 stages) over the whole mesh; DOF-stage updates
+per step = 3 stages x 3 fields x sum_e K(p_e).  The state (~40 MB in all RK
+buffers) fits in the 129 MB L2, so L2 is flushed (256 MB write) between timed
+steps and each step is timed alone with CUDA events on the solver's stream.
+With N > 1 (torchrun), every rank runs an independent replica of the workload
+(the path is replicas-only on this pool; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2311_11348_gb300 import inputs  # noqa: E402
+
+METRIC = "DOF-stage updates/s, mixed vs FP64 at stated L2 error"
+
+
+def dofs_per_step(orders, stages=3):
+    K = np.array([1, 3, 6, 10, 15])[orders.astype(np.int64)]
+    return stages * 3 * int(K.sum())
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) > 2 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 2 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_solver(w, precision, stream):
+    from paper_2311_11348_gb300 import swedg
+    s = swedg.Solver(g=w["g"], cfl=w["cfl"], rk_order=3, precision=precision, stream=stream)
+    s.set_mesh(w["xy"], w["tri"])
+    s.set_bathymetry(w["hv"])
+    s.set_orders(w["orders"])
+    return s
+
+
+def initial_state(s, w):
+    xi_v = w["ic"](w["xy"][:, 0], w["xy"][:, 1])[0]
+    c = np.zeros((3, 15, len(w["tri"])))
+    c[0, :3] = s.p1_modes(xi_v)
+    return c
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2311_11348_gb300 import swedg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    w = inputs.ocean_p123(args.n)
+    ne = len(w["tri"])
+    dps = dofs_per_step(w["orders"])
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    res = {}
+    prec_list = [("mixed", swedg.PREC_MIXED_FP32), ("fp64", swedg.PREC_FP64)]
+    if args.precision == "fp64":
+        prec_list = prec_list[::-1]
+    clocks = None
+    for name, prec in prec_list:
+        s = make_solver(w, prec, stream.cuda_stream)
+        c0 = initial_state(s, w)
+        s.set_state(c0, 0.0)
+        s.run(args.warmup)
+        s.set_state(c0, 0.0)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        if name == prec_list[0][0]:
+            clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
+        times = []
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.add_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s.run(1)
+                b.record(stream)
+                times.append((a, b))
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in times]
+        if name == prec_list[0][0]:
+            clk = clocks.stop()
+        tot = sum(ms)
+        if world > 1:
+            t = torch.tensor([tot], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot = float(t.item())
+        # per-family timing (separate profiled pass over the same steps)
+        s.set_state(c0, 0.0)
+        s.profile(True)
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.add_(1.0)
+                s.run(1)
+        torch.cuda.synchronize()
+        prof = s.profile_read()
+        s.profile(True)
+        s.set_state(c0, 0.0)
+        s.run(args.steps)
+        launches = s.profile_read()["kernels"][1]
+        s.profile(False)
+        res[name] = dict(ms_steps=ms, total_ms=tot, prof=prof, launches=launches, solver=s, c0=c0)
+    return w, dps, res, clk, stream, flush
+
+
+def accuracy(w, res, nsteps=2):
+    """relative L2 error of nsteps CFL steps against the FP64 oracle (same input)"""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    m = O.Mesh(w["xy"], w["tri"], w["hv"], w["orders"])
+    P = O.Params(g=w["g"], cfl=w["cfl"], rk_order=3)
+    out = {}
+    c0 = res["fp64"]["c0"]
+    c_o, t_o = m.run(P, c0, 0.0, nsteps)
+    for name in res:
+        s = res[name]["solver"]
+        s.set_state(c0, 0.0)
+        s.run(nsteps)
+        c_g, _ = s.get_state()
+        out[name] = float(np.linalg.norm(c_g - c_o) / np.linalg.norm(c_o))
+    return out, nsteps
+
+
+def e2e(w, res, name, steps, stream):
+    """the same step through the C ABI with pinned host buffers: state in, one
+    step, state out (host<->device copies inside the timed region)"""
+    import torch
+    s = res[name]["solver"]
+    c0 = res[name]["c0"]
+    hin = torch.from_numpy(c0.copy()).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    s.set_state(hin, 0.0)
+    s.run(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.set_state(hin, 0.0)
+        s.run(1)
+        s.get_state(hout)
+    dt = time.perf_counter() - t0
+    nbytes = hin.numel() * 8
+    return dt, nbytes
+
+
+def oracle_rate(w, steps, warmup):
+    """the FP64 oracle (single thread) on the same workload: full-mesh RK3 steps"""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    m = O.Mesh(w["xy"], w["tri"], w["hv"], w["orders"])
+    P = O.Params(g=w["g"], cfl=w["cfl"], rk_order=3)
+    xi_v = w["ic"](w["xy"][:, 0], w["xy"][:, 1])[0]
+    c = np.zeros((3, 15, len(w["tri"])))
+    c[0, :3] = m.p1_modes(xi_v)
+    for _ in range(warmup):
+        c, _, _ = m.step(P, c, 0.0)
+    t0 = time.perf_counter()
+    t = 0.0
+    for _ in range(steps):
+        c, t, _ = m.step(P, c, t)
+    return time.perf_counter() - t0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=256, help="split-square grid size (256: 131,072 triangles)")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle accuracy and cpu_baseline legs")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    workload = f"ocean_p123: 256x256 split squares ({2 * args.n * args.n} triangles), p in {{1,2,3}} 70/20/10, SSP-RK3, CFL 0.1"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        w = inputs.ocean_p123(args.n)
+        steps = max(1, min(args.steps, 8))
+        warm = min(args.warmup, 1)
+        sec = oracle_rate(w, steps, warm)
+        dps = dofs_per_step(w["orders"])
+        v = dps * steps / sec
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOF-stage/s", "n_gpus": args.gpus,
+                "steps": steps, "warmup": warm, "ms_per_step": 1e3 * sec / steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload, "triangles": len(w["tri"])},
+                "cpu_baseline": {"value": v, "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{steps} full-mesh SSP-RK3 steps of the single-threaded FP64 C oracle"},
+                "e2e": {"value": v, "unit": "DOF-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    w, dps, res, clk, stream, flush = run_ours(args, rank, world)
+    head = args.precision
+    other = "fp64" if head == "mixed" else "mixed"
+    acc, acc_steps = ({}, 0) if args.no_oracle else accuracy(w, res)
+    units = dps * args.steps * world
+    value = units / (res[head]["total_ms"] / 1e3)
+    other_value = units / (res[other]["total_ms"] / 1e3)
+    e2e_s, e2e_bytes = e2e(w, res, head, max(3, args.steps // 2), stream)
+    e2e_steps = max(3, args.steps // 2)
+    pk = peaks()
+    # dominant kernel family of the headline mode (profiled pass)
+    prof = res[head]["prof"]
+    fams = {k: v for k, v in prof.items() if k != "kernels"}
+    dom = max(fams, key=lambda k: fams[k][0])
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF-stage/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res[head]["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if head == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": workload, "triangles": len(w["tri"]), "dof_stage_per_step": dps,
+                   "precision": head, "l2": "flushed between timed steps (256 MB write)",
+                   "replicas": world},
+        head: {"value": value, "rel_l2_vs_oracle": acc.get(head), "oracle_steps": acc_steps},
+        other: {"value": other_value, "ms_per_step": res[other]["total_ms"] / args.steps,
+                "rel_l2_vs_oracle": acc.get(other), "oracle_steps": acc_steps},
+        "mixed_over_fp64": (value / other_value) if head == "mixed" else (other_value / value),
+        "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in fams.items()},
+        "dominant_kernel": dom,
+        "gpu_launches": int(res[head]["launches"]),
+        "clocks": clk,
+        "e2e": {"value": dps * e2e_steps * world / e2e_s, "unit": "DOF-stage/s",
+                "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
+    }
+    line["roofline"] = roofline(w, res[head], dom, args.steps, pk, head)
+    if rank == 0 and not args.no_oracle:
+        sec = oracle_rate(w, 1, 0)
+        line["cpu_baseline"] = {"value": dps / sec, "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
+                                "sample": "1 full-mesh SSP-RK3 step of the single-threaded FP64 C oracle"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def roofline(w, r, dom, steps, pk, head):
+    """FP64-pipe roofline of the dominant kernel family (see the design doc for the
+    per-unit operation counts)."""
+    from paper_2311_11348_gb300 import roofline as flops
+    ms, n = r["prof"][dom]
+    per_launch_ms = ms / max(n, 1)
+    f = flops.family_flops(w["orders"], dom, head)
+    if f is None:
+        return None
+    launches_per_step = n / steps
+    achieved = f["flops_per_step"] / launches_per_step / (per_launch_ms / 1e3) / 1e12
+    peak = flops.FP64_PEAK_TFLOPS
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": dom, "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (nominal)"}
+
+
+if __name__ == "__main__":
+    main()

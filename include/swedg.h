@@ -163,9 +163,14 @@ int swe_reference_tensors(double* D, double* G, double* T);
  * npts in 1..8; host pointers.  Needs no device. */
 int swe_edge_table(int npts, double* s, double* w, double* B);
 
-/* Timing of the last swe_run / swe_rk_step split by kernel family (ms, CUDA
- * events on the context stream), when enabled with swe_profile(ctx, 1).
- * names receives up to n entries; returns the number of entries. */
+/* Per-kernel-family timing (ms, CUDA events on the context stream around
+ * each family) accumulated while swe_profile(ctx, 1) is on; swe_run then
+ * launches the steps directly instead of replaying its CUDA graph.  Families:
+ * usolve, dt, edge_base, edge_corr, elem_corr, elem_base, other, and a last
+ * entry "kernels" whose launch count is every kernel the library launched
+ * since the last swe_profile call (graph replays included).  names (static
+ * strings), ms and launches receive up to n entries; returns the number of
+ * entries.  swe_profile resets all counters. */
 int swe_profile(swe_ctx* ctx, int enable);
 int swe_profile_read(swe_ctx* ctx, int n, const char** names, double* ms, int64_t* launches);
 

@@ -1,0 +1,865 @@
+// libswedg host side: the C ABI of include/swedg.h, mesh processing (the
+// "buffered geometric information" of Sect. 4), grouping of the elements by
+// polynomial order, device buffers and the SSP Runge-Kutta driver.
+//
+// One RK stage (Sect. 2 time stepping, Sect. 3 order separation):
+//   usolve(base) + usolve(correction)      uH = q on every element
+//   [first stage of a CFL step: dt = cfl * min ...]
+//   edge_base -> edge_corr                 LF fluxes at Gauss points
+//   elem_corr -> elem_base                 volume/source/edge projections and
+//                                          the SSP-RK combination
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/swedg.h"
+#include "common.h"
+#include "kernels.h"
+#include "tables.h"
+
+namespace swedg {
+static thread_local std::string g_cuda_err;
+static thread_local int64_t* g_launch_counter = nullptr;
+void count_launch(int n) {
+  if (g_launch_counter) *g_launch_counter += n;
+}
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e), what,
+           file, line);
+  g_cuda_err = buf;
+  return SWE_ECUDA;
+}
+}  // namespace swedg
+
+using namespace swedg;
+
+namespace {
+
+const char* kFamilies[] = {"usolve", "dt", "edge_base", "edge_corr", "elem_corr", "elem_base", "other"};
+enum { F_USOLVE, F_DT, F_EDGEB, F_EDGEC, F_ELEMC, F_ELEMB, F_OTHER, NFAM };
+
+}  // namespace
+
+struct swe_ctx {
+  swe_params prm{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  std::string err;
+  bool have_mesh = false;
+  bool corr32 = false;
+  // host mesh, caller's element order, oriented counter-clockwise
+  int64_t nv = 0, ne = 0;
+  std::vector<double> xy, hv;
+  std::vector<int32_t> tri;
+  std::vector<int8_t> tag, p_user;
+  std::vector<int64_t> nb;
+  std::vector<int8_t> nbk;
+  // internal numbering: perm[internal] = caller index
+  std::vector<int32_t> perm, inv;
+  Groups G{};
+  int64_t nedge = 0;
+  // device
+  std::vector<void*> allocs;
+  DevMesh dm{};
+  CorrEdges ce{};
+  int32_t* d_perm = nullptr;
+  StateDev st[3]{};
+  VelDev vel{};
+  EdgeFlux fx{};
+  void* rc = nullptr;
+  int32_t* d_edge_only = nullptr;
+  int64_t n_edge_only = 0;
+  double* d_user = nullptr;
+  double* d_user2 = nullptr;
+  double* d_dt = nullptr;
+  double* d_t = nullptr;
+  unsigned long long* d_dmin = nullptr;
+  unsigned* d_status = nullptr;
+  double* d_partial = nullptr;
+  double* d_red = nullptr;
+  int nred = 0;
+  // profiling
+  bool prof = false;
+  struct Ev { int fam; cudaEvent_t a, b; };
+  std::vector<Ev> evs;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[NFAM] = {};
+  int64_t prof_n[NFAM] = {};
+  // CUDA graph of one step
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = -1.0;
+  int64_t graph_launches = 0;
+  bool use_graph = true;
+  // kernel launches issued by the library (graph replays count their kernels)
+  int64_t launches = 0;
+};
+
+// Route count_launch() of the kernel launchers to this context while an API
+// call runs.
+struct LaunchScope {
+  LaunchScope(swe_ctx* c) { g_launch_counter = c ? &c->launches : nullptr; }
+  ~LaunchScope() { g_launch_counter = nullptr; }
+};
+
+static int fail(swe_ctx* c, int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+static int cuda_err(swe_ctx* c, int rc) {
+  if (rc == SWE_ECUDA && c) c->err = g_cuda_err;
+  return rc;
+}
+
+#define CK(call)                                                  \
+  do {                                                            \
+    int rc__ = (call);                                            \
+    if (rc__) return cuda_err(ctx, rc__);                         \
+  } while (0)
+#define CU(call)                                                  \
+  do {                                                            \
+    cudaError_t e__ = (call);                                     \
+    if (e__ != cudaSuccess) return cuda_err(ctx, cuda_fail(e__, #call, __FILE__, __LINE__)); \
+  } while (0)
+
+static const char* g_create_err = "";
+static std::string g_create_err_s;
+
+// ------------------------------------------------------------------ memory
+static void free_all(swe_ctx* ctx) {
+  if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+}
+
+template <typename P>
+static int dalloc(swe_ctx* ctx, P** out, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+  ctx->allocs.push_back(p);
+  *out = (P*)p;
+  return 0;
+}
+
+template <typename V>
+static int upload(swe_ctx* ctx, V** out, const std::vector<V>& h) {
+  int rc = dalloc(ctx, out, h.size() * sizeof(V));
+  if (rc) return rc;
+  if (!h.empty()) {
+    cudaError_t e = cudaMemcpy(*out, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy", __FILE__, __LINE__);
+  }
+  return 0;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------------ profiling
+static void prof_mark(swe_ctx* ctx, int fam, bool begin) {
+  if (!ctx->prof) return;
+  if (begin) {
+    cudaEvent_t a, b;
+    if (ctx->pool.size() >= 2) { a = ctx->pool.back(); ctx->pool.pop_back(); b = ctx->pool.back(); ctx->pool.pop_back(); }
+    else { cudaEventCreate(&a); cudaEventCreate(&b); }
+    cudaEventRecord(a, ctx->stream);
+    ctx->evs.push_back({fam, a, b});
+  } else {
+    cudaEventRecord(ctx->evs.back().b, ctx->stream);
+  }
+}
+
+static void prof_collect(swe_ctx* ctx) {
+  if (ctx->evs.empty()) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& ev : ctx->evs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev.a, ev.b);
+    ctx->prof_ms[ev.fam] += ms;
+    ctx->prof_n[ev.fam] += 1;
+    ctx->pool.push_back(ev.a);
+    ctx->pool.push_back(ev.b);
+  }
+  ctx->evs.clear();
+}
+
+struct ProfScope {
+  swe_ctx* c; int f;
+  ProfScope(swe_ctx* c_, int f_) : c(c_), f(f_) { prof_mark(c, f, true); }
+  ~ProfScope() { prof_mark(c, f, false); }
+};
+
+// ------------------------------------------------------------------ mesh
+static int build_topology(swe_ctx* ctx) {
+  const int64_t ne = ctx->ne;
+  ctx->nb.assign(3 * ne, -1);
+  ctx->nbk.assign(3 * ne, -1);
+  struct Key { int64_t a, b; int64_t e; int k; };
+  std::vector<Key> keys(3 * ne);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int k = 0; k < 3; ++k) {
+      int64_t a = ctx->tri[3 * e + (k + 1) % 3], b = ctx->tri[3 * e + (k + 2) % 3];
+      keys[3 * e + k] = {std::min(a, b), std::max(a, b), e, k};
+    }
+  std::sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
+    return x.a != y.a ? x.a < y.a : x.b != y.b ? x.b < y.b : x.e != y.e ? x.e < y.e : x.k < y.k;
+  });
+  for (size_t r = 0; r < keys.size();) {
+    size_t s = r;
+    while (s < keys.size() && keys[s].a == keys[r].a && keys[s].b == keys[r].b) ++s;
+    if (s - r > 2) return fail(ctx, SWE_EMESH, "edge (%lld,%lld) is shared by %zu triangles", (long long)keys[r].a,
+                               (long long)keys[r].b, s - r);
+    if (s - r == 2) {
+      const Key &A = keys[r], &B = keys[r + 1];
+      if (A.e == B.e) return fail(ctx, SWE_EMESH, "triangle %lld repeats a vertex", (long long)A.e);
+      ctx->nb[3 * A.e + A.k] = B.e; ctx->nbk[3 * A.e + A.k] = (int8_t)B.k;
+      ctx->nb[3 * B.e + B.k] = A.e; ctx->nbk[3 * B.e + B.k] = (int8_t)A.k;
+    }
+    r = s;
+  }
+  return 0;
+}
+
+// Build the internal order, geometry, edges and device buffers; the state is
+// reset to zero (callers that keep it go through the caller layout).
+static int build_device(swe_ctx* ctx) {
+  free_all(ctx);
+  const int64_t ne = ctx->ne;
+  const RefTables& R = tables();
+  // internal order: stable sort by p
+  ctx->perm.resize(ne);
+  std::iota(ctx->perm.begin(), ctx->perm.end(), 0);
+  std::stable_sort(ctx->perm.begin(), ctx->perm.end(),
+                   [&](int32_t a, int32_t b) { return ctx->p_user[a] < ctx->p_user[b]; });
+  ctx->inv.resize(ne);
+  for (int64_t e = 0; e < ne; ++e) ctx->inv[ctx->perm[e]] = (int32_t)e;
+  for (int p = 0; p <= 5; ++p) ctx->G.start[p] = 0;
+  {
+    int64_t cnt[5] = {0, 0, 0, 0, 0};
+    for (int64_t u = 0; u < ne; ++u) cnt[ctx->p_user[u]]++;
+    ctx->G.start[0] = 0;
+    for (int p = 0; p < 5; ++p) ctx->G.start[p + 1] = ctx->G.start[p] + cnt[p];
+  }
+  std::vector<int8_t> pint(ne);
+  for (int64_t e = 0; e < ne; ++e) pint[e] = ctx->p_user[ctx->perm[e]];
+  // geometry
+  std::vector<double> geo((size_t)NGEO * ne);
+  for (int64_t e = 0; e < ne; ++e) {
+    const int64_t u = ctx->perm[e];
+    const int32_t* v = &ctx->tri[3 * u];
+    const double x0 = ctx->xy[2 * v[0]], y0 = ctx->xy[2 * v[0] + 1];
+    const double J00 = ctx->xy[2 * v[1]] - x0, J01 = ctx->xy[2 * v[2]] - x0;
+    const double J10 = ctx->xy[2 * v[1] + 1] - y0, J11 = ctx->xy[2 * v[2] + 1] - y0;
+    const double det = J00 * J11 - J01 * J10;
+    const double s = std::sqrt(det), rs = 1.0 / s;
+    const double Ji[4] = {J11 / det, -J01 / det, -J10 / det, J00 / det};
+    auto G_ = [&](int row) -> double& { return geo[(size_t)row * ne + e]; };
+    G_(G_RS) = rs; G_(G_S) = s;
+    G_(G_JI0) = Ji[0]; G_(G_JI1) = Ji[1]; G_(G_JI2) = Ji[2]; G_(G_JI3) = Ji[3];
+    for (int q = 1; q < 3; ++q) {
+      const double gx = rs * (R.grad1[q][0] * Ji[0] + R.grad1[q][1] * Ji[2]);
+      const double gy = rs * (R.grad1[q][0] * Ji[1] + R.grad1[q][1] * Ji[3]);
+      G_(q == 1 ? G_GQ1X : G_GQ2X) = gx;
+      G_(q == 1 ? G_GQ1Y : G_GQ2Y) = gy;
+    }
+    const double h0 = ctx->hv[v[0]], h1 = ctx->hv[v[1]], h2 = ctx->hv[v[2]];
+    G_(G_DHX) = (h1 - h0) * Ji[0] + (h2 - h0) * Ji[2];
+    G_(G_DHY) = (h1 - h0) * Ji[1] + (h2 - h0) * Ji[3];
+    const double hvv[3] = {h0, h1, h2};
+    for (int i = 0; i < 3; ++i) {
+      double acc = 0.0;
+      for (int w = 0; w < 3; ++w) acc += hvv[w] * R.Lv[w][i];
+      G_(G_HB0 + i) = s * acc;
+    }
+    double per = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const int32_t a = v[(k + 1) % 3], b = v[(k + 2) % 3];
+      per += std::hypot(ctx->xy[2 * b] - ctx->xy[2 * a], ctx->xy[2 * b + 1] - ctx->xy[2 * a + 1]);
+    }
+    G_(G_DIAM) = 2.0 * det / per;
+  }
+  // edges
+  struct E { int32_t L, R, info; double len, nx, ny, hA, hB; };
+  std::vector<E> ed;
+  ed.reserve(3 * ne / 2 + 16);
+  for (int64_t u = 0; u < ne; ++u)
+    for (int k = 0; k < 3; ++k) {
+      const int64_t n = ctx->nb[3 * u + k];
+      if (n >= 0 && ctx->inv[n] < ctx->inv[u]) continue;  // created from the other side
+      E x;
+      int64_t uL = u; int kL = k;
+      int32_t R = -1, kR = 0, bc;
+      if (n >= 0) {
+        bc = 0;
+        R = ctx->inv[n]; kR = ctx->nbk[3 * u + k];
+      } else {
+        bc = ctx->tag[3 * u + k] == 2 ? 2 : 1;
+      }
+      x.L = ctx->inv[uL]; x.R = R;
+      x.info = kL | (kR << 2) | (bc << 4);
+      const int32_t a = ctx->tri[3 * uL + (kL + 1) % 3], b = ctx->tri[3 * uL + (kL + 2) % 3];
+      const double dx = ctx->xy[2 * b] - ctx->xy[2 * a], dy = ctx->xy[2 * b + 1] - ctx->xy[2 * a + 1];
+      x.len = std::hypot(dx, dy);
+      x.nx = dy / x.len; x.ny = -dx / x.len;
+      x.hA = ctx->hv[a]; x.hB = ctx->hv[b];
+      ed.push_back(x);
+    }
+  std::stable_sort(ed.begin(), ed.end(), [](const E& a, const E& b) {
+    const bool ia = a.R >= 0, ib = b.R >= 0;
+    if (ia != ib) return ia;
+    return a.L < b.L;
+  });
+  const int64_t nE = (int64_t)ed.size();
+  ctx->nedge = nE;
+  if (nE >= (1ll << 30) || ne >= (1ll << 30)) return fail(ctx, SWE_EINVAL, "mesh too large for 30-bit edge ids");
+  std::vector<int32_t> eL(nE), eR(nE), einfo(nE), eedge(3 * ne, -1);
+  std::vector<double> egeo(5 * nE);
+  int64_t nint = 0;
+  for (int64_t i = 0; i < nE; ++i) {
+    eL[i] = ed[i].L; eR[i] = ed[i].R; einfo[i] = ed[i].info;
+    egeo[i] = ed[i].len; egeo[nE + i] = ed[i].nx; egeo[2 * nE + i] = ed[i].ny;
+    egeo[3 * nE + i] = ed[i].hA; egeo[4 * nE + i] = ed[i].hB;
+    if (ed[i].R >= 0) ++nint;
+    eedge[(size_t)(ed[i].info & 3) * ne + ed[i].L] = (int32_t)(i << 1);
+    if (ed[i].R >= 0) eedge[(size_t)((ed[i].info >> 2) & 3) * ne + ed[i].R] = (int32_t)((i << 1) | 1);
+  }
+  // correction edges, grouped by max order of their sides
+  std::vector<int32_t> slot(nE, -1);
+  std::vector<int32_t> clist[5];
+  for (int64_t i = 0; i < nE; ++i) {
+    int pm = pint[eL[i]];
+    if (eR[i] >= 0) pm = std::max<int>(pm, pint[eR[i]]);
+    if (pm >= 2) {
+      slot[i] = (pm << 28) | (int32_t)clist[pm].size();
+      clist[pm].push_back((int32_t)i);
+    }
+  }
+  std::vector<uint8_t> flags(ne, 0);
+  std::vector<int32_t> edge_only;
+  for (int64_t e = 0; e < ne; ++e) {
+    bool any = false;
+    for (int k = 0; k < 3; ++k) any |= slot[eedge[(size_t)k * ne + e] >> 1] >= 0;
+    if (pint[e] >= 2) flags[e] = 1;
+    else if (any) { flags[e] = 1; edge_only.push_back((int32_t)e); }
+  }
+  // upload topology and geometry
+  double* d_geo; int8_t* d_p; int32_t *d_eedge, *d_eL, *d_eR, *d_einfo, *d_slot; double* d_egeo; uint8_t* d_flags;
+  int rc = 0;
+  if ((rc = upload(ctx, &d_geo, geo)) || (rc = upload(ctx, &d_p, pint)) || (rc = upload(ctx, &d_eedge, eedge)) ||
+      (rc = upload(ctx, &d_eL, eL)) || (rc = upload(ctx, &d_eR, eR)) || (rc = upload(ctx, &d_einfo, einfo)) ||
+      (rc = upload(ctx, &d_egeo, egeo)) || (rc = upload(ctx, &d_flags, flags)) || (rc = upload(ctx, &d_slot, slot)) ||
+      (rc = upload(ctx, &ctx->d_perm, ctx->perm)) || (rc = upload(ctx, &ctx->d_edge_only, edge_only)))
+    return cuda_err(ctx, rc);
+  ctx->n_edge_only = (int64_t)edge_only.size();
+  ctx->dm = DevMesh{ne, nE, nint, d_geo, d_p, d_eedge, d_eL, d_eR, d_einfo, d_egeo, d_flags};
+  std::memset(&ctx->ce, 0, sizeof ctx->ce);
+  ctx->ce.slot = d_slot;
+  for (int pm = 2; pm <= 4; ++pm) {
+    int32_t* d = nullptr;
+    if ((rc = upload(ctx, &d, clist[pm]))) return cuda_err(ctx, rc);
+    ctx->ce.list[pm] = d;
+    ctx->ce.n[pm] = (int64_t)clist[pm].size();
+  }
+  // state, velocity, fluxes
+  const size_t ts = ctx->corr32 ? sizeof(float) : sizeof(double);
+  for (int s = 0; s < 3; ++s) {
+    if ((rc = dalloc(ctx, &ctx->st[s].cb, sizeof(double) * 9 * ne))) return cuda_err(ctx, rc);
+    cudaMemset(ctx->st[s].cb, 0, sizeof(double) * 9 * ne);
+    for (int p = 0; p < 5; ++p) {
+      ctx->st[s].ch[p] = nullptr;
+      if (p < 2) continue;
+      const int64_t n = ctx->G.start[p + 1] - ctx->G.start[p];
+      if ((rc = dalloc(ctx, &ctx->st[s].ch[p], ts * 3 * (Kof(p) - 3) * n))) return cuda_err(ctx, rc);
+      cudaMemset(ctx->st[s].ch[p], 0, ts * 3 * (Kof(p) - 3) * std::max<int64_t>(n, 0));
+    }
+  }
+  if ((rc = dalloc(ctx, &ctx->vel.ub, sizeof(double) * 6 * ne))) return cuda_err(ctx, rc);
+  for (int p = 0; p < 5; ++p) {
+    ctx->vel.uh[p] = nullptr;
+    if (p < 2) continue;
+    const int64_t n = ctx->G.start[p + 1] - ctx->G.start[p];
+    if ((rc = dalloc(ctx, &ctx->vel.uh[p], ts * 2 * (Kof(p) - 3) * n))) return cuda_err(ctx, rc);
+  }
+  if ((rc = dalloc(ctx, &ctx->fx.Fb, sizeof(double) * 6 * nE)) || (rc = dalloc(ctx, &ctx->fx.lam, sizeof(double) * nE)))
+    return cuda_err(ctx, rc);
+  for (int pm = 0; pm < 5; ++pm) {
+    ctx->fx.Fh[pm] = ctx->fx.Ff[pm] = nullptr;
+    if (pm < 2) continue;
+    const size_t sz = ts * 3 * npts_for(pm) * ctx->ce.n[pm];
+    if ((rc = dalloc(ctx, &ctx->fx.Fh[pm], sz)) || (rc = dalloc(ctx, &ctx->fx.Ff[pm], sz))) return cuda_err(ctx, rc);
+  }
+  if ((rc = dalloc(ctx, &ctx->rc, sizeof(double) * 9 * ne))) return cuda_err(ctx, rc);
+  cudaMemset(ctx->rc, 0, sizeof(double) * 9 * ne);
+  if ((rc = dalloc(ctx, &ctx->d_user, sizeof(double) * 3 * KMAX * ne)) ||
+      (rc = dalloc(ctx, &ctx->d_user2, sizeof(double) * 3 * KMAX * ne)))
+    return cuda_err(ctx, rc);
+  if ((rc = dalloc(ctx, &ctx->d_dt, sizeof(double))) || (rc = dalloc(ctx, &ctx->d_t, sizeof(double))) ||
+      (rc = dalloc(ctx, &ctx->d_dmin, sizeof(unsigned long long))) || (rc = dalloc(ctx, &ctx->d_status, sizeof(unsigned))))
+    return cuda_err(ctx, rc);
+  ctx->nred = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (ne + 255) / 256));
+  if ((rc = dalloc(ctx, &ctx->d_partial, sizeof(double) * ctx->nred)) || (rc = dalloc(ctx, &ctx->d_red, sizeof(double) * 2)))
+    return cuda_err(ctx, rc);
+  cudaMemset(ctx->d_t, 0, sizeof(double));
+  cudaMemset(ctx->d_status, 0, sizeof(unsigned));
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(ctx, cuda_fail(e, "build_device", __FILE__, __LINE__));
+  ctx->have_mesh = true;
+  return 0;
+}
+
+// ------------------------------------------------------------------ stages
+static Phys phys(const swe_ctx* ctx) {
+  return Phys{ctx->prm.g, ctx->prm.h_min, ctx->prm.tide_amp, ctx->prm.tide_period, ctx->prm.tide_phase};
+}
+
+static int usolve_all(swe_ctx* ctx, StateDev in) {
+  ProfScope ps(ctx, F_USOLVE);
+  const Phys ph = phys(ctx);
+  CK(launch_usolve_base(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->d_status));
+  if (ctx->corr32) CK(corr32::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
+  else CK(corr64::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
+  return 0;
+}
+
+// One stage: out = a n + b (in + dt L(in)), or out = L(in) (rhs_only).
+static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, const Stage& stg, bool cfl_dt,
+                     double dt_fixed) {
+  const Phys ph = phys(ctx);
+  CK(usolve_all(ctx, in));
+  if (cfl_dt) {
+    ProfScope ps(ctx, F_DT);
+    CK(launch_reset_min(ctx->stream, ctx->d_dmin));
+    CK(launch_dt(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->d_dmin));
+    CK(launch_advance_time(ctx->stream, nullptr, ctx->d_dmin, ctx->prm.cfl, dt_fixed, ctx->d_dt));
+  }
+  {
+    ProfScope ps(ctx, F_EDGEB);
+    CK(launch_edge_base(ctx->stream, ctx->dm, ph, stg, in.cb, ctx->vel.ub, ctx->fx));
+  }
+  {
+    ProfScope ps(ctx, F_EDGEC);
+    if (ctx->corr32) CK(corr32::launch_edge_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+    else CK(corr64::launch_edge_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+  }
+  {
+    ProfScope ps(ctx, F_ELEMC);
+    if (ctx->corr32)
+      CK(corr32::launch_elem_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx,
+                                  ctx->rc, ctx->d_edge_only, ctx->n_edge_only));
+    else
+      CK(corr64::launch_elem_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx,
+                                  ctx->rc, ctx->d_edge_only, ctx->n_edge_only));
+  }
+  {
+    ProfScope ps(ctx, F_ELEMB);
+    CK(launch_elem_base(ctx->stream, ctx->dm, ctx->G, ph, stg, ctx->corr32, in.cb, nst.cb, out.cb, ctx->vel.ub,
+                        ctx->fx, ctx->rc, ctx->prm.cfl));
+  }
+  return 0;
+}
+
+// One SSP-RK step of state A (in place); the step size lives in d_dt.
+static int enqueue_step(swe_ctx* ctx, double dt_fixed) {
+  StateDev A = ctx->st[0], B = ctx->st[1], C = ctx->st[2];
+  Stage s{};
+  s.dt = ctx->d_dt;
+  s.t_dev = ctx->d_t;
+  if (dt_fixed > 0.0) {
+    ProfScope ps(ctx, F_DT);
+    CK(launch_advance_time(ctx->stream, nullptr, ctx->d_dmin, ctx->prm.cfl, dt_fixed, ctx->d_dt));
+  }
+  const bool cfl = dt_fixed <= 0.0;
+  if (ctx->prm.rk_order == 3) {
+    s.a = 0.0; s.b = 1.0; s.tau = 0.0;
+    CK(run_stage(ctx, A, A, B, s, cfl, dt_fixed));
+    s.a = 0.75; s.b = 0.25; s.tau = 1.0;
+    CK(run_stage(ctx, B, A, C, s, false, dt_fixed));
+    s.a = 1.0 / 3.0; s.b = 2.0 / 3.0; s.tau = 0.5;
+    CK(run_stage(ctx, C, A, A, s, false, dt_fixed));
+  } else {
+    s.a = 0.0; s.b = 1.0; s.tau = 0.0;
+    CK(run_stage(ctx, A, A, B, s, cfl, dt_fixed));
+    s.a = 0.5; s.b = 0.5; s.tau = 1.0;
+    CK(run_stage(ctx, B, A, A, s, false, dt_fixed));
+  }
+  ProfScope ps(ctx, F_OTHER);
+  CK(launch_advance_time(ctx->stream, ctx->d_t, nullptr, 0.0, 0.0, ctx->d_dt));
+  return 0;
+}
+
+static int read_status(swe_ctx* ctx, bool check_state) {
+  if (check_state) CK(launch_check_state(ctx->stream, ctx->dm, ctx->G, ctx->corr32, ctx->st[0], ctx->d_status));
+  unsigned st = 0;
+  CU(cudaMemcpyAsync(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  if (st) CU(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
+  if (st & ST_NONFINITE) return fail(ctx, SWE_ENONFINITE, "non-finite value in the state");
+  if (st & ST_DEPTH) return fail(ctx, SWE_EDEPTH, "an element mean depth fell to or below h_min");
+  return 0;
+}
+
+// caller layout (host or device) -> state A (or the scratch state s)
+static int state_in(swe_ctx* ctx, const double* c, int s) {
+  const size_t bytes = sizeof(double) * 3 * KMAX * ctx->ne;
+  const double* src = c;
+  if (!is_device_ptr(c)) {
+    CU(cudaMemcpyAsync(ctx->d_user, c, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    src = ctx->d_user;
+  }
+  CK(launch_from_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->corr32, src, ctx->st[s]));
+  return 0;
+}
+
+static int state_out(swe_ctx* ctx, StateDev st, const void* rc, double* c) {
+  const size_t bytes = sizeof(double) * 3 * KMAX * ctx->ne;
+  const bool dev = is_device_ptr(c);
+  double* dst = dev ? c : ctx->d_user2;
+  CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->corr32, st, (const double*)rc, dst));
+  if (!dev) CU(cudaMemcpyAsync(c, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return 0;
+}
+
+// ------------------------------------------------------------------ ABI
+extern "C" {
+
+void swe_default_params(swe_params* p) {
+  std::memset(p, 0, sizeof *p);
+  p->g = 9.81;
+  p->cfl = 0.1;
+  p->h_min = 1e-8;
+  p->rk_order = 2;
+  p->precision = SWE_PREC_FP64;
+}
+
+int swe_create(swe_ctx** out, const swe_params* params) {
+  if (!out || !params) { g_create_err = "swe_create: NULL argument"; return SWE_EINVAL; }
+  *out = nullptr;
+  if (params->rk_order != 2 && params->rk_order != 3) { g_create_err = "rk_order must be 2 or 3"; return SWE_EINVAL; }
+  if (params->precision != SWE_PREC_FP64 && params->precision != SWE_PREC_MIXED_FP32) {
+    g_create_err = "unknown precision mode"; return SWE_EINVAL;
+  }
+  if (!(params->g > 0.0) || !(params->cfl > 0.0)) { g_create_err = "g and cfl must be positive"; return SWE_EINVAL; }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    g_create_err_s = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    g_create_err = g_create_err_s.c_str();
+    return SWE_ECUDA;
+  }
+  swe_ctx* ctx = new swe_ctx;
+  ctx->prm = *params;
+  ctx->device = dev;
+  ctx->corr32 = params->precision == SWE_PREC_MIXED_FP32;
+  if (params->cuda_stream) {
+    ctx->stream = (cudaStream_t)params->cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete ctx; g_create_err = "cudaStreamCreate failed"; return SWE_ECUDA; }
+    ctx->own_stream = true;
+  }
+  upload_base_tables();
+  corr64::upload_tables();
+  corr32::upload_tables();
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    g_create_err_s = std::string("table upload failed: ") + cudaGetErrorString(e);
+    g_create_err = g_create_err_s.c_str();
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return SWE_ECUDA;
+  }
+  *out = ctx;
+  return 0;
+}
+
+void swe_destroy(swe_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  for (auto& ev : ctx->evs) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
+  for (auto ev : ctx->pool) cudaEventDestroy(ev);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* swe_last_error(const swe_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err; }
+
+int swe_set_mesh(swe_ctx* ctx, int64_t nv, const double* xy, int64_t ne, const int32_t* tri, const int8_t* bc_tag) {
+  if (!ctx) return SWE_EINVAL;
+  if (nv < 3 || ne < 1 || !xy || !tri) return fail(ctx, SWE_EINVAL, "swe_set_mesh: need nv >= 3, ne >= 1 and arrays");
+  ctx->nv = nv; ctx->ne = ne;
+  ctx->xy.assign(xy, xy + 2 * nv);
+  ctx->hv.assign(nv, 0.0);
+  ctx->tri.resize(3 * ne);
+  ctx->tag.assign(3 * ne, 0);
+  for (int64_t e = 0; e < ne; ++e) {
+    int32_t v[3] = {tri[3 * e], tri[3 * e + 1], tri[3 * e + 2]};
+    int8_t t[3] = {0, 0, 0};
+    if (bc_tag) for (int k = 0; k < 3; ++k) t[k] = bc_tag[3 * e + k];
+    for (int k = 0; k < 3; ++k)
+      if (v[k] < 0 || v[k] >= nv) { ctx->have_mesh = false; return fail(ctx, SWE_EMESH, "triangle %lld: vertex id out of range", (long long)e); }
+    for (int k = 0; k < 3; ++k)
+      if (t[k] < 0 || t[k] > 2) { ctx->have_mesh = false; return fail(ctx, SWE_EINVAL, "triangle %lld: boundary tag must be 0, 1 or 2", (long long)e); }
+    const double cr = (xy[2 * v[1]] - xy[2 * v[0]]) * (xy[2 * v[2] + 1] - xy[2 * v[0] + 1]) -
+                      (xy[2 * v[2]] - xy[2 * v[0]]) * (xy[2 * v[1] + 1] - xy[2 * v[0] + 1]);
+    if (!(cr != 0.0) || !std::isfinite(cr)) { ctx->have_mesh = false; return fail(ctx, SWE_EMESH, "triangle %lld is degenerate", (long long)e); }
+    if (cr < 0.0) { std::swap(v[1], v[2]); std::swap(t[1], t[2]); }
+    for (int k = 0; k < 3; ++k) { ctx->tri[3 * e + k] = v[k]; ctx->tag[3 * e + k] = t[k]; }
+  }
+  ctx->p_user.assign(ne, 1);
+  int rc = build_topology(ctx);
+  if (rc) { ctx->have_mesh = false; return rc; }
+  return build_device(ctx);
+}
+
+// keep the state across a rebuild through the caller layout
+static int rebuild_keep_state(swe_ctx* ctx) {
+  std::vector<double> c((size_t)3 * KMAX * ctx->ne);
+  double t = 0.0;
+  int rc = swe_get_state(ctx, c.data(), &t);
+  if (rc) return rc;
+  if ((rc = build_device(ctx))) return rc;
+  return swe_set_state(ctx, c.data(), t);
+}
+
+int swe_set_bathymetry(swe_ctx* ctx, const double* hb_vertex) {
+  if (!ctx || !ctx->have_mesh || !hb_vertex) return fail(ctx, SWE_EINVAL, "swe_set_bathymetry: no mesh or NULL");
+  for (int64_t v = 0; v < ctx->nv; ++v)
+    if (!std::isfinite(hb_vertex[v])) return fail(ctx, SWE_EINVAL, "bathymetry at vertex %lld is not finite", (long long)v);
+  ctx->hv.assign(hb_vertex, hb_vertex + ctx->nv);
+  return rebuild_keep_state(ctx);
+}
+
+int swe_set_orders(swe_ctx* ctx, const int8_t* p) {
+  if (!ctx || !ctx->have_mesh || !p) return fail(ctx, SWE_EINVAL, "swe_set_orders: no mesh or NULL");
+  for (int64_t e = 0; e < ctx->ne; ++e)
+    if (p[e] < 0 || p[e] > 4) return fail(ctx, SWE_EINVAL, "order of element %lld is %d, not in 0..4", (long long)e, (int)p[e]);
+  std::vector<double> c((size_t)3 * KMAX * ctx->ne);
+  double t = 0.0;
+  int rc = swe_get_state(ctx, c.data(), &t);
+  if (rc) return rc;
+  ctx->p_user.assign(p, p + ctx->ne);
+  if ((rc = build_device(ctx))) return rc;
+  return swe_set_state(ctx, c.data(), t);
+}
+
+int swe_set_state(swe_ctx* ctx, const double* c, double t) {
+  if (!ctx || !ctx->have_mesh || !c) return fail(ctx, SWE_EINVAL, "swe_set_state: no mesh or NULL");
+  LaunchScope ls(ctx);
+  CK(state_in(ctx, c, 0));
+  CU(cudaMemcpyAsync(ctx->d_t, &t, sizeof t, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return 0;
+}
+
+int swe_get_state(swe_ctx* ctx, double* c_out, double* t_out) {
+  if (!ctx || !ctx->have_mesh || !c_out) return fail(ctx, SWE_EINVAL, "swe_get_state: no mesh or NULL");
+  LaunchScope ls(ctx);
+  CK(state_out(ctx, ctx->st[0], nullptr, c_out));
+  if (t_out) {
+    CU(cudaMemcpyAsync(t_out, ctx->d_t, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  return 0;
+}
+
+int swe_p1_modes(swe_ctx* ctx, const double* vals, double* modes_out) {
+  if (!ctx || !ctx->have_mesh || !vals || !modes_out) return fail(ctx, SWE_EINVAL, "swe_p1_modes: no mesh or NULL");
+  const RefTables& R = tables();
+  const int64_t ne = ctx->ne;
+  std::vector<double> out((size_t)3 * ne);
+  for (int64_t e = 0; e < ne; ++e) {
+    const int32_t* v = &ctx->tri[3 * e];
+    const double x0 = ctx->xy[2 * v[0]], y0 = ctx->xy[2 * v[0] + 1];
+    const double det = (ctx->xy[2 * v[1]] - x0) * (ctx->xy[2 * v[2] + 1] - y0) -
+                       (ctx->xy[2 * v[2]] - x0) * (ctx->xy[2 * v[1] + 1] - y0);
+    const double s = std::sqrt(det);
+    for (int i = 0; i < 3; ++i) {
+      double acc = 0.0;
+      for (int w = 0; w < 3; ++w) acc += vals[v[w]] * R.Lv[w][i];
+      out[(size_t)i * ne + e] = s * acc;
+    }
+  }
+  if (is_device_ptr(modes_out)) {
+    CU(cudaMemcpy(modes_out, out.data(), sizeof(double) * out.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::memcpy(modes_out, out.data(), sizeof(double) * out.size());
+  }
+  return 0;
+}
+
+static int rhs_impl(swe_ctx* ctx, const double* c_in, double* out0, double* out1) {
+  if (!ctx || !ctx->have_mesh || !c_in || !out0) return fail(ctx, SWE_EINVAL, "swe_rhs: no mesh or NULL");
+  LaunchScope ls(ctx);
+  CK(state_in(ctx, c_in, 1));
+  Stage s{};
+  s.rhs_only = 1;
+  s.dt = nullptr; s.dt_host = 0.0;
+  s.t_dev = ctx->d_t; s.tau = 0.0;
+  s.parts = out1 != nullptr;
+  CK(run_stage(ctx, ctx->st[1], ctx->st[1], ctx->st[2], s, false, 0.0));
+  int rc = read_status(ctx, false);
+  if (rc) return rc;
+  if (!out1) {
+    // the correction of the base modes is already merged into the base output
+    StateDev o = ctx->st[2];
+    CK(state_out(ctx, o, nullptr, out0));
+  } else {
+    StateDev b = ctx->st[2];
+    for (int p = 0; p < 5; ++p) b.ch[p] = nullptr;
+    CK(state_out(ctx, b, nullptr, out0));
+    CK(state_out(ctx, ctx->st[2], ctx->rc, out1));
+  }
+  return 0;
+}
+
+int swe_rhs(swe_ctx* ctx, const double* c_in, double* rhs_out) { return rhs_impl(ctx, c_in, rhs_out, nullptr); }
+
+int swe_rhs_parts(swe_ctx* ctx, const double* c_in, double* base_out, double* corr_out) {
+  if (!corr_out) return fail(ctx, SWE_EINVAL, "swe_rhs_parts: NULL output");
+  return rhs_impl(ctx, c_in, base_out, corr_out);
+}
+
+int swe_rk_step(swe_ctx* ctx, double dt, double* dt_used) {
+  if (!ctx || !ctx->have_mesh) return fail(ctx, SWE_EINVAL, "swe_rk_step: no mesh");
+  LaunchScope ls(ctx);
+  CK(enqueue_step(ctx, dt));
+  if (dt_used) CU(cudaMemcpyAsync(dt_used, ctx->d_dt, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = read_status(ctx, true);
+  prof_collect(ctx);
+  return rc;
+}
+
+// Capture one step into a CUDA graph (replayed by swe_run); on a stream that
+// cannot be captured the steps are launched directly.
+static int build_graph(swe_ctx* ctx, double dt_fixed) {
+  if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+  const int64_t before = ctx->launches;
+  if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->use_graph = false;
+    return 0;
+  }
+  const int rc = enqueue_step(ctx, dt_fixed);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  ctx->graph_launches = ctx->launches - before;
+  ctx->launches = before;
+  if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+  if (e != cudaSuccess) return cuda_err(ctx, cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__));
+  const cudaError_t ei = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return cuda_err(ctx, cuda_fail(ei, "cudaGraphInstantiate", __FILE__, __LINE__));
+  ctx->graph_dt = dt_fixed;
+  return 0;
+}
+
+int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out) {
+  if (!ctx || !ctx->have_mesh || nsteps < 0) return fail(ctx, SWE_EINVAL, "swe_run: no mesh or negative count");
+  LaunchScope ls(ctx);
+  if (ctx->use_graph && !ctx->prof && nsteps > 0) {
+    if (!ctx->graph || ctx->graph_dt != dt_fixed) CK(build_graph(ctx, dt_fixed));
+  }
+  if (ctx->use_graph && !ctx->prof && ctx->graph) {
+    for (int64_t s = 0; s < nsteps; ++s) {
+      CU(cudaGraphLaunch(ctx->graph, ctx->stream));
+      ctx->launches += ctx->graph_launches;
+    }
+  } else {
+    for (int64_t s = 0; s < nsteps; ++s) CK(enqueue_step(ctx, dt_fixed));
+  }
+  int rc = read_status(ctx, true);
+  prof_collect(ctx);
+  if (t_out) {
+    CU(cudaMemcpyAsync(t_out, ctx->d_t, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  return rc;
+}
+
+int swe_mass(swe_ctx* ctx, double* m) {
+  if (!ctx || !ctx->have_mesh || !m) return fail(ctx, SWE_EINVAL, "swe_mass: no mesh or NULL");
+  LaunchScope ls(ctx);
+  CK(launch_mass(ctx->stream, ctx->dm, ctx->st[0].cb, ctx->d_partial, ctx->nred, ctx->d_red));
+  CU(cudaMemcpyAsync(m, ctx->d_red, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return 0;
+}
+
+int swe_energy(swe_ctx* ctx, double* en) {
+  if (!ctx || !ctx->have_mesh || !en) return fail(ctx, SWE_EINVAL, "swe_energy: no mesh or NULL");
+  LaunchScope ls(ctx);
+  CK(usolve_all(ctx, ctx->st[0]));
+  CK(launch_energy(ctx->stream, ctx->dm, ctx->G, ctx->corr32, phys(ctx), ctx->st[0], ctx->vel, ctx->d_partial,
+                   ctx->nred, ctx->d_red));
+  CU(cudaMemcpyAsync(en, ctx->d_red, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  return read_status(ctx, false);
+}
+
+int swe_reference_tensors(double* D, double* G, double* T) {
+  const RefTables& R = tables();
+  if (D) std::memcpy(D, R.D, sizeof R.D);
+  if (G) std::memcpy(G, R.G, sizeof R.G);
+  if (T) std::memcpy(T, R.T, sizeof R.T);
+  return 0;
+}
+
+int swe_edge_table(int npts, double* s, double* w, double* B) {
+  if (npts < 1 || npts > 8) return SWE_EINVAL;
+  const RefTables& R = tables();
+  for (int g = 0; g < npts; ++g) {
+    if (s) s[g] = R.es[npts][g];
+    if (w) w[g] = R.ew[npts][g];
+  }
+  if (B)
+    for (int k = 0; k < 3; ++k)
+      for (int i = 0; i < KMAX; ++i)
+        for (int g = 0; g < npts; ++g) B[(k * KMAX + i) * npts + g] = R.EB[npts][k][i][g];
+  return 0;
+}
+
+int swe_profile(swe_ctx* ctx, int enable) {
+  if (!ctx) return SWE_EINVAL;
+  ctx->prof = enable != 0;
+  ctx->launches = 0;
+  for (int f = 0; f < NFAM; ++f) { ctx->prof_ms[f] = 0.0; ctx->prof_n[f] = 0; }
+  return 0;
+}
+
+int swe_profile_read(swe_ctx* ctx, int n, const char** names, double* ms, int64_t* launches) {
+  if (!ctx) return SWE_EINVAL;
+  prof_collect(ctx);
+  int k = 0;
+  for (int f = 0; f < NFAM && k < n; ++f, ++k) {
+    if (names) names[k] = kFamilies[f];
+    if (ms) ms[k] = ctx->prof_ms[f];
+    if (launches) launches[k] = ctx->prof_n[f];
+  }
+  if (k < n) {  // every kernel launched since swe_profile(ctx, .)
+    if (names) names[k] = "kernels";
+    if (ms) ms[k] = 0.0;
+    if (launches) launches[k] = ctx->launches;
+    ++k;
+  }
+  return k;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// Internal declarations of libswedg shared by the host code and the kernels.
+//
+// Data layout in HBM (internal element order = caller's elements stably sorted
+// by polynomial order p, so every order group is one contiguous range):
+//   base state    cb[3 fields][3 modes][ne]            FP64   (modes of degree <= 1)
+//   corr state    ch_p[3 fields][K(p)-3][n_p]  p = 2..4  FP64 or FP32
+//   velocity      ub[2][3][ne] FP64,  uh_p[2][K(p)-3][n_p]
+//   geometry      geo[NGEO][ne] FP64 (one row per quantity, coalesced)
+//   edges         SoA arrays over interior edges first, then boundary edges
+// All per-element arrays are structure-of-arrays so that consecutive threads
+// (consecutive elements of one order group) issue coalesced 8-byte loads.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swedg {
+
+constexpr int KMAX = 15;
+constexpr int NB = 3;  // base modes: K(1)
+
+__host__ __device__ constexpr int Kof(int p) { return (p + 1) * (p + 2) / 2; }
+__host__ __device__ constexpr int deg_of(int i) { return i < 1 ? 0 : i < 3 ? 1 : i < 6 ? 2 : i < 10 ? 3 : 4; }
+// Gauss-Legendre points per edge so that products of three traces of degree
+// <= pmax (degree 3 pmax along the edge) are integrated exactly.
+__host__ __device__ constexpr int npts_for(int pmax) { return pmax <= 1 ? 2 : (3 * pmax + 2) / 2; }
+
+// rows of the per-element geometry table
+enum {
+  G_RS = 0,  // 1 / s_e, s_e = sqrt|det J_e|
+  G_S,       // s_e
+  G_JI0,     // d xhat / dx
+  G_JI1,     // d xhat / dy
+  G_JI2,     // d yhat / dx
+  G_JI3,     // d yhat / dy
+  G_GQ1X,    // grad phi_{e,2} (constant): x, y
+  G_GQ1Y,
+  G_GQ2X,    // grad phi_{e,3}
+  G_GQ2Y,
+  G_DHX,     // grad h_b
+  G_DHY,
+  G_HB0,     // modal h_b (P1 interpolant): 3 rows
+  G_HB1,
+  G_HB2,
+  G_DIAM,    // inscribed diameter 4 |Omega_e| / perimeter
+  NGEO
+};
+
+// Per-stage SSP-RK combination  out = a * c^n + b * (c^(s) + dt * rhs),
+// or out = rhs itself when rhs_only is set.
+struct Stage {
+  double a, b;
+  int rhs_only;
+  const double* dt;   // device scalar (CFL step) ...
+  double dt_host;     // ... or this value when dt == nullptr
+  double t;           // stage time for the open-sea boundary (host value) ...
+  const double* t_dev;  // ... plus dev_t_scale * (*t_dev) when non-null
+  double tau;         // stage time = t_n + tau * dt
+  int parts;          // 1: keep the correction of the base modes out of the base output
+};
+
+struct Phys {
+  double g, h_min;
+  double tide_amp, tide_period, tide_phase;
+};
+
+// Mesh topology and geometry on the device (internal order).
+struct DevMesh {
+  int64_t ne;
+  int64_t nedge, nint;    // all edges, interior edges (boundary ones follow)
+  const double* geo;      // [NGEO][ne]
+  const int8_t* p;        // [ne]
+  const int32_t* eedge;   // [3][ne]: (edge << 1) | side (side 1: the edge's right element)
+  const int32_t* eL;      // [nedge] left element
+  const int32_t* eR;      // [nedge] right element or -1
+  const int32_t* einfo;   // [nedge] kL | kR << 2 | bc << 4   (bc: 0 interior, 1 land, 2 open sea)
+  const double* egeo;     // [5][nedge]: |E|, nx, ny, h_b at gamma(0), h_b at gamma(1) (left element's direction)
+  const uint8_t* flags;   // [ne]: bit 0 = element receives a correction (rc valid)
+};
+
+// Correction edges grouped by pmax = max(p_L, p_R) in 2..4.
+struct CorrEdges {
+  int64_t n[5];           // per pmax
+  const int32_t* list[5]; // edge ids
+  const int32_t* slot;    // [nedge]: (pmax << 28) | slot within group, or -1
+};
+
+}  // namespace swedg
+
+#define SWE_CUDA_OK(call)                                      \
+  do {                                                         \
+    cudaError_t e__ = (call);                                  \
+    if (e__ != cudaSuccess) return ::swedg::cuda_fail(e__, #call, __FILE__, __LINE__); \
+  } while (0)
+
+namespace swedg {
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+}

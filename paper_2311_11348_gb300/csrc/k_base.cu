@@ -1,0 +1,558 @@
+// Base part of the order-separated scheme (Sect. 3): every term whose test
+// index and coefficient indices are modes of degree <= 1, on every element,
+// in FP64.  Plus the layout conversions, the CFL reduction, the time update
+// and the diagnostics.
+//
+// Kernels (one thread per element or per edge, FP64-pipe bound on GB300):
+//   k_usolve_base  auxiliary system uH = q (Sect. 3) for p <= 1 elements
+//   k_dt           CFL step: min over elements, exact (order independent)
+//   k_edge_base    Lax-Friedrichs flux (Sect. 2) of the P1 traces at the two
+//                  Gauss points of every edge, lambda of Eq. (10) from means
+//   k_elem_base    volume + source terms (Eq. 13 with the degree-1 tensors in
+//                  closed form), edge projections, correction merge and the
+//                  SSP-RK stage combination of the base modes
+#include <cfloat>
+
+#include "kernels.h"
+#include "tables.h"
+
+namespace swedg {
+
+__constant__ double cB2[3][3][2];   // phihat_i(gamma_k(s_g)), i < 3, 2-point rule
+__constant__ double cW2[2];         // weights of the 2-point rule on [0,1]
+__constant__ double cS2[2];         // its points
+__constant__ double cT1[3][3][3];   // T[n][i][j] for n, i, j < 3
+__constant__ double cPhi0;          // phihat_1 = sqrt 2
+
+void upload_base_tables() {
+  const RefTables& R = tables();
+  double B[3][3][2], T1[3][3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int g = 0; g < 2; ++g) B[k][i][g] = R.EB[2][k][i][g];
+  for (int n = 0; n < 3; ++n)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) T1[n][i][j] = R.T[n][i][j];
+  cudaMemcpyToSymbol(cB2, B, sizeof B);
+  cudaMemcpyToSymbol(cW2, R.ew[2], sizeof(double) * 2);
+  cudaMemcpyToSymbol(cS2, R.es[2], sizeof(double) * 2);
+  cudaMemcpyToSymbol(cT1, T1, sizeof T1);
+  cudaMemcpyToSymbol(cPhi0, &R.phi0, sizeof(double));
+}
+
+static inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+template <typename T>
+__device__ __forceinline__ T* chp(void* p) { return reinterpret_cast<T*>(p); }
+
+// ---------------------------------------------------------------------------
+// layout conversion: caller layout c[3][15][ne_user] <-> internal state
+// ---------------------------------------------------------------------------
+template <typename TC>
+__global__ void k_from_user(DevMesh m, Groups G, const int32_t* perm, const double* __restrict__ cu, StateDev st) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.ne) return;
+  const int64_t ne = m.ne, u = perm[e];
+  const int p = m.p[e], K = Kof(p);
+  for (int f = 0; f < 3; ++f)
+    for (int i = 0; i < 3; ++i) st.cb[(f * 3 + i) * ne + e] = i < K ? cu[(f * KMAX + i) * ne + u] : 0.0;
+  if (p >= 2) {
+    const int64_t n = G.start[p + 1] - G.start[p], l = e - G.start[p];
+    TC* h = chp<TC>(st.ch[p]);
+    for (int f = 0; f < 3; ++f)
+      for (int i = 3; i < K; ++i) h[(f * (K - 3) + (i - 3)) * n + l] = (TC)cu[(f * KMAX + i) * ne + u];
+  }
+}
+
+// rc != nullptr: write the correction part of the base modes from rc instead
+// of the base state (used for the split rhs).
+template <typename TC>
+__global__ void k_to_user(DevMesh m, Groups G, const int32_t* perm, StateDev st, const double* __restrict__ rc,
+                          double* __restrict__ cu) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.ne) return;
+  const int64_t ne = m.ne, u = perm[e];
+  const int p = m.p[e], K = Kof(p);
+  for (int f = 0; f < 3; ++f) {
+    for (int i = 0; i < 3; ++i) {
+      double v = 0.0;
+      if (i < K) {
+        if (rc) v = (m.flags[e] & 1) ? rc[(f * 3 + i) * ne + e] : 0.0;
+        else v = st.cb[(f * 3 + i) * ne + e];
+      }
+      cu[(f * KMAX + i) * ne + u] = v;
+    }
+    for (int i = 3; i < KMAX; ++i) {
+      double v = 0.0;
+      if (i < K && st.ch[p]) {
+        const int64_t n = G.start[p + 1] - G.start[p], l = e - G.start[p];
+        v = (double)chp<TC>(st.ch[p])[(f * (K - 3) + (i - 3)) * n + l];
+      }
+      cu[(f * KMAX + i) * ne + u] = v;
+    }
+  }
+}
+
+int launch_from_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
+                     const double* cu, StateDev st) {
+  if (m.ne == 0) return 0;
+  if (corr_fp32) k_from_user<float><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, cu, st);
+  else k_from_user<double><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, cu, st);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
+                   StateDev st, const double* rc, double* cu) {
+  if (m.ne == 0) return 0;
+  if (corr_fp32)
+    k_to_user<float><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, st, rc, cu);
+  else
+    k_to_user<double><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, st, rc, cu);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// auxiliary system for p <= 1 (Sect. 3):  M_H u = U, M_H v = V with
+//   M_H[i][j] = (1/s) sum_{n < K(i,j)} H_n T[n][i][j],  K(1,1) = 1, else 3.
+// The 3 x 3 symmetric system is solved with its adjugate (one division).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_usolve_base(DevMesh m, int64_t n_end, Phys ph, const double* __restrict__ cb,
+                                                     double* __restrict__ ub, unsigned* status) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n_end) return;
+  const int64_t ne = m.ne;
+  const double rs = m.geo[G_RS * ne + e];
+  const double H0 = cb[0 * ne + e] + m.geo[G_HB0 * ne + e];
+  const double U0 = cb[3 * ne + e], V0 = cb[6 * ne + e];
+  if (!(H0 * cPhi0 * rs > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
+  if (m.p[e] == 0) {
+    const double r = 1.0 / (H0 * cT1[0][0][0] * rs);
+    ub[0 * ne + e] = U0 * r; ub[1 * ne + e] = 0.0; ub[2 * ne + e] = 0.0;
+    ub[3 * ne + e] = V0 * r; ub[4 * ne + e] = 0.0; ub[5 * ne + e] = 0.0;
+    return;
+  }
+  const double H1 = cb[1 * ne + e] + m.geo[G_HB1 * ne + e];
+  const double H2 = cb[2 * ne + e] + m.geo[G_HB2 * ne + e];
+  const double U1 = cb[4 * ne + e], U2 = cb[5 * ne + e];
+  const double V1 = cb[7 * ne + e], V2 = cb[8 * ne + e];
+  // entries (scaled by s: the 1/s factor cancels in the adjugate solve up to a final scale)
+  const double a = H0 * cT1[0][0][0];
+  const double b = H0 * cT1[0][0][1] + H1 * cT1[1][0][1] + H2 * cT1[2][0][1];
+  const double c = H0 * cT1[0][0][2] + H1 * cT1[1][0][2] + H2 * cT1[2][0][2];
+  const double d = H0 * cT1[0][1][1] + H1 * cT1[1][1][1] + H2 * cT1[2][1][1];
+  const double f = H0 * cT1[0][1][2] + H1 * cT1[1][1][2] + H2 * cT1[2][1][2];
+  const double h = H0 * cT1[0][2][2] + H1 * cT1[1][2][2] + H2 * cT1[2][2][2];
+  // M = (1/s) [[a b c][b d f][c f h]];  u = s * adj(S) U / det(S), S = s M
+  const double C00 = d * h - f * f, C01 = c * f - b * h, C02 = b * f - c * d;
+  const double C11 = a * h - c * c, C12 = b * c - a * f, C22 = a * d - b * b;
+  const double det = a * C00 + b * C01 + c * C02;
+  const double r = 1.0 / (det * rs);
+  ub[0 * ne + e] = (C00 * U0 + C01 * U1 + C02 * U2) * r;
+  ub[1 * ne + e] = (C01 * U0 + C11 * U1 + C12 * U2) * r;
+  ub[2 * ne + e] = (C02 * U0 + C12 * U1 + C22 * U2) * r;
+  ub[3 * ne + e] = (C00 * V0 + C01 * V1 + C02 * V2) * r;
+  ub[4 * ne + e] = (C01 * V0 + C11 * V1 + C12 * V2) * r;
+  ub[5 * ne + e] = (C02 * V0 + C12 * V1 + C22 * V2) * r;
+}
+
+int launch_usolve_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
+                       double* ub, unsigned* status) {
+  const int64_t n = G.start[2];
+  if (n == 0) return 0;
+  k_usolve_base<<<nblocks(n, 256), 256, 0, s>>>(m, n, ph, cb, ub, status);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// CFL reduction: min_e d_e / ((|u_bar| + sqrt(g H_bar)) (2p+1)).  Positive
+// doubles order like their bit patterns, so an integer atomicMin gives the
+// exact minimum independent of the order of the blocks.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_dt(DevMesh m, Phys ph, const double* __restrict__ cb,
+                                            const double* __restrict__ ub, unsigned long long* dmin) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t ne = m.ne;
+  double d = DBL_MAX;
+  if (e < ne) {
+    const double r = cPhi0 * m.geo[G_RS * ne + e];
+    const double ubar = ub[0 * ne + e] * r, vbar = ub[3 * ne + e] * r;
+    const double Hbar = (cb[e] + m.geo[G_HB0 * ne + e]) * r;
+    const double sp = sqrt(ubar * ubar + vbar * vbar) + sqrt(ph.g * Hbar);
+    const double dd = m.geo[G_DIAM * ne + e] / (sp * (2.0 * m.p[e] + 1.0));
+    if (dd > 0.0 && dd < d) d = dd;  // NaN never wins; it is reported by the status checks
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = d;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMin(dmin, (unsigned long long)__double_as_longlong(red[0]));
+}
+
+__global__ void k_reset_min(unsigned long long* dmin) { *dmin = (unsigned long long)__double_as_longlong(DBL_MAX); }
+
+int launch_reset_min(cudaStream_t s, unsigned long long* dmin) {
+  k_reset_min<<<1, 1, 0, s>>>(dmin);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+int launch_dt(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
+              const double* ub, unsigned long long* dmin) {
+  (void)G;
+  if (m.ne == 0) return 0;
+  k_dt<<<nblocks(m.ne, 256), 256, 0, s>>>(m, ph, cb, ub, dmin);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+// dt_dev = dt_fixed > 0 ? dt_fixed : cfl * min;   then t += dt (after the step)
+__global__ void k_set_dt(double* dt_dev, const unsigned long long* dmin, double cfl, double dt_fixed) {
+  *dt_dev = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)*dmin);
+}
+__global__ void k_advance_time(double* t_dev, const double* dt_dev) { *t_dev += *dt_dev; }
+
+int launch_advance_time(cudaStream_t s, double* t_dev, const unsigned long long* dmin, double cfl, double dt_fixed,
+                        double* dt_dev) {
+  if (t_dev == nullptr) k_set_dt<<<1, 1, 0, s>>>(dt_dev, dmin, cfl, dt_fixed);
+  else k_advance_time<<<1, 1, 0, s>>>(t_dev, dt_dev);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+__device__ __forceinline__ double stage_dt(const Stage& st) { return st.dt ? *st.dt : st.dt_host; }
+__device__ __forceinline__ double stage_time(const Stage& st) {
+  return (st.t_dev ? *st.t_dev : st.t) + st.tau * stage_dt(st);
+}
+
+__device__ __forceinline__ double tide_value(const Phys& ph, double t) {
+  if (ph.tide_period <= 0.0) return ph.tide_amp;
+  return ph.tide_amp * sin(2.0 * 3.14159265358979323846 * t / ph.tide_period + ph.tide_phase);
+}
+
+// ---------------------------------------------------------------------------
+// Base edge flux.  For the P1 parts of both sides: traces at the two Gauss
+// points, the LF flux (Sect. 2)
+//   A_hat = 1/2 ((A(c) + A(c+)).n + lambda (c - c+)),
+//   A.n = (q.n,  U (u.n) + g nx (xi^2/2 + xi h_b),  V (u.n) + g ny (...)),
+// with lambda from the element means (Eq. 10, Sect. 3), stored pre-weighted
+// by |E| w_g at the points in the left element's direction.
+// ---------------------------------------------------------------------------
+struct Side5 { double xi, U, V, u, v; };
+
+__global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cb,
+                                                   const double* __restrict__ ub, double* __restrict__ Fb,
+                                                   double* __restrict__ lamo) {
+  const int64_t ed = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ed >= m.nedge) return;
+  const int64_t ne = m.ne, nE = m.nedge;
+  const int L = m.eL[ed], R = m.eR[ed], info = m.einfo[ed];
+  const int kL = info & 3, kR = (info >> 2) & 3, bc = info >> 4;
+  const double len = m.egeo[ed], nx = m.egeo[nE + ed], ny = m.egeo[2 * nE + ed];
+  const double hA = m.egeo[3 * nE + ed], hB = m.egeo[4 * nE + ed];
+  const double rsL = m.geo[G_RS * ne + L];
+  double cL[5][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cL[0][i] = cb[(0 * 3 + i) * ne + L]; cL[1][i] = cb[(1 * 3 + i) * ne + L]; cL[2][i] = cb[(2 * 3 + i) * ne + L];
+    cL[3][i] = ub[(0 * 3 + i) * ne + L]; cL[4][i] = ub[(1 * 3 + i) * ne + L];
+  }
+  Side5 tl[2], tr[2];
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    double t[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) t[f] = rsL * (cL[f][0] * cB2[kL][0][g] + cL[f][1] * cB2[kL][1][g] + cL[f][2] * cB2[kL][2][g]);
+    tl[g] = Side5{t[0], t[1], t[2], t[3], t[4]};
+  }
+  const double hmid = 0.5 * (hA + hB);
+  const double mL = cPhi0 * rsL;
+  const double unL = (cL[3][0] * nx + cL[4][0] * ny) * mL;
+  const double HL = cL[0][0] * mL + hmid;
+  double unR, HR;
+  if (R >= 0) {
+    const double rsR = m.geo[G_RS * ne + R];
+    double cR[5][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      cR[0][i] = cb[(0 * 3 + i) * ne + R]; cR[1][i] = cb[(1 * 3 + i) * ne + R]; cR[2][i] = cb[(2 * 3 + i) * ne + R];
+      cR[3][i] = ub[(0 * 3 + i) * ne + R]; cR[4][i] = ub[(1 * 3 + i) * ne + R];
+    }
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int gr = 1 - g;  // the right element runs the edge backwards
+      double t[5];
+#pragma unroll
+      for (int f = 0; f < 5; ++f)
+        t[f] = rsR * (cR[f][0] * cB2[kR][0][gr] + cR[f][1] * cB2[kR][1][gr] + cR[f][2] * cB2[kR][2][gr]);
+      tr[g] = Side5{t[0], t[1], t[2], t[3], t[4]};
+    }
+    const double mR = cPhi0 * rsR;
+    unR = (cR[3][0] * nx + cR[4][0] * ny) * mR;
+    HR = cR[0][0] * mR + hmid;
+  } else if (bc == 2) {
+    const double xh = tide_value(ph, stage_time(stg));
+#pragma unroll
+    for (int g = 0; g < 2; ++g) tr[g] = Side5{xh, tl[g].U, tl[g].V, tl[g].u, tl[g].v};
+    unR = unL;
+    HR = xh + hmid;
+  } else {
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const double qn = tl[g].U * nx + tl[g].V * ny, wn = tl[g].u * nx + tl[g].v * ny;
+      tr[g] = Side5{tl[g].xi, tl[g].U - 2.0 * qn * nx, tl[g].V - 2.0 * qn * ny, tl[g].u - 2.0 * wn * nx,
+                    tl[g].v - 2.0 * wn * ny};
+    }
+    unR = -unL;
+    HR = HL;
+  }
+  const double lam = fmax(fabs(unL), fabs(unR)) + sqrt(ph.g * fmax(HL, HR));
+  lamo[ed] = lam;
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const double hb = hA + cS2[g] * (hB - hA);
+    const Side5 a = tl[g], b = tr[g];
+    const double wa = a.u * nx + a.v * ny, wb = b.u * nx + b.v * ny;
+    const double pa = ph.g * a.xi * (0.5 * a.xi + hb), pb = ph.g * b.xi * (0.5 * b.xi + hb);
+    const double F0 = (a.U + b.U) * nx + (a.V + b.V) * ny + lam * (a.xi - b.xi);
+    const double F1 = a.U * wa + b.U * wb + (pa + pb) * nx + lam * (a.U - b.U);
+    const double F2 = a.V * wa + b.V * wb + (pa + pb) * ny + lam * (a.V - b.V);
+    const double wgt = 0.5 * len * cW2[g];
+    Fb[(0 * 2 + g) * nE + ed] = wgt * F0;
+    Fb[(1 * 2 + g) * nE + ed] = wgt * F1;
+    Fb[(2 * 2 + g) * nE + ed] = wgt * F2;
+  }
+}
+
+int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Stage& stg, const double* cb,
+                     const double* ub, EdgeFlux fx) {
+  if (m.nedge == 0) return 0;
+  k_edge_base<<<nblocks(m.nedge, 128), 128, 0, s>>>(m, ph, stg, cb, ub, fx.Fb, fx.lam);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Base element update.  For test modes q of degree 1, grad phi_q is constant,
+// so by orthonormality (Eq. 13 restricted to indices <= 3)
+//   (A_xi, grad phi_q) = grad phi_q . (U_1, V_1) sqrt|Omega|
+//   (A_U , grad phi_q) = d_x phi_q sum_i (U_i u_i + g(xi_i^2/2 + xi_i hb_i))
+//                      + d_y phi_q sum_i U_i v_i          (and alike for V),
+// the source (r, phi_q) = g grad h_b xi_q, and the edge terms are
+// -sum_g F_g phi_q(x_g) over the three edges (sign flipped for the right side).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cbS,
+                                                   const double* __restrict__ cbN, double* __restrict__ cbO,
+                                                   const double* __restrict__ ub, const double* __restrict__ Fb,
+                                                   const double* __restrict__ rc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.ne) return;
+  const int64_t ne = m.ne, nE = m.nedge;
+  const double* geo = m.geo;
+  double c[3][3], u[2][3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[f][i] = cbS[(f * 3 + i) * ne + e];
+#pragma unroll
+  for (int f = 0; f < 2; ++f)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) u[f][i] = ub[(f * 3 + i) * ne + e];
+  const double rs = geo[G_RS * ne + e], sv = geo[G_S * ne + e];
+  const double hb[3] = {geo[G_HB0 * ne + e], geo[G_HB1 * ne + e], geo[G_HB2 * ne + e]};
+  const double g = ph.g;
+  double r[3][3];
+  // volume terms
+  double Axx = 0.0, Axy = 0.0, Ayx = 0.0, Ayy = 0.0, P = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Axx += c[1][i] * u[0][i]; Axy += c[1][i] * u[1][i];
+    Ayx += c[2][i] * u[0][i]; Ayy += c[2][i] * u[1][i];
+    P += c[0][i] * (0.5 * c[0][i] + hb[i]);
+  }
+  P *= g;
+  const double m0 = sv / cPhi0;  // int phi_{e,1} = sqrt|Omega_e|
+  const double gq[2][2] = {{geo[G_GQ1X * ne + e], geo[G_GQ1Y * ne + e]}, {geo[G_GQ2X * ne + e], geo[G_GQ2Y * ne + e]}};
+  const double dhx = geo[G_DHX * ne + e], dhy = geo[G_DHY * ne + e];
+  r[0][0] = 0.0;
+  r[1][0] = g * dhx * c[0][0];
+  r[2][0] = g * dhy * c[0][0];
+#pragma unroll
+  for (int q = 1; q < 3; ++q) {
+    const double gx = gq[q - 1][0], gy = gq[q - 1][1];
+    r[0][q] = (gx * c[1][0] + gy * c[2][0]) * m0;
+    r[1][q] = gx * (Axx + P) + gy * Axy + g * dhx * c[0][q];
+    r[2][q] = gx * Ayx + gy * (Ayy + P) + g * dhy * c[0][q];
+  }
+  // edge terms
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int ee = m.eedge[k * ne + e];
+    const int64_t ed = ee >> 1;
+    const bool right = ee & 1;
+    double F[3][2];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      F[f][0] = Fb[(f * 2 + 0) * nE + ed];
+      F[f][1] = Fb[(f * 2 + 1) * nE + ed];
+    }
+    const double sg = right ? rs : -rs;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double b0 = right ? cB2[k][q][1] : cB2[k][q][0];
+      const double b1 = right ? cB2[k][q][0] : cB2[k][q][1];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) r[f][q] += sg * (F[f][0] * b0 + F[f][1] * b1);
+    }
+  }
+  if (!stg.parts && (m.flags[e] & 1)) {
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) r[f][q] += rc[(f * 3 + q) * ne + e];
+  }
+  const int K = m.p[e] == 0 ? 1 : 3;
+  const double dt = stage_dt(stg), a = stg.a, b = stg.b;
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int64_t ix = (f * 3 + q) * ne + e;
+      double v = 0.0;
+      if (q < K) {
+        if (stg.rhs_only) v = r[f][q];
+        else v = (a != 0.0 ? a * cbN[ix] : 0.0) + b * (c[f][q] + dt * r[f][q]);
+      }
+      cbO[ix] = v;
+    }
+}
+
+int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
+                     int corr_fp32, const double* cbS, const double* cbN, double* cbO, const double* ub,
+                     EdgeFlux fx, const void* rc, double cfl) {
+  (void)G; (void)cfl;
+  if (m.ne == 0) return 0;
+  (void)corr_fp32;
+  k_elem_base<<<nblocks(m.ne, 128), 128, 0, s>>>(m, ph, stg, cbS, cbN, cbO, ub, fx.Fb, (const double*)rc);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// status: non-finite values in the state
+// ---------------------------------------------------------------------------
+template <typename TC>
+__global__ void k_check(DevMesh m, Groups G, StateDev st, unsigned* status) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.ne) return;
+  const int64_t ne = m.ne;
+  bool bad = false;
+  for (int i = 0; i < 9; ++i) bad |= !isfinite(st.cb[i * ne + e]);
+  const int p = m.p[e];
+  if (p >= 2) {
+    const int K = Kof(p);
+    const int64_t n = G.start[p + 1] - G.start[p], l = e - G.start[p];
+    const TC* h = chp<TC>(st.ch[p]);
+    for (int i = 0; i < 3 * (K - 3); ++i) bad |= !isfinite((double)h[i * n + l]);
+  }
+  if (bad) atomicOr(status, (unsigned)ST_NONFINITE);
+}
+
+int launch_check_state(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp32, StateDev st,
+                       unsigned* status) {
+  if (m.ne == 0) return 0;
+  if (corr_fp32) k_check<float><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, st, status);
+  else k_check<double><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, st, status);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// deterministic reductions (fixed tree per block, blocks summed in order)
+// ---------------------------------------------------------------------------
+__device__ void block_sum_store(double v, double* partial) {
+  __shared__ double red[256];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_partials(const double* partial, int n, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += partial[i];
+    *out = s;
+  }
+}
+
+__global__ void k_mass(DevMesh m, const double* __restrict__ cb, double* partial) {
+  double v = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m.ne; e += (int64_t)gridDim.x * blockDim.x)
+    v += m.geo[G_S * m.ne + e] / cPhi0 * cb[e];
+  block_sum_store(v, partial);
+}
+
+int launch_mass(cudaStream_t s, const DevMesh& m, const double* cb, double* partial, int nblk, double* out) {
+  k_mass<<<nblk, 256, 0, s>>>(m, cb, partial);
+  count_launch();
+  k_sum_partials<<<1, 32, 0, s>>>(partial, nblk, out);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+template <typename TC>
+__global__ void k_energy(DevMesh m, Groups G, Phys ph, StateDev c, VelDev u, double* partial) {
+  double v = 0.0;
+  const int64_t ne = m.ne;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = m.p[e], K = Kof(p);
+    for (int i = 0; i < 3 && i < K; ++i) {
+      const double x = c.cb[i * ne + e];
+      v += 0.5 * ph.g * x * x + 0.5 * (c.cb[(3 + i) * ne + e] * u.ub[i * ne + e] + c.cb[(6 + i) * ne + e] * u.ub[(3 + i) * ne + e]);
+    }
+    if (p >= 2) {
+      const int64_t n = G.start[p + 1] - G.start[p], l = e - G.start[p];
+      const TC* h = chp<TC>(c.ch[p]);
+      const TC* uh = chp<TC>(u.uh[p]);
+      const int Kh = K - 3;
+      for (int i = 0; i < Kh; ++i) {
+        const double x = h[i * n + l];
+        v += 0.5 * ph.g * x * x + 0.5 * ((double)h[(Kh + i) * n + l] * (double)uh[i * n + l] +
+                                         (double)h[(2 * Kh + i) * n + l] * (double)uh[(Kh + i) * n + l]);
+      }
+    }
+  }
+  block_sum_store(v, partial);
+}
+
+int launch_energy(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp32, const Phys& ph, StateDev c,
+                  VelDev u, double* partial, int nblk, double* out) {
+  if (corr_fp32) k_energy<float><<<nblk, 256, 0, s>>>(m, G, ph, c, u, partial);
+  else k_energy<double><<<nblk, 256, 0, s>>>(m, G, ph, c, u, partial);
+  count_launch();
+  k_sum_partials<<<1, 32, 0, s>>>(partial, nblk, out);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace swedg

@@ -1,0 +1,77 @@
+// Launchers of the libswedg kernels (all asynchronous on the given stream).
+#pragma once
+#include "common.h"
+
+namespace swedg {
+
+// Device view of one modal state (base + correction parts) in internal order.
+struct StateDev {
+  double* cb;        // [3][3][ne]
+  void* ch[5];       // per order p = 2..4: [3][K(p)-3][n_p] of the correction type
+};
+
+struct VelDev {
+  double* ub;        // [2][3][ne]
+  void* uh[5];       // per p = 2..4: [2][K(p)-3][n_p]
+};
+
+struct Groups {
+  int64_t start[6];  // internal element ranges per order p: [start[p], start[p+1])
+};
+
+struct EdgeFlux {
+  double* Fb;        // [3][2][nedge] base flux (weighted by |E| w_g) at the 2-point rule
+  double* lam;       // [nedge]
+  void* Fh[5];       // per pmax = 2..4: [3][N][n] correction flux (full - base)
+  void* Ff[5];       // per pmax: [3][N][n] full flux
+};
+
+// every kernel launch of the library is counted (for launch accounting)
+void count_launch(int n = 1);
+
+// status bits set by kernels
+enum { ST_DEPTH = 1, ST_NONFINITE = 2 };
+
+// base-path tables (host -> constant memory of the base kernels)
+void upload_base_tables();
+
+int launch_from_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
+                     const double* cu, StateDev st);
+int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
+                   StateDev st, const double* rc, double* cu);
+
+int launch_usolve_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
+                       double* ub, unsigned* status);
+int launch_dt(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
+              const double* ub, unsigned long long* dmin);
+int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Stage& stg, const double* cb,
+                     const double* ub, EdgeFlux fx);
+int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
+                     int corr_fp32, const double* cbS, const double* cbN, double* cbO, const double* ub,
+                     EdgeFlux fx, const void* rc, double cfl);
+int launch_advance_time(cudaStream_t s, double* t_dev, const unsigned long long* dmin, double cfl,
+                        double dt_fixed, double* dt_dev);
+int launch_reset_min(cudaStream_t s, unsigned long long* dmin);
+int launch_check_state(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp32, StateDev st,
+                       unsigned* status);
+// deterministic two-pass reductions: mass and energy of a state
+int launch_mass(cudaStream_t s, const DevMesh& m, const double* cb, double* partial, int nblk, double* out);
+int launch_energy(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp32, const Phys& ph, StateDev c,
+                  VelDev u, double* partial, int nblk, double* out);
+
+// correction kernels, one namespace per arithmetic type (FP64 / FP32)
+#define SWE_CORR_DECL(NS)                                                                                        \
+  namespace NS {                                                                                                 \
+  void upload_tables();                                                                                          \
+  int launch_usolve_corr(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u, \
+                         unsigned* status);                                                                      \
+  int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,   \
+                       const Stage& stg, StateDev c, VelDev u, EdgeFlux fx);                                      \
+  int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,   \
+                       const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc,  \
+                       const int32_t* edge_only, int64_t n_edge_only);                                            \
+  }
+SWE_CORR_DECL(corr64)
+SWE_CORR_DECL(corr32)
+
+}  // namespace swedg

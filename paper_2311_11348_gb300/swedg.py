@@ -1,0 +1,230 @@
+"""Thin ctypes binding of libswedg (include/swedg.h): argument marshalling only.
+
+Every call lands in the CUDA library; there is no Python or CPU fallback.
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); they must be
+C-contiguous float64 (int32/int8 for the mesh arrays).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KMAX = 15
+PREC_FP64 = 0
+PREC_MIXED_FP32 = 1
+
+_ERRORS = {-1: "invalid argument", -2: "bad mesh", -3: "depth <= h_min", -4: "non-finite state",
+           -5: "CUDA error", -6: "device wait timeout"}
+
+
+class SweError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libswedg error {code} ({_ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("g", C.c_double), ("cfl", C.c_double), ("h_min", C.c_double), ("rk_order", C.c_int),
+                ("precision", C.c_int), ("tide_amp", C.c_double), ("tide_period", C.c_double),
+                ("tide_phase", C.c_double), ("cuda_stream", C.c_void_p)]
+
+
+_lib = None
+
+# every symbol include/swedg.h declares
+SYMBOLS = ("swe_default_params", "swe_create", "swe_destroy", "swe_last_error", "swe_set_mesh",
+           "swe_set_bathymetry", "swe_set_orders", "swe_set_state", "swe_get_state", "swe_p1_modes", "swe_rhs",
+           "swe_rhs_parts", "swe_rk_step", "swe_run", "swe_mass", "swe_energy", "swe_reference_tensors",
+           "swe_edge_table", "swe_profile", "swe_profile_read")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the in-tree libswedg.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"libswedg is not built ({path}); run `python -m paper_2311_11348_gb300.build`")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    i64 = C.c_int64
+    d = C.c_double
+    lib.swe_default_params.argtypes = [C.POINTER(Params)]
+    lib.swe_create.argtypes = [C.POINTER(P), C.POINTER(Params)]
+    lib.swe_destroy.argtypes = [P]
+    lib.swe_last_error.argtypes = [P]
+    lib.swe_last_error.restype = C.c_char_p
+    lib.swe_set_mesh.argtypes = [P, i64, P, i64, P, P]
+    lib.swe_set_bathymetry.argtypes = [P, P]
+    lib.swe_set_orders.argtypes = [P, P]
+    lib.swe_set_state.argtypes = [P, P, d]
+    lib.swe_get_state.argtypes = [P, P, C.POINTER(d)]
+    lib.swe_p1_modes.argtypes = [P, P, P]
+    lib.swe_rhs.argtypes = [P, P, P]
+    lib.swe_rhs_parts.argtypes = [P, P, P, P]
+    lib.swe_rk_step.argtypes = [P, d, C.POINTER(d)]
+    lib.swe_run.argtypes = [P, i64, d, C.POINTER(d)]
+    lib.swe_mass.argtypes = [P, C.POINTER(d)]
+    lib.swe_energy.argtypes = [P, C.POINTER(d)]
+    lib.swe_reference_tensors.argtypes = [P, P, P]
+    lib.swe_edge_table.argtypes = [C.c_int, P, P, P]
+    lib.swe_profile.argtypes = [P, C.c_int]
+    lib.swe_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(i64)]
+    for s in SYMBOLS:
+        if s not in ("swe_destroy", "swe_default_params", "swe_last_error"):
+            getattr(lib, s).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a, dtype=np.float64):
+    """(pointer, keepalive) of a numpy array or torch tensor."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(C.c_void_p), arr
+
+
+def reference_tensors():
+    lib = load()
+    D = np.zeros((2, KMAX, KMAX)); G = np.zeros((2, KMAX, KMAX, KMAX)); T = np.zeros((KMAX,) * 3)
+    lib.swe_reference_tensors(D.ctypes.data_as(C.c_void_p), G.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p))
+    return D, G, T
+
+
+def edge_table(npts: int):
+    lib = load()
+    s = np.zeros(npts); w = np.zeros(npts); B = np.zeros((3, KMAX, npts))
+    rc = lib.swe_edge_table(npts, s.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p), B.ctypes.data_as(C.c_void_p))
+    if rc:
+        raise SweError(rc, "swe_edge_table")
+    return s, w, B
+
+
+class Solver:
+    """One libswedg context (one mesh, one device state)."""
+
+    def __init__(self, g=9.81, cfl=0.1, h_min=1e-8, rk_order=2, precision=PREC_FP64, tide=(0.0, 0.0, 0.0),
+                 stream=None):
+        self._lib = load()
+        p = Params()
+        self._lib.swe_default_params(C.byref(p))
+        p.g, p.cfl, p.h_min, p.rk_order, p.precision = g, cfl, h_min, rk_order, precision
+        p.tide_amp, p.tide_period, p.tide_phase = tide
+        p.cuda_stream = stream
+        h = C.c_void_p()
+        rc = self._lib.swe_create(C.byref(h), C.byref(p))
+        if rc:
+            raise SweError(rc, self._lib.swe_last_error(None).decode())
+        self.h = h
+        self.ne = 0
+        self.nv = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.swe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, rc):
+        if rc:
+            raise SweError(rc, self._lib.swe_last_error(self.h).decode())
+
+    def set_mesh(self, xy, tri, bc_tag=None):
+        pxy, kx = _ptr(xy)
+        pt, kt = _ptr(tri, np.int32)
+        pb, kb = _ptr(bc_tag, np.int8)
+        self.nv = int(xy.shape[0])
+        self.ne = int(tri.shape[0])
+        self._ck(self._lib.swe_set_mesh(self.h, self.nv, pxy, self.ne, pt, pb))
+
+    def set_bathymetry(self, hv):
+        p, k = _ptr(hv)
+        self._ck(self._lib.swe_set_bathymetry(self.h, p))
+
+    def set_orders(self, orders):
+        p, k = _ptr(orders, np.int8)
+        self._ck(self._lib.swe_set_orders(self.h, p))
+
+    def set_state(self, c, t=0.0):
+        p, k = _ptr(c)
+        self._ck(self._lib.swe_set_state(self.h, p, float(t)))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros((3, KMAX, self.ne))
+        p, k = _ptr(out)
+        t = C.c_double(0.0)
+        self._ck(self._lib.swe_get_state(self.h, p, C.byref(t)))
+        return out, t.value
+
+    def p1_modes(self, vals, out=None):
+        if out is None:
+            out = np.zeros((3, self.ne))
+        pv, kv = _ptr(vals)
+        po, ko = _ptr(out)
+        self._ck(self._lib.swe_p1_modes(self.h, pv, po))
+        return out
+
+    def rhs(self, c, out=None):
+        if out is None:
+            out = np.zeros((3, KMAX, self.ne))
+        pc, kc = _ptr(c)
+        po, ko = _ptr(out)
+        self._ck(self._lib.swe_rhs(self.h, pc, po))
+        return out
+
+    def rhs_parts(self, c):
+        b = np.zeros((3, KMAX, self.ne)); r = np.zeros((3, KMAX, self.ne))
+        pc, kc = _ptr(c)
+        self._ck(self._lib.swe_rhs_parts(self.h, pc, _ptr(b)[0], _ptr(r)[0]))
+        return b, r
+
+    def rk_step(self, dt=0.0):
+        du = C.c_double(0.0)
+        self._ck(self._lib.swe_rk_step(self.h, float(dt), C.byref(du)))
+        return du.value
+
+    def run(self, nsteps, dt_fixed=0.0):
+        t = C.c_double(0.0)
+        self._ck(self._lib.swe_run(self.h, int(nsteps), float(dt_fixed), C.byref(t)))
+        return t.value
+
+    def mass(self):
+        m = C.c_double(0.0)
+        self._ck(self._lib.swe_mass(self.h, C.byref(m)))
+        return m.value
+
+    def energy(self):
+        e = C.c_double(0.0)
+        self._ck(self._lib.swe_energy(self.h, C.byref(e)))
+        return e.value
+
+    def profile(self, enable=True):
+        self._ck(self._lib.swe_profile(self.h, int(enable)))
+
+    def profile_read(self):
+        n = 16
+        names = (C.c_char_p * n)()
+        ms = (C.c_double * n)()
+        cnt = (C.c_int64 * n)()
+        k = self._lib.swe_profile_read(self.h, n, names, ms, cnt)
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(k)}

@@ -1,0 +1,203 @@
+"""CUDA path against the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerances: the FP64 path must match the oracle to 1e-11 relative L2 after
+1000 steps (same seeded inputs); one rhs evaluation agrees to ~1e-13 (only
+the summation order and the tensors' last bits differ).  The mixed mode
+(FP32 correction) must stay within 1e-6 relative L2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2311_11348_gb300 import build, inputs, swedg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    swedg.load()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def make_pair(w, precision=swedg.PREC_FP64, tide=(0.0, 0.0, 0.0), rk=None, cfl=None):
+    m = O.Mesh(w["xy"], w["tri"], w["hv"], w["orders"], bc_tag=w.get("bc_tag"))
+    P = O.Params(g=w["g"], cfl=cfl or w["cfl"], rk_order=rk or w["rk_order"], tide_amp=tide[0], tide_period=tide[1],
+                 tide_phase=tide[2])
+    s = swedg.Solver(g=w["g"], cfl=cfl or w["cfl"], rk_order=rk or w["rk_order"], precision=precision, tide=tide)
+    s.set_mesh(w["xy"], w["tri"], w.get("bc_tag"))
+    s.set_bathymetry(w["hv"])
+    s.set_orders(w["orders"])
+    return m, P, s
+
+
+def mixed_workload(n=16, seed=1, pmin=0, pmax=4, open_west=True):
+    xy, tri = inputs.split_square_mesh(n, 1e4, jitter=0.2, seed=seed)
+    rng = np.random.default_rng(seed)
+    hv = inputs.fourier_bathymetry(xy, 1e4, lo=20.0, hi=200.0, seed=seed + 1)
+    orders = rng.integers(pmin, pmax + 1, size=len(tri)).astype(np.int8)
+    bc = inputs.boundary_tags(xy, tri, "west") if open_west else None
+
+    def ic(x, y):
+        return 0.5 * np.exp(-((x - 6e3) ** 2 + (y - 4e3) ** 2) / 2e6), 3.0 * np.exp(-((x - 5e3) ** 2) / 4e6), \
+            -2.0 * np.exp(-((y - 5e3) ** 2) / 5e6)
+
+    return dict(xy=xy, tri=tri, hv=hv, orders=orders, ic=ic, bc_tag=bc, g=9.81, rk_order=3, cfl=0.2)
+
+
+def test_rhs_unit_p1():
+    w = inputs.unit_p1()
+    m, P, s = make_pair(w)
+    c = m.project_state(w["ic"])
+    r_o = m.rhs(P, c)
+    r_g = s.rhs(c)
+    assert rel_l2(r_g, r_o) < 1e-13
+    assert np.abs(r_g - r_o).max() <= 1e-12 * np.abs(r_o).max()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_rhs_mixed_orders_open_sea(seed):
+    w = mixed_workload(seed=seed)
+    tide = (0.3, 3600.0, 0.4)
+    m, P, s = make_pair(w, tide=tide)
+    c = m.project_state(w["ic"])
+    t0 = 500.0
+    s.set_state(c, t0)
+    r_o = m.rhs(P, c, t=t0)
+    r_g = s.rhs(c)
+    assert np.abs(r_g - r_o).max() <= 1e-12 * np.abs(r_o).max()
+    b_g, k_g = s.rhs_parts(c)
+    b_o = m.rhs(P, c, t=t0, part=1)
+    k_o = m.rhs(P, c, t=t0, part=2)
+    assert np.abs(b_g - b_o).max() <= 1e-12 * np.abs(b_o).max()
+    assert np.abs(k_g - k_o).max() <= 1e-12 * np.abs(r_o).max()
+    assert np.abs(b_g + k_g - r_g).max() <= 1e-13 * np.abs(r_o).max()
+
+
+def test_single_triangle_and_p0():
+    xy = np.array([[0.0, 0.0], [2.0, 0.3], [0.5, 1.7]])
+    tri = np.array([[0, 2, 1]], dtype=np.int32)  # clockwise on purpose
+    for p in range(5):
+        w = dict(xy=xy, tri=tri, hv=np.array([1.0, 1.5, 2.0]), orders=np.array([p], np.int8), g=9.81, rk_order=2,
+                 cfl=0.1)
+        m, P, s = make_pair(w)
+        c = m.project_state(lambda x, y: (0.1 * x * y, 0.2 + 0.1 * x, -0.1 * y))
+        assert np.abs(s.rhs(c) - m.rhs(P, c)).max() <= 1e-12 * max(1.0, np.abs(m.rhs(P, c)).max())
+
+
+def test_fp64_1000_steps_unit_p1():
+    """The FP64 gate: 1000 CFL steps of SSP-RK2 on the 512-triangle p = 1 case."""
+    w = inputs.unit_p1()
+    m, P, s = make_pair(w)
+    c = m.project_state(w["ic"])
+    s.set_state(c, 0.0)
+    t_g = s.run(1000)
+    c_g, _ = s.get_state()
+    c_o, t_o = m.run(P, c, 0.0, 1000)
+    assert abs(t_g - t_o) <= 1e-12 * t_o
+    assert rel_l2(c_g, c_o) < 1e-11
+    assert abs(s.mass() - m.mass(c_o)) <= 1e-12 * abs(m.mass(c_o))
+
+
+def test_fp64_steps_mixed_orders():
+    w = mixed_workload(seed=3, pmin=1, pmax=4)
+    m, P, s = make_pair(w, tide=(0.2, 2000.0, 0.0))
+    c = m.project_state(w["ic"])
+    s.set_state(c, 0.0)
+    n = 200
+    s.run(n)
+    c_g, t_g = s.get_state()
+    c_o, t_o = m.run(P, c, 0.0, n)
+    assert abs(t_g - t_o) <= 1e-12 * t_o
+    assert rel_l2(c_g, c_o) < 1e-11
+
+
+def test_mixed_fp32_correction_accuracy():
+    w = mixed_workload(seed=4, pmin=1, pmax=3, open_west=False)
+    m, P, s = make_pair(w, precision=swedg.PREC_MIXED_FP32)
+    c = m.project_state(w["ic"])
+    s.set_state(c, 0.0)
+    n = 200
+    s.run(n, dt_fixed=0.5)
+    c_g, _ = s.get_state()
+    c_o, _ = m.run(P, c, 0.0, n, dt=0.5)
+    err = rel_l2(c_g, c_o)
+    assert err < 1e-6, err
+    # the base modes carry the mass, and the correction's share of the mean mode
+    # is accumulated in FP64 from one flux value per edge: conserved to FP64
+    # round-off even with an FP32 correction
+    m0 = m.mass(c)
+    assert abs(s.mass() - m0) <= 1e-13 * math.sqrt(n) * abs(m0)
+
+
+def test_full_size_ocean_rhs():
+    """Full-size workload (131,072 triangles, p in {1,2,3}): one rhs, all outputs."""
+    w = inputs.ocean_p123()
+    m, P, s = make_pair(w)
+    c = m.project_state(w["ic"], n=6)
+    r_o = m.rhs(P, c)
+    r_g = s.rhs(c)
+    assert np.abs(r_g - r_o).max() <= 1e-12 * np.abs(r_o).max()
+
+
+def test_lake_at_rest_and_mass_gpu():
+    w = mixed_workload(seed=5, pmin=0, pmax=4, open_west=False)
+    m, P, s = make_pair(w)
+    area = m.geometry()["area"]
+    c = np.zeros((3, 15, len(w["tri"])))
+    c[0, 0] = 0.37 * np.sqrt(area)
+    s.set_state(c, 0.0)
+    s.run(50)
+    c1, _ = s.get_state()
+    assert np.abs(c1 - c).max() <= 1e-12 * np.abs(c).max()
+    c = m.project_state(w["ic"])
+    s.set_state(c, 0.0)
+    m0 = s.mass()
+    s.run(100)
+    Mref = np.sum((m.geometry()["hb"][:, 0] + c[0, 0]) * np.sqrt(area))
+    assert abs(s.mass() - m0) <= 1e-13 * math.sqrt(100) * Mref
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = mixed_workload(seed=6, pmin=1, pmax=3, open_west=False)
+    m, P, s = make_pair(w)
+    c = m.project_state(w["ic"])
+    s.set_state(c, 0.0)
+    s.run(20)
+    ref, tref = s.get_state()
+    s.set_state(c, 0.0)
+    s.run(10)
+    mid, tmid = s.get_state()
+    _, _, s2 = make_pair(w)
+    s2.set_state(mid, tmid)
+    s2.run(10)
+    out, tout = s2.get_state()
+    assert tout == tref
+    assert np.array_equal(out, ref)
+
+
+def test_errors_are_reported_not_faulted():
+    w = inputs.unit_p1()
+    _, _, s = make_pair(w)
+    with pytest.raises(swedg.SweError) as ei:
+        s.set_orders(np.full(len(w["tri"]), 7, np.int8))
+    assert ei.value.code == -1
+    bad = w["tri"].copy()
+    bad[0] = [0, 0, 1]
+    with pytest.raises(swedg.SweError) as ei:
+        s.set_mesh(w["xy"], bad)
+    assert ei.value.code == -2
+    s.set_mesh(w["xy"], w["tri"])
+    s.set_bathymetry(np.full(len(w["xy"]), 1.0))
+    c = np.zeros((3, 15, len(w["tri"])))
+    c[0, 0] = -5.0  # xi = -5 on a 1 m deep basin
+    s.set_state(c, 0.0)
+    with pytest.raises(swedg.SweError) as ei:
+        s.rk_step(1e-3)
+    assert ei.value.code in (-3, -4)
