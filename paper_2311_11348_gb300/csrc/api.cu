@@ -74,8 +74,6 @@ struct swe_ctx {
   VelDev vel{};
   EdgeFlux fx{};
   void* rc = nullptr;
-  int32_t* d_edge_only = nullptr;
-  int64_t n_edge_only = 0;
   double* d_user = nullptr;
   double* d_user2 = nullptr;
   double* d_dt = nullptr;
@@ -351,24 +349,15 @@ static int build_device(swe_ctx* ctx) {
       clist[pm].push_back((int32_t)i);
     }
   }
-  std::vector<uint8_t> flags(ne, 0);
-  std::vector<int32_t> edge_only;
-  for (int64_t e = 0; e < ne; ++e) {
-    bool any = false;
-    for (int k = 0; k < 3; ++k) any |= slot[eedge[(size_t)k * ne + e] >> 1] >= 0;
-    if (pint[e] >= 2) flags[e] = 1;
-    else if (any) { flags[e] = 1; edge_only.push_back((int32_t)e); }
-  }
   // upload topology and geometry
-  double* d_geo; int8_t* d_p; int32_t *d_eedge, *d_eL, *d_eR, *d_einfo, *d_slot; double* d_egeo; uint8_t* d_flags;
+  double* d_geo; int8_t* d_p; int32_t *d_eedge, *d_eL, *d_eR, *d_einfo, *d_slot; double* d_egeo;
   int rc = 0;
   if ((rc = upload(ctx, &d_geo, geo)) || (rc = upload(ctx, &d_p, pint)) || (rc = upload(ctx, &d_eedge, eedge)) ||
       (rc = upload(ctx, &d_eL, eL)) || (rc = upload(ctx, &d_eR, eR)) || (rc = upload(ctx, &d_einfo, einfo)) ||
-      (rc = upload(ctx, &d_egeo, egeo)) || (rc = upload(ctx, &d_flags, flags)) || (rc = upload(ctx, &d_slot, slot)) ||
-      (rc = upload(ctx, &ctx->d_perm, ctx->perm)) || (rc = upload(ctx, &ctx->d_edge_only, edge_only)))
+      (rc = upload(ctx, &d_egeo, egeo)) || (rc = upload(ctx, &d_slot, slot)) ||
+      (rc = upload(ctx, &ctx->d_perm, ctx->perm)))
     return cuda_err(ctx, rc);
-  ctx->n_edge_only = (int64_t)edge_only.size();
-  ctx->dm = DevMesh{ne, nE, nint, d_geo, d_p, d_eedge, d_eL, d_eR, d_einfo, d_egeo, d_flags};
+  ctx->dm = DevMesh{ne, nE, nint, d_geo, d_p, d_eedge, d_eL, d_eR, d_einfo, d_egeo};
   std::memset(&ctx->ce, 0, sizeof ctx->ce);
   ctx->ce.slot = d_slot;
   for (int pm = 2; pm <= 4; ++pm) {
@@ -400,13 +389,15 @@ static int build_device(swe_ctx* ctx) {
   if ((rc = dalloc(ctx, &ctx->fx.Fb, sizeof(double) * 6 * nE)) || (rc = dalloc(ctx, &ctx->fx.lam, sizeof(double) * nE)))
     return cuda_err(ctx, rc);
   for (int pm = 0; pm < 5; ++pm) {
-    ctx->fx.Fh[pm] = ctx->fx.Ff[pm] = nullptr;
+    ctx->fx.Ff[pm] = nullptr;
     if (pm < 2) continue;
     const size_t sz = ts * 3 * npts_for(pm) * ctx->ce.n[pm];
-    if ((rc = dalloc(ctx, &ctx->fx.Fh[pm], sz)) || (rc = dalloc(ctx, &ctx->fx.Ff[pm], sz))) return cuda_err(ctx, rc);
+    if ((rc = dalloc(ctx, &ctx->fx.Ff[pm], sz))) return cuda_err(ctx, rc);
   }
-  if ((rc = dalloc(ctx, &ctx->rc, sizeof(double) * 9 * ne))) return cuda_err(ctx, rc);
-  cudaMemset(ctx->rc, 0, sizeof(double) * 9 * ne);
+  // correction of the base modes from the volume terms: [U,V][q = 2,3][elements with p >= 2]
+  const int64_t nrc = ne - ctx->G.start[2];
+  if ((rc = dalloc(ctx, &ctx->rc, sizeof(double) * 4 * std::max<int64_t>(nrc, 1)))) return cuda_err(ctx, rc);
+  cudaMemset(ctx->rc, 0, sizeof(double) * 4 * std::max<int64_t>(nrc, 1));
   if ((rc = dalloc(ctx, &ctx->d_user, sizeof(double) * 3 * KMAX * ne)) ||
       (rc = dalloc(ctx, &ctx->d_user2, sizeof(double) * 3 * KMAX * ne)))
     return cuda_err(ctx, rc);
@@ -453,19 +444,19 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
     ProfScope ps(ctx, F_EDGEB);
     CK(launch_edge_base(ctx->stream, ctx->dm, ph, stg, in.cb, ctx->vel.ub, ctx->fx));
   }
-  {
+  if (!stg.base_only) {
     ProfScope ps(ctx, F_EDGEC);
     if (ctx->corr32) CK(corr32::launch_edge_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
     else CK(corr64::launch_edge_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
   }
-  {
+  if (!stg.base_only) {
     ProfScope ps(ctx, F_ELEMC);
     if (ctx->corr32)
       CK(corr32::launch_elem_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx,
-                                  ctx->rc, ctx->d_edge_only, ctx->n_edge_only));
+                                  ctx->rc));
     else
       CK(corr64::launch_elem_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx,
-                                  ctx->rc, ctx->d_edge_only, ctx->n_edge_only));
+                                  ctx->rc));
   }
   {
     ProfScope ps(ctx, F_ELEMB);
@@ -527,11 +518,11 @@ static int state_in(swe_ctx* ctx, const double* c, int s) {
   return 0;
 }
 
-static int state_out(swe_ctx* ctx, StateDev st, const void* rc, double* c) {
+static int state_out(swe_ctx* ctx, StateDev st, double* c) {
   const size_t bytes = sizeof(double) * 3 * KMAX * ctx->ne;
   const bool dev = is_device_ptr(c);
   double* dst = dev ? c : ctx->d_user2;
-  CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->corr32, st, (const double*)rc, dst));
+  CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->corr32, st, dst));
   if (!dev) CU(cudaMemcpyAsync(c, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   return 0;
@@ -673,7 +664,7 @@ int swe_set_state(swe_ctx* ctx, const double* c, double t) {
 int swe_get_state(swe_ctx* ctx, double* c_out, double* t_out) {
   if (!ctx || !ctx->have_mesh || !c_out) return fail(ctx, SWE_EINVAL, "swe_get_state: no mesh or NULL");
   LaunchScope ls(ctx);
-  CK(state_out(ctx, ctx->st[0], nullptr, c_out));
+  CK(state_out(ctx, ctx->st[0], c_out));
   if (t_out) {
     CU(cudaMemcpyAsync(t_out, ctx->d_t, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -714,20 +705,31 @@ static int rhs_impl(swe_ctx* ctx, const double* c_in, double* out0, double* out1
   s.rhs_only = 1;
   s.dt = nullptr; s.dt_host = 0.0;
   s.t_dev = ctx->d_t; s.tau = 0.0;
-  s.parts = out1 != nullptr;
   CK(run_stage(ctx, ctx->st[1], ctx->st[1], ctx->st[2], s, false, 0.0));
   int rc = read_status(ctx, false);
   if (rc) return rc;
-  if (!out1) {
-    // the correction of the base modes is already merged into the base output
-    StateDev o = ctx->st[2];
-    CK(state_out(ctx, o, nullptr, out0));
-  } else {
-    StateDev b = ctx->st[2];
-    for (int p = 0; p < 5; ++p) b.ch[p] = nullptr;
-    CK(state_out(ctx, b, nullptr, out0));
-    CK(state_out(ctx, ctx->st[2], ctx->rc, out1));
-  }
+  if (!out1) return state_out(ctx, ctx->st[2], out0);
+  // order separation: the whole rhs, then the base part alone; corr = whole - base
+  const int64_t n = 3 * KMAX * ctx->ne;
+  CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->corr32, ctx->st[2], ctx->d_user));
+  s.base_only = 1;
+  CK(run_stage(ctx, ctx->st[1], ctx->st[1], ctx->st[2], s, false, 0.0));
+  StateDev b = ctx->st[2];
+  for (int p = 0; p < 5; ++p) b.ch[p] = nullptr;  // the base part has no higher modes
+  for (int p = 2; p < 5; ++p)
+    if (ctx->st[2].ch[p]) {
+      const int64_t np = ctx->G.start[p + 1] - ctx->G.start[p];
+      CU(cudaMemsetAsync(ctx->st[2].ch[p], 0, (ctx->corr32 ? 4 : 8) * 3 * (Kof(p) - 3) * np, ctx->stream));
+    }
+  CK(state_out(ctx, ctx->st[2], out0));
+  const bool dev0 = is_device_ptr(out0), dev1 = is_device_ptr(out1);
+  double* base_dev = dev0 ? out0 : ctx->d_user2;
+  if (!dev0) CU(cudaMemcpyAsync(base_dev, out0, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  double* corr_dev = dev1 ? out1 : ctx->d_user2;
+  CK(launch_sub(ctx->stream, ctx->d_user, base_dev, corr_dev, n));
+  if (!dev1) CU(cudaMemcpyAsync(out1, corr_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  (void)b;
   return 0;
 }
 

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+
 namespace swedg {
 
 constexpr int KMAX = 15;
@@ -20,6 +21,22 @@ constexpr int NB = 3;  // base modes: K(1)
 
 __host__ __device__ constexpr int Kof(int p) { return (p + 1) * (p + 2) / 2; }
 __host__ __device__ constexpr int deg_of(int i) { return i < 1 ? 0 : i < 3 ? 1 : i < 6 ? 2 : i < 10 ? 3 : 4; }
+// Compile-time loop: f(IC<i>{}) for i in [B, E), so the index is a constant
+// expression inside f (register arrays stay in registers and `if constexpr`
+// removes the structural zeros of the reference tensors).
+template <int N>
+struct IC {
+  static constexpr int value = N;
+  __host__ __device__ constexpr operator int() const { return N; }
+};
+template <int B, int E, typename F>
+__host__ __device__ __forceinline__ void sfor(F&& f) {
+  if constexpr (B < E) {
+    f(IC<B>{});
+    sfor<B + 1, E>(f);
+  }
+}
+
 // Gauss-Legendre points per edge so that products of three traces of degree
 // <= pmax (degree 3 pmax along the edge) are integrated exactly.
 __host__ __device__ constexpr int npts_for(int pmax) { return pmax <= 1 ? 2 : (3 * pmax + 2) / 2; }
@@ -55,7 +72,7 @@ struct Stage {
   double t;           // stage time for the open-sea boundary (host value) ...
   const double* t_dev;  // ... plus dev_t_scale * (*t_dev) when non-null
   double tau;         // stage time = t_n + tau * dt
-  int parts;          // 1: keep the correction of the base modes out of the base output
+  int base_only;      // 1: the base part alone (no correction kernels, no rc)
 };
 
 struct Phys {
@@ -74,7 +91,6 @@ struct DevMesh {
   const int32_t* eR;      // [nedge] right element or -1
   const int32_t* einfo;   // [nedge] kL | kR << 2 | bc << 4   (bc: 0 interior, 1 land, 2 open sea)
   const double* egeo;     // [5][nedge]: |E|, nx, ny, h_b at gamma(0), h_b at gamma(1) (left element's direction)
-  const uint8_t* flags;   // [ne]: bit 0 = element receives a correction (rc valid)
 };
 
 // Correction edges grouped by pmax = max(p_L, p_R) in 2..4.

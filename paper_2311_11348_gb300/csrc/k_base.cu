@@ -64,33 +64,37 @@ __global__ void k_from_user(DevMesh m, Groups G, const int32_t* perm, const doub
   }
 }
 
-// rc != nullptr: write the correction part of the base modes from rc instead
-// of the base state (used for the split rhs).
 template <typename TC>
-__global__ void k_to_user(DevMesh m, Groups G, const int32_t* perm, StateDev st, const double* __restrict__ rc,
-                          double* __restrict__ cu) {
+__global__ void k_to_user(DevMesh m, Groups G, const int32_t* perm, StateDev st, double* __restrict__ cu) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m.ne) return;
   const int64_t ne = m.ne, u = perm[e];
   const int p = m.p[e], K = Kof(p);
   for (int f = 0; f < 3; ++f) {
-    for (int i = 0; i < 3; ++i) {
-      double v = 0.0;
-      if (i < K) {
-        if (rc) v = (m.flags[e] & 1) ? rc[(f * 3 + i) * ne + e] : 0.0;
-        else v = st.cb[(f * 3 + i) * ne + e];
-      }
-      cu[(f * KMAX + i) * ne + u] = v;
-    }
+    for (int i = 0; i < 3; ++i) cu[(f * KMAX + i) * ne + u] = i < K ? st.cb[(f * 3 + i) * ne + e] : 0.0;
     for (int i = 3; i < KMAX; ++i) {
       double v = 0.0;
-      if (i < K && st.ch[p]) {
+      if (i < K) {
         const int64_t n = G.start[p + 1] - G.start[p], l = e - G.start[p];
         v = (double)chp<TC>(st.ch[p])[(f * (K - 3) + (i - 3)) * n + l];
       }
       cu[(f * KMAX + i) * ne + u] = v;
     }
   }
+}
+
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out,
+                      int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] - b[i];
+}
+
+int launch_sub(cudaStream_t s, const double* a, const double* b, double* out, int64_t n) {
+  if (n == 0) return 0;
+  k_sub<<<nblocks(n, 256), 256, 0, s>>>(a, b, out, n);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
 }
 
 int launch_from_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
@@ -104,12 +108,12 @@ int launch_from_user(cudaStream_t s, const DevMesh& m, const Groups& G, const in
 }
 
 int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
-                   StateDev st, const double* rc, double* cu) {
+                   StateDev st, double* cu) {
   if (m.ne == 0) return 0;
   if (corr_fp32)
-    k_to_user<float><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, st, rc, cu);
+    k_to_user<float><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, st, cu);
   else
-    k_to_user<double><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, st, rc, cu);
+    k_to_user<double><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, st, cu);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -356,7 +360,7 @@ int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Sta
 __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cbS,
                                                    const double* __restrict__ cbN, double* __restrict__ cbO,
                                                    const double* __restrict__ ub, const double* __restrict__ Fb,
-                                                   const double* __restrict__ rc) {
+                                                   const double* __restrict__ rc, int64_t rc_start) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m.ne) return;
   const int64_t ne = m.ne, nE = m.nedge;
@@ -417,11 +421,13 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
       for (int f = 0; f < 3; ++f) r[f][q] += sg * (F[f][0] * b0 + F[f][1] * b1);
     }
   }
-  if (!stg.parts && (m.flags[e] & 1)) {
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) r[f][q] += rc[(f * 3 + q) * ne + e];
+  // correction of the base modes from the volume terms of p >= 2 elements
+  if (!stg.base_only && e >= rc_start) {
+    const int64_t nrc = ne - rc_start, lr = e - rc_start;
+    r[1][1] += rc[0 * nrc + lr];
+    r[1][2] += rc[1 * nrc + lr];
+    r[2][1] += rc[2 * nrc + lr];
+    r[2][2] += rc[3 * nrc + lr];
   }
   const int K = m.p[e] == 0 ? 1 : 3;
   const double dt = stage_dt(stg), a = stg.a, b = stg.b;
@@ -442,10 +448,11 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
 int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
                      int corr_fp32, const double* cbS, const double* cbN, double* cbO, const double* ub,
                      EdgeFlux fx, const void* rc, double cfl) {
-  (void)G; (void)cfl;
+  (void)cfl;
   if (m.ne == 0) return 0;
   (void)corr_fp32;
-  k_elem_base<<<nblocks(m.ne, 128), 128, 0, s>>>(m, ph, stg, cbS, cbN, cbO, ub, fx.Fb, (const double*)rc);
+  k_elem_base<<<nblocks(m.ne, 128), 128, 0, s>>>(m, ph, stg, cbS, cbN, cbO, ub, fx.Fb, (const double*)rc,
+                                                 G.start[2]);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;

@@ -50,7 +50,8 @@ __constant__ T cEB[3][3][KMAX][8];  // per PM-2: phihat_i(gamma_k(s_g)) at npts_
 __constant__ T cEW[3][8];           // weights on [0,1]
 __constant__ T cES[3][8];           // points on [0,1]
 __constant__ T cPhi0;
-__constant__ double cEBd[3][3][3][8];  // the q < 3 rows of cEB in FP64 (conservative base-mode projection)
+__constant__ T cS2b[2];             // points of the two-point base rule on [0,1]
+__constant__ T cRS2b;               // 1 / (s_1 - s_0)
 
 void upload_tables() {
   const RefTables& R = tables();
@@ -74,12 +75,10 @@ void upload_tables() {
         for (int i = 0; i < KMAX; ++i) eb[pm - 2][k][i][gg] = gg < N ? (T)R.EB[N][k][i][gg] : (T)0;
     }
   }
-  static double ebd[3][3][3][8];
-  for (int pm = 2; pm <= 4; ++pm)
-    for (int k = 0; k < 3; ++k)
-      for (int i = 0; i < 3; ++i)
-        for (int gg = 0; gg < 8; ++gg) ebd[pm - 2][k][i][gg] = gg < npts_for(pm) ? R.EB[npts_for(pm)][k][i][gg] : 0.0;
-  cudaMemcpyToSymbol(cEBd, ebd, sizeof ebd);
+  const T s2b[2] = {(T)R.es[2][0], (T)R.es[2][1]};
+  const T rs2b = (T)(1.0 / (R.es[2][1] - R.es[2][0]));
+  cudaMemcpyToSymbol(cS2b, s2b, sizeof s2b);
+  cudaMemcpyToSymbol(cRS2b, &rs2b, sizeof rs2b);
   const T phi0 = (T)R.phi0;
   cudaMemcpyToSymbol(cT, t, sizeof t);
   cudaMemcpyToSymbol(cG, g, sizeof g);
@@ -106,8 +105,10 @@ __device__ __forceinline__ double tide_value(const Phys& ph, double t) {
 template <int K>
 __device__ __forceinline__ void load_modes(T (&out)[K], const double* __restrict__ base, int64_t ne, int64_t e,
                                            const T* __restrict__ high, int64_t n, int64_t l, int f) {
-#pragma unroll
-  for (int i = 0; i < K; ++i) out[i] = i < 3 ? (T)base[(f * 3 + i) * ne + e] : high[(f * (K - 3) + (i - 3)) * n + l];
+  sfor<0, K>([&](auto i) {
+    if constexpr (i < 3) out[i] = (T)base[(f * 3 + i) * ne + e];
+    else out[i] = high[(f * (K - 3) + (i - 3)) * n + l];
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -132,56 +133,45 @@ __global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int6
   const double sv = m.geo[G_S * ne + e];
   if (!((double)H[0] * cPhi0 / sv > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
   T A[NP];
-#pragma unroll
-  for (int j = 0; j < K; ++j)
-#pragma unroll
-    for (int i = 0; i <= j; ++i) {
+  sfor<0, K>([&](auto j) {
+    sfor<0, j + 1>([&](auto i) {
       T acc = 0;
-#pragma unroll
-      for (int nn = 0; nn < KMAX; ++nn)
-        if (nn < ktr(i, j) && tnz(nn, i, j)) acc += H[nn] * cT[nn][pk(i, j)];
+      sfor<0, ktr(i, j)>([&](auto nn) {
+        if constexpr (tnz(nn, i, j)) acc += H[nn] * cT[nn][pk(i, j)];
+      });
       A[pk(i, j)] = acc;
-    }
+    });
+  });
   // LDL^T: A[pk(i,j)] (i > j) <- L_ij;  dg[j] = d_j, rd[j] = 1/d_j
   T dg[K], rd[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
+  sfor<0, K>([&](auto j) {
     T dj = A[pk(j, j)];
-#pragma unroll
-    for (int k = 0; k < j; ++k) dj -= A[pk(j, k)] * A[pk(j, k)] * dg[k];
+    sfor<0, j>([&](auto k) { dj -= A[pk(j, k)] * A[pk(j, k)] * dg[k]; });
     dg[j] = dj;
     rd[j] = (T)1 / dj;
-#pragma unroll
-    for (int i = j + 1; i < K; ++i) {
+    sfor<j + 1, K>([&](auto i) {
       T w = A[pk(i, j)];
-#pragma unroll
-      for (int k = 0; k < j; ++k) w -= A[pk(i, k)] * A[pk(j, k)] * dg[k];
+      sfor<0, j>([&](auto k) { w -= A[pk(i, k)] * A[pk(j, k)] * dg[k]; });
       A[pk(i, j)] = w * rd[j];
-    }
-  }
+    });
+  });
   T x[2][K];
   load_modes<K>(x[0], cb, ne, e, ch, n, l, 1);
   load_modes<K>(x[1], cb, ne, e, ch, n, l, 2);
   const T s = (T)sv;
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-#pragma unroll
-      for (int k = 0; k < i; ++k) x[r][i] -= A[pk(i, k)] * x[r][k];
-#pragma unroll
-    for (int i = 0; i < K; ++i) x[r][i] *= rd[i];
-#pragma unroll
-    for (int i = K - 1; i >= 0; --i)
-#pragma unroll
-      for (int k = i + 1; k < K; ++k) x[r][i] -= A[pk(k, i)] * x[r][k];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
+  sfor<0, 2>([&](auto r) {
+    sfor<0, K>([&](auto i) { sfor<0, i>([&](auto k) { x[r][i] -= A[pk(i, k)] * x[r][k]; }); });
+    sfor<0, K>([&](auto i) { x[r][i] *= rd[i]; });
+    sfor<0, K>([&](auto ii) {
+      constexpr int i = K - 1 - ii;
+      sfor<i + 1, K>([&](auto k) { x[r][i] -= A[pk(k, i)] * x[r][k]; });
+    });
+    sfor<0, K>([&](auto i) {
       const T v = x[r][i] * s;
-      if (i < 3) ub[(r * 3 + i) * ne + e] = (double)v;
+      if constexpr (i < 3) ub[(r * 3 + i) * ne + e] = (double)v;
       else uh[(r * KH + (i - 3)) * n + l] = v;
-    }
-  }
+    });
+  });
 }
 
 template <int K>
@@ -231,36 +221,33 @@ __device__ __forceinline__ void side_traces(const DevMesh& m, const Groups& G, S
     l = e - G.start[p]; n = G.start[p + 1] - G.start[p];
     hc = (const T*)c.ch[p]; hu = (const T*)u.uh[p];
   }
-#pragma unroll
-  for (int g = 0; g < N; ++g) tr[g] = Tr{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll
-  for (int i = 0; i < KM; ++i) {
+  sfor<0, N>([&](auto g) { tr[g] = Tr{0, 0, 0, 0, 0, 0, 0, 0, 0, 0}; });
+  sfor<0, KM>([&](auto i) {
+    if (i >= K) return;
     T cx, cU, cV, cu, cv;
-    if (i < 3) {
+    if constexpr (i < 3) {
       cx = (T)c.cb[(0 * 3 + i) * ne + e]; cU = (T)c.cb[(1 * 3 + i) * ne + e]; cV = (T)c.cb[(2 * 3 + i) * ne + e];
       cu = (T)u.ub[(0 * 3 + i) * ne + e]; cv = (T)u.ub[(1 * 3 + i) * ne + e];
     } else {
-      if (i >= K) break;
       const int Kh = K - 3;
       cx = hc[(0 * Kh + i - 3) * n + l]; cU = hc[(1 * Kh + i - 3) * n + l]; cV = hc[(2 * Kh + i - 3) * n + l];
       cu = hu[(0 * Kh + i - 3) * n + l]; cv = hu[(1 * Kh + i - 3) * n + l];
     }
-#pragma unroll
-    for (int g = 0; g < N; ++g) {
+    sfor<0, N>([&](auto g) {
       const T b = rs * (reverse ? cEB[GI][k][i][N - 1 - g] : cEB[GI][k][i][g]);
-      if (i < 3) {
+      if constexpr (i < 3) {
         tr[g].xb += cx * b; tr[g].Ub += cU * b; tr[g].Vb += cV * b; tr[g].ub += cu * b; tr[g].vb += cv * b;
       } else {
         tr[g].xh += cx * b; tr[g].Uh += cU * b; tr[g].Vh += cV * b; tr[g].uh += cu * b; tr[g].vh += cv * b;
       }
-    }
-  }
+    });
+  });
 }
 
 template <int PM>
 __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __restrict__ list, int64_t nl, Groups G,
                                                    Phys ph, Stage stg, StateDev c, VelDev u,
-                                                   const double* __restrict__ lam_all, T* __restrict__ Fh,
+                                                   const double* __restrict__ lam_all, double* __restrict__ Fb,
                                                    T* __restrict__ Ff) {
   constexpr int N = npts_for(PM), GI = PM - 2;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -278,20 +265,20 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
     side_traces<PM>(m, G, c, u, R, kR, true, b);
   } else if (bc == 2) {
     const T xh = (T)tide_value(ph, stage_time(stg));
-#pragma unroll
-    for (int q = 0; q < N; ++q) { b[q] = a[q]; b[q].xb = xh; b[q].xh = 0; }
+    sfor<0, N>([&](auto q) { b[q] = a[q]; b[q].xb = xh; b[q].xh = 0; });
   } else {
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
+    sfor<0, N>([&](auto q) {
       const Tr& t = a[q];
       const T qb = t.Ub * nx + t.Vb * ny, qh = t.Uh * nx + t.Vh * ny;
       const T wb = t.ub * nx + t.vb * ny, wh = t.uh * nx + t.vh * ny;
       b[q] = Tr{t.xb, t.Ub - 2 * qb * nx, t.Vb - 2 * qb * ny, t.ub - 2 * wb * nx, t.vb - 2 * wb * ny,
                 t.xh, t.Uh - 2 * qh * nx, t.Vh - 2 * qh * ny, t.uh - 2 * wh * nx, t.vh - 2 * wh * ny};
-    }
+    });
   }
-#pragma unroll
-  for (int q = 0; q < N; ++q) {
+  // zeroth and first moments (in the left element's edge parameter s) of the
+  // weighted correction flux: they are all the test modes of degree <= 1 see
+  T M0[3] = {0, 0, 0}, M1[3] = {0, 0, 0};
+  sfor<0, N>([&](auto q) {
     const T hb = hA + cES[GI][q] * (hB - hA);
     const Tr& x = a[q];
     const Tr& y = b[q];
@@ -310,13 +297,23 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
     const T Fh2 = x.Vh * (wxb + wxh) + x.Vb * wxh + y.Vh * (wyb + wyh) + y.Vb * wyh + (pxh + pyh) * ny +
                   lam * (x.Vh - y.Vh);
     const T wgt = (T)0.5 * len * cEW[GI][q];
-    Fh[(0 * N + q) * nl + idx] = wgt * Fh0;
-    Fh[(1 * N + q) * nl + idx] = wgt * Fh1;
-    Fh[(2 * N + q) * nl + idx] = wgt * Fh2;
+    const T h0 = wgt * Fh0, h1 = wgt * Fh1, h2 = wgt * Fh2;
+    M0[0] += h0; M0[1] += h1; M0[2] += h2;
+    M1[0] += h0 * cES[GI][q]; M1[1] += h1 * cES[GI][q]; M1[2] += h2 * cES[GI][q];
     Ff[(0 * N + q) * nl + idx] = wgt * (Fb0 + Fh0);
     Ff[(1 * N + q) * nl + idx] = wgt * (Fb1 + Fh1);
     Ff[(2 * N + q) * nl + idx] = wgt * (Fb2 + Fh2);
-  }
+  });
+  // Degree-<=1 test functions are linear along the edge, so the correction's
+  // share of the base modes is fixed by (M0, M1); the two-point flux with the
+  // same moments is added to the base flux of this edge, which both sides
+  // project in FP64 (one value per edge: conservative in every mode).
+  sfor<0, 3>([&](auto f) {
+    const T f1 = (M1[f] - cS2b[0] * M0[f]) * cRS2b;
+    const T f0 = M0[f] - f1;
+    Fb[(f * 2 + 0) * nE + ed] += (double)f0;
+    Fb[(f * 2 + 1) * nE + ed] += (double)f1;
+  });
 }
 
 template <int PM>
@@ -324,7 +321,7 @@ static int edge_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
                       const Stage& stg, StateDev c, VelDev u, EdgeFlux fx) {
   const int64_t nl = ce.n[PM];
   if (nl == 0) return 0;
-  k_edge_corr<PM><<<nblocks(nl, 128), 128, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.lam, (T*)fx.Fh[PM],
+  k_edge_corr<PM><<<nblocks(nl, 128), 128, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.lam, fx.Fb,
                                                     (T*)fx.Ff[PM]);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
@@ -340,173 +337,150 @@ int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, con
 }
 
 // ---------------------------------------------------------------------------
-// projection of one correction edge onto the test modes of an element:
-//   r_f[q] -= sgn (1/s) sum_g F_g phihat_q(gamma_k(s_g))   (F_h for q < 3, F_f above).
-// The base modes (q < 3) are accumulated in FP64 from the stored flux values,
-// in the same point order on both sides of the edge, so that the mass
-// exchanged through an edge cancels to FP64 round-off in every precision mode.
+// projection of the full flux of one correction edge onto test mode Q >= 3:
+//   r_f -= sgn (1/s) sum_g F_g phihat_Q(gamma_k(s_g))
 // ---------------------------------------------------------------------------
-template <int PM, int KQ>
-__device__ __forceinline__ void project_edge(T (&r)[3][KQ], double (&rb)[3][3], const EdgeFlux& fx,
-                                             const CorrEdges& ce, int64_t sl, int k, bool right, double rs) {
+template <int PM, int Q>
+__device__ __forceinline__ void project_edge(T (&r)[3], const EdgeFlux& fx, const CorrEdges& ce, int64_t sl, int k,
+                                             bool right, T rs) {
   constexpr int N = npts_for(PM), GI = PM - 2;
   const int64_t nl = ce.n[PM];
-  const T* Fh = (const T*)fx.Fh[PM];
   const T* Ff = (const T*)fx.Ff[PM];
-  const double sg = right ? rs : -rs;
-  const T sgt = (T)sg;
-#pragma unroll
-  for (int g = 0; g < N; ++g) {
-    T fh[3], ff[3];
-#pragma unroll
-    for (int f = 0; f < 3; ++f) {
-      fh[f] = Fh[(f * N + g) * nl + sl];
-      if (KQ > 3) ff[f] = Ff[(f * N + g) * nl + sl];
-    }
-#pragma unroll
-    for (int q = 0; q < 3 && q < KQ; ++q) {
-      const double bq = sg * (right ? cEBd[GI][k][q][N - 1 - g] : cEBd[GI][k][q][g]);
-#pragma unroll
-      for (int f = 0; f < 3; ++f) rb[f][q] += (double)fh[f] * bq;
-    }
-#pragma unroll
-    for (int q = 3; q < KQ; ++q) {
-      const T bq = sgt * (right ? cEB[GI][k][q][N - 1 - g] : cEB[GI][k][q][g]);
-#pragma unroll
-      for (int f = 0; f < 3; ++f) r[f][q] += ff[f] * bq;
-    }
-  }
-}
-
-template <int KQ>
-__device__ __forceinline__ void project_all_edges(T (&r)[3][KQ], double (&rb)[3][3], const DevMesh& m,
-                                                  const EdgeFlux& fx, const CorrEdges& ce, int64_t e, double rs) {
-  const int64_t ne = m.ne;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int ee = m.eedge[k * ne + e];
-    const int64_t ed = ee >> 1;
-    const bool right = ee & 1;
-    const int cs = ce.slot[ed];
-    if (cs < 0) continue;
-    const int pm = cs >> 28;
-    const int64_t sl = cs & 0x0fffffff;
-    if (pm == 2) project_edge<2, KQ>(r, rb, fx, ce, sl, k, right, rs);
-    else if (pm == 3) project_edge<3, KQ>(r, rb, fx, ce, sl, k, right, rs);
-    else project_edge<4, KQ>(r, rb, fx, ce, sl, k, right, rs);
-  }
+  const T sg = right ? rs : -rs;
+  sfor<0, N>([&](auto g) {
+    const T bq = sg * (right ? cEB[GI][k][Q][N - 1 - g] : cEB[GI][k][Q][g]);
+    sfor<0, 3>([&](auto f) { r[f] += Ff[(f * N + g) * nl + sl] * bq; });
+  });
 }
 
 // ---------------------------------------------------------------------------
-// correction element update for one order group (K = K(p), p >= 2).
-// Volume terms (Eq. 13 and its products) with J^{-1} folded into the
-// contravariant coefficients  U^_i = (J^{-1} q_i)_xhat ..., u^_j, v^_j:
-//   r_xi[q] += sum_i U^_i D_x[q][i] + V^_i D_y[q][i]
-//   r_U[q]  += (1/s) [ sum_ij U_i (u^_j G_x[q][i][j] + v^_j G_y[q][i][j])
-//                      + g (J^-1_xx P_x[q] + J^-1_yx P_y[q]) ]
-//   r_V[q]  += (1/s) [ sum_ij V_i (...) + g (J^-1_xy P_x[q] + J^-1_yy P_y[q]) ]
-//   P_k[q]   = sum_ij xi_i (xi_j/2 + hb_j) G_k[q][i][j]
-// restricted to the non-base index triples, plus the source g grad h_b xi_q
-// for q >= 3 and the correction edge projections.
+// Volume terms of Eq. (13) for one test mode Q (non-base index triples only),
+// with J^{-1} folded into the contravariant coefficients
+//   Uc_i = (J^-1 q_i)_xhat, Vc_i = (J^-1 q_i)_yhat, uc_j, vc_j likewise, pp_j = xi_j/2 + hb_j:
+//   r_xi = sum_i Uc_i D_x[Q][i] + Vc_i D_y[Q][i]
+//   r_U  = (1/s) [ sum_ij U_i (uc_j G_x[Q][i][j] + vc_j G_y[Q][i][j]) + g (J00 P_x + J10 P_y) ]
+//   r_V  = (1/s) [ sum_ij V_i (...) + g (J01 P_x + J11 P_y) ]
+//   P_k  = sum_ij xi_i pp_j G_k[Q][i][j]
 // ---------------------------------------------------------------------------
-template <int K>
-__global__ void __launch_bounds__(128) k_elem_corr(DevMesh m, CorrEdges ce, int64_t g0, int64_t n, Phys ph,
-                                                   Stage stg, const double* __restrict__ cbS,
-                                                   const T* __restrict__ chS, const T* __restrict__ chN,
-                                                   T* __restrict__ chO, const double* __restrict__ ub,
-                                                   const T* __restrict__ uh, EdgeFlux fx, double* __restrict__ rc) {
-  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (l >= n) return;
-  const int64_t e = g0 + l, ne = m.ne;
-  constexpr int KH = K - 3;
-  const double* geo = m.geo;
-  T xi[K], U[K], V[K], uu[K], vv[K];
-  load_modes<K>(xi, cbS, ne, e, chS, n, l, 0);
-  load_modes<K>(U, cbS, ne, e, chS, n, l, 1);
-  load_modes<K>(V, cbS, ne, e, chS, n, l, 2);
-  load_modes<K>(uu, ub, ne, e, uh, n, l, 0);
-  load_modes<K>(vv, ub, ne, e, uh, n, l, 1);
-  const T rs = (T)geo[G_RS * ne + e];
-  const T J0 = (T)geo[G_JI0 * ne + e], J1 = (T)geo[G_JI1 * ne + e];
-  const T J2 = (T)geo[G_JI2 * ne + e], J3 = (T)geo[G_JI3 * ne + e];
-  const T g = (T)ph.g;
-  T hb[3] = {(T)geo[G_HB0 * ne + e], (T)geo[G_HB1 * ne + e], (T)geo[G_HB2 * ne + e]};
-  T uc[K], vc[K], pp[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    uc[j] = J0 * uu[j] + J1 * vv[j];
-    vc[j] = J2 * uu[j] + J3 * vv[j];
-    pp[j] = (T)0.5 * xi[j] + (j < 3 ? hb[j] : (T)0);
-  }
-  T r[3][K];
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    T am = 0;
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-      if (dnz(q, i) && !base2(q, i)) am += (J0 * U[i] + J1 * V[i]) * cD[0][q][i] + (J2 * U[i] + J3 * V[i]) * cD[1][q][i];
-    T aU = 0, aV = 0, Px = 0, Py = 0;
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      T w = 0, px = 0, py = 0;
-#pragma unroll
+template <int K, int Q, int KL>
+__device__ __forceinline__ void volume_q(T (&r)[3], const T (&xi)[K], const T (&U)[K], const T (&V)[K],
+                                         const T (&uc)[K], const T (&vc)[K], const T (&pp)[K], const T (&Uc)[KL],
+                                         const T (&Vc)[KL], T rs, T J0, T J1, T J2, T J3, T g) {
+  T am = 0;
+  sfor<0, KL>([&](auto i) {
+    if constexpr (dnz(Q, i) && !base2(Q, i)) am += Uc[i] * cD[0][Q][i] + Vc[i] * cD[1][Q][i];
+  });
+  T aU = 0, aV = 0, Px = 0, Py = 0;
+  sfor<0, K>([&](auto i) {
+    constexpr bool any = [] {
       for (int j = 0; j < K; ++j)
-        if (gnz(q, i, j) && !base3(q, i, j)) {
-          const T gx = cG[0][q][pk(i, j)], gy = cG[1][q][pk(i, j)];
+        if (gnz(Q, decltype(i)::value, j) && !base3(Q, decltype(i)::value, j)) return true;
+      return false;
+    }();
+    if constexpr (any) {
+      T w = 0, px = 0, py = 0;
+      sfor<0, K>([&](auto j) {
+        if constexpr (gnz(Q, i, j) && !base3(Q, i, j)) {
+          const T gx = cG[0][Q][pk(i, j)], gy = cG[1][Q][pk(i, j)];
           w += uc[j] * gx + vc[j] * gy;
           px += pp[j] * gx;
           py += pp[j] * gy;
         }
+      });
       aU += U[i] * w; aV += V[i] * w;
       Px += xi[i] * px; Py += xi[i] * py;
     }
-    r[0][q] = am;
-    r[1][q] = rs * (aU + g * (J0 * Px + J2 * Py));
-    r[2][q] = rs * (aV + g * (J1 * Px + J3 * Py));
-    if (q >= 3) {
-      r[1][q] += g * (T)geo[G_DHX * ne + e] * xi[q];
-      r[2][q] += g * (T)geo[G_DHY * ne + e] * xi[q];
-    }
-  }
-  double rb[3][3];
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) rb[f][q] = (double)r[f][q];
-  project_all_edges<K>(r, rb, m, fx, ce, e, geo[G_RS * ne + e]);
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) rc[(f * 3 + q) * ne + e] = rb[f][q];
-  const T dt = (T)stage_dt(stg), a = (T)stg.a, b = (T)stg.b;
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 3; q < K; ++q) {
-      const int64_t ix = (f * KH + (q - 3)) * n + l;
-      const T cs = f == 0 ? xi[q] : f == 1 ? U[q] : V[q];
-      chO[ix] = stg.rhs_only ? r[f][q] : (stg.a != 0.0 ? a * chN[ix] : (T)0) + b * (cs + dt * r[f][q]);
-    }
+  });
+  r[0] = am;
+  r[1] = rs * (aU + g * (J0 * Px + J2 * Py));
+  r[2] = rs * (aV + g * (J1 * Px + J3 * Py));
 }
 
-// p <= 1 elements with at least one correction edge: correction of the base modes only
-__global__ void __launch_bounds__(128) k_elem_corr_lo(DevMesh m, CorrEdges ce, const int32_t* __restrict__ list,
-                                                      int64_t nl, EdgeFlux fx, double* __restrict__ rc) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= nl) return;
-  const int64_t e = list[idx], ne = m.ne;
-  T r[3][3];
-  double rb[3][3];
+// ---------------------------------------------------------------------------
+// correction element update of one order group (K = K(p), p >= 2).
+// Block = 32 elements x (K-1) warps; warp w computes test mode q = w + 1 of
+// its lane's element (q is warp-uniform, so every warp runs one branch of
+// compile-time-specialised code).  q = 1, 2: the correction of the base
+// modes (volume terms with a higher coefficient index) -> rc;  q >= 3: the
+// full volume term, the source g grad h_b xi_q, the projections of the full
+// edge fluxes, and the SSP-RK combination of that higher mode.
+// ---------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges ce, int64_t g0, int64_t n,
+                                                            int64_t rc_off, int64_t nrc, Phys ph, Stage stg,
+                                                            const double* __restrict__ cbS,
+                                                            const T* __restrict__ chS, const T* __restrict__ chN,
+                                                            T* __restrict__ chO, const double* __restrict__ ub,
+                                                            const T* __restrict__ uh, EdgeFlux fx,
+                                                            double* __restrict__ rc) {
+  const int64_t l = blockIdx.x * 32 + threadIdx.x;
+  if (l >= n) return;
+  const int q = threadIdx.y + 1;
+  const int64_t e = g0 + l, ne = m.ne;
+  constexpr int KH = K - 3;
+  constexpr int KL = Kof(deg_of(K - 1) - 1);  // modes of degree < p (the only ones D couples)
+  const double* geo = m.geo;
+  T xi[K], U[K], V[K], uc[K], vc[K], pp[K], Uc[KL], Vc[KL];
+  const T J0 = (T)geo[G_JI0 * ne + e], J1 = (T)geo[G_JI1 * ne + e];
+  const T J2 = (T)geo[G_JI2 * ne + e], J3 = (T)geo[G_JI3 * ne + e];
+  {
+    T uu[K], vv[K];
+    load_modes<K>(xi, cbS, ne, e, chS, n, l, 0);
+    load_modes<K>(U, cbS, ne, e, chS, n, l, 1);
+    load_modes<K>(V, cbS, ne, e, chS, n, l, 2);
+    load_modes<K>(uu, ub, ne, e, uh, n, l, 0);
+    load_modes<K>(vv, ub, ne, e, uh, n, l, 1);
+    sfor<0, K>([&](auto j) {
+      uc[j] = J0 * uu[j] + J1 * vv[j];
+      vc[j] = J2 * uu[j] + J3 * vv[j];
+      if constexpr (j < 3) pp[j] = (T)0.5 * xi[j] + (T)geo[(G_HB0 + j) * ne + e];
+      else pp[j] = (T)0.5 * xi[j];
+      if constexpr (j < KL) {
+        Uc[j] = J0 * U[j] + J1 * V[j];
+        Vc[j] = J2 * U[j] + J3 * V[j];
+      }
+    });
+  }
+  const T rs = (T)geo[G_RS * ne + e];
+  const T g = (T)ph.g;
+  T r[3] = {0, 0, 0};
+  sfor<1, K>([&](auto Q) {
+    if (q == Q) volume_q<K, Q, KL>(r, xi, U, V, uc, vc, pp, Uc, Vc, rs, J0, J1, J2, J3, g);
+  });
+  if (q < 3) {
+    rc[(0 * 2 + (q - 1)) * nrc + rc_off + l] = (double)r[1];
+    rc[(1 * 2 + (q - 1)) * nrc + rc_off + l] = (double)r[2];
+    return;
+  }
+  T xq = 0, Uq = 0, Vq = 0;
+  sfor<3, K>([&](auto Q) {
+    if (q == Q) { xq = xi[Q]; Uq = U[Q]; Vq = V[Q]; }
+  });
+  r[1] += g * (T)geo[G_DHX * ne + e] * xq;
+  r[2] += g * (T)geo[G_DHY * ne + e] * xq;
+  // edges: every edge of a p >= 2 element is a correction edge
 #pragma unroll
-  for (int f = 0; f < 3; ++f)
+  for (int k = 0; k < 3; ++k) {
+    const int ee = m.eedge[k * ne + e];
+    const int cs = ce.slot[ee >> 1];
+    const bool right = ee & 1;
+    const int pm = cs >> 28;
+    const int64_t sl = cs & 0x0fffffff;
+    sfor<3, K>([&](auto Q) {
+      if (q == Q) {
+        if (pm == 2) project_edge<2, Q>(r, fx, ce, sl, k, right, rs);
+        else if (pm == 3) project_edge<3, Q>(r, fx, ce, sl, k, right, rs);
+        else project_edge<4, Q>(r, fx, ce, sl, k, right, rs);
+      }
+    });
+  }
+  const T dt = (T)stage_dt(stg), a = (T)stg.a, b = (T)stg.b;
+  const T cs3[3] = {xq, Uq, Vq};
 #pragma unroll
-    for (int q = 0; q < 3; ++q) { r[f][q] = 0; rb[f][q] = 0.0; }
-  project_all_edges<3>(r, rb, m, fx, ce, e, m.geo[G_RS * ne + e]);
-  const int K = m.p[e] == 0 ? 1 : 3;
-#pragma unroll
-  for (int f = 0; f < 3; ++f)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) rc[(f * 3 + q) * ne + e] = q < K ? rb[f][q] : 0.0;
+  for (int f = 0; f < 3; ++f) {
+    const int64_t ix = (f * KH + (q - 3)) * n + l;
+    chO[ix] = stg.rhs_only ? r[f] : (stg.a != 0.0 ? a * chN[ix] : (T)0) + b * (cs3[f] + dt * r[f]);
+  }
 }
 
 template <int K>
@@ -514,25 +488,21 @@ static int elem_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
                       const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc) {
   const int64_t g0 = G.start[p], n = G.start[p + 1] - g0;
   if (n == 0) return 0;
-  k_elem_corr<K><<<nblocks(n, 128), 128, 0, st>>>(m, ce, g0, n, ph, stg, cS.cb, (const T*)cS.ch[p],
-                                                  (const T*)cN.ch[p], (T*)cO.ch[p], u.ub, (const T*)u.uh[p], fx,
-                                                  (double*)rc);
+  const int64_t nrc = G.start[5] - G.start[2], rc_off = g0 - G.start[2];
+  dim3 blk(32, K - 1);
+  k_elem_corr<K><<<(unsigned)((n + 31) / 32), blk, 0, st>>>(m, ce, g0, n, rc_off, nrc, ph, stg, cS.cb,
+                                                           (const T*)cS.ch[p], (const T*)cN.ch[p], (T*)cO.ch[p],
+                                                           u.ub, (const T*)u.uh[p], fx, (double*)rc);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
 }
 
 int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
-                     const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc,
-                     const int32_t* edge_only, int64_t n_edge_only) {
+                     const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc) {
   int r = elem_group<6>(st, m, ce, G, 2, ph, stg, cS, cN, cO, u, fx, rc);
   if (!r) r = elem_group<10>(st, m, ce, G, 3, ph, stg, cS, cN, cO, u, fx, rc);
   if (!r) r = elem_group<15>(st, m, ce, G, 4, ph, stg, cS, cN, cO, u, fx, rc);
-  if (!r && n_edge_only > 0) {
-    k_elem_corr_lo<<<nblocks(n_edge_only, 128), 128, 0, st>>>(m, ce, edge_only, n_edge_only, fx, (double*)rc);
-    count_launch();
-    SWE_CUDA_OK(cudaGetLastError());
-  }
   return r;
 }
 

@@ -20,10 +20,10 @@ struct Groups {
 };
 
 struct EdgeFlux {
-  double* Fb;        // [3][2][nedge] base flux (weighted by |E| w_g) at the 2-point rule
+  double* Fb;        // [3][2][nedge] base flux (weighted by |E| w_g) at the 2-point rule, plus the
+                     // two-point equivalent of the correction flux's share of the base modes
   double* lam;       // [nedge]
-  void* Fh[5];       // per pmax = 2..4: [3][N][n] correction flux (full - base)
-  void* Ff[5];       // per pmax: [3][N][n] full flux
+  void* Ff[5];       // per pmax = 2..4: [3][N][n] full flux at the npts(pmax) points
 };
 
 // every kernel launch of the library is counted (for launch accounting)
@@ -38,7 +38,8 @@ void upload_base_tables();
 int launch_from_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
                      const double* cu, StateDev st);
 int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
-                   StateDev st, const double* rc, double* cu);
+                   StateDev st, double* cu);
+int launch_sub(cudaStream_t s, const double* a, const double* b, double* out, int64_t n);
 
 int launch_usolve_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
                        double* ub, unsigned* status);
@@ -68,8 +69,7 @@ int launch_energy(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp
   int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,   \
                        const Stage& stg, StateDev c, VelDev u, EdgeFlux fx);                                      \
   int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,   \
-                       const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc,  \
-                       const int32_t* edge_only, int64_t n_edge_only);                                            \
+                       const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc); \
   }
 SWE_CORR_DECL(corr64)
 SWE_CORR_DECL(corr32)
