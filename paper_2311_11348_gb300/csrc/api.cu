@@ -48,7 +48,9 @@ enum { F_USOLVE, F_DT, F_EDGEB, F_EDGEC, F_ELEMC, F_ELEMB, F_OTHER, NFAM };
 
 struct swe_ctx {
   swe_params prm{};
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;   // the caller's (or our) stream: base branch and ordering
+  cudaStream_t stream2 = nullptr;  // the correction branch runs here, concurrently with the base
+  cudaEvent_t ev_fork = nullptr, ev_u1 = nullptr, ev_u2 = nullptr, ev_c = nullptr, ev_dt = nullptr;
   bool own_stream = false;
   int device = 0;
   std::string err;
@@ -292,6 +294,9 @@ static int build_device(swe_ctx* ctx) {
       per += std::hypot(ctx->xy[2 * b] - ctx->xy[2 * a], ctx->xy[2 * b + 1] - ctx->xy[2 * a + 1]);
     }
     G_(G_DIAM) = 2.0 * det / per;
+    G_(G_GDHX) = ctx->prm.g * G_(G_DHX);
+    G_(G_GDHY) = ctx->prm.g * G_(G_DHY);
+    G_(G_SQA) = std::sqrt(0.5 * det);
   }
   // edges
   struct E { int32_t L, R, info; double len, nx, ny, hA, hB; };
@@ -328,12 +333,17 @@ static int build_device(swe_ctx* ctx) {
   ctx->nedge = nE;
   if (nE >= (1ll << 30) || ne >= (1ll << 30)) return fail(ctx, SWE_EINVAL, "mesh too large for 30-bit edge ids");
   std::vector<int32_t> eL(nE), eR(nE), einfo(nE), eedge(3 * ne, -1);
-  std::vector<double> egeo(5 * nE);
+  std::vector<double> egeo((size_t)NEGEO * nE);
   int64_t nint = 0;
   for (int64_t i = 0; i < nE; ++i) {
     eL[i] = ed[i].L; eR[i] = ed[i].R; einfo[i] = ed[i].info;
-    egeo[i] = ed[i].len; egeo[nE + i] = ed[i].nx; egeo[2 * nE + i] = ed[i].ny;
-    egeo[3 * nE + i] = ed[i].hA; egeo[4 * nE + i] = ed[i].hB;
+    auto E_ = [&](int row) -> double& { return egeo[(size_t)row * nE + i]; };
+    E_(E_LEN) = ed[i].len; E_(E_NX) = ed[i].nx; E_(E_NY) = ed[i].ny;
+    E_(E_HA) = ed[i].hA; E_(E_HB) = ed[i].hB;
+    E_(E_HG0) = ed[i].hA + R.es[2][0] * (ed[i].hB - ed[i].hA);
+    E_(E_HG1) = ed[i].hA + R.es[2][1] * (ed[i].hB - ed[i].hA);
+    E_(E_HMID) = 0.5 * (ed[i].hA + ed[i].hB);
+    E_(E_WLEN) = 0.5 * ed[i].len * R.ew[2][0];  // the two weights of the base rule are equal
     if (ed[i].R >= 0) ++nint;
     eedge[(size_t)(ed[i].info & 3) * ne + ed[i].L] = (int32_t)(i << 1);
     if (ed[i].R >= 0) eedge[(size_t)((ed[i].info >> 2) & 3) * ne + ed[i].R] = (int32_t)((i << 1) | 1);
@@ -349,6 +359,17 @@ static int build_device(swe_ctx* ctx) {
       clist[pm].push_back((int32_t)i);
     }
   }
+  // per element of order >= 2: its three correction edges (pmax, side, slot)
+  const int64_t nrc_e = ne - ctx->G.start[2];
+  std::vector<uint32_t> ecs((size_t)3 * std::max<int64_t>(nrc_e, 1), 0u);
+  for (int64_t e = ctx->G.start[2]; e < ne; ++e)
+    for (int k = 0; k < 3; ++k) {
+      const int32_t ee = eedge[(size_t)k * ne + e];
+      const uint32_t cs = (uint32_t)slot[ee >> 1];
+      ecs[(size_t)k * nrc_e + (e - ctx->G.start[2])] = (cs & 0xf0000000u) | ((uint32_t)(ee & 1) << 27) | (cs & 0x07ffffffu);
+    }
+  for (int pm = 2; pm <= 4; ++pm)
+    if ((int64_t)clist[pm].size() >= (1ll << 27)) return fail(ctx, SWE_EINVAL, "too many correction edges");
   // upload topology and geometry
   double* d_geo; int8_t* d_p; int32_t *d_eedge, *d_eL, *d_eR, *d_einfo, *d_slot; double* d_egeo;
   int rc = 0;
@@ -357,9 +378,17 @@ static int build_device(swe_ctx* ctx) {
       (rc = upload(ctx, &d_egeo, egeo)) || (rc = upload(ctx, &d_slot, slot)) ||
       (rc = upload(ctx, &ctx->d_perm, ctx->perm)))
     return cuda_err(ctx, rc);
-  ctx->dm = DevMesh{ne, nE, nint, d_geo, d_p, d_eedge, d_eL, d_eR, d_einfo, d_egeo};
+  std::vector<float> geo32(geo.begin(), geo.end()), egeo32(egeo.begin(), egeo.end());
+  float *d_geo32, *d_egeo32;
+  if ((rc = upload(ctx, &d_geo32, geo32)) || (rc = upload(ctx, &d_egeo32, egeo32))) return cuda_err(ctx, rc);
+  ctx->dm = DevMesh{ne, nE, nint, d_geo, d_p, d_eedge, d_eL, d_eR, d_einfo, d_egeo, d_geo32, d_egeo32};
   std::memset(&ctx->ce, 0, sizeof ctx->ce);
   ctx->ce.slot = d_slot;
+  {
+    uint32_t* d_ecs = nullptr;
+    if ((rc = upload(ctx, &d_ecs, ecs))) return cuda_err(ctx, rc);
+    ctx->ce.ecs = d_ecs;
+  }
   for (int pm = 2; pm <= 4; ++pm) {
     int32_t* d = nullptr;
     if ((rc = upload(ctx, &d, clist[pm]))) return cuda_err(ctx, rc);
@@ -371,6 +400,11 @@ static int build_device(swe_ctx* ctx) {
   for (int s = 0; s < 3; ++s) {
     if ((rc = dalloc(ctx, &ctx->st[s].cb, sizeof(double) * 9 * ne))) return cuda_err(ctx, rc);
     cudaMemset(ctx->st[s].cb, 0, sizeof(double) * 9 * ne);
+    ctx->st[s].cb32 = nullptr;
+    if (ctx->corr32) {
+      if ((rc = dalloc(ctx, &ctx->st[s].cb32, sizeof(float) * 9 * ne))) return cuda_err(ctx, rc);
+      cudaMemset(ctx->st[s].cb32, 0, sizeof(float) * 9 * ne);
+    }
     for (int p = 0; p < 5; ++p) {
       ctx->st[s].ch[p] = nullptr;
       if (p < 2) continue;
@@ -380,14 +414,17 @@ static int build_device(swe_ctx* ctx) {
     }
   }
   if ((rc = dalloc(ctx, &ctx->vel.ub, sizeof(double) * 6 * ne))) return cuda_err(ctx, rc);
+  ctx->vel.ub32 = nullptr;
+  if (ctx->corr32 && (rc = dalloc(ctx, &ctx->vel.ub32, sizeof(float) * 6 * ne))) return cuda_err(ctx, rc);
   for (int p = 0; p < 5; ++p) {
     ctx->vel.uh[p] = nullptr;
     if (p < 2) continue;
     const int64_t n = ctx->G.start[p + 1] - ctx->G.start[p];
     if ((rc = dalloc(ctx, &ctx->vel.uh[p], ts * 2 * (Kof(p) - 3) * n))) return cuda_err(ctx, rc);
   }
-  if ((rc = dalloc(ctx, &ctx->fx.Fb, sizeof(double) * 6 * nE)) || (rc = dalloc(ctx, &ctx->fx.lam, sizeof(double) * nE)))
+  if ((rc = dalloc(ctx, &ctx->fx.Fb, sizeof(double) * 6 * nE)) || (rc = dalloc(ctx, &ctx->fx.Fbc, sizeof(double) * 6 * nE)))
     return cuda_err(ctx, rc);
+  cudaMemset(ctx->fx.Fbc, 0, sizeof(double) * 6 * nE);
   for (int pm = 0; pm < 5; ++pm) {
     ctx->fx.Ff[pm] = nullptr;
     if (pm < 2) continue;
@@ -423,44 +460,77 @@ static Phys phys(const swe_ctx* ctx) {
 static int usolve_all(swe_ctx* ctx, StateDev in) {
   ProfScope ps(ctx, F_USOLVE);
   const Phys ph = phys(ctx);
-  CK(launch_usolve_base(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->d_status));
+  CK(launch_usolve_base(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status));
   if (ctx->corr32) CK(corr32::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
   else CK(corr64::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
   return 0;
 }
 
 // One stage: out = a n + b (in + dt L(in)), or out = L(in) (rhs_only).
+//
+// The base kernels (FP64 pipe bound) run on stream A, the correction kernels
+// on stream B, concurrently on the same SMs -- the GB300 counterpart of the
+// paper's base/correction distribution over CPU and GPU (Sect. 3-5):
+//   A: usolve_base ---------> [dt] edge_base ------------------> elem_base
+//   B: usolve_corr --------->      edge_corr -> elem_corr --------^
+// (each edge kernel needs both u-solves; elem_base needs elem_corr's rc and
+// edge_corr's share of the base-mode flux).  Profiling runs everything on A.
 static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, const Stage& stg, bool cfl_dt,
                      double dt_fixed) {
   const Phys ph = phys(ctx);
-  CK(usolve_all(ctx, in));
+  const bool conc = !ctx->prof;
+  cudaStream_t A = ctx->stream, B = conc ? ctx->stream2 : ctx->stream;
+  if (conc) {
+    CU(cudaEventRecord(ctx->ev_fork, A));
+    CU(cudaStreamWaitEvent(B, ctx->ev_fork, 0));
+  }
+  {
+    ProfScope ps(ctx, F_USOLVE);
+    CK(launch_usolve_base(A, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status));
+    if (ctx->corr32) CK(corr32::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
+    else CK(corr64::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
+  }
+  if (conc) {
+    CU(cudaEventRecord(ctx->ev_u1, A));
+    CU(cudaEventRecord(ctx->ev_u2, B));
+    CU(cudaStreamWaitEvent(A, ctx->ev_u2, 0));
+    CU(cudaStreamWaitEvent(B, ctx->ev_u1, 0));
+  }
   if (cfl_dt) {
     ProfScope ps(ctx, F_DT);
-    CK(launch_reset_min(ctx->stream, ctx->d_dmin));
-    CK(launch_dt(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->d_dmin));
-    CK(launch_advance_time(ctx->stream, nullptr, ctx->d_dmin, ctx->prm.cfl, dt_fixed, ctx->d_dt));
+    CK(launch_reset_min(A, ctx->d_dmin));
+    CK(launch_dt(A, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->d_dmin));
+    CK(launch_advance_time(A, nullptr, ctx->d_dmin, ctx->prm.cfl, dt_fixed, ctx->d_dt));
+    if (conc) {  // the correction branch reads dt (stage time, RK update)
+      CU(cudaEventRecord(ctx->ev_dt, A));
+      CU(cudaStreamWaitEvent(B, ctx->ev_dt, 0));
+    }
   }
   {
     ProfScope ps(ctx, F_EDGEB);
-    CK(launch_edge_base(ctx->stream, ctx->dm, ph, stg, in.cb, ctx->vel.ub, ctx->fx));
+    CK(launch_edge_base(A, ctx->dm, ph, stg, in.cb, ctx->vel.ub, ctx->fx));
   }
   if (!stg.base_only) {
-    ProfScope ps(ctx, F_EDGEC);
-    if (ctx->corr32) CK(corr32::launch_edge_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
-    else CK(corr64::launch_edge_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+    {
+      ProfScope ps(ctx, F_EDGEC);
+      if (ctx->corr32) CK(corr32::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+      else CK(corr64::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+    }
+    {
+      ProfScope ps(ctx, F_ELEMC);
+      if (ctx->corr32)
+        CK(corr32::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc));
+      else
+        CK(corr64::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc));
+    }
   }
-  if (!stg.base_only) {
-    ProfScope ps(ctx, F_ELEMC);
-    if (ctx->corr32)
-      CK(corr32::launch_elem_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx,
-                                  ctx->rc));
-    else
-      CK(corr64::launch_elem_corr(ctx->stream, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx,
-                                  ctx->rc));
+  if (conc) {
+    CU(cudaEventRecord(ctx->ev_c, B));
+    CU(cudaStreamWaitEvent(A, ctx->ev_c, 0));
   }
   {
     ProfScope ps(ctx, F_ELEMB);
-    CK(launch_elem_base(ctx->stream, ctx->dm, ctx->G, ph, stg, ctx->corr32, in.cb, nst.cb, out.cb, ctx->vel.ub,
+    CK(launch_elem_base(A, ctx->dm, ctx->G, ph, stg, ctx->corr32, in.cb, nst.cb, out.cb, out.cb32, ctx->vel.ub,
                         ctx->fx, ctx->rc, ctx->prm.cfl));
   }
   return 0;
@@ -566,6 +636,23 @@ int swe_create(swe_ctx** out, const swe_params* params) {
     if (e != cudaSuccess) { delete ctx; g_create_err = "cudaStreamCreate failed"; return SWE_ECUDA; }
     ctx->own_stream = true;
   }
+  {
+    // the correction branch is the longer one: give its blocks precedence
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    e = cudaStreamCreateWithPriority(&ctx->stream2, cudaStreamNonBlocking, hi);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_u1, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_u2, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_c, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_dt, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    g_create_err = "stream/event creation failed";
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return SWE_ECUDA;
+  }
   upload_base_tables();
   corr64::upload_tables();
   corr32::upload_tables();
@@ -587,6 +674,9 @@ void swe_destroy(swe_ctx* ctx) {
   free_all(ctx);
   for (auto& ev : ctx->evs) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
   for (auto ev : ctx->pool) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : {ctx->ev_fork, ctx->ev_u1, ctx->ev_u2, ctx->ev_c, ctx->ev_dt})
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->stream2) { cudaStreamSynchronize(ctx->stream2); cudaStreamDestroy(ctx->stream2); }
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

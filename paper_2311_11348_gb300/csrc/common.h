@@ -59,7 +59,24 @@ enum {
   G_HB1,
   G_HB2,
   G_DIAM,    // inscribed diameter 4 |Omega_e| / perimeter
+  G_GDHX,    // g grad h_b (source term of Eq. 5)
+  G_GDHY,
+  G_SQA,     // sqrt|Omega_e| = int phi_{e,1}
   NGEO
+};
+
+// rows of the per-edge geometry table
+enum {
+  E_LEN = 0,  // |E|
+  E_NX,       // outward unit normal of the left element
+  E_NY,
+  E_HA,       // h_b at gamma(0) and gamma(1) of the left element's parametrisation
+  E_HB,
+  E_HG0,      // h_b at the two Gauss points of the base rule
+  E_HG1,
+  E_HMID,     // h_b at the midpoint x_E (lambda, Eq. 10)
+  E_WLEN,     // |E| w_g / 2 of the two-point rule (both weights are 1/2)
+  NEGEO
 };
 
 // Per-stage SSP-RK combination  out = a * c^n + b * (c^(s) + dt * rhs),
@@ -90,7 +107,9 @@ struct DevMesh {
   const int32_t* eL;      // [nedge] left element
   const int32_t* eR;      // [nedge] right element or -1
   const int32_t* einfo;   // [nedge] kL | kR << 2 | bc << 4   (bc: 0 interior, 1 land, 2 open sea)
-  const double* egeo;     // [5][nedge]: |E|, nx, ny, h_b at gamma(0), h_b at gamma(1) (left element's direction)
+  const double* egeo;     // [NEGEO][nedge] (rows E_*), in the left element's direction
+  const float* geo32;     // FP32 copies of geo and egeo for the FP32 correction kernels
+  const float* egeo32;
 };
 
 // Correction edges grouped by pmax = max(p_L, p_R) in 2..4.
@@ -98,6 +117,7 @@ struct CorrEdges {
   int64_t n[5];           // per pmax
   const int32_t* list[5]; // edge ids
   const int32_t* slot;    // [nedge]: (pmax << 28) | slot within group, or -1
+  const uint32_t* ecs;    // [3][elements with p >= 2]: (pmax << 28) | (side << 27) | slot of each local edge
 };
 
 }  // namespace swedg

@@ -55,7 +55,11 @@ __global__ void k_from_user(DevMesh m, Groups G, const int32_t* perm, const doub
   const int64_t ne = m.ne, u = perm[e];
   const int p = m.p[e], K = Kof(p);
   for (int f = 0; f < 3; ++f)
-    for (int i = 0; i < 3; ++i) st.cb[(f * 3 + i) * ne + e] = i < K ? cu[(f * KMAX + i) * ne + u] : 0.0;
+    for (int i = 0; i < 3; ++i) {
+      const double v = i < K ? cu[(f * KMAX + i) * ne + u] : 0.0;
+      st.cb[(f * 3 + i) * ne + e] = v;
+      if (st.cb32) st.cb32[(f * 3 + i) * ne + e] = (float)v;
+    }
   if (p >= 2) {
     const int64_t n = G.start[p + 1] - G.start[p], l = e - G.start[p];
     TC* h = chp<TC>(st.ch[p]);
@@ -125,7 +129,8 @@ int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int3
 // The 3 x 3 symmetric system is solved with its adjugate (one division).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_usolve_base(DevMesh m, int64_t n_end, Phys ph, const double* __restrict__ cb,
-                                                     double* __restrict__ ub, unsigned* status) {
+                                                     double* __restrict__ ub, float* __restrict__ ub32,
+                                                     unsigned* status) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n_end) return;
   const int64_t ne = m.ne;
@@ -135,8 +140,12 @@ __global__ void __launch_bounds__(256) k_usolve_base(DevMesh m, int64_t n_end, P
   if (!(H0 * cPhi0 * rs > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
   if (m.p[e] == 0) {
     const double r = 1.0 / (H0 * cT1[0][0][0] * rs);
-    ub[0 * ne + e] = U0 * r; ub[1 * ne + e] = 0.0; ub[2 * ne + e] = 0.0;
-    ub[3 * ne + e] = V0 * r; ub[4 * ne + e] = 0.0; ub[5 * ne + e] = 0.0;
+    const double v[6] = {U0 * r, 0.0, 0.0, V0 * r, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      ub[i * ne + e] = v[i];
+      if (ub32) ub32[i * ne + e] = (float)v[i];
+    }
     return;
   }
   const double H1 = cb[1 * ne + e] + m.geo[G_HB1 * ne + e];
@@ -155,19 +164,21 @@ __global__ void __launch_bounds__(256) k_usolve_base(DevMesh m, int64_t n_end, P
   const double C11 = a * h - c * c, C12 = b * c - a * f, C22 = a * d - b * b;
   const double det = a * C00 + b * C01 + c * C02;
   const double r = 1.0 / (det * rs);
-  ub[0 * ne + e] = (C00 * U0 + C01 * U1 + C02 * U2) * r;
-  ub[1 * ne + e] = (C01 * U0 + C11 * U1 + C12 * U2) * r;
-  ub[2 * ne + e] = (C02 * U0 + C12 * U1 + C22 * U2) * r;
-  ub[3 * ne + e] = (C00 * V0 + C01 * V1 + C02 * V2) * r;
-  ub[4 * ne + e] = (C01 * V0 + C11 * V1 + C12 * V2) * r;
-  ub[5 * ne + e] = (C02 * V0 + C12 * V1 + C22 * V2) * r;
+  const double v[6] = {(C00 * U0 + C01 * U1 + C02 * U2) * r, (C01 * U0 + C11 * U1 + C12 * U2) * r,
+                       (C02 * U0 + C12 * U1 + C22 * U2) * r, (C00 * V0 + C01 * V1 + C02 * V2) * r,
+                       (C01 * V0 + C11 * V1 + C12 * V2) * r, (C02 * V0 + C12 * V1 + C22 * V2) * r};
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    ub[i * ne + e] = v[i];
+    if (ub32) ub32[i * ne + e] = (float)v[i];
+  }
 }
 
 int launch_usolve_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
-                       double* ub, unsigned* status) {
+                       double* ub, float* ub32, unsigned* status) {
   const int64_t n = G.start[2];
   if (n == 0) return 0;
-  k_usolve_base<<<nblocks(n, 256), 256, 0, s>>>(m, n, ph, cb, ub, status);
+  k_usolve_base<<<nblocks(n, 256), 256, 0, s>>>(m, n, ph, cb, ub, ub32, status);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -253,96 +264,92 @@ __device__ __forceinline__ double tide_value(const Phys& ph, double t) {
 // with lambda from the element means (Eq. 10, Sect. 3), stored pre-weighted
 // by |E| w_g at the points in the left element's direction.
 // ---------------------------------------------------------------------------
-struct Side5 { double xi, U, V, u, v; };
+// Traces of xi, U, V and w = u.n (P1 parts) of one side at the two Gauss
+// points.  Mode 1 is the constant sqrt 2 on every edge, so its trace is shared.
+struct Tr2 { double xi[2], U[2], V[2], w[2]; double xi0, w0; };
+
+__device__ __forceinline__ void p1_traces(const double* __restrict__ cb, const double* __restrict__ ub, int64_t ne,
+                                          int64_t e, int k, bool reverse, double rs, double nx, double ny, Tr2& t) {
+  const int g0 = reverse ? 1 : 0, g1 = reverse ? 0 : 1;
+  const double m0 = cPhi0 * rs;
+  const double b10 = rs * cB2[k][1][g0], b20 = rs * cB2[k][2][g0];
+  const double b11 = rs * cB2[k][1][g1], b21 = rs * cB2[k][2][g1];
+  double c[3][3], w[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) c[f][i] = cb[(f * 3 + i) * ne + e];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) w[i] = ub[i * ne + e] * nx + ub[(3 + i) * ne + e] * ny;
+  double* out[3] = {t.xi, t.U, t.V};
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    const double a0 = c[f][0] * m0;
+    out[f][0] = a0 + c[f][1] * b10 + c[f][2] * b20;
+    out[f][1] = a0 + c[f][1] * b11 + c[f][2] * b21;
+    if (f == 0) t.xi0 = a0;
+  }
+  t.w0 = w[0] * m0;
+  t.w[0] = t.w0 + w[1] * b10 + w[2] * b20;
+  t.w[1] = t.w0 + w[1] * b11 + w[2] * b21;
+}
 
 __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cb,
-                                                   const double* __restrict__ ub, double* __restrict__ Fb,
-                                                   double* __restrict__ lamo) {
+                                                   const double* __restrict__ ub, double* __restrict__ Fb) {
   const int64_t ed = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (ed >= m.nedge) return;
   const int64_t ne = m.ne, nE = m.nedge;
   const int L = m.eL[ed], R = m.eR[ed], info = m.einfo[ed];
   const int kL = info & 3, kR = (info >> 2) & 3, bc = info >> 4;
-  const double len = m.egeo[ed], nx = m.egeo[nE + ed], ny = m.egeo[2 * nE + ed];
-  const double hA = m.egeo[3 * nE + ed], hB = m.egeo[4 * nE + ed];
-  const double rsL = m.geo[G_RS * ne + L];
-  double cL[5][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    cL[0][i] = cb[(0 * 3 + i) * ne + L]; cL[1][i] = cb[(1 * 3 + i) * ne + L]; cL[2][i] = cb[(2 * 3 + i) * ne + L];
-    cL[3][i] = ub[(0 * 3 + i) * ne + L]; cL[4][i] = ub[(1 * 3 + i) * ne + L];
-  }
-  Side5 tl[2], tr[2];
-#pragma unroll
-  for (int g = 0; g < 2; ++g) {
-    double t[5];
-#pragma unroll
-    for (int f = 0; f < 5; ++f) t[f] = rsL * (cL[f][0] * cB2[kL][0][g] + cL[f][1] * cB2[kL][1][g] + cL[f][2] * cB2[kL][2][g]);
-    tl[g] = Side5{t[0], t[1], t[2], t[3], t[4]};
-  }
-  const double hmid = 0.5 * (hA + hB);
-  const double mL = cPhi0 * rsL;
-  const double unL = (cL[3][0] * nx + cL[4][0] * ny) * mL;
-  const double HL = cL[0][0] * mL + hmid;
+  const double nx = m.egeo[E_NX * nE + ed], ny = m.egeo[E_NY * nE + ed];
+  const double hmid = m.egeo[E_HMID * nE + ed];
+  Tr2 a, b;
+  p1_traces(cb, ub, ne, L, kL, false, m.geo[G_RS * ne + L], nx, ny, a);
+  const double unL = a.w0, HL = a.xi0 + hmid;
   double unR, HR;
   if (R >= 0) {
-    const double rsR = m.geo[G_RS * ne + R];
-    double cR[5][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      cR[0][i] = cb[(0 * 3 + i) * ne + R]; cR[1][i] = cb[(1 * 3 + i) * ne + R]; cR[2][i] = cb[(2 * 3 + i) * ne + R];
-      cR[3][i] = ub[(0 * 3 + i) * ne + R]; cR[4][i] = ub[(1 * 3 + i) * ne + R];
-    }
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {
-      const int gr = 1 - g;  // the right element runs the edge backwards
-      double t[5];
-#pragma unroll
-      for (int f = 0; f < 5; ++f)
-        t[f] = rsR * (cR[f][0] * cB2[kR][0][gr] + cR[f][1] * cB2[kR][1][gr] + cR[f][2] * cB2[kR][2][gr]);
-      tr[g] = Side5{t[0], t[1], t[2], t[3], t[4]};
-    }
-    const double mR = cPhi0 * rsR;
-    unR = (cR[3][0] * nx + cR[4][0] * ny) * mR;
-    HR = cR[0][0] * mR + hmid;
+    p1_traces(cb, ub, ne, R, kR, true, m.geo[G_RS * ne + R], nx, ny, b);
+    unR = b.w0;
+    HR = b.xi0 + hmid;
   } else if (bc == 2) {
     const double xh = tide_value(ph, stage_time(stg));
-#pragma unroll
-    for (int g = 0; g < 2; ++g) tr[g] = Side5{xh, tl[g].U, tl[g].V, tl[g].u, tl[g].v};
+    b = a;
+    b.xi[0] = xh; b.xi[1] = xh;
     unR = unL;
     HR = xh + hmid;
   } else {
+    // mirror state: q+ = q - 2 (q.n) n, (u.n)+ = -(u.n), xi+ = xi
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
-      const double qn = tl[g].U * nx + tl[g].V * ny, wn = tl[g].u * nx + tl[g].v * ny;
-      tr[g] = Side5{tl[g].xi, tl[g].U - 2.0 * qn * nx, tl[g].V - 2.0 * qn * ny, tl[g].u - 2.0 * wn * nx,
-                    tl[g].v - 2.0 * wn * ny};
+      const double qn2 = -2.0 * (a.U[g] * nx + a.V[g] * ny);
+      b.xi[g] = a.xi[g];
+      b.U[g] = a.U[g] + qn2 * nx;
+      b.V[g] = a.V[g] + qn2 * ny;
+      b.w[g] = -a.w[g];
     }
     unR = -unL;
     HR = HL;
   }
+  // lambda of Eq. (10) from the means (Sect. 3); max sqrt = sqrt max
   const double lam = fmax(fabs(unL), fabs(unR)) + sqrt(ph.g * fmax(HL, HR));
-  lamo[ed] = lam;
+  const double wl = m.egeo[E_WLEN * nE + ed];
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
-    const double hb = hA + cS2[g] * (hB - hA);
-    const Side5 a = tl[g], b = tr[g];
-    const double wa = a.u * nx + a.v * ny, wb = b.u * nx + b.v * ny;
-    const double pa = ph.g * a.xi * (0.5 * a.xi + hb), pb = ph.g * b.xi * (0.5 * b.xi + hb);
-    const double F0 = (a.U + b.U) * nx + (a.V + b.V) * ny + lam * (a.xi - b.xi);
-    const double F1 = a.U * wa + b.U * wb + (pa + pb) * nx + lam * (a.U - b.U);
-    const double F2 = a.V * wa + b.V * wb + (pa + pb) * ny + lam * (a.V - b.V);
-    const double wgt = 0.5 * len * cW2[g];
-    Fb[(0 * 2 + g) * nE + ed] = wgt * F0;
-    Fb[(1 * 2 + g) * nE + ed] = wgt * F1;
-    Fb[(2 * 2 + g) * nE + ed] = wgt * F2;
+    const double hb = m.egeo[(E_HG0 + g) * nE + ed];
+    const double P = ph.g * (a.xi[g] * (0.5 * a.xi[g] + hb) + b.xi[g] * (0.5 * b.xi[g] + hb));
+    const double F0 = (a.U[g] + b.U[g]) * nx + (a.V[g] + b.V[g]) * ny + lam * (a.xi[g] - b.xi[g]);
+    const double F1 = a.U[g] * a.w[g] + b.U[g] * b.w[g] + P * nx + lam * (a.U[g] - b.U[g]);
+    const double F2 = a.V[g] * a.w[g] + b.V[g] * b.w[g] + P * ny + lam * (a.V[g] - b.V[g]);
+    Fb[(0 * 2 + g) * nE + ed] = wl * F0;
+    Fb[(1 * 2 + g) * nE + ed] = wl * F1;
+    Fb[(2 * 2 + g) * nE + ed] = wl * F2;
   }
 }
 
 int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Stage& stg, const double* cb,
                      const double* ub, EdgeFlux fx) {
   if (m.nedge == 0) return 0;
-  k_edge_base<<<nblocks(m.nedge, 128), 128, 0, s>>>(m, ph, stg, cb, ub, fx.Fb, fx.lam);
+  k_edge_base<<<nblocks(m.nedge, 128), 128, 0, s>>>(m, ph, stg, cb, ub, fx.Fb);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -359,7 +366,8 @@ int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Sta
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cbS,
                                                    const double* __restrict__ cbN, double* __restrict__ cbO,
-                                                   const double* __restrict__ ub, const double* __restrict__ Fb,
+                                                   float* __restrict__ cbO32, const double* __restrict__ ub,
+                                                   const double* __restrict__ Fb, const double* __restrict__ Fbc,
                                                    const double* __restrict__ rc, int64_t rc_start) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m.ne) return;
@@ -374,9 +382,8 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
   for (int f = 0; f < 2; ++f)
 #pragma unroll
     for (int i = 0; i < 3; ++i) u[f][i] = ub[(f * 3 + i) * ne + e];
-  const double rs = geo[G_RS * ne + e], sv = geo[G_S * ne + e];
+  const double rs = geo[G_RS * ne + e], sqa = geo[G_SQA * ne + e];
   const double hb[3] = {geo[G_HB0 * ne + e], geo[G_HB1 * ne + e], geo[G_HB2 * ne + e]};
-  const double g = ph.g;
   double r[3][3];
   // volume terms
   double Axx = 0.0, Axy = 0.0, Ayx = 0.0, Ayy = 0.0, P = 0.0;
@@ -386,19 +393,20 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
     Ayx += c[2][i] * u[0][i]; Ayy += c[2][i] * u[1][i];
     P += c[0][i] * (0.5 * c[0][i] + hb[i]);
   }
-  P *= g;
-  const double m0 = sv / cPhi0;  // int phi_{e,1} = sqrt|Omega_e|
-  const double gq[2][2] = {{geo[G_GQ1X * ne + e], geo[G_GQ1Y * ne + e]}, {geo[G_GQ2X * ne + e], geo[G_GQ2Y * ne + e]}};
-  const double dhx = geo[G_DHX * ne + e], dhy = geo[G_DHY * ne + e];
+  P *= ph.g;
+  Axx += P;
+  Ayy += P;
+  const double gdx = geo[G_GDHX * ne + e], gdy = geo[G_GDHY * ne + e];
+  const double U0s = c[1][0] * sqa, V0s = c[2][0] * sqa;
   r[0][0] = 0.0;
-  r[1][0] = g * dhx * c[0][0];
-  r[2][0] = g * dhy * c[0][0];
+  r[1][0] = gdx * c[0][0];
+  r[2][0] = gdy * c[0][0];
 #pragma unroll
   for (int q = 1; q < 3; ++q) {
-    const double gx = gq[q - 1][0], gy = gq[q - 1][1];
-    r[0][q] = (gx * c[1][0] + gy * c[2][0]) * m0;
-    r[1][q] = gx * (Axx + P) + gy * Axy + g * dhx * c[0][q];
-    r[2][q] = gx * Ayx + gy * (Ayy + P) + g * dhy * c[0][q];
+    const double gx = geo[(q == 1 ? G_GQ1X : G_GQ2X) * ne + e], gy = geo[(q == 1 ? G_GQ1Y : G_GQ2Y) * ne + e];
+    r[0][q] = gx * U0s + gy * V0s;
+    r[1][q] = gx * Axx + gy * Axy + gdx * c[0][q];
+    r[2][q] = gx * Ayx + gy * Ayy + gdy * c[0][q];
   }
   // edge terms
 #pragma unroll
@@ -411,14 +419,21 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
     for (int f = 0; f < 3; ++f) {
       F[f][0] = Fb[(f * 2 + 0) * nE + ed];
       F[f][1] = Fb[(f * 2 + 1) * nE + ed];
+      if (!stg.base_only) {
+        F[f][0] += Fbc[(f * 2 + 0) * nE + ed];
+        F[f][1] += Fbc[(f * 2 + 1) * nE + ed];
+      }
     }
     const double sg = right ? rs : -rs;
+    const double s0 = sg * cPhi0;  // mode 1 is the constant sqrt 2
+    const int g0 = right ? 1 : 0, g1 = right ? 0 : 1;
+    const double b10 = sg * cB2[k][1][g0], b11 = sg * cB2[k][1][g1];
+    const double b20 = sg * cB2[k][2][g0], b21 = sg * cB2[k][2][g1];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const double b0 = right ? cB2[k][q][1] : cB2[k][q][0];
-      const double b1 = right ? cB2[k][q][0] : cB2[k][q][1];
-#pragma unroll
-      for (int f = 0; f < 3; ++f) r[f][q] += sg * (F[f][0] * b0 + F[f][1] * b1);
+    for (int f = 0; f < 3; ++f) {
+      r[f][0] += s0 * (F[f][0] + F[f][1]);
+      r[f][1] += F[f][0] * b10 + F[f][1] * b11;
+      r[f][2] += F[f][0] * b20 + F[f][1] * b21;
     }
   }
   // correction of the base modes from the volume terms of p >= 2 elements
@@ -430,7 +445,7 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
     r[2][2] += rc[3 * nrc + lr];
   }
   const int K = m.p[e] == 0 ? 1 : 3;
-  const double dt = stage_dt(stg), a = stg.a, b = stg.b;
+  const double dt = stage_dt(stg), a = stg.a, bb = stg.b;
 #pragma unroll
   for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -439,20 +454,21 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
       double v = 0.0;
       if (q < K) {
         if (stg.rhs_only) v = r[f][q];
-        else v = (a != 0.0 ? a * cbN[ix] : 0.0) + b * (c[f][q] + dt * r[f][q]);
+        else v = (a != 0.0 ? a * cbN[ix] : 0.0) + bb * (c[f][q] + dt * r[f][q]);
       }
       cbO[ix] = v;
+      if (cbO32) cbO32[ix] = (float)v;
     }
 }
 
 int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
-                     int corr_fp32, const double* cbS, const double* cbN, double* cbO, const double* ub,
+                     int corr_fp32, const double* cbS, const double* cbN, double* cbO, float* cbO32, const double* ub,
                      EdgeFlux fx, const void* rc, double cfl) {
   (void)cfl;
   if (m.ne == 0) return 0;
   (void)corr_fp32;
-  k_elem_base<<<nblocks(m.ne, 128), 128, 0, s>>>(m, ph, stg, cbS, cbN, cbO, ub, fx.Fb, (const double*)rc,
-                                                 G.start[2]);
+  k_elem_base<<<nblocks(m.ne, 128), 128, 0, s>>>(m, ph, stg, cbS, cbN, cbO, cbO32, ub, fx.Fb, fx.Fbc,
+                                                 (const double*)rc, G.start[2]);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -513,7 +529,7 @@ __global__ void k_sum_partials(const double* partial, int n, double* out) {
 __global__ void k_mass(DevMesh m, const double* __restrict__ cb, double* partial) {
   double v = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m.ne; e += (int64_t)gridDim.x * blockDim.x)
-    v += m.geo[G_S * m.ne + e] / cPhi0 * cb[e];
+    v += m.geo[G_SQA * m.ne + e] * cb[e];
   block_sum_store(v, partial);
 }
 

@@ -25,6 +25,23 @@ namespace swedg {
 namespace CORR_NS {
 
 using T = CORR_T;
+constexpr bool kF32 = sizeof(T) == 4;
+
+// The FP32 correction reads FP32 copies of the base state, velocity and
+// geometry (written once per element by the base kernels), so it runs no
+// conversions on the FP64 pipe.
+__device__ __forceinline__ const T* base_c(const StateDev& s) {
+  if constexpr (kF32) return (const T*)s.cb32; else return (const T*)s.cb;
+}
+__device__ __forceinline__ const T* base_u(const VelDev& u) {
+  if constexpr (kF32) return (const T*)u.ub32; else return (const T*)u.ub;
+}
+__device__ __forceinline__ const T* geo_t(const DevMesh& m) {
+  if constexpr (kF32) return (const T*)m.geo32; else return (const T*)m.geo;
+}
+__device__ __forceinline__ const T* egeo_t(const DevMesh& m) {
+  if constexpr (kF32) return (const T*)m.egeo32; else return (const T*)m.egeo;
+}
 
 __host__ __device__ constexpr int pk(int i, int j) { return i <= j ? j * (j + 1) / 2 + i : i * (i + 1) / 2 + j; }
 __host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
@@ -103,10 +120,10 @@ __device__ __forceinline__ double tide_value(const Phys& ph, double t) {
 // Load all K modes of field f (base rows from the FP64 base state, higher rows
 // from the group's correction array).
 template <int K>
-__device__ __forceinline__ void load_modes(T (&out)[K], const double* __restrict__ base, int64_t ne, int64_t e,
+__device__ __forceinline__ void load_modes(T (&out)[K], const T* __restrict__ base, int64_t ne, int64_t e,
                                            const T* __restrict__ high, int64_t n, int64_t l, int f) {
   sfor<0, K>([&](auto i) {
-    if constexpr (i < 3) out[i] = (T)base[(f * 3 + i) * ne + e];
+    if constexpr (i < 3) out[i] = base[(f * 3 + i) * ne + e];
     else out[i] = high[(f * (K - 3) + (i - 3)) * n + l];
   });
 }
@@ -117,21 +134,25 @@ __device__ __forceinline__ void load_modes(T (&out)[K], const double* __restrict
 // Solved as S u = s U with S = s M by an unpivoted LDL^T factorisation.
 // ---------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int64_t n, Phys ph,
-                                                     const double* __restrict__ cb, const T* __restrict__ ch,
-                                                     double* __restrict__ ub, T* __restrict__ uh,
+__global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int64_t n, Phys ph, StateDev c,
+                                                     const T* __restrict__ ch, double* __restrict__ ub,
+                                                     float* __restrict__ ub32, T* __restrict__ uh,
                                                      unsigned* status) {
   const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (l >= n) return;
   const int64_t e = g0 + l, ne = m.ne;
   constexpr int KH = K - 3, NP = K * (K + 1) / 2;
+  const T* cb = base_c(c);
+  const T* geo = geo_t(m);
   T H[K];
   load_modes<K>(H, cb, ne, e, ch, n, l, 0);
-  H[0] += (T)m.geo[G_HB0 * ne + e];
-  H[1] += (T)m.geo[G_HB1 * ne + e];
-  H[2] += (T)m.geo[G_HB2 * ne + e];
-  const double sv = m.geo[G_S * ne + e];
-  if (!((double)H[0] * cPhi0 / sv > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
+  H[0] += geo[G_HB0 * ne + e];
+  H[1] += geo[G_HB1 * ne + e];
+  H[2] += geo[G_HB2 * ne + e];
+  // depth check on the FP64 mean (base modes are FP64 in every mode)
+  const double H0d = c.cb[e] + m.geo[G_HB0 * ne + e];
+  if (!(H0d * m.geo[G_RS * ne + e] * 1.4142135623730951 > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
+  const T sv = geo[G_S * ne + e];
   T A[NP];
   sfor<0, K>([&](auto j) {
     sfor<0, j + 1>([&](auto i) {
@@ -158,7 +179,7 @@ __global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int6
   T x[2][K];
   load_modes<K>(x[0], cb, ne, e, ch, n, l, 1);
   load_modes<K>(x[1], cb, ne, e, ch, n, l, 2);
-  const T s = (T)sv;
+  const T s = sv;
   sfor<0, 2>([&](auto r) {
     sfor<0, K>([&](auto i) { sfor<0, i>([&](auto k) { x[r][i] -= A[pk(i, k)] * x[r][k]; }); });
     sfor<0, K>([&](auto i) { x[r][i] *= rd[i]; });
@@ -168,8 +189,12 @@ __global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int6
     });
     sfor<0, K>([&](auto i) {
       const T v = x[r][i] * s;
-      if constexpr (i < 3) ub[(r * 3 + i) * ne + e] = (double)v;
-      else uh[(r * KH + (i - 3)) * n + l] = v;
+      if constexpr (i < 3) {
+        ub[(r * 3 + i) * ne + e] = (double)v;
+        if constexpr (kF32) ub32[(r * 3 + i) * ne + e] = v;
+      } else {
+        uh[(r * KH + (i - 3)) * n + l] = v;
+      }
     });
   });
 }
@@ -179,8 +204,8 @@ static int usolve_group(cudaStream_t st, const DevMesh& m, const Groups& G, int 
                         VelDev u, unsigned* status) {
   const int64_t g0 = G.start[p], n = G.start[p + 1] - g0;
   if (n == 0) return 0;
-  k_usolve_corr<K><<<nblocks(n, 128), 128, 0, st>>>(m, g0, n, ph, c.cb, (const T*)c.ch[p], u.ub, (T*)u.uh[p],
-                                                    status);
+  k_usolve_corr<K><<<nblocks(n, 128), 128, 0, st>>>(m, g0, n, ph, c, (const T*)c.ch[p], u.ub, u.ub32,
+                                                    (T*)u.uh[p], status);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -213,7 +238,9 @@ __device__ __forceinline__ void side_traces(const DevMesh& m, const Groups& G, S
   constexpr int N = npts_for(PM), KM = Kof(PM), GI = PM - 2;
   const int64_t ne = m.ne;
   const int p = m.p[e], K = Kof(p);
-  const T rs = (T)m.geo[G_RS * ne + e];
+  const T rs = geo_t(m)[G_RS * ne + e];
+  const T* cbt = base_c(c);
+  const T* ubt = base_u(u);
   int64_t l = 0, n = 1;
   const T* hc = nullptr;
   const T* hu = nullptr;
@@ -226,8 +253,8 @@ __device__ __forceinline__ void side_traces(const DevMesh& m, const Groups& G, S
     if (i >= K) return;
     T cx, cU, cV, cu, cv;
     if constexpr (i < 3) {
-      cx = (T)c.cb[(0 * 3 + i) * ne + e]; cU = (T)c.cb[(1 * 3 + i) * ne + e]; cV = (T)c.cb[(2 * 3 + i) * ne + e];
-      cu = (T)u.ub[(0 * 3 + i) * ne + e]; cv = (T)u.ub[(1 * 3 + i) * ne + e];
+      cx = cbt[(0 * 3 + i) * ne + e]; cU = cbt[(1 * 3 + i) * ne + e]; cV = cbt[(2 * 3 + i) * ne + e];
+      cu = ubt[(0 * 3 + i) * ne + e]; cv = ubt[(1 * 3 + i) * ne + e];
     } else {
       const int Kh = K - 3;
       cx = hc[(0 * Kh + i - 3) * n + l]; cU = hc[(1 * Kh + i - 3) * n + l]; cV = hc[(2 * Kh + i - 3) * n + l];
@@ -247,26 +274,42 @@ __device__ __forceinline__ void side_traces(const DevMesh& m, const Groups& G, S
 template <int PM>
 __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __restrict__ list, int64_t nl, Groups G,
                                                    Phys ph, Stage stg, StateDev c, VelDev u,
-                                                   const double* __restrict__ lam_all, double* __restrict__ Fb,
-                                                   T* __restrict__ Ff) {
+                                                   double* __restrict__ Fbc, T* __restrict__ Ff) {
   constexpr int N = npts_for(PM), GI = PM - 2;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= nl) return;
   const int64_t ed = list[idx], nE = m.nedge;
   const int L = m.eL[ed], R = m.eR[ed], info = m.einfo[ed];
   const int kL = info & 3, kR = (info >> 2) & 3, bc = info >> 4;
-  const T len = (T)m.egeo[ed], nx = (T)m.egeo[nE + ed], ny = (T)m.egeo[2 * nE + ed];
-  const T hA = (T)m.egeo[3 * nE + ed], hB = (T)m.egeo[4 * nE + ed];
-  const T lam = (T)lam_all[ed];
+  const T* eg = egeo_t(m);
+  const T len = eg[E_LEN * nE + ed], nx = eg[E_NX * nE + ed], ny = eg[E_NY * nE + ed];
+  const T hA = eg[E_HA * nE + ed], hB = eg[E_HB * nE + ed];
   const T g = (T)ph.g;
+  const T hmid = eg[E_HMID * nE + ed];
+  // lambda of Eq. (10) from the element means (Sect. 3), as in the base flux
+  const T* cbt = base_c(c);
+  const T* ubt = base_u(u);
+  const T* geo = geo_t(m);
+  const int64_t ne = m.ne;
+  const T mL = (T)1.4142135623730951 * geo[G_RS * ne + L];
+  const T unL = (ubt[L] * nx + ubt[3 * ne + L] * ny) * mL;
+  const T HL = cbt[L] * mL + hmid;
+  T unR, HR;
   Tr a[N], b[N];
   side_traces<PM>(m, G, c, u, L, kL, false, a);
   if (R >= 0) {
     side_traces<PM>(m, G, c, u, R, kR, true, b);
+    const T mR = (T)1.4142135623730951 * geo[G_RS * ne + R];
+    unR = (ubt[R] * nx + ubt[3 * ne + R] * ny) * mR;
+    HR = cbt[R] * mR + hmid;
   } else if (bc == 2) {
     const T xh = (T)tide_value(ph, stage_time(stg));
     sfor<0, N>([&](auto q) { b[q] = a[q]; b[q].xb = xh; b[q].xh = 0; });
+    unR = unL;
+    HR = xh + hmid;
   } else {
+    unR = -unL;
+    HR = HL;
     sfor<0, N>([&](auto q) {
       const Tr& t = a[q];
       const T qb = t.Ub * nx + t.Vb * ny, qh = t.Uh * nx + t.Vh * ny;
@@ -275,6 +318,7 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
                 t.xh, t.Uh - 2 * qh * nx, t.Vh - 2 * qh * ny, t.uh - 2 * wh * nx, t.vh - 2 * wh * ny};
     });
   }
+  const T lam = fmax(fabs(unL), fabs(unR)) + sqrt(g * fmax(HL, HR));
   // zeroth and first moments (in the left element's edge parameter s) of the
   // weighted correction flux: they are all the test modes of degree <= 1 see
   T M0[3] = {0, 0, 0}, M1[3] = {0, 0, 0};
@@ -306,13 +350,13 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
   });
   // Degree-<=1 test functions are linear along the edge, so the correction's
   // share of the base modes is fixed by (M0, M1); the two-point flux with the
-  // same moments is added to the base flux of this edge, which both sides
-  // project in FP64 (one value per edge: conservative in every mode).
+  // same moments is stored next to the base flux of this edge, and both sides
+  // project their sum in FP64 (one value per edge: conservative in every mode).
   sfor<0, 3>([&](auto f) {
     const T f1 = (M1[f] - cS2b[0] * M0[f]) * cRS2b;
     const T f0 = M0[f] - f1;
-    Fb[(f * 2 + 0) * nE + ed] += (double)f0;
-    Fb[(f * 2 + 1) * nE + ed] += (double)f1;
+    Fbc[(f * 2 + 0) * nE + ed] = (double)f0;
+    Fbc[(f * 2 + 1) * nE + ed] = (double)f1;
   });
 }
 
@@ -321,7 +365,7 @@ static int edge_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
                       const Stage& stg, StateDev c, VelDev u, EdgeFlux fx) {
   const int64_t nl = ce.n[PM];
   if (nl == 0) return 0;
-  k_edge_corr<PM><<<nblocks(nl, 128), 128, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.lam, fx.Fb,
+  k_edge_corr<PM><<<nblocks(nl, 128), 128, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc,
                                                     (T*)fx.Ff[PM]);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
@@ -408,9 +452,9 @@ __device__ __forceinline__ void volume_q(T (&r)[3], const T (&xi)[K], const T (&
 template <int K>
 __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges ce, int64_t g0, int64_t n,
                                                             int64_t rc_off, int64_t nrc, Phys ph, Stage stg,
-                                                            const double* __restrict__ cbS,
+                                                            const T* __restrict__ cbS,
                                                             const T* __restrict__ chS, const T* __restrict__ chN,
-                                                            T* __restrict__ chO, const double* __restrict__ ub,
+                                                            T* __restrict__ chO, const T* __restrict__ ub,
                                                             const T* __restrict__ uh, EdgeFlux fx,
                                                             double* __restrict__ rc) {
   const int64_t l = blockIdx.x * 32 + threadIdx.x;
@@ -418,11 +462,14 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
   const int q = threadIdx.y + 1;
   const int64_t e = g0 + l, ne = m.ne;
   constexpr int KH = K - 3;
+  uint32_t ecs[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ecs[k] = ce.ecs[k * nrc + rc_off + l];
   constexpr int KL = Kof(deg_of(K - 1) - 1);  // modes of degree < p (the only ones D couples)
-  const double* geo = m.geo;
+  const T* geo = geo_t(m);
   T xi[K], U[K], V[K], uc[K], vc[K], pp[K], Uc[KL], Vc[KL];
-  const T J0 = (T)geo[G_JI0 * ne + e], J1 = (T)geo[G_JI1 * ne + e];
-  const T J2 = (T)geo[G_JI2 * ne + e], J3 = (T)geo[G_JI3 * ne + e];
+  const T J0 = geo[G_JI0 * ne + e], J1 = geo[G_JI1 * ne + e];
+  const T J2 = geo[G_JI2 * ne + e], J3 = geo[G_JI3 * ne + e];
   {
     T uu[K], vv[K];
     load_modes<K>(xi, cbS, ne, e, chS, n, l, 0);
@@ -433,7 +480,7 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
     sfor<0, K>([&](auto j) {
       uc[j] = J0 * uu[j] + J1 * vv[j];
       vc[j] = J2 * uu[j] + J3 * vv[j];
-      if constexpr (j < 3) pp[j] = (T)0.5 * xi[j] + (T)geo[(G_HB0 + j) * ne + e];
+      if constexpr (j < 3) pp[j] = (T)0.5 * xi[j] + geo[(G_HB0 + j) * ne + e];
       else pp[j] = (T)0.5 * xi[j];
       if constexpr (j < KL) {
         Uc[j] = J0 * U[j] + J1 * V[j];
@@ -441,7 +488,7 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
       }
     });
   }
-  const T rs = (T)geo[G_RS * ne + e];
+  const T rs = geo[G_RS * ne + e];
   const T g = (T)ph.g;
   T r[3] = {0, 0, 0};
   sfor<1, K>([&](auto Q) {
@@ -456,16 +503,15 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
   sfor<3, K>([&](auto Q) {
     if (q == Q) { xq = xi[Q]; Uq = U[Q]; Vq = V[Q]; }
   });
-  r[1] += g * (T)geo[G_DHX * ne + e] * xq;
-  r[2] += g * (T)geo[G_DHY * ne + e] * xq;
+  r[1] += geo[G_GDHX * ne + e] * xq;
+  r[2] += geo[G_GDHY * ne + e] * xq;
   // edges: every edge of a p >= 2 element is a correction edge
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const int ee = m.eedge[k * ne + e];
-    const int cs = ce.slot[ee >> 1];
-    const bool right = ee & 1;
+    const uint32_t cs = ecs[k];
+    const bool right = (cs >> 27) & 1;
     const int pm = cs >> 28;
-    const int64_t sl = cs & 0x0fffffff;
+    const int64_t sl = cs & 0x07ffffff;
     sfor<3, K>([&](auto Q) {
       if (q == Q) {
         if (pm == 2) project_edge<2, Q>(r, fx, ce, sl, k, right, rs);
@@ -483,6 +529,13 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
   }
 }
 
+static const T* base_c_host(const StateDev& s) {
+  if constexpr (kF32) return (const T*)s.cb32; else return (const T*)s.cb;
+}
+static const T* base_u_host(const VelDev& u) {
+  if constexpr (kF32) return (const T*)u.ub32; else return (const T*)u.ub;
+}
+
 template <int K>
 static int elem_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, int p, const Phys& ph,
                       const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc) {
@@ -490,9 +543,9 @@ static int elem_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
   if (n == 0) return 0;
   const int64_t nrc = G.start[5] - G.start[2], rc_off = g0 - G.start[2];
   dim3 blk(32, K - 1);
-  k_elem_corr<K><<<(unsigned)((n + 31) / 32), blk, 0, st>>>(m, ce, g0, n, rc_off, nrc, ph, stg, cS.cb,
+  k_elem_corr<K><<<(unsigned)((n + 31) / 32), blk, 0, st>>>(m, ce, g0, n, rc_off, nrc, ph, stg, base_c_host(cS),
                                                            (const T*)cS.ch[p], (const T*)cN.ch[p], (T*)cO.ch[p],
-                                                           u.ub, (const T*)u.uh[p], fx, (double*)rc);
+                                                           base_u_host(u), (const T*)u.uh[p], fx, (double*)rc);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;

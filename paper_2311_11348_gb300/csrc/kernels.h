@@ -8,11 +8,13 @@ namespace swedg {
 struct StateDev {
   double* cb;        // [3][3][ne]
   void* ch[5];       // per order p = 2..4: [3][K(p)-3][n_p] of the correction type
+  float* cb32;       // FP32 copy of cb for the FP32 correction (nullptr in FP64 mode)
 };
 
 struct VelDev {
   double* ub;        // [2][3][ne]
   void* uh[5];       // per p = 2..4: [2][K(p)-3][n_p]
+  float* ub32;       // FP32 copy of ub (FP32 correction mode only)
 };
 
 struct Groups {
@@ -20,9 +22,9 @@ struct Groups {
 };
 
 struct EdgeFlux {
-  double* Fb;        // [3][2][nedge] base flux (weighted by |E| w_g) at the 2-point rule, plus the
-                     // two-point equivalent of the correction flux's share of the base modes
-  double* lam;       // [nedge]
+  double* Fb;        // [3][2][nedge] base flux (weighted by |E| w_g) at the 2-point rule
+  double* Fbc;       // [3][2][nedge] two-point equivalent of the correction flux's share of the
+                     // base modes (zero on edges without a p >= 2 side)
   void* Ff[5];       // per pmax = 2..4: [3][N][n] full flux at the npts(pmax) points
 };
 
@@ -42,14 +44,14 @@ int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int3
 int launch_sub(cudaStream_t s, const double* a, const double* b, double* out, int64_t n);
 
 int launch_usolve_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
-                       double* ub, unsigned* status);
+                       double* ub, float* ub32, unsigned* status);
 int launch_dt(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
               const double* ub, unsigned long long* dmin);
 int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Stage& stg, const double* cb,
                      const double* ub, EdgeFlux fx);
 int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
-                     int corr_fp32, const double* cbS, const double* cbN, double* cbO, const double* ub,
-                     EdgeFlux fx, const void* rc, double cfl);
+                     int corr_fp32, const double* cbS, const double* cbN, double* cbO, float* cbO32,
+                     const double* ub, EdgeFlux fx, const void* rc, double cfl);
 int launch_advance_time(cudaStream_t s, double* t_dev, const unsigned long long* dmin, double cfl,
                         double dt_fixed, double* dt_dev);
 int launch_reset_min(cudaStream_t s, unsigned long long* dmin);
