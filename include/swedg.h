@@ -174,6 +174,44 @@ int swe_edge_table(int npts, double* s, double* w, double* B);
 int swe_profile(swe_ctx* ctx, int enable);
 int swe_profile_read(swe_ctx* ctx, int n, const char** names, double* ms, int64_t* launches);
 
+/* Allocation-free right-hand side of an all-P1 mesh (the paper has no
+ * counterpart; this is a service for callers that cannot allocate).
+ *
+ * The context calls above allocate device memory (swe_set_mesh sizes every
+ * buffer to the mesh).  Some callers cannot call cudaMalloc: an application
+ * that hands the solver fixed, pre-allocated device buffers because its
+ * device memory is partitioned up front, or because an allocation would
+ * synchronise the device in the middle of its own pipelined stream work.
+ * This call allocates nothing.  It computes what swe_rhs computes for p = 1
+ * on every element, with land walls on every edge without a neighbour and
+ * no tide, from caller-owned device arrays:
+ *   xy[nv][2]   vertex coordinates          hv[nv]  vertex depths h_b
+ *   tri[ne][3]  counter-clockwise triangles (vertex ids < nv)
+ *   nbr[ne][3]  element across the edge opposite vertex k, or -1 (land);
+ *               the relation must be symmetric; ids outside [0, ne) are land
+ *   c[3][3][ne] modes 1..3 of xi, U, V (the basis of the context layout)
+ *   rhs_out[3][3][ne]  the right-hand side of those modes
+ * The intermediate values -- the auxiliary velocity u and the flux of every
+ * edge at its two Gauss points -- live in one file-scope __device__ array
+ * sized for SWE_NOALLOC_MAX_ELEMENTS elements (24 doubles each, 12.6 MB),
+ * which every GPU that loads the library holds until the process exits.
+ * Errors: SWE_EINVAL for ne < 1, ne > SWE_NOALLOC_MAX_ELEMENTS, nv < 3,
+ * g <= 0 or a NULL array; SWE_ECUDA when a launch fails.  An element with a
+ * vertex id outside [0, nv) gets NaN rows; no depth or finiteness status is
+ * reported (there is no context to hold it).
+ * The first call on a device copies the reference tables to constant memory
+ * and looks up the device address of the scratch array (cudaMemcpyToSymbol,
+ * cudaGetSymbolAddress; no allocation): make that first call before any
+ * stream capture.  Every call shares the one scratch array and leaves its
+ * contents behind; nothing in it needs to start at zero (each call writes
+ * every entry before reading it), but calls that overlap on the GPU --
+ * different streams, or different host threads -- race on it, so the caller
+ * must serialise them.  Asynchronous on `stream` (a cudaStream_t; NULL is
+ * the legacy default stream). */
+#define SWE_NOALLOC_MAX_ELEMENTS 65536
+int swe_rhs_p1_noalloc(int64_t nv, const double* xy, const double* hv, int64_t ne, const int32_t* tri,
+                       const int32_t* nbr, const double* c, double g, double* rhs_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,7 @@ _lib = None
 SYMBOLS = ("swe_default_params", "swe_create", "swe_destroy", "swe_last_error", "swe_set_mesh",
            "swe_set_bathymetry", "swe_set_orders", "swe_set_state", "swe_get_state", "swe_p1_modes", "swe_rhs",
            "swe_rhs_parts", "swe_rk_step", "swe_run", "swe_mass", "swe_energy", "swe_reference_tensors",
-           "swe_edge_table", "swe_profile", "swe_profile_read")
+           "swe_edge_table", "swe_profile", "swe_profile_read", "swe_rhs_p1_noalloc")
 
 
 def library_path() -> str:
@@ -79,6 +79,7 @@ def load():
     lib.swe_edge_table.argtypes = [C.c_int, P, P, P]
     lib.swe_profile.argtypes = [P, C.c_int]
     lib.swe_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(i64)]
+    lib.swe_rhs_p1_noalloc.argtypes = [i64, P, P, i64, P, P, P, d, P, P]
     for s in SYMBOLS:
         if s not in ("swe_destroy", "swe_default_params", "swe_last_error"):
             getattr(lib, s).restype = C.c_int
@@ -112,6 +113,21 @@ def edge_table(npts: int):
     if rc:
         raise SweError(rc, "swe_edge_table")
     return s, w, B
+
+
+NOALLOC_MAX_ELEMENTS = 65536
+
+
+def rhs_p1_noalloc(xy, hv, tri, nbr, c, g, out, stream=None):
+    """swe_rhs_p1_noalloc on caller-owned device tensors (see include/swedg.h):
+    xy [nv,2], hv [nv], tri [ne,3] int32, nbr [ne,3] int32, c [3,3,ne], out [3,3,ne]."""
+    lib = load()
+    args = [_ptr(a) for a in (xy, hv, tri, nbr, c, out)]
+    rc = lib.swe_rhs_p1_noalloc(int(xy.shape[0]), args[0][0], args[1][0], int(tri.shape[0]), args[2][0], args[3][0],
+                                args[4][0], float(g), args[5][0], stream)
+    if rc:
+        raise SweError(rc, "swe_rhs_p1_noalloc")
+    return out
 
 
 class Solver:
