@@ -653,6 +653,11 @@ int swe_create(swe_ctx** out, const swe_params* params) {
     delete ctx;
     return SWE_ECUDA;
   }
+  {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    set_sm_count(nsm);
+  }
   upload_base_tables();
   corr64::upload_tables();
   corr32::upload_tables();

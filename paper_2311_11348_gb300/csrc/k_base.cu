@@ -16,6 +16,10 @@
 #include "kernels.h"
 #include "tables.h"
 
+#ifndef BASE_BLOCKS_PER_SM
+#define BASE_BLOCKS_PER_SM 2
+#endif
+
 namespace swedg {
 
 __constant__ double cB2[3][3][2];   // phihat_i(gamma_k(s_g)), i < 3, 2-point rule
@@ -41,6 +45,16 @@ void upload_base_tables() {
 }
 
 static inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
+
+// Grid of the FP64-pipe-bound base kernels: `per_sm` resident blocks per SM,
+// grid-stride loops over the work.  A few warps per SM already keep the FP64
+// pipe busy; the rest of the SM stays free for the concurrent FP32 correction.
+static int g_sm_count = 152;
+void set_sm_count(int n) { g_sm_count = n > 0 ? n : 152; }
+static inline int capped_blocks(int64_t n, int t, int per_sm) {
+  const int64_t b = (n + t - 1) / t, cap = (int64_t)g_sm_count * per_sm;
+  return (int)(b < cap ? b : cap);
+}
 
 template <typename T>
 __device__ __forceinline__ T* chp(void* p) { return reinterpret_cast<T*>(p); }
@@ -296,8 +310,7 @@ __device__ __forceinline__ void p1_traces(const double* __restrict__ cb, const d
 
 __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cb,
                                                    const double* __restrict__ ub, double* __restrict__ Fb) {
-  const int64_t ed = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (ed >= m.nedge) return;
+  for (int64_t ed = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ed < m.nedge; ed += (int64_t)gridDim.x * blockDim.x) {
   const int64_t ne = m.ne, nE = m.nedge;
   const int L = m.eL[ed], R = m.eR[ed], info = m.einfo[ed];
   const int kL = info & 3, kR = (info >> 2) & 3, bc = info >> 4;
@@ -344,12 +357,13 @@ __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg
     Fb[(1 * 2 + g) * nE + ed] = wl * F1;
     Fb[(2 * 2 + g) * nE + ed] = wl * F2;
   }
+  }
 }
 
 int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Stage& stg, const double* cb,
                      const double* ub, EdgeFlux fx) {
   if (m.nedge == 0) return 0;
-  k_edge_base<<<nblocks(m.nedge, 128), 128, 0, s>>>(m, ph, stg, cb, ub, fx.Fb);
+  k_edge_base<<<capped_blocks(m.nedge, 128, BASE_BLOCKS_PER_SM), 128, 0, s>>>(m, ph, stg, cb, ub, fx.Fb);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -369,10 +383,9 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
                                                    float* __restrict__ cbO32, const double* __restrict__ ub,
                                                    const double* __restrict__ Fb, const double* __restrict__ Fbc,
                                                    const double* __restrict__ rc, int64_t rc_start) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= m.ne) return;
   const int64_t ne = m.ne, nE = m.nedge;
   const double* geo = m.geo;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
   double c[3][3], u[2][3];
 #pragma unroll
   for (int f = 0; f < 3; ++f)
@@ -459,6 +472,7 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
       cbO[ix] = v;
       if (cbO32) cbO32[ix] = (float)v;
     }
+  }
 }
 
 int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
@@ -467,7 +481,7 @@ int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Ph
   (void)cfl;
   if (m.ne == 0) return 0;
   (void)corr_fp32;
-  k_elem_base<<<nblocks(m.ne, 128), 128, 0, s>>>(m, ph, stg, cbS, cbN, cbO, cbO32, ub, fx.Fb, fx.Fbc,
+  k_elem_base<<<capped_blocks(m.ne, 128, BASE_BLOCKS_PER_SM), 128, 0, s>>>(m, ph, stg, cbS, cbN, cbO, cbO32, ub, fx.Fb, fx.Fbc,
                                                  (const double*)rc, G.start[2]);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());

@@ -36,6 +36,7 @@ enum { ST_DEPTH = 1, ST_NONFINITE = 2 };
 
 // base-path tables (host -> constant memory of the base kernels)
 void upload_base_tables();
+void set_sm_count(int n);
 
 int launch_from_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
                      const double* cu, StateDev st);

@@ -1,19 +1,20 @@
-"""Algorithmic operation and byte counts of the libswedg kernel families.
+"""Algorithmic operation counts of the libswedg kernel families (bench roofline).
 
-The counts mirror the arithmetic the kernels perform (same loops, same
-compile-time sparsity predicates of the reference tensors); an FMA counts
-as 2 floating-point operations, a division or square root as 1.  They are
-the "algorithmic flops per unit" of the roofline in bench.py:
+The counts mirror the arithmetic of the kernels (same loops, the same
+compile-time sparsity predicates of the reference tensors): an FMA counts as
+2 floating-point operations, an add, multiply, division or square root as 1;
+loads, conversions and selects count 0.  They are the "algorithmic flops per
+unit" of the roofline that bench.py reports:
 
-  family      unit                          what one unit computes
-  usolve      element                       truncated uH = q system (Sect. 3)
-  edge_base   edge                          P1 traces + LF flux at 2 points
-  edge_corr   correction edge (pmax >= 2)   traces + flux at npts(pmax) points
-  elem_corr   element p >= 2 (+ p <= 1 elements next to a correction edge)
-  elem_base   element                       volume, source, projections, RK
+  family      unit                         arithmetic       count per unit
+  usolve      element (p<=1 / p>=2)        FP64 / corr      USOLVE_P1 / usolve_flops(K)
+  dt          element                      FP64             DT
+  edge_base   edge                         FP64             EDGE_BASE
+  elem_base   element                      FP64             ELEM_BASE
+  edge_corr   edge with max(p_L,p_R) >= 2  corr type        edge_corr_flops(K_L, K_R, pmax)
+  elem_corr   element p >= 2               corr type        elem_corr_flops(K)
 
-Bytes per unit count every array element the kernel reads or writes once
-(perfect reuse of neighbour data in L2 is assumed for edges).
+"corr type" is FP64 in the FP64 mode and FP32 in the mixed mode.
 """
 from __future__ import annotations
 
@@ -21,10 +22,17 @@ import numpy as np
 
 DEG = [0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4]
 KP = [1, 3, 6, 10, 15]
-# FP64 pipe of a GB300: 152 SMs x 4 flop/clk (2 DFMA) x 2.07 GHz (max SM clock)
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
-# FP32 pipe: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 256 * 2.07e9 / 1e12
+SM_COUNT = 152
+SM_MAX_GHZ = 2.07
+# FP64 pipe of a GB300: 2 DFMA = 4 flop per clock per SM (measured 1.19 TFLOP/s at 1.92 GHz)
+FP64_PEAK_TFLOPS = SM_COUNT * 4 * SM_MAX_GHZ / 1e3
+# FP32 pipe: 128 FMA = 256 flop per clock per SM
+FP32_PEAK_TFLOPS = SM_COUNT * 256 * SM_MAX_GHZ / 1e3
+
+USOLVE_P1 = 92
+EDGE_BASE = 175
+ELEM_BASE = 241
+DT = 12
 
 
 def npts(pm):
@@ -54,65 +62,69 @@ def ktr(i, j):
 
 
 def usolve_flops(K):
-    if K <= 3:
-        return 92 if K == 3 else 6
-    f = 4  # H + h_b, depth check
+    """truncated K x K assembly, LDL^T, two right-hand sides"""
+    f = 3
     for j in range(K):
         for i in range(j + 1):
-            f += 2 * sum(1 for n in range(15) if n < ktr(i, j) and tnz(n, i, j))
+            f += 2 * sum(1 for n in range(ktr(i, j)) if tnz(n, i, j))
     for j in range(K):
-        f += 3 * j + 1
-        for i in range(j + 1, K):
-            f += 3 * j + 1
-    f += 2 * (2 * (K * (K - 1) // 2) * 2 + 2 * K)  # two right-hand sides: L, D, L^T, scale by s
+        f += 3 * j + 1 + (K - 1 - j) * (3 * j + 1)
+    f += 2 * (K * (K - 1) + K + K * (K - 1) + K)
     return f
 
 
-def elem_corr_flops(K, edge_pms):
-    f = 8 * K
-    for q in range(K):
+def elem_corr_flops(K):
+    """volume contraction (non-base triples), source, edge projections, RK"""
+    KL = KP[DEG[K - 1] - 1]
+    f = K * 6 + KL * 6  # contravariant coefficients and xi/2 + h_b
+    for q in range(1, K):
         for i in range(K):
             if dnz(q, i) and not (q < 3 and i < 3):
-                f += 9
+                f += 4
             inner = sum(1 for j in range(K) if gnz(q, i, j) and not (q < 3 and i < 3 and j < 3))
             f += 8 * inner + (8 if inner else 0)
-        f += 12 + (4 if q >= 3 else 0)
-    for pm in edge_pms:
-        N = npts(pm)
-        f += N * (3 + 3 * 3 * 2 + (K - 3) * 7)
-    f += 3 * (K - 3) * 5
+        f += 10
+        if q >= 3:
+            f += 4 + 3 * npts(DEG[K - 1]) * (1 + 3 * 2) + 3 * 5
     return f
 
 
-def edge_corr_flops(KL, KR, pm, interior=True):
+def edge_corr_flops(KL, KR, pm):
     N = npts(pm)
-    f = N * 11 * KL + (N * 11 * KR if interior else N * 30)
-    return f + N * 100
+    return 12 + N * (2 * 10 * (KL + KR) + 95)
 
 
-ELEM_BASE = 258   # per element (stage with a != 0); see the module docstring
-EDGE_BASE = 234   # per interior edge
-DT = 20           # per element, first stage of a CFL step
-
-
-def family_flops(orders, fam, mode="fp64", edges=None):
-    """FP64 (fp64 mode) or FP64+FP32 flops per step of one kernel family."""
+def family_flops(orders, fam, nedge=None):
+    """flops per SSP-RK3 step (3 stages) of one kernel family on an order map"""
     p = np.asarray(orders)
     ne = len(p)
     n = [int((p == q).sum()) for q in range(5)]
-    stages = 3
+    nedge = nedge or int(round(1.5 * ne))
+    st = 3
     if fam == "elem_base":
-        return {"flops_per_step": stages * ELEM_BASE * ne, "unit": "element"}
+        return st * ELEM_BASE * ne
     if fam == "edge_base":
-        nedge = int(1.5 * ne)
-        return {"flops_per_step": stages * EDGE_BASE * nedge, "unit": "edge"}
+        return st * EDGE_BASE * nedge
+    if fam == "dt":
+        return DT * ne
     if fam == "usolve":
-        f = n[1] * 92 + n[0] * 6 + sum(n[q] * usolve_flops(KP[q]) for q in (2, 3, 4))
-        return {"flops_per_step": stages * f, "unit": "element"}
+        return st * (n[1] * USOLVE_P1 + n[0] * 6 + sum(n[q] * usolve_flops(KP[q]) for q in (2, 3, 4)))
     if fam == "elem_corr":
-        f = sum(n[q] * elem_corr_flops(KP[q], [q] * 3) for q in (2, 3, 4))
-        return {"flops_per_step": stages * f, "unit": "element"}
+        return st * sum(n[q] * elem_corr_flops(KP[q]) for q in (2, 3, 4))
     if fam == "edge_corr":
-        f = sum(n[q] * 1.5 * edge_corr_flops(KP[q], KP[q], q) for q in (2, 3, 4))
-        return {"flops_per_step": stages * f, "unit": "edge"}
+        # i.i.d. orders: an edge's pmax is the larger of two independent draws
+        frac = np.array(n, float) / max(ne, 1)
+        cdf = np.cumsum(frac)
+        tot = 0.0
+        for pm in (2, 3, 4):
+            pr = cdf[pm] ** 2 - cdf[pm - 1] ** 2
+            tot += pr * nedge * edge_corr_flops(KP[pm], KP[max(1, pm - 1)], pm)
+        return st * tot
     return None
+
+
+def pipe_of(fam, mode):
+    """which arithmetic pipe bounds a family: 'fp64' or 'fp32'"""
+    if fam in ("edge_corr", "elem_corr") and mode == "mixed":
+        return "fp32"
+    return "fp64"
