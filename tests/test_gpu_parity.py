@@ -201,3 +201,32 @@ def test_errors_are_reported_not_faulted():
     with pytest.raises(swedg.SweError) as ei:
         s.rk_step(1e-3)
     assert ei.value.code in (-3, -4)
+
+
+def test_full_size_shelf_rhs_p1234_open_sea():
+    """The paper's mesh size (2,097,152 triangles) with p in {1..4} and the M2
+    open-sea boundary on x = 0: one rhs, all outputs, against the oracle."""
+    w = inputs.shelf_p1234()
+    amp, period, phase = w["tide"]
+    tide = (amp, period, phase)
+    m, P, s = make_pair(w, tide=tide)
+    # P1 interpolants of smooth fields plus seeded higher modes (a full L2
+    # projection at this size takes minutes in the oracle)
+    x, y = w["xy"][:, 0], w["xy"][:, 1]
+    ne = len(w["tri"])
+    c = np.zeros((3, 15, ne))
+    c[0, :3] = m.p1_modes(w["ic"](x, y)[0])
+    c[1, :3] = m.p1_modes(50.0 * np.sin(2 * np.pi * y / 5e5))
+    c[2, :3] = m.p1_modes(-30.0 * np.cos(2 * np.pi * x / 5e5))
+    rng = np.random.default_rng(12)
+    K = np.array([1, 3, 6, 10, 15])[w["orders"]]
+    scale = np.abs(c[:, :3]).max(axis=(1, 2))
+    for f in range(3):
+        hi = rng.standard_normal((12, ne)) * 1e-3 * scale[f]
+        c[f, 3:] = np.where(np.arange(3, 15)[:, None] < K[None, :], hi, 0.0)
+    t0 = 3600.0
+    s.set_state(c, t0)
+    r_o = m.rhs(P, c, t=t0)
+    r_g = s.rhs(c)
+    assert np.abs(r_g - r_o).max() <= 1e-12 * np.abs(r_o).max()
+    s.close()
