@@ -140,6 +140,24 @@ int swe_rk_step(swe_ctx* ctx, double dt, double* dt_used);
  * NULL) receives the final time.  Checks the status word once at the end. */
 int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out);
 
+/* Dynamic p-adaptivity (Sect. 2, end, and Sect. 3: with a hierarchical basis
+ * an order change only adds or removes terms).  The paper's indicator (JRL)
+ * is defined in an earlier paper, not in this one; this library uses a
+ * modal-decay indicator of the elevation,
+ *   s_e = sum_{deg i = p_e} xi_i^2 / sum_{deg i >= 1} xi_i^2   (0 if p_e = 0),
+ * and sets p_e + 1 if s_e > theta_up and p_e < p_max, p_e - 1 if
+ * s_e < theta_down and p_e > p_min.  The state is kept hierarchically (as in
+ * swe_set_orders).  n_changed (or NULL) receives the number of elements whose
+ * order changed, orders_out (host [ne] or NULL) the new orders.
+ * SWE_EINVAL unless 0 <= p_min <= p_max <= 4 and theta_down <= theta_up. */
+int swe_adapt(swe_ctx* ctx, double theta_up, double theta_down, int p_min, int p_max, int64_t* n_changed,
+              int8_t* orders_out);
+
+/* swe_run with swe_adapt after every `every` steps (the paper's dynamically
+ * p-adaptive runs adapt during the simulation, Sect. 5). */
+int swe_run_adaptive(swe_ctx* ctx, int64_t nsteps, int64_t every, double dt_fixed, double theta_up,
+                     double theta_down, int p_min, int p_max, double* t_out);
+
 /* Diagnostics of the context state:
  *   mass   = int xi dx = sum_e sqrt|Omega_e| xi_e1
  *   energy = 1/2 g int xi^2 + 1/2 int q.u  (u from the auxiliary system) */

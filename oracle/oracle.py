@@ -81,6 +81,8 @@ def _load():
     lib.or_mass.restype = d
     lib.or_energy.argtypes = [P, P, P, C.POINTER(C.c_int)]
     lib.or_energy.restype = d
+    lib.or_indicator.argtypes = [P, P, d, d, C.c_int, C.c_int, P, P]
+    lib.or_indicator.restype = i64
     lib.or_Ktr.argtypes = [C.c_int, C.c_int]
     lib.or_Ktr.restype = C.c_int
     lib.or_poly_grid.restype = C.c_int
@@ -266,6 +268,24 @@ class Mesh:
         if st != 0:
             raise FloatingPointError(f"oracle run status {st}")
         return c, tt.value
+
+    def indicator(self, c, theta_up, theta_down, p_min, p_max):
+        """Modal-decay adaptivity indicator (module docstring of swe_oracle.c):
+        returns (new orders [ne] int8, s [ne], number changed)."""
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        po = np.zeros(self.ne, np.int8)
+        so = np.zeros(self.ne)
+        n = self._lib.or_indicator(self.h, _ptr(c), float(theta_up), float(theta_down), int(p_min), int(p_max),
+                                   _ptr(po), _ptr(so))
+        return po, so, int(n)
+
+    def adapt_state(self, c, new_orders):
+        """Hierarchical order change: modes beyond K(p_new) dropped, new modes zero."""
+        c = np.array(c, dtype=np.float64, copy=True)
+        K = np.array(K_OF_P)[np.asarray(new_orders, dtype=np.int64)]
+        c[:, np.arange(KMAX)[:, None] >= K[None, :]] = 0.0
+        self.set_orders(new_orders)
+        return c
 
     def mass(self, c) -> float:
         c = np.ascontiguousarray(c, dtype=np.float64)

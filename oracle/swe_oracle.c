@@ -852,3 +852,34 @@ double or_energy(const or_mesh* m, const or_params* P, const double* c, int* sta
   free(u);
   return s;
 }
+
+/* ------------------------------------------------------------------ */
+/* p-adaptivity (Sect. 2, end; Sect. 3: with a hierarchical basis an   */
+/* order change adds or removes terms).  The paper's JRL indicator is  */
+/* defined elsewhere; the reading used here is a modal-decay indicator: */
+/*   s_e = sum_{deg i = p_e} xi_i^2 / sum_{deg i >= 1} xi_i^2           */
+/* p_e + 1 if s_e > theta_up and p_e < p_max, p_e - 1 if s_e <         */
+/* theta_down and p_e > p_min (s_e = 0 for p_e = 0 or a flat element).  */
+/* ------------------------------------------------------------------ */
+int64_t or_indicator(const or_mesh* m, const double* c, double theta_up, double theta_down, int p_min, int p_max,
+                     int8_t* p_out, double* s_out) {
+  ensure_ready();
+  int64_t ne = m->ne, changed = 0;
+  for (int64_t e = 0; e < ne; ++e) {
+    int p = m->p[e], K = KP[p];
+    double num = 0.0, den = 0.0;
+    for (int i = 1; i < K; ++i) {
+      double x = C_(c, 0, i, e, ne);
+      den += x * x;
+      if (g_deg[i] == p) num += x * x;
+    }
+    double s = (p > 0 && den > 0.0) ? num / den : 0.0;
+    int q = p;
+    if (s > theta_up && p < p_max) q = p + 1;
+    else if (s < theta_down && p > p_min) q = p - 1;
+    p_out[e] = (int8_t)q;
+    if (s_out) s_out[e] = s;
+    changed += q != p;
+  }
+  return changed;
+}

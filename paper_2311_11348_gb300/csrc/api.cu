@@ -84,6 +84,7 @@ struct swe_ctx {
   unsigned* d_status = nullptr;
   double* d_partial = nullptr;
   double* d_red = nullptr;
+  int8_t* d_newp = nullptr;  // orders proposed by the adaptivity indicator (caller order)
   int nred = 0;
   // profiling
   bool prof = false;
@@ -438,6 +439,7 @@ static int build_device(swe_ctx* ctx) {
   if ((rc = dalloc(ctx, &ctx->d_user, sizeof(double) * 3 * KMAX * ne)) ||
       (rc = dalloc(ctx, &ctx->d_user2, sizeof(double) * 3 * KMAX * ne)))
     return cuda_err(ctx, rc);
+  if ((rc = dalloc(ctx, &ctx->d_newp, (size_t)ne))) return cuda_err(ctx, rc);
   if ((rc = dalloc(ctx, &ctx->d_dt, sizeof(double))) || (rc = dalloc(ctx, &ctx->d_t, sizeof(double))) ||
       (rc = dalloc(ctx, &ctx->d_dmin, sizeof(unsigned long long))) || (rc = dalloc(ctx, &ctx->d_status, sizeof(unsigned))))
     return cuda_err(ctx, rc);
@@ -890,6 +892,39 @@ int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out) {
     CU(cudaStreamSynchronize(ctx->stream));
   }
   return rc;
+}
+
+int swe_adapt(swe_ctx* ctx, double theta_up, double theta_down, int p_min, int p_max, int64_t* n_changed,
+              int8_t* orders_out) {
+  if (!ctx || !ctx->have_mesh) return fail(ctx, SWE_EINVAL, "swe_adapt: no mesh");
+  if (p_min < 0 || p_max > 4 || p_min > p_max || !(theta_down <= theta_up))
+    return fail(ctx, SWE_EINVAL, "swe_adapt: need 0 <= p_min <= p_max <= 4 and theta_down <= theta_up");
+  LaunchScope ls(ctx);
+  CK(launch_indicator(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->corr32, ctx->st[0], theta_up, theta_down,
+                      p_min, p_max, ctx->d_newp));
+  std::vector<int8_t> np((size_t)ctx->ne);
+  CU(cudaMemcpyAsync(np.data(), ctx->d_newp, (size_t)ctx->ne, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  int64_t changed = 0;
+  for (int64_t e = 0; e < ctx->ne; ++e) changed += np[e] != ctx->p_user[e];
+  if (n_changed) *n_changed = changed;
+  if (orders_out) std::memcpy(orders_out, np.data(), (size_t)ctx->ne);
+  if (changed == 0) return 0;
+  return swe_set_orders(ctx, np.data());
+}
+
+int swe_run_adaptive(swe_ctx* ctx, int64_t nsteps, int64_t every, double dt_fixed, double theta_up,
+                     double theta_down, int p_min, int p_max, double* t_out) {
+  if (!ctx || !ctx->have_mesh || nsteps < 0 || every < 1) return fail(ctx, SWE_EINVAL, "swe_run_adaptive: bad arguments");
+  int64_t done = 0;
+  while (done < nsteps) {
+    const int64_t n = std::min(every, nsteps - done);
+    int rc = swe_run(ctx, n, dt_fixed, t_out);
+    if (rc) return rc;
+    done += n;
+    if (done % every == 0 && (rc = swe_adapt(ctx, theta_up, theta_down, p_min, p_max, nullptr, nullptr))) return rc;
+  }
+  return 0;
 }
 
 int swe_mass(swe_ctx* ctx, double* m) {

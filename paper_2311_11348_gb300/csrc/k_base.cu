@@ -489,6 +489,51 @@ int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Ph
 }
 
 // ---------------------------------------------------------------------------
+// p-adaptivity indicator (modal decay of xi, FP64 in every mode):
+//   s_e = sum_{deg i = p_e} xi_i^2 / sum_{deg i >= 1} xi_i^2
+// p_e + 1 if s_e > theta_up (p_e < p_max), p_e - 1 if s_e < theta_down
+// (p_e > p_min).  The new orders are written in the caller's element order.
+// ---------------------------------------------------------------------------
+template <typename TC>
+__global__ void k_indicator(DevMesh m, Groups G, const int32_t* __restrict__ perm, StateDev st, double up,
+                            double down, int pmin, int pmax, int8_t* __restrict__ p_user) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= m.ne) return;
+  const int64_t ne = m.ne;
+  const int p = m.p[e], K = Kof(p);
+  double num = 0.0, den = 0.0;
+  for (int i = 1; i < K && i < 3; ++i) {
+    const double x = st.cb[i * ne + e];
+    den += x * x;
+    if (p == 1) num += x * x;
+  }
+  if (p >= 2) {
+    const int64_t n = G.start[p + 1] - G.start[p], l = e - G.start[p];
+    const TC* h = chp<TC>(st.ch[p]);
+    for (int i = 3; i < K; ++i) {
+      const double x = (double)h[(i - 3) * n + l];
+      den += x * x;
+      if (deg_of(i) == p) num += x * x;
+    }
+  }
+  const double s = (p > 0 && den > 0.0) ? num / den : 0.0;
+  int q = p;
+  if (s > up && p < pmax) q = p + 1;
+  else if (s < down && p > pmin) q = p - 1;
+  p_user[perm[e]] = (int8_t)q;
+}
+
+int launch_indicator(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
+                     StateDev st, double up, double down, int pmin, int pmax, int8_t* p_user) {
+  if (m.ne == 0) return 0;
+  if (corr_fp32) k_indicator<float><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, st, up, down, pmin, pmax, p_user);
+  else k_indicator<double><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, st, up, down, pmin, pmax, p_user);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
 // status: non-finite values in the state
 // ---------------------------------------------------------------------------
 template <typename TC>

@@ -56,6 +56,8 @@ int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Ph
 int launch_advance_time(cudaStream_t s, double* t_dev, const unsigned long long* dmin, double cfl,
                         double dt_fixed, double* dt_dev);
 int launch_reset_min(cudaStream_t s, unsigned long long* dmin);
+int launch_indicator(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
+                     StateDev st, double up, double down, int pmin, int pmax, int8_t* p_user);
 int launch_check_state(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp32, StateDev st,
                        unsigned* status);
 // deterministic two-pass reductions: mass and energy of a state

@@ -39,7 +39,8 @@ _lib = None
 SYMBOLS = ("swe_default_params", "swe_create", "swe_destroy", "swe_last_error", "swe_set_mesh",
            "swe_set_bathymetry", "swe_set_orders", "swe_set_state", "swe_get_state", "swe_p1_modes", "swe_rhs",
            "swe_rhs_parts", "swe_rk_step", "swe_run", "swe_mass", "swe_energy", "swe_reference_tensors",
-           "swe_edge_table", "swe_profile", "swe_profile_read", "swe_rhs_p1_noalloc")
+           "swe_edge_table", "swe_profile", "swe_profile_read", "swe_rhs_p1_noalloc", "swe_adapt",
+           "swe_run_adaptive")
 
 
 def library_path() -> str:
@@ -80,6 +81,8 @@ def load():
     lib.swe_profile.argtypes = [P, C.c_int]
     lib.swe_profile_read.argtypes = [P, C.c_int, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(i64)]
     lib.swe_rhs_p1_noalloc.argtypes = [i64, P, P, i64, P, P, P, d, P, P]
+    lib.swe_adapt.argtypes = [P, d, d, C.c_int, C.c_int, C.POINTER(i64), P]
+    lib.swe_run_adaptive.argtypes = [P, i64, i64, d, d, d, C.c_int, C.c_int, C.POINTER(d)]
     for s in SYMBOLS:
         if s not in ("swe_destroy", "swe_default_params", "swe_last_error"):
             getattr(lib, s).restype = C.c_int
@@ -222,6 +225,20 @@ class Solver:
     def run(self, nsteps, dt_fixed=0.0):
         t = C.c_double(0.0)
         self._ck(self._lib.swe_run(self.h, int(nsteps), float(dt_fixed), C.byref(t)))
+        return t.value
+
+    def adapt(self, theta_up, theta_down, p_min=1, p_max=4):
+        """one indicator pass; returns (new orders, number changed)"""
+        n = C.c_int64(0)
+        out = np.zeros(self.ne, np.int8)
+        self._ck(self._lib.swe_adapt(self.h, float(theta_up), float(theta_down), int(p_min), int(p_max), C.byref(n),
+                                     out.ctypes.data_as(C.c_void_p)))
+        return out, n.value
+
+    def run_adaptive(self, nsteps, every, theta_up, theta_down, p_min=1, p_max=4, dt_fixed=0.0):
+        t = C.c_double(0.0)
+        self._ck(self._lib.swe_run_adaptive(self.h, int(nsteps), int(every), float(dt_fixed), float(theta_up),
+                                            float(theta_down), int(p_min), int(p_max), C.byref(t)))
         return t.value
 
     def mass(self):

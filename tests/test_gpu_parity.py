@@ -230,3 +230,36 @@ def test_full_size_shelf_rhs_p1234_open_sea():
     r_g = s.rhs(c)
     assert np.abs(r_g - r_o).max() <= 1e-12 * np.abs(r_o).max()
     s.close()
+
+
+def test_dynamic_adaptivity_matches_oracle():
+    """swe_run_adaptive (indicator every 10 steps, hierarchical order changes)
+    against the oracle doing the same: orders bit-exact, state to 1e-11."""
+    w = mixed_workload(seed=7, pmin=1, pmax=2, open_west=False)
+    up, down, pmin, pmax = 5e-2, 1e-3, 1, 3
+    m, P, s = make_pair(w)
+    c = m.project_state(w["ic"])
+    s.set_state(c, 0.0)
+    dt = 0.5
+    orders = w["orders"].copy()
+    co = c.copy()
+    nchanged = []
+    for rnd in range(3):
+        co, _ = m.run(P, co, 0.0, 10, dt=dt)
+        new, sv, n = m.indicator(co, up, down, pmin, pmax)
+        # no indicator value within round-off of a threshold (the decision would be ambiguous)
+        for th in (up, down):
+            assert np.all(np.abs(sv - th) > 1e-9 * th)
+        co = m.adapt_state(co, new)
+        orders = new
+        nchanged.append(n)
+    assert min(nchanged) > 0 and len(set(orders)) == 3
+    s.run_adaptive(30, 10, up, down, pmin, pmax, dt_fixed=dt)
+    cg, _ = s.get_state()
+    assert rel_l2(cg, co) < 1e-11
+    # the library's current orders equal the oracle's
+    _, nchg = s.adapt(1e300, -1.0, pmin, pmax)  # thresholds that change nothing
+    assert nchg == 0
+    o2, _ = s.adapt(up, down, pmin, pmax)
+    po, _, _ = m.indicator(co, up, down, pmin, pmax)
+    assert np.array_equal(o2, po)

@@ -311,3 +311,26 @@ def test_cfl_step_definition():
     d = 4 * area / (4 + 2 * math.sqrt(2))
     expect = 0.5 * d / ((5.0 + math.sqrt(49.0)) * 3)
     assert abs(m.dt(P, c) - expect) <= 1e-15 * expect
+
+
+def test_adaptivity_indicator_decisions():
+    """Modal-decay indicator (the reading for the paper's dynamically p-adaptive
+    runs, Sect. 2 end): hand-computed energy fractions decide the new orders."""
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    tri = np.array([[0, 1, 2], [1, 3, 2]])
+    m = O.Mesh(xy, tri, np.ones(4), np.array([2, 3], np.int8))
+    c = np.zeros((3, 15, 2))
+    # element 0, p = 2: degree-1 energy 2, degree-2 energy 0.03 -> s = 0.03 / 2.03
+    c[0, :6, 0] = [5.0, 1.0, 1.0, 0.1, 0.1, 0.1]
+    # element 1, p = 3: degree-3 modes zero -> s = 0
+    c[0, :10, 1] = [3.0, 1.0, 0.5, 0.2, 0.0, 0.1, 0.0, 0.0, 0.0, 0.0]
+    p, s, n = m.indicator(c, 0.01, 1e-4, 1, 4)
+    assert abs(s[0] - 0.03 / 2.03) < 1e-15 and s[1] == 0.0
+    assert list(p) == [3, 2] and n == 2
+    p, s, n = m.indicator(c, 0.02, 1e-4, 1, 2)   # s[0] below theta_up; p_max caps nothing
+    assert list(p) == [2, 2] and n == 1
+    p, s, n = m.indicator(c, 0.01, 1e-4, 3, 4)   # p_min = 3 keeps element 1 at 3
+    assert list(p) == [3, 3]
+    # hierarchical order change: dropped modes vanish, kept ones are untouched
+    c2 = m.adapt_state(c, np.array([1, 3], np.int8))
+    assert np.all(c2[:, 3:, 0] == 0.0) and np.all(c2[:, :3, 0] == c[:, :3, 0]) and np.all(c2[:, :, 1] == c[:, :, 1])
