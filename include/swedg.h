@@ -140,6 +140,29 @@ int swe_rk_step(swe_ctx* ctx, double dt, double* dt_used);
  * NULL) receives the final time.  Checks the status word once at the end. */
 int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out);
 
+/* Batched ensemble.  The mesh of swe_set_mesh may be the disjoint union of
+ * independent members (e.g. the vertex and triangle arrays of several meshes
+ * concatenated); member (host [ne], caller order) names the member 0 ..
+ * nmembers-1 of every element, and the two elements of an edge must belong
+ * to the same member.  Every member then keeps its own CFL time step and its
+ * own time, while each kernel of a stage is still one launch over all
+ * members.  The state is kept; every member's time is set to the context
+ * time (swe_get_state's t).  nmembers = 1 with member = NULL restores a
+ * single member.  SWE_EINVAL for ids out of range or a shared edge across
+ * members. */
+int swe_set_members(swe_ctx* ctx, int32_t nmembers, const int32_t* member);
+
+/* Times of the members (host [nmembers]); swe_get_member_times also returns
+ * the last step of every member in dt_out (host [nmembers], or NULL).  The
+ * single-member calls (swe_set_state, swe_get_state, swe_run, swe_rk_step)
+ * set every member's time and report member 0. */
+int swe_set_member_times(swe_ctx* ctx, const double* t);
+int swe_get_member_times(swe_ctx* ctx, double* t_out, double* dt_out);
+
+/* Device memory held by the context (bytes); a serving loop admits requests
+ * by this footprint. */
+int swe_memory_bytes(swe_ctx* ctx, int64_t* bytes);
+
 /* Dynamic p-adaptivity (Sect. 2, end, and Sect. 3: with a hierarchical basis
  * an order change only adds or removes terms).  The paper's indicator (JRL)
  * is defined in an earlier paper, not in this one; this library uses a

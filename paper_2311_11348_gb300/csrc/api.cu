@@ -61,6 +61,8 @@ struct swe_ctx {
   std::vector<double> xy, hv;
   std::vector<int32_t> tri;
   std::vector<int8_t> tag, p_user;
+  std::vector<int32_t> member_user;  // ensemble member of each element (caller order)
+  int32_t nmem = 1;
   std::vector<int64_t> nb;
   std::vector<int8_t> nbk;
   // internal numbering: perm[internal] = caller index
@@ -100,6 +102,7 @@ struct swe_ctx {
   bool use_graph = true;
   // kernel launches issued by the library (graph replays count their kernels)
   int64_t launches = 0;
+  int64_t dev_bytes = 0;  // device memory held by the context
 };
 
 // Route count_launch() of the kernel launchers to this context while an API
@@ -143,6 +146,7 @@ static void free_all(swe_ctx* ctx) {
   if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
+  ctx->dev_bytes = 0;
 }
 
 template <typename P>
@@ -152,6 +156,7 @@ static int dalloc(swe_ctx* ctx, P** out, size_t bytes) {
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
   ctx->allocs.push_back(p);
+  ctx->dev_bytes += (int64_t)bytes;
   *out = (P*)p;
   return 0;
 }
@@ -382,7 +387,13 @@ static int build_device(swe_ctx* ctx) {
   std::vector<float> geo32(geo.begin(), geo.end()), egeo32(egeo.begin(), egeo.end());
   float *d_geo32, *d_egeo32;
   if ((rc = upload(ctx, &d_geo32, geo32)) || (rc = upload(ctx, &d_egeo32, egeo32))) return cuda_err(ctx, rc);
-  ctx->dm = DevMesh{ne, nE, nint, d_geo, d_p, d_eedge, d_eL, d_eR, d_einfo, d_egeo, d_geo32, d_egeo32};
+  std::vector<int32_t> mem((size_t)ne), emem((size_t)nE);
+  for (int64_t e = 0; e < ne; ++e) mem[e] = ctx->member_user[ctx->perm[e]];
+  for (int64_t i = 0; i < nE; ++i) emem[i] = mem[eL[i]];
+  int32_t *d_mem, *d_emem;
+  if ((rc = upload(ctx, &d_mem, mem)) || (rc = upload(ctx, &d_emem, emem))) return cuda_err(ctx, rc);
+  ctx->dm = DevMesh{ne, nE, nint, d_geo, d_p, d_eedge, d_eL, d_eR, d_einfo, d_egeo, d_geo32, d_egeo32,
+                    d_mem, d_emem, ctx->nmem};
   std::memset(&ctx->ce, 0, sizeof ctx->ce);
   ctx->ce.slot = d_slot;
   {
@@ -440,13 +451,16 @@ static int build_device(swe_ctx* ctx) {
       (rc = dalloc(ctx, &ctx->d_user2, sizeof(double) * 3 * KMAX * ne)))
     return cuda_err(ctx, rc);
   if ((rc = dalloc(ctx, &ctx->d_newp, (size_t)ne))) return cuda_err(ctx, rc);
-  if ((rc = dalloc(ctx, &ctx->d_dt, sizeof(double))) || (rc = dalloc(ctx, &ctx->d_t, sizeof(double))) ||
-      (rc = dalloc(ctx, &ctx->d_dmin, sizeof(unsigned long long))) || (rc = dalloc(ctx, &ctx->d_status, sizeof(unsigned))))
+  const size_t nm = (size_t)ctx->nmem;
+  if ((rc = dalloc(ctx, &ctx->d_dt, sizeof(double) * nm)) || (rc = dalloc(ctx, &ctx->d_t, sizeof(double) * nm)) ||
+      (rc = dalloc(ctx, &ctx->d_dmin, sizeof(unsigned long long) * nm)) ||
+      (rc = dalloc(ctx, &ctx->d_status, sizeof(unsigned))))
     return cuda_err(ctx, rc);
+  cudaMemset(ctx->d_dt, 0, sizeof(double) * nm);
   ctx->nred = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (ne + 255) / 256));
   if ((rc = dalloc(ctx, &ctx->d_partial, sizeof(double) * ctx->nred)) || (rc = dalloc(ctx, &ctx->d_red, sizeof(double) * 2)))
     return cuda_err(ctx, rc);
-  cudaMemset(ctx->d_t, 0, sizeof(double));
+  cudaMemset(ctx->d_t, 0, sizeof(double) * nm);
   cudaMemset(ctx->d_status, 0, sizeof(unsigned));
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_err(ctx, cuda_fail(e, "build_device", __FILE__, __LINE__));
@@ -500,9 +514,9 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
   }
   if (cfl_dt) {
     ProfScope ps(ctx, F_DT);
-    CK(launch_reset_min(A, ctx->d_dmin));
+    CK(launch_reset_min(A, ctx->d_dmin, ctx->nmem));
     CK(launch_dt(A, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->d_dmin));
-    CK(launch_advance_time(A, nullptr, ctx->d_dmin, ctx->prm.cfl, dt_fixed, ctx->d_dt));
+    CK(launch_advance_time(A, nullptr, ctx->d_dmin, ctx->prm.cfl, dt_fixed, ctx->d_dt, ctx->nmem));
     if (conc) {  // the correction branch reads dt (stage time, RK update)
       CU(cudaEventRecord(ctx->ev_dt, A));
       CU(cudaStreamWaitEvent(B, ctx->ev_dt, 0));
@@ -546,7 +560,7 @@ static int enqueue_step(swe_ctx* ctx, double dt_fixed) {
   s.t_dev = ctx->d_t;
   if (dt_fixed > 0.0) {
     ProfScope ps(ctx, F_DT);
-    CK(launch_advance_time(ctx->stream, nullptr, ctx->d_dmin, ctx->prm.cfl, dt_fixed, ctx->d_dt));
+    CK(launch_advance_time(ctx->stream, nullptr, ctx->d_dmin, ctx->prm.cfl, dt_fixed, ctx->d_dt, ctx->nmem));
   }
   const bool cfl = dt_fixed <= 0.0;
   if (ctx->prm.rk_order == 3) {
@@ -563,7 +577,7 @@ static int enqueue_step(swe_ctx* ctx, double dt_fixed) {
     CK(run_stage(ctx, B, A, A, s, false, dt_fixed));
   }
   ProfScope ps(ctx, F_OTHER);
-  CK(launch_advance_time(ctx->stream, ctx->d_t, nullptr, 0.0, 0.0, ctx->d_dt));
+  CK(launch_advance_time(ctx->stream, ctx->d_t, nullptr, 0.0, 0.0, ctx->d_dt, ctx->nmem));
   return 0;
 }
 
@@ -713,6 +727,8 @@ int swe_set_mesh(swe_ctx* ctx, int64_t nv, const double* xy, int64_t ne, const i
     for (int k = 0; k < 3; ++k) { ctx->tri[3 * e + k] = v[k]; ctx->tag[3 * e + k] = t[k]; }
   }
   ctx->p_user.assign(ne, 1);
+  ctx->member_user.assign(ne, 0);
+  ctx->nmem = 1;
   int rc = build_topology(ctx);
   if (rc) { ctx->have_mesh = false; return rc; }
   return build_device(ctx);
@@ -753,7 +769,8 @@ int swe_set_state(swe_ctx* ctx, const double* c, double t) {
   if (!ctx || !ctx->have_mesh || !c) return fail(ctx, SWE_EINVAL, "swe_set_state: no mesh or NULL");
   LaunchScope ls(ctx);
   CK(state_in(ctx, c, 0));
-  CU(cudaMemcpyAsync(ctx->d_t, &t, sizeof t, cudaMemcpyHostToDevice, ctx->stream));
+  const std::vector<double> tv((size_t)ctx->nmem, t);
+  CU(cudaMemcpyAsync(ctx->d_t, tv.data(), sizeof(double) * tv.size(), cudaMemcpyHostToDevice, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   return 0;
 }
@@ -924,6 +941,51 @@ int swe_run_adaptive(swe_ctx* ctx, int64_t nsteps, int64_t every, double dt_fixe
     done += n;
     if (done % every == 0 && (rc = swe_adapt(ctx, theta_up, theta_down, p_min, p_max, nullptr, nullptr))) return rc;
   }
+  return 0;
+}
+
+int swe_set_members(swe_ctx* ctx, int32_t nmembers, const int32_t* member) {
+  if (!ctx || !ctx->have_mesh || nmembers < 1 || (nmembers > 1 && !member))
+    return fail(ctx, SWE_EINVAL, "swe_set_members: no mesh, nmembers < 1 or NULL");
+  std::vector<int32_t> mv((size_t)ctx->ne, 0);
+  if (member) mv.assign(member, member + ctx->ne);
+  for (int64_t e = 0; e < ctx->ne; ++e)
+    if (mv[e] < 0 || mv[e] >= nmembers)
+      return fail(ctx, SWE_EINVAL, "member of element %lld is %d, not in 0..%d", (long long)e, mv[e], nmembers - 1);
+  for (int64_t e = 0; e < ctx->ne; ++e)
+    for (int k = 0; k < 3; ++k) {
+      const int64_t n = ctx->nb[3 * e + k];
+      if (n >= 0 && mv[n] != mv[e])
+        return fail(ctx, SWE_EINVAL, "elements %lld and %lld share an edge but not a member", (long long)e, (long long)n);
+    }
+  std::vector<double> c((size_t)3 * KMAX * ctx->ne);
+  double t = 0.0;
+  int rc = swe_get_state(ctx, c.data(), &t);
+  if (rc) return rc;
+  ctx->member_user = mv;
+  ctx->nmem = nmembers;
+  if ((rc = build_device(ctx))) return rc;
+  return swe_set_state(ctx, c.data(), t);
+}
+
+int swe_set_member_times(swe_ctx* ctx, const double* t) {
+  if (!ctx || !ctx->have_mesh || !t) return fail(ctx, SWE_EINVAL, "swe_set_member_times: no mesh or NULL");
+  CU(cudaMemcpyAsync(ctx->d_t, t, sizeof(double) * ctx->nmem, cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return 0;
+}
+
+int swe_get_member_times(swe_ctx* ctx, double* t_out, double* dt_out) {
+  if (!ctx || !ctx->have_mesh || !t_out) return fail(ctx, SWE_EINVAL, "swe_get_member_times: no mesh or NULL");
+  CU(cudaMemcpyAsync(t_out, ctx->d_t, sizeof(double) * ctx->nmem, cudaMemcpyDeviceToHost, ctx->stream));
+  if (dt_out) CU(cudaMemcpyAsync(dt_out, ctx->d_dt, sizeof(double) * ctx->nmem, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return 0;
+}
+
+int swe_memory_bytes(swe_ctx* ctx, int64_t* bytes) {
+  if (!ctx || !bytes) return SWE_EINVAL;
+  *bytes = ctx->dev_bytes;
   return 0;
 }
 

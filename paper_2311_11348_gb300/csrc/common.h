@@ -84,10 +84,10 @@ enum {
 struct Stage {
   double a, b;
   int rhs_only;
-  const double* dt;   // device scalar (CFL step) ...
-  double dt_host;     // ... or this value when dt == nullptr
-  double t;           // stage time for the open-sea boundary (host value) ...
-  const double* t_dev;  // ... plus dev_t_scale * (*t_dev) when non-null
+  const double* dt;   // device array [members]: step of each ensemble member ...
+  double dt_host;     // ... or this value for all members when dt == nullptr
+  double t;           // time at the start of the step (host value, all members) ...
+  const double* t_dev;  // ... or the device array [members] when non-null
   double tau;         // stage time = t_n + tau * dt
   int base_only;      // 1: the base part alone (no correction kernels, no rc)
 };
@@ -110,6 +110,9 @@ struct DevMesh {
   const double* egeo;     // [NEGEO][nedge] (rows E_*), in the left element's direction
   const float* geo32;     // FP32 copies of geo and egeo for the FP32 correction kernels
   const float* egeo32;
+  const int32_t* mem;     // [ne] ensemble member of each element (all 0 for a single mesh)
+  const int32_t* emem;    // [nedge] member of each edge
+  int32_t nmem;
 };
 
 // Correction edges grouped by pmax = max(p_L, p_R) in 2..4.
@@ -119,6 +122,11 @@ struct CorrEdges {
   const int32_t* slot;    // [nedge]: (pmax << 28) | slot within group, or -1
   const uint32_t* ecs;    // [3][elements with p >= 2]: (pmax << 28) | (side << 27) | slot of each local edge
 };
+
+__device__ __forceinline__ double stage_dt(const Stage& st, int mem) { return st.dt ? st.dt[mem] : st.dt_host; }
+__device__ __forceinline__ double stage_time(const Stage& st, int mem) {
+  return (st.t_dev ? st.t_dev[mem] : st.t) + st.tau * stage_dt(st, mem);
+}
 
 }  // namespace swedg
 

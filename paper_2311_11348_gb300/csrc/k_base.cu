@@ -208,7 +208,9 @@ __global__ void __launch_bounds__(256) k_dt(DevMesh m, Phys ph, const double* __
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t ne = m.ne;
   double d = DBL_MAX;
+  int mem = 0;
   if (e < ne) {
+    mem = m.mem[e];
     const double r = cPhi0 * m.geo[G_RS * ne + e];
     const double ubar = ub[0 * ne + e] * r, vbar = ub[3 * ne + e] * r;
     const double Hbar = (cb[e] + m.geo[G_HB0 * ne + e]) * r;
@@ -216,20 +218,24 @@ __global__ void __launch_bounds__(256) k_dt(DevMesh m, Phys ph, const double* __
     const double dd = m.geo[G_DIAM * ne + e] / (sp * (2.0 * m.p[e] + 1.0));
     if (dd > 0.0 && dd < d) d = dd;  // NaN never wins; it is reported by the status checks
   }
-  __shared__ double red[256];
-  red[threadIdx.x] = d;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + w]);
-    __syncthreads();
+  // one atomic per warp when its elements share a member (the usual case)
+  const unsigned full = 0xffffffffu;
+  const int mem0 = __shfl_sync(full, mem, 0);
+  if (__all_sync(full, mem == mem0)) {
+    for (int o = 16; o > 0; o >>= 1) d = fmin(d, __shfl_xor_sync(full, d, o));
+    if ((threadIdx.x & 31) == 0 && d < DBL_MAX) atomicMin(dmin + mem0, (unsigned long long)__double_as_longlong(d));
+  } else if (d < DBL_MAX) {
+    atomicMin(dmin + mem, (unsigned long long)__double_as_longlong(d));
   }
-  if (threadIdx.x == 0) atomicMin(dmin, (unsigned long long)__double_as_longlong(red[0]));
 }
 
-__global__ void k_reset_min(unsigned long long* dmin) { *dmin = (unsigned long long)__double_as_longlong(DBL_MAX); }
+__global__ void k_reset_min(unsigned long long* dmin, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dmin[i] = (unsigned long long)__double_as_longlong(DBL_MAX);
+}
 
-int launch_reset_min(cudaStream_t s, unsigned long long* dmin) {
-  k_reset_min<<<1, 1, 0, s>>>(dmin);
+int launch_reset_min(cudaStream_t s, unsigned long long* dmin, int nmem) {
+  k_reset_min<<<nblocks(nmem, 128), 128, 0, s>>>(dmin, nmem);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -245,24 +251,23 @@ int launch_dt(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph,
   return 0;
 }
 
-// dt_dev = dt_fixed > 0 ? dt_fixed : cfl * min;   then t += dt (after the step)
-__global__ void k_set_dt(double* dt_dev, const unsigned long long* dmin, double cfl, double dt_fixed) {
-  *dt_dev = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)*dmin);
+// per member: dt = dt_fixed > 0 ? dt_fixed : cfl * min (before the step); t += dt (after it)
+__global__ void k_set_dt(double* dt_dev, const unsigned long long* dmin, double cfl, double dt_fixed, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dt_dev[i] = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)dmin[i]);
 }
-__global__ void k_advance_time(double* t_dev, const double* dt_dev) { *t_dev += *dt_dev; }
+__global__ void k_advance_time(double* t_dev, const double* dt_dev, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) t_dev[i] += dt_dev[i];
+}
 
 int launch_advance_time(cudaStream_t s, double* t_dev, const unsigned long long* dmin, double cfl, double dt_fixed,
-                        double* dt_dev) {
-  if (t_dev == nullptr) k_set_dt<<<1, 1, 0, s>>>(dt_dev, dmin, cfl, dt_fixed);
-  else k_advance_time<<<1, 1, 0, s>>>(t_dev, dt_dev);
+                        double* dt_dev, int nmem) {
+  if (t_dev == nullptr) k_set_dt<<<nblocks(nmem, 128), 128, 0, s>>>(dt_dev, dmin, cfl, dt_fixed, nmem);
+  else k_advance_time<<<nblocks(nmem, 128), 128, 0, s>>>(t_dev, dt_dev, nmem);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
-}
-
-__device__ __forceinline__ double stage_dt(const Stage& st) { return st.dt ? *st.dt : st.dt_host; }
-__device__ __forceinline__ double stage_time(const Stage& st) {
-  return (st.t_dev ? *st.t_dev : st.t) + st.tau * stage_dt(st);
 }
 
 __device__ __forceinline__ double tide_value(const Phys& ph, double t) {
@@ -325,7 +330,7 @@ __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg
     unR = b.w0;
     HR = b.xi0 + hmid;
   } else if (bc == 2) {
-    const double xh = tide_value(ph, stage_time(stg));
+    const double xh = tide_value(ph, stage_time(stg, m.emem[ed]));
     b = a;
     b.xi[0] = xh; b.xi[1] = xh;
     unR = unL;
@@ -458,7 +463,7 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
     r[2][2] += rc[3 * nrc + lr];
   }
   const int K = m.p[e] == 0 ? 1 : 3;
-  const double dt = stage_dt(stg), a = stg.a, bb = stg.b;
+  const double dt = stage_dt(stg, m.mem[e]), a = stg.a, bb = stg.b;
 #pragma unroll
   for (int f = 0; f < 3; ++f)
 #pragma unroll

@@ -108,10 +108,6 @@ void upload_tables() {
 
 static inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-__device__ __forceinline__ double stage_dt(const Stage& st) { return st.dt ? *st.dt : st.dt_host; }
-__device__ __forceinline__ double stage_time(const Stage& st) {
-  return (st.t_dev ? *st.t_dev : st.t) + st.tau * stage_dt(st);
-}
 __device__ __forceinline__ double tide_value(const Phys& ph, double t) {
   if (ph.tide_period <= 0.0) return ph.tide_amp;
   return ph.tide_amp * sin(2.0 * 3.14159265358979323846 * t / ph.tide_period + ph.tide_phase);
@@ -303,7 +299,7 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
     unR = (ubt[R] * nx + ubt[3 * ne + R] * ny) * mR;
     HR = cbt[R] * mR + hmid;
   } else if (bc == 2) {
-    const T xh = (T)tide_value(ph, stage_time(stg));
+    const T xh = (T)tide_value(ph, stage_time(stg, m.emem[ed]));
     sfor<0, N>([&](auto q) { b[q] = a[q]; b[q].xb = xh; b[q].xh = 0; });
     unR = unL;
     HR = xh + hmid;
@@ -520,7 +516,7 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
       }
     });
   }
-  const T dt = (T)stage_dt(stg), a = (T)stg.a, b = (T)stg.b;
+  const T dt = (T)stage_dt(stg, m.mem[e]), a = (T)stg.a, b = (T)stg.b;
   const T cs3[3] = {xq, Uq, Vq};
 #pragma unroll
   for (int f = 0; f < 3; ++f) {

@@ -54,8 +54,8 @@ int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Ph
                      int corr_fp32, const double* cbS, const double* cbN, double* cbO, float* cbO32,
                      const double* ub, EdgeFlux fx, const void* rc, double cfl);
 int launch_advance_time(cudaStream_t s, double* t_dev, const unsigned long long* dmin, double cfl,
-                        double dt_fixed, double* dt_dev);
-int launch_reset_min(cudaStream_t s, unsigned long long* dmin);
+                        double dt_fixed, double* dt_dev, int nmem);
+int launch_reset_min(cudaStream_t s, unsigned long long* dmin, int nmem);
 int launch_indicator(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
                      StateDev st, double up, double down, int pmin, int pmax, int8_t* p_user);
 int launch_check_state(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp32, StateDev st,

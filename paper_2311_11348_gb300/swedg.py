@@ -40,7 +40,8 @@ SYMBOLS = ("swe_default_params", "swe_create", "swe_destroy", "swe_last_error", 
            "swe_set_bathymetry", "swe_set_orders", "swe_set_state", "swe_get_state", "swe_p1_modes", "swe_rhs",
            "swe_rhs_parts", "swe_rk_step", "swe_run", "swe_mass", "swe_energy", "swe_reference_tensors",
            "swe_edge_table", "swe_profile", "swe_profile_read", "swe_rhs_p1_noalloc", "swe_adapt",
-           "swe_run_adaptive")
+           "swe_run_adaptive", "swe_set_members", "swe_set_member_times", "swe_get_member_times",
+           "swe_memory_bytes")
 
 
 def library_path() -> str:
@@ -83,6 +84,10 @@ def load():
     lib.swe_rhs_p1_noalloc.argtypes = [i64, P, P, i64, P, P, P, d, P, P]
     lib.swe_adapt.argtypes = [P, d, d, C.c_int, C.c_int, C.POINTER(i64), P]
     lib.swe_run_adaptive.argtypes = [P, i64, i64, d, d, d, C.c_int, C.c_int, C.POINTER(d)]
+    lib.swe_set_members.argtypes = [P, C.c_int32, P]
+    lib.swe_set_member_times.argtypes = [P, P]
+    lib.swe_get_member_times.argtypes = [P, P, P]
+    lib.swe_memory_bytes.argtypes = [P, C.POINTER(i64)]
     for s in SYMBOLS:
         if s not in ("swe_destroy", "swe_default_params", "swe_last_error"):
             getattr(lib, s).restype = C.c_int
@@ -240,6 +245,26 @@ class Solver:
         self._ck(self._lib.swe_run_adaptive(self.h, int(nsteps), int(every), float(dt_fixed), float(theta_up),
                                             float(theta_down), int(p_min), int(p_max), C.byref(t)))
         return t.value
+
+    def set_members(self, nmembers, member=None):
+        pm, km = _ptr(member, np.int32)
+        self._ck(self._lib.swe_set_members(self.h, int(nmembers), pm))
+        self.nmembers = int(nmembers)
+
+    def member_times(self):
+        n = getattr(self, "nmembers", 1)
+        t = np.zeros(n); dt = np.zeros(n)
+        self._ck(self._lib.swe_get_member_times(self.h, t.ctypes.data_as(C.c_void_p), dt.ctypes.data_as(C.c_void_p)))
+        return t, dt
+
+    def set_member_times(self, t):
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        self._ck(self._lib.swe_set_member_times(self.h, t.ctypes.data_as(C.c_void_p)))
+
+    def memory_bytes(self):
+        b = C.c_int64(0)
+        self._ck(self._lib.swe_memory_bytes(self.h, C.byref(b)))
+        return b.value
 
     def mass(self):
         m = C.c_double(0.0)

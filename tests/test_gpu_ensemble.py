@@ -1,0 +1,82 @@
+"""Batched ensembles and the serving loop on the GPU: every member's result
+is the same alone and in the mix (bitwise: the per-element arithmetic and the
+per-member CFL minimum do not depend on the other members)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2311_11348_gb300 import build, ensemble, inputs, serve, swedg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    swedg.load()
+
+
+def member(n, L, seed, pmin, pmax, open_west=False):
+    xy, tri = inputs.split_square_mesh(n, L, jitter=0.2, seed=seed)
+    hv = inputs.fourier_bathymetry(xy, L, lo=30.0, hi=300.0, seed=seed + 1)
+    rng = np.random.default_rng(seed)
+    orders = rng.integers(pmin, pmax + 1, size=len(tri)).astype(np.int8)
+    bc = inputs.boundary_tags(xy, tri, "west") if open_west else None
+    m = O.Mesh(xy, tri, hv, orders, bc_tag=bc)
+    c = m.project_state(lambda x, y: (0.4 * np.exp(-((x - 0.6 * L) ** 2 + (y - 0.4 * L) ** 2) / (0.02 * L * L)),
+                                      0.0 * x + 2.0, 0.0 * y - 1.0), n=5)
+    return dict(xy=xy, tri=tri, hv=hv, orders=orders, bc_tag=bc), c
+
+
+def alone(mesh, c, steps, **kw):
+    s = swedg.Solver(**kw)
+    s.set_mesh(mesh["xy"], mesh["tri"], mesh.get("bc_tag"))
+    s.set_bathymetry(mesh["hv"])
+    s.set_orders(mesh["orders"])
+    s.set_state(c, 0.0)
+    t = s.run(steps)
+    out, _ = s.get_state()
+    nbytes = s.memory_bytes()
+    s.close()
+    return out, t, nbytes
+
+
+@pytest.mark.parametrize("precision", [swedg.PREC_FP64, swedg.PREC_MIXED_FP32])
+def test_ensemble_member_equals_alone(precision):
+    kw = dict(g=9.81, cfl=0.2, rk_order=3, precision=precision, tide=(0.2, 900.0, 0.0))
+    specs = [member(8, 2e3, 1, 1, 2), member(14, 5e3, 2, 1, 3, open_west=True), member(5, 1e3, 3, 2, 4)]
+    ens = ensemble.Ensemble([m for m, _ in specs], **kw)
+    ens.set_states([c for _, c in specs])
+    ens.run(15)
+    got = ens.states()
+    t_ens, dt_ens = ens.times()
+    ens.close()
+    assert len(set(np.round(dt_ens, 12))) == 3  # every member took its own CFL step
+    for i, (m, c) in enumerate(specs):
+        ref, t, nbytes = alone(m, c, 15, **kw)
+        assert t_ens[i] == t
+        assert np.array_equal(got[i], ref)
+        print("bytes per element", nbytes / len(m["tri"]))
+
+
+def test_serving_results_equal_alone_with_admission_by_footprint():
+    kw = dict(g=9.81, cfl=0.2, rk_order=3, precision=swedg.PREC_MIXED_FP32)
+    specs = [member(8, 2e3, 11, 1, 2), member(10, 3e3, 12, 1, 3), member(6, 1e3, 13, 1, 2), member(9, 2e3, 14, 2, 3)]
+    steps = [25, 10, 40, 15]
+    per = serve.BYTES_PER_ELEMENT_MIXED
+    budget = per * (len(specs[0][0]["tri"]) + len(specs[1][0]["tri"]) + 1)  # two at a time
+    srv = serve.Server(budget, precision=kw["precision"], g=9.81, cfl=0.2, rk_order=3, max_chunk=8)
+    for i, ((m, c), st) in enumerate(zip(specs, steps)):
+        srv.submit(serve.Request(rid=i, mesh=m, state=c, steps=st))
+        if i == 1:
+            srv.step()  # the later requests arrive while the first two run
+    srv.run_until_idle()
+    srv.close()
+    assert srv.rebuilds >= 3
+    done = {r.rid: r for r in srv.done}
+    for i, ((m, c), st) in enumerate(zip(specs, steps)):
+        ref, t, _ = alone(m, c, st, **kw)
+        assert done[i].t_final == t
+        assert np.array_equal(done[i].result, ref)
+    lat = srv.latencies()
+    assert np.all(lat > 0)

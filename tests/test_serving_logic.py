@@ -1,0 +1,73 @@
+"""Scheduling logic of the serving loop on the CPU (no GPU): admission by
+device footprint, chunking by the smallest remaining step count, retirement
+and re-batching.  The union context is replaced by a recording fake."""
+import numpy as np
+
+from paper_2311_11348_gb300 import serve, swedg
+
+
+class FakeUnion:
+    log = []
+
+    def __init__(self, meshes, **kw):
+        self.meshes = meshes
+        self.ne = [len(m["tri"]) for m in meshes]
+        self.t = np.zeros(len(meshes))
+        FakeUnion.log.append(("build", len(meshes)))
+
+    def set_states(self, states, times=None):
+        self.c = [np.array(s, copy=True) for s in states]
+        self.t = np.zeros(len(states)) if times is None else np.array(times, float)
+
+    def states(self, device=False):
+        return [c.copy() for c in self.c]
+
+    def times(self):
+        return self.t.copy(), np.ones_like(self.t)
+
+    def run(self, n, dt_fixed=0.0):
+        FakeUnion.log.append(("run", n, len(self.c)))
+        for c in self.c:
+            c += n  # a state that counts steps
+        self.t += n
+
+    def close(self):
+        pass
+
+
+def make_req(rid, ne, steps):
+    mesh = dict(xy=np.zeros((3, 2)), tri=np.zeros((ne, 3), np.int32), hv=np.ones(3), orders=np.ones(ne, np.int8))
+    return serve.Request(rid=rid, mesh=mesh, state=np.zeros((3, 15, ne)), steps=steps, arrival=1.0)
+
+
+def test_admission_chunking_and_results(monkeypatch):
+    monkeypatch.setattr(serve, "Ensemble", FakeUnion)
+    FakeUnion.log = []
+    per = serve.BYTES_PER_ELEMENT_MIXED
+    srv = serve.Server(budget_bytes=per * 250, precision=swedg.PREC_MIXED_FP32, max_chunk=40, clock=lambda: 2.0,
+                       device_resident=False)
+    for rid, ne, steps in [(0, 100, 30), (1, 100, 70), (2, 120, 20)]:
+        srv.submit(make_req(rid, ne, steps))
+    srv.run_until_idle()
+    done = {r.rid: r for r in srv.done}
+    assert set(done) == {0, 1, 2}
+    for r in done.values():
+        assert np.all(r.result == r.steps) and r.t_final == r.steps  # every request ran exactly its steps
+    runs = [e for e in FakeUnion.log if e[0] == "run"]
+    # 0 and 1 fit the budget together, 2 only after 0 leaves; chunks stop at the first finisher
+    assert runs[0] == ("run", 30, 2)
+    assert runs[1] == ("run", 20, 2)
+    assert runs[2] == ("run", 20, 1)
+    assert sum(n for _, n, _ in runs if True) == 70
+    assert srv.latencies().shape == (3,)
+
+
+def test_a_request_larger_than_the_budget_still_runs_alone(monkeypatch):
+    monkeypatch.setattr(serve, "Ensemble", FakeUnion)
+    FakeUnion.log = []
+    srv = serve.Server(budget_bytes=10, max_chunk=50, clock=lambda: 0.0, device_resident=False)
+    srv.submit(make_req(0, 1000, 10))
+    srv.submit(make_req(1, 1000, 10))
+    srv.run_until_idle()
+    runs = [e for e in FakeUnion.log if e[0] == "run"]
+    assert runs == [("run", 10, 1), ("run", 10, 1)]
