@@ -22,10 +22,58 @@ from . import swedg
 from .ensemble import Ensemble
 
 KMAX = swedg.KMAX
-# device bytes per element of a union context, measured from swe_memory_bytes
-# of representative meshes (state x3, velocity, fluxes, geometry, staging)
-BYTES_PER_ELEMENT_FP64 = 2600
-BYTES_PER_ELEMENT_MIXED = 2200
+KP = (1, 3, 6, 10, 15)
+NGEO, NEGEO = 19, 9  # rows of the element and edge geometry tables
+
+
+def _npts(pm):
+    return 2 if pm <= 1 else (3 * pm + 2) // 2
+
+
+def device_bytes(meshes, precision):
+    """Device bytes a context holds after swe_set_mesh + swe_set_orders (+
+    swe_set_members) of the disjoint union of `meshes`: the same allocations
+    the library makes (swe_memory_bytes reports them), counted on the host so
+    that admission needs no context.  Per element: FP64 geometry and its FP32
+    copy, topology, three RK states, velocity, the user-layout staging; per
+    edge: geometry, base fluxes and the correction flux buffers of its max
+    order; the correction arrays scale with K(p) - 3 at the correction type's
+    width (4 bytes in the mixed mode, 8 in FP64)."""
+    corr32 = precision == swedg.PREC_MIXED_FP32
+    ts = 4 if corr32 else 8
+    ne = nE = 0
+    n = [0] * 5
+    ncl = [0] * 5
+    for m in meshes:
+        tri = np.asarray(m["tri"], np.int64)
+        p = np.asarray(m["orders"], np.int64)
+        ne += len(tri)
+        for q in range(5):
+            n[q] += int((p == q).sum())
+        a = tri.reshape(-1)
+        b = tri[:, [1, 2, 0]].reshape(-1)
+        key = np.minimum(a, b) * (int(tri.max(initial=0)) + 1) + np.maximum(a, b)
+        owner = np.repeat(np.arange(len(tri)), 3)
+        order = np.argsort(key, kind="stable")
+        key, owner = key[order], owner[order]
+        first = np.ones(len(key), bool)
+        first[1:] = key[1:] != key[:-1]
+        pm = np.maximum.reduceat(p[owner], np.flatnonzero(first)) if len(key) else np.zeros(0, np.int64)
+        nE += int(first.sum())
+        for q in (2, 3, 4):
+            ncl[q] += int((pm == q).sum())
+    nm = max(len(meshes), 1)
+    nrc = n[2] + n[3] + n[4]
+    b = NGEO * 12 * ne                      # geo + geo32
+    b += ne * (1 + 12 + 4 + 4 + 1)          # p, eedge, perm, member, new orders
+    b += nE * (12 + 4 + 4 + NEGEO * 12)     # eL/eR/einfo, slot, edge member, egeo + egeo32
+    b += 12 * max(nrc, 1) + 4 * sum(ncl)    # element correction-edge slots, correction edge lists
+    b += 3 * ne * (72 + (36 if corr32 else 0)) + sum(3 * ts * 3 * (KP[q] - 3) * n[q] for q in (2, 3, 4))
+    b += ne * (48 + (24 if corr32 else 0)) + sum(ts * 2 * (KP[q] - 3) * n[q] for q in (2, 3, 4))
+    b += 96 * nE + sum(ts * 3 * _npts(q) * ncl[q] for q in (2, 3, 4))
+    b += 32 * max(nrc, 1) + 2 * 8 * 3 * KMAX * ne
+    b += 24 * nm + 4 + 8 * min(1024, max(1, (ne + 255) // 256)) + 16
+    return b
 
 
 @dataclasses.dataclass
@@ -41,11 +89,14 @@ class Request:
     result: np.ndarray = None
     t_final: float = 0.0
     done_steps: int = 0
+    nbytes: int = None
 
 
 def footprint(req: Request, precision: int) -> int:
-    per = BYTES_PER_ELEMENT_MIXED if precision == swedg.PREC_MIXED_FP32 else BYTES_PER_ELEMENT_FP64
-    return per * len(req.mesh["tri"])
+    """device bytes the request adds to a union context (computed once)"""
+    if req.nbytes is None:
+        req.nbytes = device_bytes([req.mesh], precision)
+    return req.nbytes
 
 
 class Server:

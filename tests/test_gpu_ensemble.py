@@ -50,21 +50,22 @@ def test_ensemble_member_equals_alone(precision):
     ens.run(15)
     got = ens.states()
     t_ens, dt_ens = ens.times()
+    assert ens.solver.memory_bytes() == serve.device_bytes([m for m, _ in specs], precision)
     ens.close()
     assert len(set(np.round(dt_ens, 12))) == 3  # every member took its own CFL step
     for i, (m, c) in enumerate(specs):
         ref, t, nbytes = alone(m, c, 15, **kw)
         assert t_ens[i] == t
         assert np.array_equal(got[i], ref)
-        print("bytes per element", nbytes / len(m["tri"]))
+        assert nbytes == serve.device_bytes([m], precision)
 
 
 def test_serving_results_equal_alone_with_admission_by_footprint():
     kw = dict(g=9.81, cfl=0.2, rk_order=3, precision=swedg.PREC_MIXED_FP32)
     specs = [member(8, 2e3, 11, 1, 2), member(10, 3e3, 12, 1, 3), member(6, 1e3, 13, 1, 2), member(9, 2e3, 14, 2, 3)]
     steps = [25, 10, 40, 15]
-    per = serve.BYTES_PER_ELEMENT_MIXED
-    budget = per * (len(specs[0][0]["tri"]) + len(specs[1][0]["tri"]) + 1)  # two at a time
+    fp = [serve.device_bytes([m], kw["precision"]) for m, _ in specs]
+    budget = fp[0] + fp[1] + 1  # two at a time
     srv = serve.Server(budget, precision=kw["precision"], g=9.81, cfl=0.2, rk_order=3, max_chunk=8)
     for i, ((m, c), st) in enumerate(zip(specs, steps)):
         srv.submit(serve.Request(rid=i, mesh=m, state=c, steps=st))

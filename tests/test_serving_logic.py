@@ -43,11 +43,13 @@ def make_req(rid, ne, steps):
 def test_admission_chunking_and_results(monkeypatch):
     monkeypatch.setattr(serve, "Ensemble", FakeUnion)
     FakeUnion.log = []
-    per = serve.BYTES_PER_ELEMENT_MIXED
-    srv = serve.Server(budget_bytes=per * 250, precision=swedg.PREC_MIXED_FP32, max_chunk=40, clock=lambda: 2.0,
+    reqs = [make_req(rid, ne, steps) for rid, ne, steps in [(0, 100, 30), (1, 100, 70), (2, 120, 20)]]
+    f = [serve.footprint(r, swedg.PREC_MIXED_FP32) for r in reqs]
+    assert f[0] < f[2]
+    srv = serve.Server(budget_bytes=f[1] + f[2], precision=swedg.PREC_MIXED_FP32, max_chunk=40, clock=lambda: 2.0,
                        device_resident=False)
-    for rid, ne, steps in [(0, 100, 30), (1, 100, 70), (2, 120, 20)]:
-        srv.submit(make_req(rid, ne, steps))
+    for r in reqs:
+        srv.submit(r)
     srv.run_until_idle()
     done = {r.rid: r for r in srv.done}
     assert set(done) == {0, 1, 2}
@@ -71,3 +73,17 @@ def test_a_request_larger_than_the_budget_still_runs_alone(monkeypatch):
     srv.run_until_idle()
     runs = [e for e in FakeUnion.log if e[0] == "run"]
     assert runs == [("run", 10, 1), ("run", 10, 1)]
+
+
+def test_device_bytes_counts_edges_orders_and_precision():
+    from paper_2311_11348_gb300 import inputs
+    xy, tri = inputs.split_square_mesh(4, 1.0)
+    p1 = dict(tri=tri, orders=np.ones(len(tri), np.int8))
+    p3 = dict(tri=tri, orders=np.full(len(tri), 3, np.int8))
+    b64 = serve.device_bytes([p1], swedg.PREC_FP64)
+    assert serve.device_bytes([p1], swedg.PREC_MIXED_FP32) > b64  # FP32 copies of the P1 data
+    assert serve.device_bytes([p3], swedg.PREC_FP64) > serve.device_bytes([p3], swedg.PREC_MIXED_FP32) > b64
+    # a union holds the same per-element and per-edge arrays as its members
+    both = serve.device_bytes([p1, p3], swedg.PREC_FP64)
+    alone = b64 + serve.device_bytes([p3], swedg.PREC_FP64)
+    assert 0 < alone - both < 200
