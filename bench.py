@@ -12,7 +12,15 @@ per step = 3 stages x 3 fields x sum_e K(p_e).  The state (~40 MB in all RK
 buffers) fits in the 129 MB L2, so L2 is flushed (256 MB write) between timed
 steps and each step is timed alone with CUDA events on the solver's stream.
 With N > 1 (torchrun), every rank runs an independent replica of the workload
-(the path is replicas-only on this pool; no data-path collective).
+(the path is replicas-only on this pool; no data-path collective).  The
+default line also carries a short serving leg (p50/p99 completion latency).
+
+Other workloads (one JSON line each):
+    --workload ensemble   64 members, log-uniform 8k..600k triangles (9.3M in
+                          all), p in {1..4}, one union context, per-member dt
+    --workload serving    Poisson arrivals of such members (5k..200k
+                          triangles, 100..500 steps by default), continuous
+                          batching, p50/p99 latency and throughput
 """
 from __future__ import annotations
 
@@ -32,7 +40,7 @@ sys.path.insert(0, ROOT)
 
 from paper_2311_11348_gb300 import inputs  # noqa: E402
 
-METRIC = "DOF-stage updates/s, mixed vs FP64 at stated L2 error"
+METRIC = "DOF-stage updates/s, mixed vs FP64 at stated L2 error; p50/p99 solve latency"
 
 
 def dofs_per_step(orders, stages=3):
@@ -106,14 +114,15 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     res = {}
-    prec_list = [("mixed", swedg.PREC_MIXED_FP32), ("fp64", swedg.PREC_FP64)]
-    if args.precision == "fp64":
-        prec_list = prec_list[::-1]
+    modes = {"mixed": swedg.PREC_MIXED_FP32, "fp64": swedg.PREC_FP64, "tf32": swedg.PREC_MIXED_TF32}
+    order = [args.precision] + [k for k in ("mixed", "fp64", "tf32") if k != args.precision]
+    prec_list = [(k, modes[k]) for k in order]
     clocks = None
     for name, prec in prec_list:
         s = make_solver(w, prec, stream.cuda_stream)
         c0 = initial_state(s, w)
         s.set_state(c0, 0.0)
+        shape = s.autotune(steps=5)[0] if args.autotune else s.launch_shape()
         s.run(args.warmup)
         s.set_state(c0, 0.0)
         torch.cuda.synchronize()
@@ -154,7 +163,7 @@ def run_ours(args, rank, world):
         s.run(args.steps)
         launches = s.profile_read()["kernels"][1]
         s.profile(False)
-        res[name] = dict(ms_steps=ms, total_ms=tot, prof=prof, launches=launches, solver=s, c0=c0)
+        res[name] = dict(ms_steps=ms, total_ms=tot, prof=prof, launches=launches, solver=s, c0=c0, shape=shape)
     return w, dps, res, clk, stream, flush
 
 
@@ -215,15 +224,235 @@ def oracle_rate(w, steps, warmup):
     return time.perf_counter() - t0
 
 
+def ensemble_state(ens, members):
+    """initial union state: P1 interpolant of each member's vertex elevation, momenta at rest"""
+    xi = np.concatenate([m["xi_vertex"] for m in members])
+    c = np.zeros((3, 15, int(ens.e0[-1])))
+    c[0, :3] = ens.solver.p1_modes(xi)
+    return c
+
+
+def bench_ensemble(args, world):
+    """Batched ensemble: every member in one union context; each timed step is
+    one SSP-RK3 step of all members (graph replay), every member at its own
+    CFL step."""
+    import torch
+    from paper_2311_11348_gb300 import ensemble, swedg
+    members = inputs.ensemble_members(args.members)
+    orders = np.concatenate([m["orders"] for m in members])
+    dps = dofs_per_step(orders)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    res = {}
+    clk = None
+    small = int(np.argmin([len(m["tri"]) for m in members]))
+    for name, prec in [("mixed", swedg.PREC_MIXED_FP32), ("fp64", swedg.PREC_FP64), ("tf32", swedg.PREC_MIXED_TF32)]:
+        t_build = time.perf_counter()
+        ens = ensemble.Ensemble(members, g=9.81, cfl=0.1, rk_order=3, precision=prec, stream=stream.cuda_stream)
+        c0 = ensemble_state(ens, members)
+        t_build = time.perf_counter() - t_build
+        ens.solver.set_state(c0, 0.0)
+        shape = ens.solver.autotune(steps=2)[0] if args.autotune else ens.solver.launch_shape()
+        ens.run(args.warmup)
+        ens.solver.set_state(c0, 0.0)
+        ens.solver.set_member_times(np.zeros(ens.n))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        if clk is None:
+            clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
+        times = []
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.add_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ens.run(1)
+                b.record(stream)
+                times.append((a, b))
+        torch.cuda.synchronize()
+        if clk is None:
+            clk = clocks.stop()
+        tot = sum(a.elapsed_time(b) for a, b in times)
+        if world > 1:
+            t = torch.tensor([tot], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot = float(t.item())
+        ens.solver.set_state(c0, 0.0)
+        ens.solver.set_member_times(np.zeros(ens.n))
+        ens.solver.profile(True)
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                flush.add_(1.0)
+                ens.run(1)
+        torch.cuda.synchronize()
+        prof = ens.solver.profile_read()
+        ens.solver.profile(True)
+        ens.solver.set_state(c0, 0.0)
+        ens.solver.set_member_times(np.zeros(ens.n))
+        ens.run(args.steps)
+        launches = ens.solver.profile_read()["kernels"][1]
+        ens.solver.profile(False)
+        err = None
+        if not args.no_oracle:  # the smallest member after 2 of its own CFL steps, against the oracle
+            sys.path.insert(0, os.path.join(ROOT, "oracle"))
+            import oracle as O
+            ens.solver.set_state(c0, 0.0)
+            ens.solver.set_member_times(np.zeros(ens.n))
+            ens.run(2)
+            got = ens.states()[small]
+            m = members[small]
+            om = O.Mesh(m["xy"], m["tri"], m["hv"], m["orders"])
+            ref, _ = om.run(O.Params(g=9.81, cfl=0.1, rk_order=3), c0[:, :, ens.e0[small]:ens.e0[small + 1]], 0.0, 2)
+            err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        res[name] = dict(total_ms=tot, prof=prof, launches=launches, err=err, build_s=t_build,
+                         bytes=ens.solver.memory_bytes(), shape=shape)
+        ens.close()
+    units = dps * args.steps * world
+    value = units / (res["mixed"]["total_ms"] / 1e3)
+    fp64 = units / (res["fp64"]["total_ms"] / 1e3)
+    tf32 = units / (res["tf32"]["total_ms"] / 1e3)
+    fams = {k: v for k, v in res["mixed"]["prof"].items() if k != "kernels"}
+    dom = max(fams, key=lambda k: fams[k][0])
+    ne = len(orders)
+    w = dict(orders=orders)
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF-stage/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["mixed"]["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": f"ensemble: {len(members)} members, log-uniform {ne // len(members)} mean "
+                               f"({min(len(m['tri']) for m in members)}..{max(len(m['tri']) for m in members)}) "
+                               f"triangles, {ne} in all, p in {{1..4}} 40/30/20/10, SSP-RK3, CFL 0.1, per-member dt",
+                   "members": len(members), "triangles": ne, "dof_stage_per_step": dps, "precision": "mixed",
+                   "l2": "inputs larger than L2; 256 MB flush between timed steps", "replicas": world},
+        "mixed": {"value": value, "rel_l2_vs_oracle": res["mixed"]["err"], "oracle_member_triangles":
+                  len(members[small]["tri"]), "oracle_steps": 2, "device_bytes": res["mixed"]["bytes"],
+                  "setup_s": res["mixed"]["build_s"], "launch_shape": res["mixed"]["shape"]},
+        "fp64": {"value": fp64, "ms_per_step": res["fp64"]["total_ms"] / args.steps,
+                 "rel_l2_vs_oracle": res["fp64"]["err"], "device_bytes": res["fp64"]["bytes"],
+                 "launch_shape": res["fp64"]["shape"]},
+        "tf32": {"value": tf32, "ms_per_step": res["tf32"]["total_ms"] / args.steps,
+                 "rel_l2_vs_oracle": res["tf32"]["err"], "device_bytes": res["tf32"]["bytes"],
+                 "launch_shape": res["tf32"]["shape"],
+                 "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in res["tf32"]["prof"].items()
+                                        if k != "kernels"}},
+        "mixed_over_fp64": value / fp64,
+        "tf32_over_fp64": tf32 / fp64,
+        "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in fams.items()},
+        "dominant_kernel": dom, "gpu_launches": int(res["mixed"]["launches"]), "clocks": clk,
+        "e2e": None,
+    }
+    line["roofline"] = roofline(w, res["mixed"], dom, args.steps, peaks(), "mixed")
+    return line
+
+
+def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, chunk, warmup, seed=7):
+    """Continuous-batching serving loop against a wall clock: requests arrive
+    by a seeded Poisson process, are admitted by device footprint, share RK
+    launches with the running ones and leave when done.  Returns a summary."""
+    import torch
+    from paper_2311_11348_gb300 import serve, swedg
+    reqs = inputs.serving_requests(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, seed=seed)
+    prepared = []
+    for k, (t_arr, m, steps) in enumerate(reqs):  # client side: initial states, before the clock starts
+        s = swedg.Solver()
+        s.set_mesh(m["xy"], m["tri"])
+        c = np.zeros((3, 15, len(m["tri"])))
+        c[0, :3] = s.p1_modes(m["xi_vertex"])
+        s.close()
+        mesh = dict(xy=m["xy"], tri=m["tri"], hv=m["hv"], orders=m["orders"])
+        prepared.append((t_arr, serve.Request(rid=k, mesh=mesh, state=c, steps=steps)))
+    kw = dict(precision=swedg.PREC_MIXED_FP32, g=9.81, cfl=0.1, rk_order=3, max_chunk=chunk)
+    # warm-up: one small request through the same path (module load, graph capture)
+    srv = serve.Server(int(budget_gb * 1e9), **kw)
+    w0 = prepared[0][1]
+    srv.submit(serve.Request(rid=-1, mesh=w0.mesh, state=w0.state, steps=max(3, warmup), arrival=1.0))
+    srv.run_until_idle()
+    srv.close()
+    torch.cuda.synchronize()
+    srv = serve.Server(int(budget_gb * 1e9), **kw)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
+    t0 = time.perf_counter()
+    pending = list(prepared)
+    busy = 0.0
+    while pending or srv.waiting or srv.active:
+        now = time.perf_counter() - t0
+        while pending and pending[0][0] <= now:
+            t_arr, r = pending.pop(0)
+            r.arrival = t0 + t_arr
+            srv.submit(r)
+        if not srv.waiting and not srv.active:
+            time.sleep(max(0.0, min(0.05, pending[0][0] - now)))
+            continue
+        tb = time.perf_counter()
+        srv.step()
+        busy += time.perf_counter() - tb
+    makespan = time.perf_counter() - t0
+    clk = clocks.stop()
+    srv.close()
+    lat = srv.latencies()
+    work = srv.dof_stage_updates
+    offered = sum(r.steps * 3 * 3 * int(np.array([1, 3, 6, 10, 15])[r.mesh["orders"].astype(np.int64)].sum())
+                  for _, r in prepared) / duration
+    state_bytes = sum(r.state.nbytes for _, r in prepared)
+    return dict(value=work / makespan, requests=len(prepared), makespan_s=makespan,
+                p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+                mean_s=float(lat.mean()), max_s=float(lat.max()), offered_dof_stage_per_s=offered,
+                dof_stage_updates=work, rebuilds=srv.rebuilds, rebuild_s=srv.rebuild_s, busy_s=busy,
+                launches=srv.launches, state_bytes=state_bytes,
+                total_steps=sum(r.steps for _, r in prepared),
+                mean_triangles=float(np.mean([len(r.mesh["tri"]) for _, r in prepared])), clocks=clk)
+
+
+def bench_serving(args, world):
+    r = serving_run(args.rate, args.duration, args.tri_lo, args.tri_hi, args.steps_lo, args.steps_hi,
+                    args.budget_gb, args.chunk, args.warmup)
+    line = {
+        "metric": METRIC, "value": r["value"] * world, "unit": "DOF-stage/s", "n_gpus": world,
+        "steps": r["total_steps"], "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": f"serving: Poisson arrivals {args.rate}/s for {args.duration} s, triangles "
+                               f"log-uniform [{int(args.tri_lo)}, {int(args.tri_hi)}], steps uniform "
+                               f"[{args.steps_lo}, {args.steps_hi}], p in {{1..4}} 40/30/20/10, mixed, "
+                               f"{args.budget_gb} GB admission budget, chunks of <= {args.chunk} steps",
+                   "requests": r["requests"], "mean_triangles": r["mean_triangles"], "replicas": world,
+                   "l2": "wall clock, end to end (state in from host, result out to host)"},
+        "latency_s": {"p50": r["p50_s"], "p99": r["p99_s"], "mean": r["mean_s"], "max": r["max_s"]},
+        "offered_dof_stage_per_s": r["offered_dof_stage_per_s"],
+        "makespan_s": r["makespan_s"], "rebuilds": r["rebuilds"], "rebuild_s": r["rebuild_s"],
+        "gpu_launches": r["launches"], "clocks": r["clocks"],
+        "e2e": {"value": r["value"] * world, "unit": "DOF-stage/s",
+                "h2d_bytes_per_step": r["state_bytes"] / max(r["total_steps"], 1),
+                "d2h_bytes_per_step": r["state_bytes"] / max(r["total_steps"], 1)},
+        "roofline": None,
+    }
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "tf32"],
+                    help="headline mode: FP32 correction, FP64 throughout, or tensor-core (TF32 x3) correction")
     ap.add_argument("--n", type=int, default=256, help="split-square grid size (256: 131,072 triangles)")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle accuracy and cpu_baseline legs")
+    ap.add_argument("--workload", default="ocean", choices=["ocean", "ensemble", "serving"])
+    ap.add_argument("--members", type=int, default=64, help="ensemble members")
+    ap.add_argument("--rate", type=float, default=4.0, help="serving: arrivals per second")
+    ap.add_argument("--duration", type=float, default=30.0, help="serving: seconds of arrivals")
+    ap.add_argument("--tri-lo", type=float, default=5e3)
+    ap.add_argument("--tri-hi", type=float, default=2e5)
+    ap.add_argument("--steps-lo", type=int, default=100)
+    ap.add_argument("--steps-hi", type=int, default=500)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--chunk", type=int, default=50, help="serving: max steps between scheduling points")
+    ap.add_argument("--no-serving", action="store_true", help="skip the short serving leg of the ocean workload")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch shape instead of autotuning it per mode")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -251,13 +480,21 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
+    if args.workload != "ocean":
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        line = bench_ensemble(args, world) if args.workload == "ensemble" else bench_serving(args, world)
+        if rank == 0:
+            print(json.dumps(line))
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     w, dps, res, clk, stream, flush = run_ours(args, rank, world)
     head = args.precision
-    other = "fp64" if head == "mixed" else "mixed"
+    others = [k for k in res if k != head]
     acc, acc_steps = ({}, 0) if args.no_oracle else accuracy(w, res)
     units = dps * args.steps * world
     value = units / (res[head]["total_ms"] / 1e3)
-    other_value = units / (res[other]["total_ms"] / 1e3)
+    rate = {k: units / (res[k]["total_ms"] / 1e3) for k in res}
     e2e_s, e2e_bytes = e2e(w, res, head, max(3, args.steps // 2), stream)
     e2e_steps = max(3, args.steps // 2)
     pk = peaks()
@@ -268,15 +505,16 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "DOF-stage/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res[head]["total_ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if head == "mixed" else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"mixed": "f64+f32", "fp64": "f64", "tf32": "f64+f32+tf32"}[head],
         "data": "synthetic",
         "config": {"workload": workload, "triangles": len(w["tri"]), "dof_stage_per_step": dps,
                    "precision": head, "l2": "flushed between timed steps (256 MB write)",
                    "replicas": world},
-        head: {"value": value, "rel_l2_vs_oracle": acc.get(head), "oracle_steps": acc_steps},
-        other: {"value": other_value, "ms_per_step": res[other]["total_ms"] / args.steps,
-                "rel_l2_vs_oracle": acc.get(other), "oracle_steps": acc_steps},
-        "mixed_over_fp64": (value / other_value) if head == "mixed" else (other_value / value),
+        "modes": {k: {"value": rate[k], "ms_per_step": res[k]["total_ms"] / args.steps,
+                      "rel_l2_vs_oracle": acc.get(k), "oracle_steps": acc_steps,
+                      "launch_shape": res[k]["shape"]} for k in res},
+        "mixed_over_fp64": rate["mixed"] / rate["fp64"],
+        "tf32_over_fp64": rate["tf32"] / rate["fp64"],
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in fams.items()},
         "dominant_kernel": dom,
         "gpu_launches": int(res[head]["launches"]),
@@ -285,6 +523,14 @@ def main():
                 "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
     }
     line["roofline"] = roofline(w, res[head], dom, args.steps, pk, head)
+    if not args.no_serving:
+        r = serving_run(rate=3.0, duration=8.0, tri_lo=5e3, tri_hi=1e5, steps_lo=100, steps_hi=300, budget_gb=150.0,
+                        chunk=50, warmup=args.warmup)
+        line["serving"] = {"p50_s": r["p50_s"], "p99_s": r["p99_s"], "value": r["value"], "unit": "DOF-stage/s",
+                           "requests": r["requests"], "offered_dof_stage_per_s": r["offered_dof_stage_per_s"],
+                           "rebuild_s": r["rebuild_s"], "makespan_s": r["makespan_s"],
+                           "workload": "Poisson 3/s for 8 s, triangles log-uniform [5k, 100k], steps U[100, 300], "
+                                       "p in {1..4} 40/30/20/10, mixed, wall clock end to end"}
     if rank == 0 and not args.no_oracle:
         sec = oracle_rate(w, 1, 0)
         line["cpu_baseline"] = {"value": dps / sec, "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
@@ -304,13 +550,20 @@ def roofline(w, r, dom, steps, pk, head):
     ms, n = r["prof"][dom]
     if n == 0:
         return None
-    f = rl.family_flops(w["orders"], dom)
+    f = rl.family_flops(w["orders"], dom, mode=head)
     if f is None:
         return None
     per_launch_s = ms / n / 1e3
     launches_per_step = n / steps
     achieved = f / launches_per_step / per_launch_s / 1e12
     pipe = rl.pipe_of(dom, head)
+    if pipe == "tensor":
+        bf16 = pk.get("bf16_tflops_sustained")
+        peak = bf16 * rl.TF32_OVER_BF16 if bf16 else 1700.0 * rl.TF32_OVER_BF16
+        note = ("dense TF32 = measured sustained BF16 (MEASURED_PEAKS.json) x 1.1/2.25 (nominal ratio)" if bf16
+                else "dense TF32 = fallback 1.7 PFLOP/s sustained BF16 x 1.1/2.25")
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom, "pipe": pipe, "flops_per_step": f, "peak_source": note}
     peak = rl.FP64_PEAK_TFLOPS if pipe == "fp64" else rl.FP32_PEAK_TFLOPS
     note = ("FP64 pipe, 152 SMs x 4 flop/clk x 2.07 GHz (nominal; measured DFMA loop 1.19 TFLOP/s at 1.92 GHz)"
             if pipe == "fp64" else "FP32 pipe, 152 SMs x 256 flop/clk x 2.07 GHz (nominal; measured FFMA loop 74.6 "

@@ -53,6 +53,10 @@ extern "C" {
  * base modes) is FP64 in every mode. */
 #define SWE_PREC_FP64 0       /* correction in FP64 as well                          */
 #define SWE_PREC_MIXED_FP32 1 /* correction arithmetic and storage in FP32           */
+#define SWE_PREC_MIXED_TF32 2 /* as MIXED_FP32, but the momentum volume terms of the
+                               * correction (the G contractions of Eq. 13) run on the
+                               * tensor cores: every FP32 operand split into two TF32
+                               * parts, three partial products, FP32 accumulation   */
 
 typedef struct swe_ctx swe_ctx; /* opaque */
 
@@ -66,10 +70,17 @@ typedef struct {
   double tide_period; /*   + phase); period <= 0 gives the constant xi_hat = amp     */
   double tide_phase;
   void* cuda_stream;  /* cudaStream_t to run on; NULL = a stream the library creates */
+  /* source terms of Eq. (5) (zero by default): bottom friction -tau_bf u with
+   * tau_bf = fric_lin H + fric_quad |u| evaluated from the element means of H
+   * and u (Sect. 3; the paper's setups use fric_lin = 1e-4 and fric_quad =
+   * 0.009), and Coriolis f_c (V, -U).  fric_* >= 0, f_c finite, else -1. */
+  double fric_lin;
+  double fric_quad;
+  double f_c;
 } swe_params;
 
 /* Fill *p with defaults: g = 9.81, cfl = 0.1, h_min = 1e-8, rk_order = 2,
- * FP64, no tide, library stream. */
+ * FP64, no tide, no friction or Coriolis, library stream. */
 void swe_default_params(swe_params* p);
 
 /* Create a context on the current CUDA device.  *out is set on success. */
@@ -204,10 +215,52 @@ int swe_reference_tensors(double* D, double* G, double* T);
  * npts in 1..8; host pointers.  Needs no device. */
 int swe_edge_table(int npts, double* s, double* w, double* B);
 
+/* Shared-memory image of the constant tensor-core operands of the
+ * SWE_PREC_MIXED_TF32 volume contraction for K = 6, 10 or 15 modes (the paper
+ * has no counterpart: it is the GB300 layout of the G_k tensors of Eq. 13).
+ * With P = K(K+1)/2 symmetric pairs (i <= j, pair index j(j+1)/2 + i),
+ * RS = 2P and RP = P rounded up to multiples of 32, the image holds
+ *   S part 0, 1 [16][RS]:  row q, column k*P + pair = G_k[q][i][j]
+ *   P part 0, 1 [32][RP]:  row 16k + q, column pair = G_k[q][i][j]
+ * one after another (k = 0: d/dxhat, 1: d/dyhat; zero for the base triples
+ * q, i, j < 3, for structural zeros and in the padding).  The two parts are
+ * TF32 values (10 mantissa bits): part 0 = G rounded to the nearest TF32
+ * value (ties away from zero), part 1 = G - part 0 rounded the same way, so
+ * their sum equals G to within 2^-22 |G|.  An operand of R rows stores
+ * (row r, column c) at float offset
+ *   (c / 32) * 32 R + (r / 8) * 256 + ((c % 32) / 4) * 32 + (r % 8) * 4 + c % 4.
+ * Returns the number of floats (out may be NULL to query it), or SWE_EINVAL
+ * for another K or cap too small.  Host pointer; needs no device. */
+int64_t swe_tc_operand_image(int K, float* out, int64_t cap);
+
+/* Launch shapes (the paper has no counterpart: they tune the GPU kernels to
+ * the mesh, orders and device).  shape[4]:
+ *   [0] resident blocks per SM of the grid-stride base edge and element
+ *       kernels, 0..32 (0: no cap, one block per base_threads units of work)
+ *   [1] threads per block of those kernels, 32..128, a multiple of 32
+ *   [2] threads per block of the base u-solve, 32..256, a multiple of 32
+ *   [3] threads per block of the correction u-solve and edge kernels,
+ *       32..128, a multiple of 32
+ * Defaults {2, 128, 256, 128}.  Results do not depend on the shape (every
+ * unit of work is computed by one thread in the same order).  SWE_EINVAL for
+ * a shape out of range. */
+int swe_get_launch_shape(swe_ctx* ctx, int32_t* shape);
+int swe_set_launch_shape(swe_ctx* ctx, const int32_t* shape);
+
+/* Autotuner: for candidate launch shapes (coordinate descent: blocks per SM
+ * in {1,2,3,4,6,0}, then base threads {64,128}, u-solve threads {128,256},
+ * correction threads {64,128}), runs `steps` CFL steps of the context's own
+ * mesh and state, times them with CUDA events on the context stream, keeps
+ * the fastest shape and restores the state and member times.  shape_out[4]
+ * and ms_out (time per step of the choice) may be NULL.  Needs the state to
+ * stay valid for the trial steps (errors of swe_run are returned). */
+int swe_autotune(swe_ctx* ctx, int steps, int32_t* shape_out, double* ms_out);
+
 /* Per-kernel-family timing (ms, CUDA events on the context stream around
  * each family) accumulated while swe_profile(ctx, 1) is on; swe_run then
  * launches the steps directly instead of replaying its CUDA graph.  Families:
- * usolve, dt, edge_base, edge_corr, elem_corr, elem_base, other, and a last
+ * usolve, dt, edge_base, edge_corr, elem_corr, elem_base, other, vol_tc (the
+ * tensor-core volume contraction of SWE_PREC_MIXED_TF32), and a last
  * entry "kernels" whose launch count is every kernel the library launched
  * since the last swe_profile call (graph replays included).  names (static
  * strings), ms and launches receive up to n entries; returns the number of

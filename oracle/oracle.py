@@ -46,7 +46,8 @@ def build(force: bool = False) -> str:
 
 class _Params(C.Structure):
     _fields_ = [("g", C.c_double), ("cfl", C.c_double), ("h_min", C.c_double), ("rk_order", C.c_int),
-                ("tide_amp", C.c_double), ("tide_period", C.c_double), ("tide_phase", C.c_double)]
+                ("tide_amp", C.c_double), ("tide_period", C.c_double), ("tide_phase", C.c_double),
+                ("fric_lin", C.c_double), ("fric_quad", C.c_double), ("f_c", C.c_double)]
 
 
 def _load():
@@ -151,8 +152,11 @@ def tri_rule(n: int):
 
 
 class Params:
-    def __init__(self, g=9.81, cfl=0.1, h_min=1e-8, rk_order=2, tide_amp=0.0, tide_period=0.0, tide_phase=0.0):
-        self.s = _Params(g, cfl, h_min, rk_order, tide_amp, tide_period, tide_phase)
+    def __init__(self, g=9.81, cfl=0.1, h_min=1e-8, rk_order=2, tide_amp=0.0, tide_period=0.0, tide_phase=0.0,
+                 fric_lin=0.0, fric_quad=0.0, f_c=0.0):
+        """fric_lin, fric_quad: bottom friction tau_bf = fric_lin H + fric_quad |u| from the
+        element means (Sect. 3; the paper's setups use 1e-4 H and 0.009 |u|); f_c: Coriolis."""
+        self.s = _Params(g, cfl, h_min, rk_order, tide_amp, tide_period, tide_phase, fric_lin, fric_quad, f_c)
 
     @property
     def g(self):

@@ -361,6 +361,9 @@ typedef struct {
   double g, cfl, h_min;
   int rk_order;
   double tide_amp, tide_period, tide_phase;
+  /* source terms of Eq. (5): bottom friction tau_bf = fric_lin H + fric_quad |u|
+   * (the linear and the quadratic law of the paper's setups) and Coriolis f_c */
+  double fric_lin, fric_quad, f_c;
 } or_params;
 
 #define C_(c, f, i, e, ne) (c)[((int64_t)(f) * KMAX + (i)) * (ne) + (e)]
@@ -665,6 +668,12 @@ int or_rhs(const or_mesh* m, const or_params* P, const double* c, double t, doub
     }
     /* fields vanish beyond K; h_b keeps its three P1 modes even when K = 1 */
     int Kx = K < 3 ? 3 : K;
+    /* bottom friction coefficient from the element means (Sect. 3): H and |u|
+     * of the piecewise constant part; mode 0 of a field is its mean times
+     * sqrt|Omega_e| */
+    double rA = 1.0 / sqrt(m->area[e]);
+    double Hm = (xi[0] + hb[0]) * rA, um = uu[0] * rA, vm = vv[0] * rA;
+    double tau = P->fric_lin * Hm + P->fric_quad * sqrt(um * um + vm * vm);
     double r[3][KMAX];
     memset(r, 0, sizeof r);
     /* volume terms (A, grad phi_q) and source (r, phi_q) */
@@ -683,8 +692,10 @@ int or_rhs(const or_mesh* m, const or_params* P, const double* c, double t, doub
         }
       }
       if (use_term(part, q < 3)) {
-        r[1][q] += g * m->dhb[2 * e] * xi[q];
-        r[2][q] += g * m->dhb[2 * e + 1] * xi[q];
+        /* (r, phi_q) of Eq. (5); tau_bf and f_c are constant on the element, so
+         * with the orthonormal basis (tau u, phi_q) = tau u_q */
+        r[1][q] += g * m->dhb[2 * e] * xi[q] - tau * uu[q] + P->f_c * V[q];
+        r[2][q] += g * m->dhb[2 * e + 1] * xi[q] - tau * vv[q] - P->f_c * U[q];
       }
     }
     /* edge terms -<A_hat, phi_q> */

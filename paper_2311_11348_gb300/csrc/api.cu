@@ -25,9 +25,12 @@
 namespace swedg {
 static thread_local std::string g_cuda_err;
 static thread_local int64_t* g_launch_counter = nullptr;
+static thread_local const LaunchShape* g_shape = nullptr;
+static const LaunchShape kDefaultShape{2, 128, 256, 128};
 void count_launch(int n) {
   if (g_launch_counter) *g_launch_counter += n;
 }
+const LaunchShape& launch_shape() { return g_shape ? *g_shape : kDefaultShape; }
 int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
   char buf[512];
   snprintf(buf, sizeof buf, "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e), cudaGetErrorString(e), what,
@@ -41,8 +44,8 @@ using namespace swedg;
 
 namespace {
 
-const char* kFamilies[] = {"usolve", "dt", "edge_base", "edge_corr", "elem_corr", "elem_base", "other"};
-enum { F_USOLVE, F_DT, F_EDGEB, F_EDGEC, F_ELEMC, F_ELEMB, F_OTHER, NFAM };
+const char* kFamilies[] = {"usolve", "dt", "edge_base", "edge_corr", "elem_corr", "elem_base", "other", "vol_tc"};
+enum { F_USOLVE, F_DT, F_EDGEB, F_EDGEC, F_ELEMC, F_ELEMB, F_OTHER, F_VOLTC, NFAM };
 
 }  // namespace
 
@@ -54,8 +57,13 @@ struct swe_ctx {
   bool own_stream = false;
   int device = 0;
   std::string err;
-  bool have_mesh = false;
-  bool corr32 = false;
+  bool have_mesh = false;   // a valid host mesh (topology built)
+  bool dirty = true;        // the device data lag the host description
+  bool keep_valid = false;  // keep_c holds the state to restore after the next device build
+  std::vector<double> keep_c;
+  double keep_t = 0.0;
+  bool corr32 = false;  // FP32 correction (both mixed modes)
+  bool tc = false;      // momentum volume terms of the correction on the tensor cores
   // host mesh, caller's element order, oriented counter-clockwise
   int64_t nv = 0, ne = 0;
   std::vector<double> xy, hv;
@@ -78,6 +86,7 @@ struct swe_ctx {
   VelDev vel{};
   EdgeFlux fx{};
   void* rc = nullptr;
+  float* vol = nullptr;  // tensor-core volume terms [32][elements of order >= 2]
   double* d_user = nullptr;
   double* d_user2 = nullptr;
   double* d_dt = nullptr;
@@ -103,13 +112,17 @@ struct swe_ctx {
   // kernel launches issued by the library (graph replays count their kernels)
   int64_t launches = 0;
   int64_t dev_bytes = 0;  // device memory held by the context
+  LaunchShape shape = kDefaultShape;
 };
 
 // Route count_launch() of the kernel launchers to this context while an API
 // call runs.
 struct LaunchScope {
-  LaunchScope(swe_ctx* c) { g_launch_counter = c ? &c->launches : nullptr; }
-  ~LaunchScope() { g_launch_counter = nullptr; }
+  LaunchScope(swe_ctx* c) {
+    g_launch_counter = c ? &c->launches : nullptr;
+    g_shape = c ? &c->shape : nullptr;
+  }
+  ~LaunchScope() { g_launch_counter = nullptr; g_shape = nullptr; }
 };
 
 static int fail(swe_ctx* c, int code, const char* fmt, ...) {
@@ -447,6 +460,11 @@ static int build_device(swe_ctx* ctx) {
   const int64_t nrc = ne - ctx->G.start[2];
   if ((rc = dalloc(ctx, &ctx->rc, sizeof(double) * 4 * std::max<int64_t>(nrc, 1)))) return cuda_err(ctx, rc);
   cudaMemset(ctx->rc, 0, sizeof(double) * 4 * std::max<int64_t>(nrc, 1));
+  ctx->vol = nullptr;
+  if (ctx->tc) {
+    if ((rc = dalloc(ctx, &ctx->vol, sizeof(float) * 32 * std::max<int64_t>(nrc, 1)))) return cuda_err(ctx, rc);
+    cudaMemset(ctx->vol, 0, sizeof(float) * 32 * std::max<int64_t>(nrc, 1));
+  }
   if ((rc = dalloc(ctx, &ctx->d_user, sizeof(double) * 3 * KMAX * ne)) ||
       (rc = dalloc(ctx, &ctx->d_user2, sizeof(double) * 3 * KMAX * ne)))
     return cuda_err(ctx, rc);
@@ -464,20 +482,22 @@ static int build_device(swe_ctx* ctx) {
   cudaMemset(ctx->d_status, 0, sizeof(unsigned));
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_err(ctx, cuda_fail(e, "build_device", __FILE__, __LINE__));
-  ctx->have_mesh = true;
   return 0;
 }
 
 // ------------------------------------------------------------------ stages
 static Phys phys(const swe_ctx* ctx) {
-  return Phys{ctx->prm.g, ctx->prm.h_min, ctx->prm.tide_amp, ctx->prm.tide_period, ctx->prm.tide_phase};
+  const swe_params& p = ctx->prm;
+  return Phys{p.g, p.h_min, p.tide_amp, p.tide_period, p.tide_phase, p.fric_lin, p.fric_quad, p.f_c,
+              (p.fric_lin != 0.0 || p.fric_quad != 0.0 || p.f_c != 0.0) ? 1 : 0};
 }
 
 static int usolve_all(swe_ctx* ctx, StateDev in) {
   ProfScope ps(ctx, F_USOLVE);
   const Phys ph = phys(ctx);
   CK(launch_usolve_base(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status));
-  if (ctx->corr32) CK(corr32::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
+  if (ctx->tc) CK(corrtc::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
+  else if (ctx->corr32) CK(corr32::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
   else CK(corr64::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
   return 0;
 }
@@ -503,7 +523,8 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
   {
     ProfScope ps(ctx, F_USOLVE);
     CK(launch_usolve_base(A, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status));
-    if (ctx->corr32) CK(corr32::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
+    if (ctx->tc) CK(corrtc::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
+    else if (ctx->corr32) CK(corr32::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
     else CK(corr64::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
   }
   if (conc) {
@@ -529,12 +550,20 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
   if (!stg.base_only) {
     {
       ProfScope ps(ctx, F_EDGEC);
-      if (ctx->corr32) CK(corr32::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+      if (ctx->tc) CK(corrtc::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+      else if (ctx->corr32) CK(corr32::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
       else CK(corr64::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+    }
+    if (ctx->tc) {
+      ProfScope ps(ctx, F_VOLTC);
+      CK(corrtc::launch_vol_tc(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->vol, ctx->d_status));
     }
     {
       ProfScope ps(ctx, F_ELEMC);
-      if (ctx->corr32)
+      if (ctx->tc)
+        CK(corrtc::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
+                                    ctx->vol));
+      else if (ctx->corr32)
         CK(corr32::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc));
       else
         CK(corr64::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc));
@@ -587,6 +616,7 @@ static int read_status(swe_ctx* ctx, bool check_state) {
   CU(cudaMemcpyAsync(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   if (st) CU(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
+  if (st & ST_TIMEOUT) return fail(ctx, SWE_ETIMEOUT, "a tensor-core wait ran out");
   if (st & ST_NONFINITE) return fail(ctx, SWE_ENONFINITE, "non-finite value in the state");
   if (st & ST_DEPTH) return fail(ctx, SWE_EDEPTH, "an element mean depth fell to or below h_min");
   return 0;
@@ -630,10 +660,14 @@ int swe_create(swe_ctx** out, const swe_params* params) {
   if (!out || !params) { g_create_err = "swe_create: NULL argument"; return SWE_EINVAL; }
   *out = nullptr;
   if (params->rk_order != 2 && params->rk_order != 3) { g_create_err = "rk_order must be 2 or 3"; return SWE_EINVAL; }
-  if (params->precision != SWE_PREC_FP64 && params->precision != SWE_PREC_MIXED_FP32) {
+  if (params->precision != SWE_PREC_FP64 && params->precision != SWE_PREC_MIXED_FP32 &&
+      params->precision != SWE_PREC_MIXED_TF32) {
     g_create_err = "unknown precision mode"; return SWE_EINVAL;
   }
   if (!(params->g > 0.0) || !(params->cfl > 0.0)) { g_create_err = "g and cfl must be positive"; return SWE_EINVAL; }
+  if (!(params->fric_lin >= 0.0) || !(params->fric_quad >= 0.0) || !std::isfinite(params->f_c)) {
+    g_create_err = "friction coefficients must be >= 0 and f_c finite"; return SWE_EINVAL;
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
@@ -644,7 +678,8 @@ int swe_create(swe_ctx** out, const swe_params* params) {
   swe_ctx* ctx = new swe_ctx;
   ctx->prm = *params;
   ctx->device = dev;
-  ctx->corr32 = params->precision == SWE_PREC_MIXED_FP32;
+  ctx->corr32 = params->precision == SWE_PREC_MIXED_FP32 || params->precision == SWE_PREC_MIXED_TF32;
+  ctx->tc = params->precision == SWE_PREC_MIXED_TF32;
   if (params->cuda_stream) {
     ctx->stream = (cudaStream_t)params->cuda_stream;
   } else {
@@ -677,6 +712,13 @@ int swe_create(swe_ctx** out, const swe_params* params) {
   upload_base_tables();
   corr64::upload_tables();
   corr32::upload_tables();
+  corrtc::upload_tables();
+  if (corrtc::upload_tc_tables() != 0) {
+    g_create_err = "tensor-core operand upload failed";
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return SWE_ECUDA;
+  }
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     g_create_err_s = std::string("table upload failed: ") + cudaGetErrorString(e);
@@ -731,42 +773,64 @@ int swe_set_mesh(swe_ctx* ctx, int64_t nv, const double* xy, int64_t ne, const i
   ctx->nmem = 1;
   int rc = build_topology(ctx);
   if (rc) { ctx->have_mesh = false; return rc; }
-  return build_device(ctx);
+  ctx->have_mesh = true;
+  ctx->dirty = true;
+  ctx->keep_valid = false;
+  std::vector<double>().swap(ctx->keep_c);
+  return 0;
 }
 
-// keep the state across a rebuild through the caller layout
-static int rebuild_keep_state(swe_ctx* ctx) {
-  std::vector<double> c((size_t)3 * KMAX * ctx->ne);
-  double t = 0.0;
-  int rc = swe_get_state(ctx, c.data(), &t);
+// The device data follow the host description lazily: a setter marks the
+// context dirty, keeping the current state in the caller layout when the
+// device holds one, and the first call that needs the device builds it once
+// (so mesh + bathymetry + orders + members cost one build).
+static int mark_dirty_keep_state(swe_ctx* ctx) {
+  if (!ctx->dirty) {
+    ctx->keep_c.resize((size_t)3 * KMAX * ctx->ne);
+    int rc = swe_get_state(ctx, ctx->keep_c.data(), &ctx->keep_t);
+    if (rc) return rc;
+    ctx->keep_valid = true;
+  }
+  ctx->dirty = true;
+  return 0;
+}
+
+static int ensure_built(swe_ctx* ctx) {
+  if (!ctx->dirty) return 0;
+  int rc = build_device(ctx);
   if (rc) return rc;
-  if ((rc = build_device(ctx))) return rc;
-  return swe_set_state(ctx, c.data(), t);
+  ctx->dirty = false;
+  if (ctx->keep_valid) {
+    ctx->keep_valid = false;
+    rc = swe_set_state(ctx, ctx->keep_c.data(), ctx->keep_t);
+    std::vector<double>().swap(ctx->keep_c);
+  }
+  return rc;
 }
 
 int swe_set_bathymetry(swe_ctx* ctx, const double* hb_vertex) {
   if (!ctx || !ctx->have_mesh || !hb_vertex) return fail(ctx, SWE_EINVAL, "swe_set_bathymetry: no mesh or NULL");
   for (int64_t v = 0; v < ctx->nv; ++v)
     if (!std::isfinite(hb_vertex[v])) return fail(ctx, SWE_EINVAL, "bathymetry at vertex %lld is not finite", (long long)v);
+  int rc = mark_dirty_keep_state(ctx);
+  if (rc) return rc;
   ctx->hv.assign(hb_vertex, hb_vertex + ctx->nv);
-  return rebuild_keep_state(ctx);
+  return 0;
 }
 
 int swe_set_orders(swe_ctx* ctx, const int8_t* p) {
   if (!ctx || !ctx->have_mesh || !p) return fail(ctx, SWE_EINVAL, "swe_set_orders: no mesh or NULL");
   for (int64_t e = 0; e < ctx->ne; ++e)
     if (p[e] < 0 || p[e] > 4) return fail(ctx, SWE_EINVAL, "order of element %lld is %d, not in 0..4", (long long)e, (int)p[e]);
-  std::vector<double> c((size_t)3 * KMAX * ctx->ne);
-  double t = 0.0;
-  int rc = swe_get_state(ctx, c.data(), &t);
+  int rc = mark_dirty_keep_state(ctx);
   if (rc) return rc;
   ctx->p_user.assign(p, p + ctx->ne);
-  if ((rc = build_device(ctx))) return rc;
-  return swe_set_state(ctx, c.data(), t);
+  return 0;
 }
 
 int swe_set_state(swe_ctx* ctx, const double* c, double t) {
   if (!ctx || !ctx->have_mesh || !c) return fail(ctx, SWE_EINVAL, "swe_set_state: no mesh or NULL");
+  CK(ensure_built(ctx));
   LaunchScope ls(ctx);
   CK(state_in(ctx, c, 0));
   const std::vector<double> tv((size_t)ctx->nmem, t);
@@ -777,6 +841,7 @@ int swe_set_state(swe_ctx* ctx, const double* c, double t) {
 
 int swe_get_state(swe_ctx* ctx, double* c_out, double* t_out) {
   if (!ctx || !ctx->have_mesh || !c_out) return fail(ctx, SWE_EINVAL, "swe_get_state: no mesh or NULL");
+  CK(ensure_built(ctx));
   LaunchScope ls(ctx);
   CK(state_out(ctx, ctx->st[0], c_out));
   if (t_out) {
@@ -813,6 +878,7 @@ int swe_p1_modes(swe_ctx* ctx, const double* vals, double* modes_out) {
 
 static int rhs_impl(swe_ctx* ctx, const double* c_in, double* out0, double* out1) {
   if (!ctx || !ctx->have_mesh || !c_in || !out0) return fail(ctx, SWE_EINVAL, "swe_rhs: no mesh or NULL");
+  CK(ensure_built(ctx));
   LaunchScope ls(ctx);
   CK(state_in(ctx, c_in, 1));
   Stage s{};
@@ -856,6 +922,7 @@ int swe_rhs_parts(swe_ctx* ctx, const double* c_in, double* base_out, double* co
 
 int swe_rk_step(swe_ctx* ctx, double dt, double* dt_used) {
   if (!ctx || !ctx->have_mesh) return fail(ctx, SWE_EINVAL, "swe_rk_step: no mesh");
+  CK(ensure_built(ctx));
   LaunchScope ls(ctx);
   CK(enqueue_step(ctx, dt));
   if (dt_used) CU(cudaMemcpyAsync(dt_used, ctx->d_dt, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -890,6 +957,7 @@ static int build_graph(swe_ctx* ctx, double dt_fixed) {
 
 int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out) {
   if (!ctx || !ctx->have_mesh || nsteps < 0) return fail(ctx, SWE_EINVAL, "swe_run: no mesh or negative count");
+  CK(ensure_built(ctx));
   LaunchScope ls(ctx);
   if (ctx->use_graph && !ctx->prof && nsteps > 0) {
     if (!ctx->graph || ctx->graph_dt != dt_fixed) CK(build_graph(ctx, dt_fixed));
@@ -914,6 +982,7 @@ int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out) {
 int swe_adapt(swe_ctx* ctx, double theta_up, double theta_down, int p_min, int p_max, int64_t* n_changed,
               int8_t* orders_out) {
   if (!ctx || !ctx->have_mesh) return fail(ctx, SWE_EINVAL, "swe_adapt: no mesh");
+  CK(ensure_built(ctx));
   if (p_min < 0 || p_max > 4 || p_min > p_max || !(theta_down <= theta_up))
     return fail(ctx, SWE_EINVAL, "swe_adapt: need 0 <= p_min <= p_max <= 4 and theta_down <= theta_up");
   LaunchScope ls(ctx);
@@ -933,6 +1002,7 @@ int swe_adapt(swe_ctx* ctx, double theta_up, double theta_down, int p_min, int p
 int swe_run_adaptive(swe_ctx* ctx, int64_t nsteps, int64_t every, double dt_fixed, double theta_up,
                      double theta_down, int p_min, int p_max, double* t_out) {
   if (!ctx || !ctx->have_mesh || nsteps < 0 || every < 1) return fail(ctx, SWE_EINVAL, "swe_run_adaptive: bad arguments");
+  CK(ensure_built(ctx));
   int64_t done = 0;
   while (done < nsteps) {
     const int64_t n = std::min(every, nsteps - done);
@@ -958,18 +1028,16 @@ int swe_set_members(swe_ctx* ctx, int32_t nmembers, const int32_t* member) {
       if (n >= 0 && mv[n] != mv[e])
         return fail(ctx, SWE_EINVAL, "elements %lld and %lld share an edge but not a member", (long long)e, (long long)n);
     }
-  std::vector<double> c((size_t)3 * KMAX * ctx->ne);
-  double t = 0.0;
-  int rc = swe_get_state(ctx, c.data(), &t);
+  int rc = mark_dirty_keep_state(ctx);
   if (rc) return rc;
   ctx->member_user = mv;
   ctx->nmem = nmembers;
-  if ((rc = build_device(ctx))) return rc;
-  return swe_set_state(ctx, c.data(), t);
+  return 0;
 }
 
 int swe_set_member_times(swe_ctx* ctx, const double* t) {
   if (!ctx || !ctx->have_mesh || !t) return fail(ctx, SWE_EINVAL, "swe_set_member_times: no mesh or NULL");
+  CK(ensure_built(ctx));
   CU(cudaMemcpyAsync(ctx->d_t, t, sizeof(double) * ctx->nmem, cudaMemcpyHostToDevice, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   return 0;
@@ -977,6 +1045,7 @@ int swe_set_member_times(swe_ctx* ctx, const double* t) {
 
 int swe_get_member_times(swe_ctx* ctx, double* t_out, double* dt_out) {
   if (!ctx || !ctx->have_mesh || !t_out) return fail(ctx, SWE_EINVAL, "swe_get_member_times: no mesh or NULL");
+  CK(ensure_built(ctx));
   CU(cudaMemcpyAsync(t_out, ctx->d_t, sizeof(double) * ctx->nmem, cudaMemcpyDeviceToHost, ctx->stream));
   if (dt_out) CU(cudaMemcpyAsync(dt_out, ctx->d_dt, sizeof(double) * ctx->nmem, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
@@ -985,12 +1054,14 @@ int swe_get_member_times(swe_ctx* ctx, double* t_out, double* dt_out) {
 
 int swe_memory_bytes(swe_ctx* ctx, int64_t* bytes) {
   if (!ctx || !bytes) return SWE_EINVAL;
+  if (ctx->have_mesh) CK(ensure_built(ctx));
   *bytes = ctx->dev_bytes;
   return 0;
 }
 
 int swe_mass(swe_ctx* ctx, double* m) {
   if (!ctx || !ctx->have_mesh || !m) return fail(ctx, SWE_EINVAL, "swe_mass: no mesh or NULL");
+  CK(ensure_built(ctx));
   LaunchScope ls(ctx);
   CK(launch_mass(ctx->stream, ctx->dm, ctx->st[0].cb, ctx->d_partial, ctx->nred, ctx->d_red));
   CU(cudaMemcpyAsync(m, ctx->d_red, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1000,6 +1071,7 @@ int swe_mass(swe_ctx* ctx, double* m) {
 
 int swe_energy(swe_ctx* ctx, double* en) {
   if (!ctx || !ctx->have_mesh || !en) return fail(ctx, SWE_EINVAL, "swe_energy: no mesh or NULL");
+  CK(ensure_built(ctx));
   LaunchScope ls(ctx);
   CK(usolve_all(ctx, ctx->st[0]));
   CK(launch_energy(ctx->stream, ctx->dm, ctx->G, ctx->corr32, phys(ctx), ctx->st[0], ctx->vel, ctx->d_partial,
@@ -1027,6 +1099,93 @@ int swe_edge_table(int npts, double* s, double* w, double* B) {
     for (int k = 0; k < 3; ++k)
       for (int i = 0; i < KMAX; ++i)
         for (int g = 0; g < npts; ++g) B[(k * KMAX + i) * npts + g] = R.EB[npts][k][i][g];
+  return 0;
+}
+
+int64_t swe_tc_operand_image(int K, float* out, int64_t cap) {
+  const int64_t n = corrtc::tc_operand_image(K, out, cap);
+  return n < 0 ? SWE_EINVAL : n;
+}
+
+static bool shape_ok(const int32_t* v) {
+  return v[0] >= 0 && v[0] <= 32 && v[1] >= 32 && v[1] <= 128 && v[1] % 32 == 0 && v[2] >= 32 && v[2] <= 256 &&
+         v[2] % 32 == 0 && v[3] >= 32 && v[3] <= 128 && v[3] % 32 == 0;
+}
+
+int swe_get_launch_shape(swe_ctx* ctx, int32_t* shape) {
+  if (!ctx || !shape) return SWE_EINVAL;
+  shape[0] = ctx->shape.base_bpsm; shape[1] = ctx->shape.base_threads;
+  shape[2] = ctx->shape.usolve_threads; shape[3] = ctx->shape.corr_threads;
+  return 0;
+}
+
+int swe_set_launch_shape(swe_ctx* ctx, const int32_t* shape) {
+  if (!ctx || !shape || !shape_ok(shape)) return fail(ctx, SWE_EINVAL, "swe_set_launch_shape: shape out of range");
+  ctx->shape = LaunchShape{shape[0], shape[1], shape[2], shape[3]};
+  if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }  // captured with the old shape
+  return 0;
+}
+
+// Coordinate descent over the launch shape: every candidate runs `steps` CFL
+// steps from the same saved state (graph captured first, then timed with CUDA
+// events on the context stream); the fastest is kept, the state and member
+// times are restored.
+int swe_autotune(swe_ctx* ctx, int steps, int32_t* shape_out, double* ms_out) {
+  if (!ctx || !ctx->have_mesh || steps < 1) return fail(ctx, SWE_EINVAL, "swe_autotune: no mesh or steps < 1");
+  CK(ensure_built(ctx));
+  const size_t n = (size_t)3 * KMAX * ctx->ne;
+  double* save = nullptr;
+  CU(cudaMalloc(&save, sizeof(double) * n));
+  std::vector<double> tm((size_t)ctx->nmem);
+  cudaEvent_t a = nullptr, b = nullptr;
+  int rc = swe_get_state(ctx, save, nullptr);
+  if (!rc) rc = swe_get_member_times(ctx, tm.data(), nullptr);
+  if (!rc && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
+    rc = fail(ctx, SWE_ECUDA, "swe_autotune: event creation failed");
+  auto restore = [&]() -> int {
+    int r = swe_set_state(ctx, save, 0.0);
+    return r ? r : swe_set_member_times(ctx, tm.data());
+  };
+  auto measure = [&](const LaunchShape& sh, double* ms) -> int {
+    ctx->shape = sh;
+    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+    int r = restore();
+    if (!r) r = swe_run(ctx, 1, 0.0, nullptr);  // capture and warm up
+    if (r) return r;
+    if (cudaEventRecord(a, ctx->stream) != cudaSuccess) return fail(ctx, SWE_ECUDA, "cudaEventRecord");
+    r = swe_run(ctx, steps, 0.0, nullptr);
+    if (r) return r;
+    if (cudaEventRecord(b, ctx->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess)
+      return fail(ctx, SWE_ECUDA, "cudaEventSynchronize");
+    float f = 0.0f;
+    cudaEventElapsedTime(&f, a, b);
+    *ms = f / steps;
+    return 0;
+  };
+  LaunchShape best = ctx->shape;
+  double best_ms = 0.0;
+  if (!rc) rc = measure(best, &best_ms);
+  const std::vector<int> cand[4] = {{1, 2, 3, 4, 6, 0}, {64, 128}, {128, 256}, {64, 128}};
+  for (int k = 0; k < 4 && !rc; ++k)
+    for (int v : cand[k]) {
+      LaunchShape sh = best;
+      int* f = k == 0 ? &sh.base_bpsm : k == 1 ? &sh.base_threads : k == 2 ? &sh.usolve_threads : &sh.corr_threads;
+      if (*f == v) continue;
+      *f = v;
+      double ms = 0.0;
+      if ((rc = measure(sh, &ms))) break;
+      if (ms < best_ms) { best_ms = ms; best = sh; }
+    }
+  ctx->shape = best;
+  if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+  const int rr = restore();
+  if (!rc) rc = rr;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(save);
+  if (rc) return rc;
+  if (shape_out) swe_get_launch_shape(ctx, shape_out);
+  if (ms_out) *ms_out = best_ms;
   return 0;
 }
 

@@ -95,6 +95,8 @@ struct Stage {
 struct Phys {
   double g, h_min;
   double tide_amp, tide_period, tide_phase;
+  double fric_lin, fric_quad, f_c;  // bottom friction tau = fric_lin H + fric_quad |u| (means), Coriolis
+  int src;                          // any of the three is nonzero
 };
 
 // Mesh topology and geometry on the device (internal order).

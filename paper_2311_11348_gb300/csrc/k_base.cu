@@ -16,9 +16,6 @@
 #include "kernels.h"
 #include "tables.h"
 
-#ifndef BASE_BLOCKS_PER_SM
-#define BASE_BLOCKS_PER_SM 2
-#endif
 
 namespace swedg {
 
@@ -53,7 +50,7 @@ static int g_sm_count = 152;
 void set_sm_count(int n) { g_sm_count = n > 0 ? n : 152; }
 static inline int capped_blocks(int64_t n, int t, int per_sm) {
   const int64_t b = (n + t - 1) / t, cap = (int64_t)g_sm_count * per_sm;
-  return (int)(b < cap ? b : cap);
+  return (int)(per_sm <= 0 || b < cap ? b : cap);
 }
 
 template <typename T>
@@ -192,7 +189,8 @@ int launch_usolve_base(cudaStream_t s, const DevMesh& m, const Groups& G, const 
                        double* ub, float* ub32, unsigned* status) {
   const int64_t n = G.start[2];
   if (n == 0) return 0;
-  k_usolve_base<<<nblocks(n, 256), 256, 0, s>>>(m, n, ph, cb, ub, ub32, status);
+  const int ut = launch_shape().usolve_threads;
+  k_usolve_base<<<nblocks(n, ut), ut, 0, s>>>(m, n, ph, cb, ub, ub32, status);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -368,7 +366,8 @@ __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg
 int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Stage& stg, const double* cb,
                      const double* ub, EdgeFlux fx) {
   if (m.nedge == 0) return 0;
-  k_edge_base<<<capped_blocks(m.nedge, 128, BASE_BLOCKS_PER_SM), 128, 0, s>>>(m, ph, stg, cb, ub, fx.Fb);
+  const LaunchShape& L = launch_shape();
+  k_edge_base<<<capped_blocks(m.nedge, L.base_threads, L.base_bpsm), L.base_threads, 0, s>>>(m, ph, stg, cb, ub, fx.Fb);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -380,7 +379,8 @@ int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Sta
 //   (A_xi, grad phi_q) = grad phi_q . (U_1, V_1) sqrt|Omega|
 //   (A_U , grad phi_q) = d_x phi_q sum_i (U_i u_i + g(xi_i^2/2 + xi_i hb_i))
 //                      + d_y phi_q sum_i U_i v_i          (and alike for V),
-// the source (r, phi_q) = g grad h_b xi_q, and the edge terms are
+// the source (r, phi_q) = g grad h_b xi_q (- tau u_q + f_c V_q, - tau v_q -
+// f_c U_q with bottom friction and Coriolis), and the edge terms are
 // -sum_g F_g phi_q(x_g) over the three edges (sign flipped for the right side).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cbS,
@@ -425,6 +425,18 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
     r[0][q] = gx * U0s + gy * V0s;
     r[1][q] = gx * Axx + gy * Axy + gdx * c[0][q];
     r[2][q] = gx * Ayx + gy * Ayy + gdy * c[0][q];
+  }
+  if (ph.src) {
+    // bottom friction and Coriolis of Eq. (5); tau from the element means of H
+    // and u (Sect. 3), mean = mode 0 / sqrt|Omega| = mode 0 * sqrt 2 / s_e
+    const double ra = 1.4142135623730951 * rs;
+    const double Hm = (c[0][0] + hb[0]) * ra, um = u[0][0] * ra, vm = u[1][0] * ra;
+    const double tau = ph.fric_lin * Hm + ph.fric_quad * sqrt(um * um + vm * vm);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      r[1][q] += ph.f_c * c[2][q] - tau * u[0][q];
+      r[2][q] -= ph.f_c * c[1][q] + tau * u[1][q];
+    }
   }
   // edge terms
 #pragma unroll
@@ -486,7 +498,8 @@ int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Ph
   (void)cfl;
   if (m.ne == 0) return 0;
   (void)corr_fp32;
-  k_elem_base<<<capped_blocks(m.ne, 128, BASE_BLOCKS_PER_SM), 128, 0, s>>>(m, ph, stg, cbS, cbN, cbO, cbO32, ub, fx.Fb, fx.Fbc,
+  const LaunchShape& L = launch_shape();
+  k_elem_base<<<capped_blocks(m.ne, L.base_threads, L.base_bpsm), L.base_threads, 0, s>>>(m, ph, stg, cbS, cbN, cbO, cbO32, ub, fx.Fb, fx.Fbc,
                                                  (const double*)rc, G.start[2]);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());

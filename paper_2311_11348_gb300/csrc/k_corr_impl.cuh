@@ -16,6 +16,10 @@
 //                      correction of the base modes (rc) and the SSP-RK
 //                      update of the higher modes
 //   k_elem_corr_lo     p <= 1 elements touching a correction edge: rc only
+//
+// With CORR_TC defined (k_corr_tc.cu) the volume terms of the momentum rows
+// come from a buffer that the tensor-core contraction k_vol_tc<K> wrote;
+// k_elem_corr then computes only the elevation row's volume term itself.
 #include <cstdio>
 
 #include "kernels.h"
@@ -200,7 +204,8 @@ static int usolve_group(cudaStream_t st, const DevMesh& m, const Groups& G, int 
                         VelDev u, unsigned* status) {
   const int64_t g0 = G.start[p], n = G.start[p + 1] - g0;
   if (n == 0) return 0;
-  k_usolve_corr<K><<<nblocks(n, 128), 128, 0, st>>>(m, g0, n, ph, c, (const T*)c.ch[p], u.ub, u.ub32,
+  const int ct = launch_shape().corr_threads;
+  k_usolve_corr<K><<<nblocks(n, ct), ct, 0, st>>>(m, g0, n, ph, c, (const T*)c.ch[p], u.ub, u.ub32,
                                                     (T*)u.uh[p], status);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
@@ -361,7 +366,8 @@ static int edge_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
                       const Stage& stg, StateDev c, VelDev u, EdgeFlux fx) {
   const int64_t nl = ce.n[PM];
   if (nl == 0) return 0;
-  k_edge_corr<PM><<<nblocks(nl, 128), 128, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc,
+  const int ct = launch_shape().corr_threads;
+  k_edge_corr<PM><<<nblocks(nl, ct), ct, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc,
                                                     (T*)fx.Ff[PM]);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
@@ -436,6 +442,24 @@ __device__ __forceinline__ void volume_q(T (&r)[3], const T (&xi)[K], const T (&
   r[2] = rs * (aV + g * (J1 * Px + J3 * Py));
 }
 
+// the elevation row of volume_q alone
+template <int K, int Q, int KL>
+__device__ __forceinline__ T volume_xi(const T (&Uc)[KL], const T (&Vc)[KL]) {
+  T am = 0;
+  sfor<0, KL>([&](auto i) {
+    if constexpr (dnz(Q, i) && !base2(Q, i)) am += Uc[i] * cD[0][Q][i] + Vc[i] * cD[1][Q][i];
+  });
+  return am;
+}
+
+#ifdef CORR_TC
+#define CORR_VOL_PARAM , const float* __restrict__ vol
+#define CORR_VOL_ARG , vol
+#else
+#define CORR_VOL_PARAM
+#define CORR_VOL_ARG
+#endif
+
 // ---------------------------------------------------------------------------
 // correction element update of one order group (K = K(p), p >= 2).
 // Block = 32 elements x (K-1) warps; warp w computes test mode q = w + 1 of
@@ -452,7 +476,7 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
                                                             const T* __restrict__ chS, const T* __restrict__ chN,
                                                             T* __restrict__ chO, const T* __restrict__ ub,
                                                             const T* __restrict__ uh, EdgeFlux fx,
-                                                            double* __restrict__ rc) {
+                                                            double* __restrict__ rc CORR_VOL_PARAM) {
   const int64_t l = blockIdx.x * 32 + threadIdx.x;
   if (l >= n) return;
   const int q = threadIdx.y + 1;
@@ -487,9 +511,18 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
   const T rs = geo[G_RS * ne + e];
   const T g = (T)ph.g;
   T r[3] = {0, 0, 0};
+#ifdef CORR_TC
+  (void)g;
+  sfor<1, K>([&](auto Q) {
+    if (q == Q) r[0] = volume_xi<K, Q, KL>(Uc, Vc);
+  });
+  r[1] = (T)vol[q * nrc + rc_off + l];
+  r[2] = (T)vol[(16 + q) * nrc + rc_off + l];
+#else
   sfor<1, K>([&](auto Q) {
     if (q == Q) volume_q<K, Q, KL>(r, xi, U, V, uc, vc, pp, Uc, Vc, rs, J0, J1, J2, J3, g);
   });
+#endif
   if (q < 3) {
     rc[(0 * 2 + (q - 1)) * nrc + rc_off + l] = (double)r[1];
     rc[(1 * 2 + (q - 1)) * nrc + rc_off + l] = (double)r[2];
@@ -501,6 +534,15 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
   });
   r[1] += geo[G_GDHX * ne + e] * xq;
   r[2] += geo[G_GDHY * ne + e] * xq;
+  if (ph.src) {  // bottom friction (tau from the element means, Sect. 3) and Coriolis of Eq. (5)
+    const T ra = (T)1.4142135623730951 * rs;
+    const T Hm = (xi[0] + geo[G_HB0 * ne + e]) * ra;
+    const T um = ub[0 * ne + e] * ra, vm = ub[3 * ne + e] * ra;  // mode 0 of u, v (layout [2][3][ne])
+    const T tau = (T)ph.fric_lin * Hm + (T)ph.fric_quad * sqrt(um * um + vm * vm);
+    const T uq = uh[(0 * KH + (q - 3)) * n + l], vq = uh[(1 * KH + (q - 3)) * n + l];
+    r[1] += (T)ph.f_c * Vq - tau * uq;
+    r[2] -= (T)ph.f_c * Uq + tau * vq;
+  }
   // edges: every edge of a p >= 2 element is a correction edge
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -534,24 +576,27 @@ static const T* base_u_host(const VelDev& u) {
 
 template <int K>
 static int elem_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, int p, const Phys& ph,
-                      const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc) {
+                      const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx,
+                      void* rc CORR_VOL_PARAM) {
   const int64_t g0 = G.start[p], n = G.start[p + 1] - g0;
   if (n == 0) return 0;
   const int64_t nrc = G.start[5] - G.start[2], rc_off = g0 - G.start[2];
   dim3 blk(32, K - 1);
   k_elem_corr<K><<<(unsigned)((n + 31) / 32), blk, 0, st>>>(m, ce, g0, n, rc_off, nrc, ph, stg, base_c_host(cS),
                                                            (const T*)cS.ch[p], (const T*)cN.ch[p], (T*)cO.ch[p],
-                                                           base_u_host(u), (const T*)u.uh[p], fx, (double*)rc);
+                                                           base_u_host(u), (const T*)u.uh[p], fx,
+                                                           (double*)rc CORR_VOL_ARG);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
 }
 
 int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
-                     const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc) {
-  int r = elem_group<6>(st, m, ce, G, 2, ph, stg, cS, cN, cO, u, fx, rc);
-  if (!r) r = elem_group<10>(st, m, ce, G, 3, ph, stg, cS, cN, cO, u, fx, rc);
-  if (!r) r = elem_group<15>(st, m, ce, G, 4, ph, stg, cS, cN, cO, u, fx, rc);
+                     const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx,
+                     void* rc CORR_VOL_PARAM) {
+  int r = elem_group<6>(st, m, ce, G, 2, ph, stg, cS, cN, cO, u, fx, rc CORR_VOL_ARG);
+  if (!r) r = elem_group<10>(st, m, ce, G, 3, ph, stg, cS, cN, cO, u, fx, rc CORR_VOL_ARG);
+  if (!r) r = elem_group<15>(st, m, ce, G, 4, ph, stg, cS, cN, cO, u, fx, rc CORR_VOL_ARG);
   return r;
 }
 

@@ -32,7 +32,17 @@ struct EdgeFlux {
 void count_launch(int n = 1);
 
 // status bits set by kernels
-enum { ST_DEPTH = 1, ST_NONFINITE = 2 };
+enum { ST_DEPTH = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
+
+// Launch shapes the autotuner chooses (per context; the launchers read the
+// shape of the context whose API call is running).
+struct LaunchShape {
+  int base_bpsm;       // resident blocks per SM of the grid-stride base edge / element kernels (0: uncapped)
+  int base_threads;    // threads per block of those kernels (32..128)
+  int usolve_threads;  // threads per block of the base u-solve (32..256)
+  int corr_threads;    // threads per block of the correction u-solve and edge kernels (32..128)
+};
+const LaunchShape& launch_shape();
 
 // base-path tables (host -> constant memory of the base kernels)
 void upload_base_tables();
@@ -78,5 +88,24 @@ int launch_energy(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp
   }
 SWE_CORR_DECL(corr64)
 SWE_CORR_DECL(corr32)
+
+// FP32 correction whose momentum volume terms run on the tensor cores
+// (k_corr_tc.cu): the same launchers as corr32, elem_corr reads the volume
+// terms that launch_vol_tc wrote to vol[32][elements of order >= 2].
+namespace corrtc {
+void upload_tables();
+int upload_tc_tables();
+int launch_usolve_corr(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u,
+                       unsigned* status);
+int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
+                     const Stage& stg, StateDev c, VelDev u, EdgeFlux fx);
+int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
+                     const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc,
+                     const float* vol);
+int launch_vol_tc(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u,
+                  float* vol, unsigned* status);
+// host: the shared-memory image of the B operands for K = 6, 10, 15 (floats written, or needed when out is NULL)
+int64_t tc_operand_image(int K, float* out, int64_t cap);
+}  // namespace corrtc
 
 }  // namespace swedg

@@ -158,3 +158,51 @@ def shelf_p1234(n: int = 1024):
                 orders=orders_fractions(len(tri), {1: 0.4, 2: 0.3, 3: 0.2, 4: 0.1}, seed=5),
                 ic=ic, bc_tag=boundary_tags(xy, tri, "west"), g=9.81, rk_order=3, cfl=0.1, steps=5000,
                 tide=(1.0, 44714.0, 0.0))
+
+
+# ---------------- many-mesh workloads ----------------
+
+def _member(T: float, seed: int, L: float = 1e5, fractions=None):
+    """one ocean-like member of about T triangles: its own jitter, Fourier
+    bathymetry (50..4000 m), order map and Gaussian hump (1 m, sigma = 5 % of L)"""
+    n = max(2, int(round(math.sqrt(T / 2.0))))
+    xy, tri = split_square_mesh(n, L, jitter=0.2, seed=seed)
+    hv = fourier_bathymetry(xy, L, seed=seed + 1)
+    orders = orders_fractions(len(tri), fractions or {1: 0.4, 2: 0.3, 3: 0.2, 4: 0.1}, seed=seed + 2)
+    cx, cy = np.random.default_rng(seed + 3).uniform(0.3 * L, 0.7 * L, size=2)
+    sig = 0.05 * L
+    xi_v = np.exp(-((xy[:, 0] - cx) ** 2 + (xy[:, 1] - cy) ** 2) / (2.0 * sig * sig))
+    return dict(xy=xy, tri=tri, hv=hv, orders=orders, xi_vertex=xi_v)
+
+
+def log_uniform_sizes(count: int, lo: float, hi: float, seed: int):
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(math.log(lo), math.log(hi), size=count))
+
+
+def ensemble_members(count: int = 64, lo: float = 8e3, hi: float = 6e5, seed: int = 6):
+    """Batched ensemble: `count` members with triangle counts log-uniform in
+    [lo, hi] (seeded), each an ocean-like member with orders p in {1..4}
+    (40/30/20/10 %).  Each dict has xy, tri, hv, orders and xi_vertex (the
+    initial elevation at the vertices; momenta start at rest)."""
+    sizes = log_uniform_sizes(count, lo, hi, seed)
+    return [_member(T, 1000 * seed + 10 * m) for m, T in enumerate(sizes)]
+
+
+def serving_requests(rate: float, duration: float, lo: float = 5e3, hi: float = 2e6, steps_lo: int = 100,
+                     steps_hi: int = 2000, seed: int = 7):
+    """Poisson arrivals at `rate` per second over `duration` seconds; each
+    request an ensemble-style member of log-uniform [lo, hi] triangles with a
+    step count uniform in [steps_lo, steps_hi].  Returns a list of
+    (arrival offset in s, member dict, steps)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    t = rng.exponential(1.0 / rate)
+    k = 0
+    while t < duration:
+        T = math.exp(rng.uniform(math.log(lo), math.log(hi)))
+        steps = int(rng.integers(steps_lo, steps_hi + 1))
+        out.append((t, _member(T, 7000 + 10 * k), steps))
+        t += rng.exponential(1.0 / rate)
+        k += 1
+    return out

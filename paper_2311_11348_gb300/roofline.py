@@ -12,9 +12,14 @@ unit" of the roofline that bench.py reports:
   edge_base   edge                         FP64             EDGE_BASE
   elem_base   element                      FP64             ELEM_BASE
   edge_corr   edge with max(p_L,p_R) >= 2  corr type        edge_corr_flops(K_L, K_R, pmax)
-  elem_corr   element p >= 2               corr type        elem_corr_flops(K)
+  elem_corr   element p >= 2               corr type        elem_corr_flops(K, tc)
+  vol_tc      element p >= 2               TF32 tensor      vol_tc_flops(K)
 
-"corr type" is FP64 in the FP64 mode and FP32 in the mixed mode.
+"corr type" is FP64 in the FP64 mode and FP32 in both mixed modes.  In the
+tensor-core mode ("tf32") elem_corr leaves the momentum volume terms to
+vol_tc, whose count is the MMA work it issues: three TF32 passes (head x
+head, tail x head, head x tail) of the U, V (N = 16) and P (N = 32) GEMMs over
+the padded reduction lengths.
 """
 from __future__ import annotations
 
@@ -28,6 +33,8 @@ SM_MAX_GHZ = 2.07
 FP64_PEAK_TFLOPS = SM_COUNT * 4 * SM_MAX_GHZ / 1e3
 # FP32 pipe: 128 FMA = 256 flop per clock per SM
 FP32_PEAK_TFLOPS = SM_COUNT * 256 * SM_MAX_GHZ / 1e3
+# dense TF32 : BF16 tensor rate of the part (1.1 : 2.25 PFLOP/s nominal)
+TF32_OVER_BF16 = 1.1 / 2.25
 
 USOLVE_P1 = 92
 EDGE_BASE = 175
@@ -73,20 +80,30 @@ def usolve_flops(K):
     return f
 
 
-def elem_corr_flops(K):
-    """volume contraction (non-base triples), source, edge projections, RK"""
+def elem_corr_flops(K, tc=False):
+    """volume contraction (non-base triples), source, edge projections, RK;
+    with tc the momentum rows' volume terms are vol_tc's"""
     KL = KP[DEG[K - 1] - 1]
-    f = K * 6 + KL * 6  # contravariant coefficients and xi/2 + h_b
+    f = KL * 6 if tc else K * 6 + KL * 6  # contravariant coefficients and xi/2 + h_b
     for q in range(1, K):
         for i in range(K):
             if dnz(q, i) and not (q < 3 and i < 3):
                 f += 4
+            if tc:
+                continue
             inner = sum(1 for j in range(K) if gnz(q, i, j) and not (q < 3 and i < 3 and j < 3))
             f += 8 * inner + (8 if inner else 0)
-        f += 10
+        f += 0 if tc else 10
         if q >= 3:
             f += 4 + 3 * npts(DEG[K - 1]) * (1 + 3 * 2) + 3 * 5
     return f
+
+
+def vol_tc_flops(K):
+    P = K * (K + 1) // 2
+    RS = -(-2 * P // 32) * 32
+    RP = -(-P // 32) * 32
+    return 3 * (2 * 2 * 16 * RS + 2 * 32 * RP)
 
 
 def edge_corr_flops(KL, KR, pm):
@@ -94,7 +111,7 @@ def edge_corr_flops(KL, KR, pm):
     return 12 + N * (2 * 10 * (KL + KR) + 95)
 
 
-def family_flops(orders, fam, nedge=None):
+def family_flops(orders, fam, nedge=None, mode="mixed"):
     """flops per SSP-RK3 step (3 stages) of one kernel family on an order map"""
     p = np.asarray(orders)
     ne = len(p)
@@ -110,7 +127,9 @@ def family_flops(orders, fam, nedge=None):
     if fam == "usolve":
         return st * (n[1] * USOLVE_P1 + n[0] * 6 + sum(n[q] * usolve_flops(KP[q]) for q in (2, 3, 4)))
     if fam == "elem_corr":
-        return st * sum(n[q] * elem_corr_flops(KP[q]) for q in (2, 3, 4))
+        return st * sum(n[q] * elem_corr_flops(KP[q], tc=(mode == "tf32")) for q in (2, 3, 4))
+    if fam == "vol_tc":
+        return st * sum(n[q] * vol_tc_flops(KP[q]) for q in (2, 3, 4))
     if fam == "edge_corr":
         # i.i.d. orders: an edge's pmax is the larger of two independent draws
         frac = np.array(n, float) / max(ne, 1)
@@ -124,7 +143,9 @@ def family_flops(orders, fam, nedge=None):
 
 
 def pipe_of(fam, mode):
-    """which arithmetic pipe bounds a family: 'fp64' or 'fp32'"""
-    if fam in ("edge_corr", "elem_corr") and mode == "mixed":
+    """which arithmetic pipe bounds a family: 'fp64', 'fp32' or 'tensor'"""
+    if fam == "vol_tc":
+        return "tensor"
+    if fam in ("edge_corr", "elem_corr") and mode in ("mixed", "tf32"):
         return "fp32"
     return "fp64"

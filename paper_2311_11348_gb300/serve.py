@@ -1,18 +1,24 @@
 """Serving loop: continuous batching of shallow water simulations on one GPU.
 
 Requests (a mesh, an initial state and a step count) arrive over time.  The
-server keeps every admitted request's state on the device inside one union
-context (ensemble.Ensemble / swe_set_members), so the RK stages of all active
-requests run in shared launches, each request with its own CFL step and time.
-Between chunks of steps it retires finished requests (their state is copied
-out) and admits waiting ones while the device footprint stays within the
-memory budget; the union context is rebuilt on every membership change and
-the continuing requests' states are moved device to device.
+server admits waiting requests while the device footprint stays within the
+memory budget; the requests admitted at one scheduling point form a cohort,
+one union context (ensemble.Ensemble / swe_set_members) in which the RK
+stages of all its requests run in shared launches, each request with its own
+CFL step and time.  All cohorts advance together, chunk by chunk, each from
+its own host thread on its own CUDA streams, so their launches overlap on the
+GPU.  A finished request's state is copied out at once; its cohort is
+compacted (rebuilt with the continuing requests, states moved device to
+device) when requests wait for memory or less than half of it is still live,
+and the two smallest cohorts are merged when there are more than max_cohorts.
+Admitting a request therefore costs one context build of its own cohort, not
+of everything on the GPU.
 
 This module is host-side scheduling only; every step runs in the CUDA library.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
 import time
 
@@ -39,7 +45,7 @@ def device_bytes(meshes, precision):
     edge: geometry, base fluxes and the correction flux buffers of its max
     order; the correction arrays scale with K(p) - 3 at the correction type's
     width (4 bytes in the mixed mode, 8 in FP64)."""
-    corr32 = precision == swedg.PREC_MIXED_FP32
+    corr32 = precision in (swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32)
     ts = 4 if corr32 else 8
     ne = nE = 0
     n = [0] * 5
@@ -64,15 +70,19 @@ def device_bytes(meshes, precision):
             ncl[q] += int((pm == q).sum())
     nm = max(len(meshes), 1)
     nrc = n[2] + n[3] + n[4]
-    b = NGEO * 12 * ne                      # geo + geo32
-    b += ne * (1 + 12 + 4 + 4 + 1)          # p, eedge, perm, member, new orders
-    b += nE * (12 + 4 + 4 + NEGEO * 12)     # eL/eR/einfo, slot, edge member, egeo + egeo32
-    b += 12 * max(nrc, 1) + 4 * sum(ncl)    # element correction-edge slots, correction edge lists
-    b += 3 * ne * (72 + (36 if corr32 else 0)) + sum(3 * ts * 3 * (KP[q] - 3) * n[q] for q in (2, 3, 4))
-    b += ne * (48 + (24 if corr32 else 0)) + sum(ts * 2 * (KP[q] - 3) * n[q] for q in (2, 3, 4))
-    b += 96 * nE + sum(ts * 3 * _npts(q) * ncl[q] for q in (2, 3, 4))
-    b += 32 * max(nrc, 1) + 2 * 8 * 3 * KMAX * ne
-    b += 24 * nm + 4 + 8 * min(1024, max(1, (ne + 255) // 256)) + 16
+    allocs = [NGEO * 8 * ne, ne, 12 * ne, 4 * nE, 4 * nE, 4 * nE, NEGEO * 8 * nE, 4 * nE, 4 * ne,  # geo .. perm
+              NGEO * 4 * ne, NEGEO * 4 * nE, 4 * ne, 4 * nE,                                  # FP32 copies, members
+              12 * max(nrc, 1)] + [4 * ncl[q] for q in (2, 3, 4)]                             # correction edges
+    for _ in range(3):                                                                        # RK states
+        allocs += [72 * ne] + ([36 * ne] if corr32 else []) + [ts * 3 * (KP[q] - 3) * n[q] for q in (2, 3, 4)]
+    allocs += [48 * ne] + ([24 * ne] if corr32 else []) + [ts * 2 * (KP[q] - 3) * n[q] for q in (2, 3, 4)]
+    allocs += [48 * nE, 48 * nE] + [ts * 3 * _npts(q) * ncl[q] for q in (2, 3, 4)]         # fluxes
+    allocs += [32 * max(nrc, 1)]
+    if precision == swedg.PREC_MIXED_TF32:
+        allocs += [32 * 4 * max(nrc, 1)]                                                      # tensor-core volume terms
+    allocs += [8 * 3 * KMAX * ne, 8 * 3 * KMAX * ne, ne, 8 * nm, 8 * nm, 8 * nm, 4,
+               8 * min(1024, max(1, (ne + 255) // 256)), 16]
+    b = sum(a if a > 0 else 16 for a in allocs)  # the library allocates 16 bytes for an empty array
     return b
 
 
@@ -99,92 +109,134 @@ def footprint(req: Request, precision: int) -> int:
     return req.nbytes
 
 
+class Cohort:
+    """one union context over some requests; `live` marks those still running"""
+
+    def __init__(self, reqs, kw, precision, device_resident, keep):
+        self.reqs = list(reqs)
+        self.live = [True] * len(self.reqs)
+        self.nbytes = sum(footprint(r, precision) for r in self.reqs)
+        self.ens = Ensemble([r.mesh for r in self.reqs], **kw)
+        states = [keep.get(r.rid, r.state) for r in self.reqs]
+        if device_resident:
+            import torch
+            states = [x if hasattr(x, "is_cuda") else torch.from_numpy(np.ascontiguousarray(x)).cuda()
+                      for x in states]
+        self.ens.set_states(states, [keep.get(("t", r.rid), 0.0) for r in self.reqs])
+
+    def live_fraction(self):
+        ne = [len(r.mesh["tri"]) for r in self.reqs]
+        return sum(n for n, l in zip(ne, self.live) if l) / max(sum(ne), 1)
+
+
 class Server:
     def __init__(self, budget_bytes: int, precision=swedg.PREC_MIXED_FP32, g=9.81, cfl=0.1, rk_order=3,
-                 max_chunk=50, clock=time.perf_counter, device_resident=True):
+                 max_chunk=50, clock=time.perf_counter, device_resident=True, max_cohorts=8):
         self.budget = budget_bytes
         self.device_resident = device_resident
         self.kw = dict(g=g, cfl=cfl, rk_order=rk_order, precision=precision)
         self.precision = precision
         self.max_chunk = max_chunk
+        self.max_cohorts = max_cohorts
         self.clock = clock
         self.waiting: list[Request] = []
-        self.active: list[Request] = []
+        self.cohorts: list[Cohort] = []
         self.done: list[Request] = []
-        self.union: Ensemble | None = None
         self.dof_stage_updates = 0
         self.rebuilds = 0
+        self.rebuild_s = 0.0    # host time spent building cohort contexts
+        self.launches = 0       # kernels launched by closed cohort contexts
+        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=max_cohorts + 1)
+
+    @property
+    def active(self):
+        return [r for c in self.cohorts for r, l in zip(c.reqs, c.live) if l]
 
     def submit(self, req: Request):
         req.arrival = self.clock() if req.arrival <= 0.0 else req.arrival
         self.waiting.append(req)
 
     def _used(self):
-        return sum(footprint(r, self.precision) for r in self.active)
+        return sum(c.nbytes for c in self.cohorts)
 
-    def _rebuild(self, keep_states):
-        if self.union is not None:
-            self.union.close()
-            self.union = None
-        if not self.active:
-            return
-        self.union = Ensemble([r.mesh for r in self.active], **self.kw)
-        states = [keep_states.get(r.rid, r.state) for r in self.active]
-        if self.device_resident:
-            import torch
-            states = [s if hasattr(s, "is_cuda") else torch.from_numpy(np.ascontiguousarray(s)).cuda() for s in states]
-        times = [keep_states.get(("t", r.rid), 0.0) for r in self.active]
-        self.union.set_states(states, times)
+    def _close(self, c):
+        prof = getattr(c.ens.solver, "profile_read", None) if hasattr(c.ens, "solver") else None
+        if prof is not None:
+            self.launches += int(prof()["kernels"][1])
+        c.ens.close()
+
+    def _build(self, reqs, keep):
+        t0 = self.clock()
+        c = Cohort(reqs, self.kw, self.precision, self.device_resident, keep)
         self.rebuilds += 1
+        self.rebuild_s += self.clock() - t0
+        return c
+
+    def _rebuild(self, cohorts):
+        """one cohort holding the live requests of `cohorts` (states and times kept on the device)"""
+        keep, reqs = {}, []
+        for c in cohorts:
+            states = c.ens.states(device=self.device_resident)
+            t, _ = c.ens.times()
+            for i, r in enumerate(c.reqs):
+                if c.live[i]:
+                    keep[r.rid] = states[i]
+                    keep[("t", r.rid)] = t[i]
+                    reqs.append(r)
+            self._close(c)
+        return self._build(reqs, keep) if reqs else None
 
     def step(self):
-        """One scheduling round: admit, run a chunk, retire.  Returns False when idle."""
-        # admit while the device footprint fits the budget (at least one request)
+        """One scheduling round: admit, run a chunk on every cohort, retire.  Returns False when idle."""
         admitted = []
+        used = self._used()
         while self.waiting:
             r = self.waiting[0]
-            if self.active and self._used() + footprint(r, self.precision) > self.budget:
+            f = footprint(r, self.precision)
+            if (self.cohorts or admitted) and used + f > self.budget:
                 break
             self.waiting.pop(0)
             r.admitted = self.clock()
-            self.active.append(r)
             admitted.append(r)
+            used += f
         if admitted:
-            keep = {}
-            if self.union is not None:
-                states = self.union.states(device=self.device_resident)
-                t, _ = self.union.times()
-                old = [r for r in self.active if r not in admitted]
-                for i, r in enumerate(old):
-                    keep[r.rid] = states[i]
-                    keep[("t", r.rid)] = t[i]
-            self._rebuild(keep)
-        if not self.active:
+            self.cohorts.append(self._build(admitted, {}))
+        active = self.active
+        if not active:
             return False
-        chunk = min(self.max_chunk, min(r.steps - r.done_steps for r in self.active))
-        self.union.run(chunk)
-        for r in self.active:
+        chunk = min(self.max_chunk, min(r.steps - r.done_steps for r in active))
+        list(self.pool.map(lambda c: c.ens.run(chunk), self.cohorts))
+        for r in active:
             r.done_steps += chunk
-            K = np.array([1, 3, 6, 10, 15])[np.asarray(r.mesh["orders"], np.int64)]
+            K = np.array(KP)[np.asarray(r.mesh["orders"], np.int64)]
             self.dof_stage_updates += chunk * self.kw["rk_order"] * 3 * int(K.sum())
-        finished = [r for r in self.active if r.done_steps >= r.steps]
-        if finished:
-            states = self.union.states(device=self.device_resident)
-            t, _ = self.union.times()
-            now = self.clock()
-            for i, r in enumerate(self.active):
-                if r in finished:
+        # retire
+        now = None
+        keep_cohorts = []
+        for c in self.cohorts:
+            fin = [i for i, r in enumerate(c.reqs) if c.live[i] and r.done_steps >= r.steps]
+            if fin:
+                states = c.ens.states(device=self.device_resident)
+                t, _ = c.ens.times()
+                now = self.clock()
+                for i in fin:
+                    r = c.reqs[i]
                     r.result = states[i].cpu().numpy() if hasattr(states[i], "cpu") else states[i]
                     r.t_final = float(t[i])
                     r.finished = now
-            keep = {}
-            for i, r in enumerate(self.active):
-                if r not in finished:
-                    keep[r.rid] = states[i]
-                    keep[("t", r.rid)] = t[i]
-            self.active = [r for r in self.active if r not in finished]
-            self.done.extend(finished)
-            self._rebuild(keep)
+                    c.live[i] = False
+                    self.done.append(r)
+            if not any(c.live):
+                self._close(c)
+            elif fin and (self.waiting or c.live_fraction() < 0.5):
+                keep_cohorts.append(self._rebuild([c]))
+            else:
+                keep_cohorts.append(c)
+        self.cohorts = keep_cohorts
+        while len(self.cohorts) > self.max_cohorts:
+            a, b = sorted(self.cohorts, key=lambda c: c.nbytes)[:2]
+            self.cohorts = [c for c in self.cohorts if c is not a and c is not b]
+            self.cohorts.append(self._rebuild([a, b]))
         return True
 
     def run_until_idle(self):
@@ -195,6 +247,7 @@ class Server:
         return np.array([r.finished - r.arrival for r in self.done])
 
     def close(self):
-        if self.union is not None:
-            self.union.close()
-            self.union = None
+        for c in self.cohorts:
+            self._close(c)
+        self.cohorts = []
+        self.pool.shutdown(wait=True)

@@ -16,6 +16,7 @@ from . import build as _build
 KMAX = 15
 PREC_FP64 = 0
 PREC_MIXED_FP32 = 1
+PREC_MIXED_TF32 = 2
 
 _ERRORS = {-1: "invalid argument", -2: "bad mesh", -3: "depth <= h_min", -4: "non-finite state",
            -5: "CUDA error", -6: "device wait timeout"}
@@ -30,7 +31,8 @@ class SweError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("g", C.c_double), ("cfl", C.c_double), ("h_min", C.c_double), ("rk_order", C.c_int),
                 ("precision", C.c_int), ("tide_amp", C.c_double), ("tide_period", C.c_double),
-                ("tide_phase", C.c_double), ("cuda_stream", C.c_void_p)]
+                ("tide_phase", C.c_double), ("cuda_stream", C.c_void_p), ("fric_lin", C.c_double),
+                ("fric_quad", C.c_double), ("f_c", C.c_double)]
 
 
 _lib = None
@@ -41,7 +43,8 @@ SYMBOLS = ("swe_default_params", "swe_create", "swe_destroy", "swe_last_error", 
            "swe_rhs_parts", "swe_rk_step", "swe_run", "swe_mass", "swe_energy", "swe_reference_tensors",
            "swe_edge_table", "swe_profile", "swe_profile_read", "swe_rhs_p1_noalloc", "swe_adapt",
            "swe_run_adaptive", "swe_set_members", "swe_set_member_times", "swe_get_member_times",
-           "swe_memory_bytes")
+           "swe_memory_bytes", "swe_tc_operand_image", "swe_get_launch_shape", "swe_set_launch_shape",
+           "swe_autotune")
 
 
 def library_path() -> str:
@@ -91,6 +94,7 @@ def load():
     for s in SYMBOLS:
         if s not in ("swe_destroy", "swe_default_params", "swe_last_error"):
             getattr(lib, s).restype = C.c_int
+    lib.swe_tc_operand_image.restype = C.c_int64
     _lib = lib
     return lib
 
@@ -112,6 +116,17 @@ def reference_tensors():
     D = np.zeros((2, KMAX, KMAX)); G = np.zeros((2, KMAX, KMAX, KMAX)); T = np.zeros((KMAX,) * 3)
     lib.swe_reference_tensors(D.ctypes.data_as(C.c_void_p), G.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p))
     return D, G, T
+
+
+def tc_operand_image(K: int):
+    """the shared-memory image of the tensor-core B operands for K modes (host only)"""
+    lib = load()
+    n = lib.swe_tc_operand_image(int(K), None, C.c_int64(0))
+    if n < 0:
+        raise SweError(int(n), "swe_tc_operand_image")
+    out = np.zeros(n, np.float32)
+    lib.swe_tc_operand_image(int(K), out.ctypes.data_as(C.c_void_p), C.c_int64(n))
+    return out
 
 
 def edge_table(npts: int):
@@ -142,12 +157,15 @@ class Solver:
     """One libswedg context (one mesh, one device state)."""
 
     def __init__(self, g=9.81, cfl=0.1, h_min=1e-8, rk_order=2, precision=PREC_FP64, tide=(0.0, 0.0, 0.0),
+                 friction=(0.0, 0.0), f_c=0.0,
                  stream=None):
         self._lib = load()
         p = Params()
         self._lib.swe_default_params(C.byref(p))
         p.g, p.cfl, p.h_min, p.rk_order, p.precision = g, cfl, h_min, rk_order, precision
         p.tide_amp, p.tide_period, p.tide_phase = tide
+        p.fric_lin, p.fric_quad = friction
+        p.f_c = f_c
         p.cuda_stream = stream
         h = C.c_void_p()
         rc = self._lib.swe_create(C.byref(h), C.byref(p))
@@ -260,6 +278,22 @@ class Solver:
     def set_member_times(self, t):
         t = np.ascontiguousarray(t, dtype=np.float64)
         self._ck(self._lib.swe_set_member_times(self.h, t.ctypes.data_as(C.c_void_p)))
+
+    def launch_shape(self):
+        v = np.zeros(4, np.int32)
+        self._ck(self._lib.swe_get_launch_shape(self.h, v.ctypes.data_as(C.c_void_p)))
+        return tuple(int(x) for x in v)
+
+    def set_launch_shape(self, shape):
+        v = np.ascontiguousarray(shape, dtype=np.int32)
+        self._ck(self._lib.swe_set_launch_shape(self.h, v.ctypes.data_as(C.c_void_p)))
+
+    def autotune(self, steps=5):
+        """choose the launch shape by timing trial steps; returns (shape, ms per step)"""
+        v = np.zeros(4, np.int32)
+        ms = C.c_double(0.0)
+        self._ck(self._lib.swe_autotune(self.h, int(steps), v.ctypes.data_as(C.c_void_p), C.byref(ms)))
+        return tuple(int(x) for x in v), ms.value
 
     def memory_bytes(self):
         b = C.c_int64(0)

@@ -142,11 +142,15 @@ class Tri:
         return g @ Ji
 
 
-def brute_force_rhs(msh: Tri, hv, orders, c, u, g, bc_open=None, xi_hat=0.0, nq=12):
+def brute_force_rhs(msh: Tri, hv, orders, c, u, g, bc_open=None, xi_hat=0.0, nq=12, fric_lin=0.0, fric_quad=0.0,
+                    f_c=0.0):
     """Evaluate Eq. (8) with the LF flux by quadrature of the pointwise fields.
 
     c[3,15,ne], u[2,15,ne] (same u_Delta as the scheme).  Edges without a
-    neighbour are land (mirror state) unless listed in bc_open as (e, k)."""
+    neighbour are land (mirror state) unless listed in bc_open as (e, k).
+    Source r of Eq. (5): g xi grad h_b, bottom friction -tau u with tau =
+    fric_lin H + fric_quad |u| evaluated from the element means of H and u
+    (Sect. 3), Coriolis f_c (V, -U)."""
     bc_open = set(bc_open or [])
     ne = msh.ne
     K = [K_OF_P[p] for p in orders]
@@ -174,7 +178,11 @@ def brute_force_rhs(msh: Tri, hv, orders, c, u, g, bc_open=None, xi_hat=0.0, nq=
         P = g * xi * (0.5 * xi + hb)
         A = [(U, V), (U * uu + P, U * vv), (V * uu, V * vv + P)]
         dh = msh.grad_hb(e, hv)
-        r = [np.zeros(0), g * xi * dh[0], g * xi * dh[1]]
+        # element means by quadrature of the pointwise fields
+        Hm = np.sum(w * (xi + hb)) / msh.area[e]
+        um, vm = np.sum(w * uu) / msh.area[e], np.sum(w * vv) / msh.area[e]
+        tau = fric_lin * Hm + fric_quad * np.hypot(um, vm)
+        r = [np.zeros(0), g * xi * dh[0] - tau * uu + f_c * V, g * xi * dh[1] - tau * vv - f_c * U]
         for q in range(k):
             for f in range(3):
                 val = np.sum(w * (A[f][0] * gx[q] + A[f][1] * gy[q]))

@@ -136,6 +136,45 @@ def test_mixed_fp32_correction_accuracy():
     assert abs(s.mass() - m0) <= 1e-13 * math.sqrt(n) * abs(m0)
 
 
+@pytest.mark.parametrize("precision", [swedg.PREC_FP64, swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32])
+def test_friction_and_coriolis(precision):
+    """Bottom friction (tau from the element means, Sect. 3) and Coriolis of
+    Eq. (5): one rhs with inflated coefficients (so that the source terms are a
+    visible part of it) and 100 CFL steps with the paper's tidal-setup values."""
+    w = mixed_workload(seed=8, pmin=0, pmax=4)
+    big = dict(fric_lin=0.05, fric_quad=0.5, f_c=0.02)
+    m = O.Mesh(w["xy"], w["tri"], w["hv"], w["orders"], bc_tag=w["bc_tag"])
+    c = m.project_state(w["ic"])
+    s = swedg.Solver(g=w["g"], cfl=w["cfl"], rk_order=3, precision=precision,
+                     friction=(big["fric_lin"], big["fric_quad"]), f_c=big["f_c"])
+    s.set_mesh(w["xy"], w["tri"], w["bc_tag"])
+    s.set_bathymetry(w["hv"])
+    s.set_orders(w["orders"])
+    s.set_state(c, 0.0)
+    r_o = m.rhs(O.Params(g=w["g"], **big), c)
+    r_0 = m.rhs(O.Params(g=w["g"]), c)
+    assert np.abs(r_o - r_0).max() > 1e-3 * np.abs(r_o).max()
+    r_g = s.rhs(c)
+    tol = 1e-12 if precision == swedg.PREC_FP64 else 5e-6
+    assert rel_l2(r_g, r_o) < tol, rel_l2(r_g, r_o)
+    s.close()
+    real = dict(fric_lin=0.0, fric_quad=0.009, f_c=3.19e-5)
+    s = swedg.Solver(g=w["g"], cfl=w["cfl"], rk_order=3, precision=precision,
+                     friction=(real["fric_lin"], real["fric_quad"]), f_c=real["f_c"])
+    s.set_mesh(w["xy"], w["tri"], w["bc_tag"])
+    s.set_bathymetry(w["hv"])
+    s.set_orders(w["orders"])
+    s.set_state(c, 0.0)
+    s.run(100)
+    c_g, t_g = s.get_state()
+    P = O.Params(g=w["g"], cfl=w["cfl"], rk_order=3, **real)
+    c_o, t_o = m.run(P, c, 0.0, 100)
+    err = rel_l2(c_g, c_o)
+    print("friction + Coriolis, 100 steps, precision", precision, "rel L2", err)
+    assert err < (1e-11 if precision == swedg.PREC_FP64 else 1e-6), err
+    s.close()
+
+
 def test_full_size_ocean_rhs():
     """Full-size workload (131,072 triangles, p in {1,2,3}): one rhs, all outputs."""
     w = inputs.ocean_p123()

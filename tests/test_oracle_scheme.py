@@ -74,6 +74,54 @@ def test_rhs_equals_brute_force_weak_form(case, seed):
     assert np.abs(r - rb).max() <= 1e-12 * max(1.0, np.abs(rb).max())
 
 
+@pytest.mark.parametrize("case", range(3))
+def test_friction_and_coriolis_equal_brute_force_weak_form(case):
+    """Source of Eq. (5) with bottom friction from the element means (Sect. 3):
+    the oracle against quadrature of the pointwise source on tiny meshes,
+    orders 0..4 (coefficients inflated so that the source terms dominate)."""
+    xy, tri = tiny_meshes()[case]
+    rng = np.random.default_rng(40 + case)
+    ne = len(tri)
+    orders = rng.integers(0, 5, size=ne).astype(np.int8)
+    hv = 1.0 + 0.3 * rng.uniform(size=len(xy))
+    g = 9.81
+    m = O.Mesh(xy, tri, hv, orders)
+    geo = m.geometry()
+    c = scale_state_means(random_state(ne, orders, rng), geo["area"])
+    c[1, 0] += 0.4 * np.sqrt(geo["area"])  # a mean flow, so that |u| matters
+    fr = dict(fric_lin=0.7, fric_quad=2.0, f_c=0.9)
+    r, u = m.rhs(O.Params(g=g, **fr), c, t=0.0, with_u=True)
+    r0 = m.rhs(O.Params(g=g), c, t=0.0)
+    assert np.abs(r - r0).max() > 1e-2  # the source terms are exercised
+    msh = dgref.Tri(xy, tri)
+    rb = dgref.brute_force_rhs(msh, hv, orders, c, u, g, **fr)
+    assert np.abs(r - rb).max() <= 1e-12 * max(1.0, np.abs(rb).max())
+
+
+def test_friction_and_coriolis_closed_form_on_a_free_stream():
+    """Uniform flow over a flat bottom: every flux cancels, and the rhs of the
+    mean mode is the pointwise source (-tau u + f_c V, -tau v - f_c U) times
+    sqrt|Omega| with tau = fric_lin H + fric_quad |u| (Eq. 5)."""
+    xy, tri, hv, orders = jittered_mixed(seed=9)
+    H0, xi0, U0, V0 = 3.0, 0.2, 0.5, -0.3
+    hv = np.full(len(xy), H0 - xi0)
+    m = O.Mesh(xy, tri, hv, orders)
+    sa = np.sqrt(m.geometry()["area"])
+    ne = len(tri)
+    c = np.zeros((3, 15, ne))
+    c[0, 0], c[1, 0], c[2, 0] = xi0 * sa, U0 * sa, V0 * sa
+    fl, fq, fc = 1e-4, 0.009, 3.19e-5
+    r = m.rhs(O.Params(g=9.81, fric_lin=fl, fric_quad=fq, f_c=fc), c)
+    u0, v0 = U0 / H0, V0 / H0
+    tau = fl * H0 + fq * np.hypot(u0, v0)
+    inner = np.all(m.neighbours()["bc"] == 0, axis=1)
+    # the fluxes cancel to round-off (1e-12 as in the free-stream pin), the source is ~4e-5
+    assert np.allclose(r[1, 0, inner], (-tau * u0 + fc * V0) * sa[inner], rtol=0, atol=1e-12)
+    assert np.allclose(r[2, 0, inner], (-tau * v0 - fc * U0) * sa[inner], rtol=0, atol=1e-12)
+    assert np.abs((-tau * u0 + fc * V0) * sa).min() > 1e-5
+    assert np.abs(r[0, :, inner]).max() < 1e-12 and np.abs(r[:, 1:, inner]).max() < 1e-12
+
+
 def fv_rhs(xy, tri, hv, means, g):
     """First-order finite volumes with the paper's LF flux (lambda of Eq. 10
     from cell means), pressure g xi (xi/2 + h_b(x_E)) |E| and source

@@ -51,17 +51,35 @@ def test_admission_chunking_and_results(monkeypatch):
     for r in reqs:
         srv.submit(r)
     srv.run_until_idle()
+    srv.close()
     done = {r.rid: r for r in srv.done}
     assert set(done) == {0, 1, 2}
     for r in done.values():
         assert np.all(r.result == r.steps) and r.t_final == r.steps  # every request ran exactly its steps
     runs = [e for e in FakeUnion.log if e[0] == "run"]
-    # 0 and 1 fit the budget together, 2 only after 0 leaves; chunks stop at the first finisher
+    builds = [e for e in FakeUnion.log if e[0] == "build"]
+    # 0 and 1 fit the budget together and form one cohort; the chunk stops at 0's end;
+    # 1's cohort is compacted because 2 waits, and 2 forms its own cohort
     assert runs[0] == ("run", 30, 2)
-    assert runs[1] == ("run", 20, 2)
-    assert runs[2] == ("run", 20, 1)
-    assert sum(n for _, n, _ in runs if True) == 70
+    assert sorted(runs[1:3]) == [("run", 20, 1), ("run", 20, 1)]
+    assert runs[3:] == [("run", 20, 1)]
+    assert builds == [("build", 2), ("build", 1), ("build", 1)]
     assert srv.latencies().shape == (3,)
+
+
+def test_cohorts_merge_beyond_the_limit(monkeypatch):
+    monkeypatch.setattr(serve, "Ensemble", FakeUnion)
+    FakeUnion.log = []
+    srv = serve.Server(budget_bytes=1 << 40, max_chunk=10, clock=lambda: 0.0, device_resident=False, max_cohorts=2)
+    for k in range(4):  # one arrival per scheduling round: four cohorts, merged down to two
+        srv.submit(make_req(k, 50 + k, 100))
+        srv.step()
+        assert len(srv.cohorts) <= 2
+    srv.run_until_idle()
+    srv.close()
+    assert sorted(r.rid for r in srv.done) == [0, 1, 2, 3]
+    for r in srv.done:
+        assert np.all(r.result == r.steps) and r.t_final == r.steps
 
 
 def test_a_request_larger_than_the_budget_still_runs_alone(monkeypatch):
@@ -83,7 +101,9 @@ def test_device_bytes_counts_edges_orders_and_precision():
     b64 = serve.device_bytes([p1], swedg.PREC_FP64)
     assert serve.device_bytes([p1], swedg.PREC_MIXED_FP32) > b64  # FP32 copies of the P1 data
     assert serve.device_bytes([p3], swedg.PREC_FP64) > serve.device_bytes([p3], swedg.PREC_MIXED_FP32) > b64
-    # a union holds the same per-element and per-edge arrays as its members
+    # a union holds the same per-element and per-edge arrays as its members;
+    # only the fixed per-context arrays (and 16-byte empty ones) are shared
     both = serve.device_bytes([p1, p3], swedg.PREC_FP64)
     alone = b64 + serve.device_bytes([p3], swedg.PREC_FP64)
-    assert 0 < alone - both < 200
+    assert 0 < alone - both < 1024
+    assert serve.device_bytes([p3], swedg.PREC_MIXED_TF32) > serve.device_bytes([p3], swedg.PREC_MIXED_FP32)
