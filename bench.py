@@ -306,8 +306,25 @@ def bench_ensemble(args, world):
             om = O.Mesh(m["xy"], m["tri"], m["hv"], m["orders"])
             ref, _ = om.run(O.Params(g=9.81, cfl=0.1, rk_order=3), c0[:, :, ens.e0[small]:ens.e0[small + 1]], 0.0, 2)
             err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        e2e_rate = e2e_bytes = None
+        if name == "mixed":  # end to end through the API: pinned host state in, one step, state out
+            hin = torch.from_numpy(c0).pin_memory()
+            hout = torch.empty_like(hin).pin_memory()
+            ens.solver.set_state(hin, 0.0)
+            ens.run(1)
+            torch.cuda.synchronize()
+            n_e2e = 3
+            t0 = time.perf_counter()
+            for _ in range(n_e2e):
+                ens.solver.set_state(hin, 0.0)
+                ens.solver.set_member_times(np.zeros(ens.n))
+                ens.run(1)
+                ens.solver.get_state(hout)
+            e2e_rate = dps * n_e2e / (time.perf_counter() - t0)
+            e2e_bytes = hin.numel() * 8
+            del hin, hout
         res[name] = dict(total_ms=tot, prof=prof, launches=launches, err=err, build_s=t_build,
-                         bytes=ens.solver.memory_bytes(), shape=shape)
+                         bytes=ens.solver.memory_bytes(), shape=shape, e2e=e2e_rate, e2e_bytes=e2e_bytes)
         ens.close()
     units = dps * args.steps * world
     value = units / (res["mixed"]["total_ms"] / 1e3)
@@ -341,7 +358,8 @@ def bench_ensemble(args, world):
         "tf32_over_fp64": tf32 / fp64,
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in fams.items()},
         "dominant_kernel": dom, "gpu_launches": int(res["mixed"]["launches"]), "clocks": clk,
-        "e2e": None,
+        "e2e": {"value": res["mixed"]["e2e"] * world, "unit": "DOF-stage/s",
+                "h2d_bytes_per_step": res["mixed"]["e2e_bytes"], "d2h_bytes_per_step": res["mixed"]["e2e_bytes"]},
     }
     line["roofline"] = roofline(w, res["mixed"], dom, args.steps, peaks(), "mixed")
     return line

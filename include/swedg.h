@@ -218,17 +218,18 @@ int swe_edge_table(int npts, double* s, double* w, double* B);
 /* Shared-memory image of the constant tensor-core operands of the
  * SWE_PREC_MIXED_TF32 volume contraction for K = 6, 10 or 15 modes (the paper
  * has no counterpart: it is the GB300 layout of the G_k tensors of Eq. 13).
- * With P = K(K+1)/2 symmetric pairs (i <= j, pair index j(j+1)/2 + i),
- * RS = 2P and RP = P rounded up to multiples of 32, the image holds
- *   S part 0, 1 [16][RS]:  row q, column k*P + pair = G_k[q][i][j]
- *   P part 0, 1 [32][RP]:  row 16k + q, column pair = G_k[q][i][j]
- * one after another (k = 0: d/dxhat, 1: d/dyhat; zero for the base triples
- * q, i, j < 3, for structural zeros and in the padding).  The two parts are
- * TF32 values (10 mantissa bits): part 0 = G rounded to the nearest TF32
- * value (ties away from zero), part 1 = G - part 0 rounded the same way, so
- * their sum equals G to within 2^-22 |G|.  An operand of R rows stores
- * (row r, column c) at float offset
- *   (c / 32) * 32 R + (r / 8) * 256 + ((c % 32) / 4) * 32 + (r % 8) * 4 + c % 4.
+ * The reduction runs over coefficient rows i < K of 16 columns j (zero for
+ * j >= K), two rows per chunk of 32 columns; with C = ceil(K/2) chunks per
+ * row set, each of the two parts of the image holds, one after another,
+ *   C chunks [16][32] for d/dxhat:  row q, column 16 (i % 2) + j of chunk i / 2
+ *                                   = G_x[q][i][j]
+ *   C chunks [16][32] for d/dyhat:  the same with G_y
+ *   C chunks [32][32]:              row 16k + q, same columns = G_k[q][i][j]
+ * (zero for the base triples q, i, j < 3 and for structural zeros).  The two
+ * parts are TF32 values (10 mantissa bits): part 0 = G rounded to the nearest
+ * TF32 value (ties away from zero), part 1 = G - part 0 rounded the same way,
+ * so their sum equals G to within 2^-22 |G|.  A chunk of R rows stores (row r,
+ * column c) at float offset (r / 8) * 256 + (c / 4) * 32 + (r % 8) * 4 + c % 4.
  * Returns the number of floats (out may be NULL to query it), or SWE_EINVAL
  * for another K or cap too small.  Host pointer; needs no device. */
 int64_t swe_tc_operand_image(int K, float* out, int64_t cap);

@@ -386,15 +386,18 @@ int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, con
 // projection of the full flux of one correction edge onto test mode Q >= 3:
 //   r_f -= sgn (1/s) sum_g F_g phihat_Q(gamma_k(s_g))
 // ---------------------------------------------------------------------------
-template <int PM, int Q>
+// (q is warp-uniform: one constant-cache broadcast per trace value; a
+// runtime q keeps one copy of this code per pmax and edge instead of one per
+// test mode, which kept the higher-order kernels out of the instruction cache)
+template <int PM>
 __device__ __forceinline__ void project_edge(T (&r)[3], const EdgeFlux& fx, const CorrEdges& ce, int64_t sl, int k,
-                                             bool right, T rs) {
+                                             bool right, T rs, int q) {
   constexpr int N = npts_for(PM), GI = PM - 2;
   const int64_t nl = ce.n[PM];
   const T* Ff = (const T*)fx.Ff[PM];
   const T sg = right ? rs : -rs;
   sfor<0, N>([&](auto g) {
-    const T bq = sg * (right ? cEB[GI][k][Q][N - 1 - g] : cEB[GI][k][Q][g]);
+    const T bq = sg * (right ? cEB[GI][k][q][N - 1 - g] : cEB[GI][k][q][g]);
     sfor<0, 3>([&](auto f) { r[f] += Ff[(f * N + g) * nl + sl] * bq; });
   });
 }
@@ -455,31 +458,40 @@ __device__ __forceinline__ T volume_xi(const T (&Uc)[KL], const T (&Vc)[KL]) {
 #ifdef CORR_TC
 #define CORR_VOL_PARAM , const float* __restrict__ vol
 #define CORR_VOL_ARG , vol
+// orders whose momentum volume terms come from the tensor cores; for K = 6
+// the CUDA-core contraction measured as fast as the tensor-core kernel plus
+// the buffer round trip, so it stays here
+__host__ __device__ constexpr bool tc_vol(int K) { return K >= 10; }
 #else
 #define CORR_VOL_PARAM
 #define CORR_VOL_ARG
+__host__ __device__ constexpr bool tc_vol(int K) { return false; }
 #endif
 
 // ---------------------------------------------------------------------------
 // correction element update of one order group (K = K(p), p >= 2).
-// Block = 32 elements x (K-1) warps; warp w computes test mode q = w + 1 of
-// its lane's element (q is warp-uniform, so every warp runs one branch of
-// compile-time-specialised code).  q = 1, 2: the correction of the base
+// Block = 128 elements of one test mode q: the grid is ordered q-major
+// (blocks 0..nb-1 compute q = 1, the next nb q = 2, ...), so the blocks that
+// run at the same time on an SM mostly share one branch of the
+// compile-time-specialised code -- one branch per test mode does not fit the
+// instruction cache all at once (ncu: no_instruction stalls when the K - 1
+// warps of a block each ran a different q).  q = 1, 2: the correction of the base
 // modes (volume terms with a higher coefficient index) -> rc;  q >= 3: the
 // full volume term, the source g grad h_b xi_q, the projections of the full
 // edge fluxes, and the SSP-RK combination of that higher mode.
 // ---------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges ce, int64_t g0, int64_t n,
+__global__ void __launch_bounds__(128, kF32 ? 3 : 2) k_elem_corr(DevMesh m, CorrEdges ce, int64_t g0, int64_t n,
                                                             int64_t rc_off, int64_t nrc, Phys ph, Stage stg,
                                                             const T* __restrict__ cbS,
                                                             const T* __restrict__ chS, const T* __restrict__ chN,
                                                             T* __restrict__ chO, const T* __restrict__ ub,
                                                             const T* __restrict__ uh, EdgeFlux fx,
                                                             double* __restrict__ rc CORR_VOL_PARAM) {
-  const int64_t l = blockIdx.x * 32 + threadIdx.x;
+  const int64_t nb = (n + 127) / 128;
+  const int q = 1 + (int)(blockIdx.x / nb);
+  const int64_t l = (blockIdx.x % nb) * 128 + threadIdx.x;
   if (l >= n) return;
-  const int q = threadIdx.y + 1;
   const int64_t e = g0 + l, ne = m.ne;
   constexpr int KH = K - 3;
   uint32_t ecs[3];
@@ -511,18 +523,19 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
   const T rs = geo[G_RS * ne + e];
   const T g = (T)ph.g;
   T r[3] = {0, 0, 0};
+  if constexpr (tc_vol(K)) {
 #ifdef CORR_TC
-  (void)g;
-  sfor<1, K>([&](auto Q) {
-    if (q == Q) r[0] = volume_xi<K, Q, KL>(Uc, Vc);
-  });
-  r[1] = (T)vol[q * nrc + rc_off + l];
-  r[2] = (T)vol[(16 + q) * nrc + rc_off + l];
-#else
-  sfor<1, K>([&](auto Q) {
-    if (q == Q) volume_q<K, Q, KL>(r, xi, U, V, uc, vc, pp, Uc, Vc, rs, J0, J1, J2, J3, g);
-  });
+    sfor<1, K>([&](auto Q) {
+      if (q == Q) r[0] = volume_xi<K, Q, KL>(Uc, Vc);
+    });
+    r[1] = (T)vol[q * nrc + rc_off + l];
+    r[2] = (T)vol[(16 + q) * nrc + rc_off + l];
 #endif
+  } else {
+    sfor<1, K>([&](auto Q) {
+      if (q == Q) volume_q<K, Q, KL>(r, xi, U, V, uc, vc, pp, Uc, Vc, rs, J0, J1, J2, J3, g);
+    });
+  }
   if (q < 3) {
     rc[(0 * 2 + (q - 1)) * nrc + rc_off + l] = (double)r[1];
     rc[(1 * 2 + (q - 1)) * nrc + rc_off + l] = (double)r[2];
@@ -550,13 +563,9 @@ __global__ void __launch_bounds__(32 * (K - 1)) k_elem_corr(DevMesh m, CorrEdges
     const bool right = (cs >> 27) & 1;
     const int pm = cs >> 28;
     const int64_t sl = cs & 0x07ffffff;
-    sfor<3, K>([&](auto Q) {
-      if (q == Q) {
-        if (pm == 2) project_edge<2, Q>(r, fx, ce, sl, k, right, rs);
-        else if (pm == 3) project_edge<3, Q>(r, fx, ce, sl, k, right, rs);
-        else project_edge<4, Q>(r, fx, ce, sl, k, right, rs);
-      }
-    });
+    if (pm == 2) project_edge<2>(r, fx, ce, sl, k, right, rs, q);
+    else if (pm == 3) project_edge<3>(r, fx, ce, sl, k, right, rs, q);
+    else project_edge<4>(r, fx, ce, sl, k, right, rs, q);
   }
   const T dt = (T)stage_dt(stg, m.mem[e]), a = (T)stg.a, b = (T)stg.b;
   const T cs3[3] = {xq, Uq, Vq};
@@ -581,8 +590,7 @@ static int elem_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
   const int64_t g0 = G.start[p], n = G.start[p + 1] - g0;
   if (n == 0) return 0;
   const int64_t nrc = G.start[5] - G.start[2], rc_off = g0 - G.start[2];
-  dim3 blk(32, K - 1);
-  k_elem_corr<K><<<(unsigned)((n + 31) / 32), blk, 0, st>>>(m, ce, g0, n, rc_off, nrc, ph, stg, base_c_host(cS),
+  k_elem_corr<K><<<(unsigned)(((n + 127) / 128) * (K - 1)), 128, 0, st>>>(m, ce, g0, n, rc_off, nrc, ph, stg, base_c_host(cS),
                                                            (const T*)cS.ch[p], (const T*)cN.ch[p], (T*)cO.ch[p],
                                                            base_u_host(u), (const T*)u.uh[p], fx,
                                                            (double*)rc CORR_VOL_ARG);

@@ -18,8 +18,7 @@ unit" of the roofline that bench.py reports:
 "corr type" is FP64 in the FP64 mode and FP32 in both mixed modes.  In the
 tensor-core mode ("tf32") elem_corr leaves the momentum volume terms to
 vol_tc, whose count is the MMA work it issues: three TF32 passes (head x
-head, tail x head, head x tail) of the U, V (N = 16) and P (N = 32) GEMMs over
-the padded reduction lengths.
+head, tail x head, head x tail) over the padded K x 16 product blocks.
 """
 from __future__ import annotations
 
@@ -100,10 +99,10 @@ def elem_corr_flops(K, tc=False):
 
 
 def vol_tc_flops(K):
-    P = K * (K + 1) // 2
-    RS = -(-2 * P // 32) * 32
-    RP = -(-P // 32) * 32
-    return 3 * (2 * 2 * 16 * RS + 2 * 32 * RP)
+    """TF32 MMA flops per element: three products (hh, ht, th), four K = 8 steps
+    per 32-column chunk, ceil(K/2) chunks for each of the five product blocks
+    (four with N = 16 test modes, one with N = 32)"""
+    return 3 * 4 * 2 * 8 * (4 * 16 + 32) * ((K + 1) // 2)
 
 
 def edge_corr_flops(KL, KR, pm):
@@ -127,9 +126,9 @@ def family_flops(orders, fam, nedge=None, mode="mixed"):
     if fam == "usolve":
         return st * (n[1] * USOLVE_P1 + n[0] * 6 + sum(n[q] * usolve_flops(KP[q]) for q in (2, 3, 4)))
     if fam == "elem_corr":
-        return st * sum(n[q] * elem_corr_flops(KP[q], tc=(mode == "tf32")) for q in (2, 3, 4))
-    if fam == "vol_tc":
-        return st * sum(n[q] * vol_tc_flops(KP[q]) for q in (2, 3, 4))
+        return st * sum(n[q] * elem_corr_flops(KP[q], tc=(mode == "tf32" and q >= 3)) for q in (2, 3, 4))
+    if fam == "vol_tc":  # orders 3 and 4 (order 2 stays on the CUDA cores)
+        return st * sum(n[q] * vol_tc_flops(KP[q]) for q in (3, 4))
     if fam == "edge_corr":
         # i.i.d. orders: an edge's pmax is the larger of two independent draws
         frac = np.array(n, float) / max(ne, 1)

@@ -24,21 +24,34 @@ def pairs(K):
 
 
 def decode(K, img):
-    P = K * (K + 1) // 2
-    RS = -(-2 * P // 32) * 32
-    RP = -(-P // 32) * 32
+    """the two parts of the image as Gx, Gy [part][16][K][16] (from the U/V
+    operand) and Gp [part][2][16][K][16] (from the pressure operand)"""
+    C = (K + 1) // 2
+    bpart = C * (2 * 16 * 32 + 32 * 32)
+    assert len(img) == 2 * bpart
 
-    def op(base, R, C):
-        out = np.zeros((R, C), np.float32)
-        for r in range(R):
-            for c in range(C):
-                out[r, c] = img[base + (c // 32) * 32 * R + (r // 8) * 256 + ((c % 32) // 4) * 32 + (r % 8) * 4 + c % 4]
-        return out
+    def at(r, c):
+        return (r // 8) * 256 + (c // 4) * 32 + (r % 8) * 4 + c % 4
 
-    S = [op(k * 16 * RS, 16, RS) for k in range(2)]
-    Pp = [op(32 * RS + k * 32 * RP, 32, RP) for k in range(2)]
-    assert len(img) == 32 * RS + 64 * RP
-    return P, S, Pp
+    Gx = np.zeros((2, 16, K, 16), np.float32)
+    Gy = np.zeros((2, 16, K, 16), np.float32)
+    Gp = np.zeros((2, 2, 16, K, 16), np.float32)
+    for part in range(2):
+        base = part * bpart
+        for i in range(K):
+            c, col0 = i // 2, 16 * (i % 2)
+            for q in range(16):
+                for j in range(16):
+                    Gx[part, q, i, j] = img[base + c * 512 + at(q, col0 + j)]
+                    Gy[part, q, i, j] = img[base + (C + c) * 512 + at(q, col0 + j)]
+                    for k in range(2):
+                        Gp[part, k, q, i, j] = img[base + 2 * C * 512 + c * 1024 + at(16 * k + q, col0 + j)]
+        if K % 2:  # the padding row of the last chunk is zero
+            c = K // 2
+            for q in range(16):
+                for j in range(16):
+                    assert img[base + c * 512 + at(q, 16 + j)] == 0
+    return Gx, Gy, Gp
 
 
 def used(q, i, j):
@@ -55,28 +68,24 @@ def used(q, i, j):
 
 @pytest.mark.parametrize("K", [6, 10, 15])
 def test_operand_images_hold_G_split_into_tf32_head_and_tail(lib, K):
-    img = swedg.tc_operand_image(K)
-    P, Sp, Pp = decode(K, img)
+    Gx, Gy, Gp = decode(K, swedg.tc_operand_image(K))
     G = O.tensors()["G"]
-    for a in Sp + Pp:  # every part is a TF32 value: no bits below the 10-bit mantissa
+    for a in (Gx, Gy, Gp):  # every part is a TF32 value: no bits below the 10-bit mantissa
         assert np.all(a.view(np.uint32) & 0x1FFF == 0)
-    S = sum(a.astype(np.float64) for a in Sp)
-    Pm = sum(a.astype(np.float64) for a in Pp)
-    sh = Sp[0]
+    S = [Gx.astype(np.float64).sum(0), Gy.astype(np.float64).sum(0)]
+    Pm = Gp.astype(np.float64).sum(0)
     floor = 1e-14 * np.abs(G).max()  # the library's tables agree with the oracle's to this
     for k in range(2):
+        assert np.array_equal(Pm[k], S[k])  # both operands hold the same values
         for q in range(16):
-            for pr, (i, j) in enumerate(pairs(K)):
-                want = G[k, q, i, j] if (q < K and used(q, i, j)) else 0.0
-                tol = 2.0 ** -21 * abs(want) + floor  # the parts sum to G within 2^-22 |G|
-                assert abs(S[q, k * P + pr] - want) <= tol, (k, q, i, j)
-                assert abs(Pm[16 * k + q, pr] - want) <= tol, (k, q, i, j)
-                # part 0 is G rounded to 10 mantissa bits
-                if want:
-                    assert abs(sh[q, k * P + pr] - want) <= 2.0 ** -11 * abs(want) + floor
-    # padding columns and unused rows are exact zeros
-    assert not np.any(S[:, 2 * P:]) and not np.any(Pm[:, P:])
-    assert not np.any(S[K:]) and not np.any(Pm[K:16]) and not np.any(Pm[16 + K:])
+            for i in range(K):
+                for j in range(16):
+                    want = G[k, q, i, j] if (q < K and j < K and used(q, i, j)) else 0.0
+                    tol = 2.0 ** -21 * abs(want) + floor  # the parts sum to G within 2^-22 |G|
+                    assert abs(S[k][q, i, j] - want) <= tol, (k, q, i, j)
+                    if want:  # part 0 is G rounded to 10 mantissa bits
+                        part0 = (Gx if k == 0 else Gy)[0, q, i, j]
+                        assert abs(part0 - want) <= 2.0 ** -11 * abs(want) + floor
 
 
 @pytest.mark.parametrize("K", [6, 10, 15])
@@ -88,15 +97,9 @@ def test_gemm_decomposition_reproduces_the_volume_contraction(lib, K):
     J = rng.standard_normal((n, 4))
     rs = rng.uniform(0.5, 2.0, n)
     g = 9.81
-    # the G values the images hold (sum of the parts), as a full symmetric tensor
-    P, Sp, Pp = decode(K, swedg.tc_operand_image(K))
-    BS = sum(a.astype(np.float64) for a in Sp)[:K, :2 * P]
-    BP = sum(a.astype(np.float64) for a in Pp)[:, :P]
-    Gm = np.zeros((2, K, K, K))
-    for k in range(2):
-        for pr, (i, j) in enumerate(pairs(K)):
-            Gm[k, :, i, j] = Gm[k, :, j, i] = BS[:, k * P + pr]
-            assert np.array_equal(BP[16 * k:16 * k + K, pr], BS[:, k * P + pr])
+    # the G values the images hold (sum of the parts)
+    Gx, Gy, Gp = decode(K, swedg.tc_operand_image(K))
+    Gm = np.stack([Gx.astype(np.float64).sum(0)[:K, :, :K], Gy.astype(np.float64).sum(0)[:K, :, :K]])
     mask = np.array([[[used(q, i, j) for j in range(K)] for i in range(K)] for q in range(K)])
     assert not np.any(Gm[:, ~mask])
     # direct contraction (non-base triples only), physical gradients through J^-1
@@ -110,20 +113,25 @@ def test_gemm_decomposition_reproduces_the_volume_contraction(lib, K):
                         + g * (J[:, [0]] * Px + J[:, [2]] * Py))
     rV = rs[:, None] * (np.einsum("qij,ei,ej->eq", Gm[0], V, uc) + np.einsum("qij,ei,ej->eq", Gm[1], V, vc)
                         + g * (J[:, [1]] * Px + J[:, [3]] * Py))
-    # the kernel's GEMMs: symmetrised products x the images
+    # the kernel's GEMMs: rows i x 16 columns j of coefficient products against the images
+    def rows(a, b):
+        bb = np.zeros((n, 16))
+        bb[:, :K] = b
+        return (a[:, :, None] * bb[:, None, :]).reshape(n, K * 16)
 
-    def sym(a, b):
-        return np.stack([a[:, i] * b[:, j] + (a[:, j] * b[:, i] if i != j else 0.0) for i, j in pairs(K)], axis=1)
-
-    AU = np.concatenate([sym(U, uc), sym(U, vc)], axis=1)
-    AV = np.concatenate([sym(V, uc), sym(V, vc)], axis=1)
-    # h_b's mean mode stays out of the P GEMM and is added as hb0 sum_i xi_i G_k[q][i][0]
+    BSx = Gx.astype(np.float64).sum(0)[:K].reshape(K, K * 16)
+    BSy = Gy.astype(np.float64).sum(0)[:K].reshape(K, K * 16)
+    BPx = Gp[:, 0].astype(np.float64).sum(0)[:K].reshape(K, K * 16)
+    BPy = Gp[:, 1].astype(np.float64).sum(0)[:K].reshape(K, K * 16)
+    DU = rows(U, uc) @ BSx.T + rows(U, vc) @ BSy.T
+    DV = rows(V, uc) @ BSx.T + rows(V, vc) @ BSy.T
+    # h_b's mean mode stays out of the pressure GEMM and is added as hb0 sum_i xi_i G_k[q][i][0]
     pp_tc = pp.copy()
     pp_tc[:, 0] -= hb[:, 0]
-    AP = sym(xi, pp_tc)
-    DU, DV, DP = AU @ BS.T, AV @ BS.T, AP @ BP.T
-    DP[:, :K] += hb[:, [0]] * np.einsum("qi,ei->eq", Gm[0, :, :, 0], xi)
-    DP[:, 16:16 + K] += hb[:, [0]] * np.einsum("qi,ei->eq", Gm[1, :, :, 0], xi)
+    DPx = rows(xi, pp_tc) @ BPx.T + hb[:, [0]] * np.einsum("qi,ei->eq", Gm[0, :, :, 0], xi)
+    DPy = rows(xi, pp_tc) @ BPy.T + hb[:, [0]] * np.einsum("qi,ei->eq", Gm[1, :, :, 0], xi)
+    DP = np.zeros((n, 32))
+    DP[:, :K], DP[:, 16:16 + K] = DPx, DPy
     gU = rs[:, None] * (DU + g * (J[:, [0]] * DP[:, :K] + J[:, [2]] * DP[:, 16:16 + K]))
     gV = rs[:, None] * (DV + g * (J[:, [1]] * DP[:, :K] + J[:, [3]] * DP[:, 16:16 + K]))
     tol = 1e-9 * max(np.abs(rU).max(), np.abs(rV).max())
