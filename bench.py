@@ -559,6 +559,12 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+# DRAM bytes (read + write) per launch of the base kernels on the default
+# ocean workload (256x256), from the full ncu capture summarised in
+# profiles/ocean_p123_kernels_ncu_full.md (cold cache); None elsewhere
+MEASURED_TRAFFIC = {"edge_base": 28.632576e6 + 6.4e3, "elem_base": 59.157248e6 + 777.216e3}
+
+
 def roofline(w, r, dom, steps, pk, head):
     """Roofline of the dominant kernel family: algorithmic flops per launch
     (roofline.py) over the family's mean CUDA-event time per launch (profiled
@@ -586,8 +592,9 @@ def roofline(w, r, dom, steps, pk, head):
     note = ("FP64 pipe, 152 SMs x 4 flop/clk x 2.07 GHz (nominal; measured DFMA loop 1.19 TFLOP/s at 1.92 GHz)"
             if pipe == "fp64" else "FP32 pipe, 152 SMs x 256 flop/clk x 2.07 GHz (nominal; measured FFMA loop 74.6 "
             "TFLOP/s at 1.92 GHz)")
+    traffic = MEASURED_TRAFFIC.get(dom) if len(w["orders"]) == 131072 and pipe == "fp64" else None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": dom, "pipe": pipe, "flops_per_step": f, "peak_source": note}
+            "traffic": traffic, "kernel": dom, "pipe": pipe, "flops_per_step": f, "peak_source": note}
 
 
 if __name__ == "__main__":

@@ -229,7 +229,8 @@ int swe_edge_table(int npts, double* s, double* w, double* B);
  * parts are TF32 values (10 mantissa bits): part 0 = G rounded to the nearest
  * TF32 value (ties away from zero), part 1 = G - part 0 rounded the same way,
  * so their sum equals G to within 2^-22 |G|.  A chunk of R rows stores (row r,
- * column c) at float offset (r / 8) * 256 + (c / 4) * 32 + (r % 8) * 4 + c % 4.
+ * column c) at float offset (r / 8) * 256 + (r % 8) * 32 + ((c / 4) ^ (r % 8)) * 4
+ * + c % 4 (rows of 128 bytes, 16-byte units XOR-swizzled by the row index).
  * Returns the number of floats (out may be NULL to query it), or SWE_EINVAL
  * for another K or cap too small.  Host pointer; needs no device. */
 int64_t swe_tc_operand_image(int K, float* out, int64_t cap);

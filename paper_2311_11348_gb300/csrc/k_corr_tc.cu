@@ -49,11 +49,16 @@
 // TMEM: 256 columns per CTA, three sets of 64 (D_U 0..15, D_V 16..31, D_P
 // 32..63), summed and read back with tcgen05.ld in the epilogue.
 //
-// Shared-memory operand layout (no swizzle, K-major): core matrices of
-// 8 rows x 16 bytes, row r / column k of a 32-column chunk at float offset
-//   (r / 8) * 256 + (k / 4) * 32 + (r % 8) * 4 + (k % 4)
-// i.e. leading-dimension byte offset 128 (next core matrix along k) and
-// stride-dimension byte offset 1024 (next group of 8 rows).
+// Shared-memory operand layout: K-major with the 128-byte swizzle.  A row of
+// a chunk is 32 floats = 128 bytes; rows are 128 bytes apart, groups of 8 rows
+// 1024 bytes apart (the descriptor's stride-dimension byte offset), and the
+// 16-byte unit u of row r is stored at unit u ^ (r % 8): (row r, column c) at
+// float offset
+//   (r / 8) * 256 + (r % 8) * 32 + (((c / 4) ^ (r % 8)) * 4) + c % 4
+// (chunks start on 1024-byte boundaries, so the XOR matches the address bits
+// the tensor cores swizzle with).  An MMA step k of 8 columns starts 32 bytes
+// further into the rows.  The swizzle spreads a core matrix's rows over all
+// banks; the unswizzled layout measured ~5000 cycles per 32-column chunk.
 //
 // Every mbarrier wait is bounded; a wait that runs out sets ST_TIMEOUT in the
 // status word, skips the result and still frees the CTA's TMEM.
@@ -96,7 +101,9 @@ __host__ __device__ constexpr int tc_boff(int K) {
 }
 constexpr int TC_BTOTAL = tc_bfloats(6) + tc_bfloats(10) + tc_bfloats(15);
 // float offset of (row r, column c) in a chunk of 32 columns
-__host__ __device__ constexpr int tc_at(int r, int c) { return (r / 8) * 256 + (c / 4) * 32 + (r % 8) * 4 + (c % 4); }
+__host__ __device__ constexpr int tc_at(int r, int c) {
+  return (r / 8) * 256 + (r % 8) * 32 + (((c / 4) ^ (r % 8)) * 4) + (c % 4);
+}
 // shared memory of k_vol_tc: A ring, B ring, per-thread U, V, xi rows, barriers + TMEM slot
 constexpr int TC_SMEM = (2 * TC_PARTS * TC_ABUF + TC_BST * TC_PARTS * TC_BSLOT + 3 * TC_W * TC_M) * 4 + 96;
 static_assert((TC_BST + 4) * 8 + 4 <= 96, "barriers and TMEM slot");
@@ -143,10 +150,12 @@ int64_t tc_operand_image(int K, float* out, int64_t cap) {
 // ------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: K-major, no swizzle, LBO 128 B, SBO 1024 B
+// shared-memory matrix descriptor: K-major, 128-byte swizzle (layout type 2),
+// SBO 1024 B between groups of 8 rows; LBO is not used by swizzled K-major
+// layouts whose K step fits in the 128-byte row (encoded as 1)
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46);
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 // instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, M x N
 __host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
@@ -320,7 +329,8 @@ __global__ void __launch_bounds__(TC_M) k_vol_tc(DevMesh m, int64_t g0, int64_t 
   };
   if (t == 0) issue_b(0);
 
-  bool ok = true;
+  // the swizzle XOR acts on address bits 4-9: every chunk must start on 1024 bytes
+  bool ok = (smem_u32(sA) & 1023u) == 0 && (smem_u32(sB) & 1023u) == 0;
   float wv[TC_W];
 #pragma unroll 1
   for (int c = 0; c < NC; ++c) {
@@ -372,8 +382,8 @@ __global__ void __launch_bounds__(TC_M) k_vol_tc(DevMesh m, int64_t g0, int64_t 
       const uint32_t ap = TC_ABUF * 4, bp = TC_BSLOT * 4;  // bytes between the parts
       // the three products accumulate in three TMEM sets (independent MMA chains), summed in the epilogue
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {  // K = 8 per MMA: two core matrices (256 B) along k
-        const uint32_t o = 256u * s, acc = s == 0 ? acc0 : 1u;
+      for (int s = 0; s < 4; ++s) {  // K = 8 per MMA: 32 bytes further into the swizzled rows
+        const uint32_t o = 32u * s, acc = s == 0 ? acc0 : 1u;
         tc_mma(d, tc_desc(a0 + o), tc_desc(b0 + o), idesc, acc);                          // h h
         tc_mma(d + TC_ACC, tc_desc(a0 + o), tc_desc(b0 + bp + o), idesc, acc);            // h t
         tc_mma(d + 2 * TC_ACC, tc_desc(a0 + ap + o), tc_desc(b0 + o), idesc, acc);       // t h

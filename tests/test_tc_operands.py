@@ -30,8 +30,8 @@ def decode(K, img):
     bpart = C * (2 * 16 * 32 + 32 * 32)
     assert len(img) == 2 * bpart
 
-    def at(r, c):
-        return (r // 8) * 256 + (c // 4) * 32 + (r % 8) * 4 + c % 4
+    def at(r, c):  # K-major, 128-byte swizzle: 16-byte unit c/4 of row r at unit (c/4) ^ (r%8)
+        return (r // 8) * 256 + (r % 8) * 32 + (((c // 4) ^ (r % 8)) * 4) + c % 4
 
     Gx = np.zeros((2, 16, K, 16), np.float32)
     Gy = np.zeros((2, 16, K, 16), np.float32)
