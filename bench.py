@@ -88,10 +88,32 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def single_mesh_workload(args):
+    """the single-mesh workload of the run and its label"""
+    if args.workload == "shelf":
+        w = inputs.shelf_p1234(args.n_shelf)
+        n = args.n_shelf
+        return w, (f"shelf_p1234: {n}x{n} split squares ({2 * n * n} triangles), tanh shelf 4000 -> 20 m, "
+                   f"M2 tide on x = 0, p in {{1..4}} 40/30/20/10, SSP-RK3, CFL 0.1")
+    w = inputs.ocean_p123(args.n)
+    return w, (f"ocean_p123: {args.n}x{args.n} split squares ({2 * args.n * args.n} triangles), "
+               f"p in {{1,2,3}} 70/20/10, SSP-RK3, CFL 0.1")
+
+
+def oracle_mesh_params(w):
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    tide = w.get("tide", (0.0, 0.0, 0.0))
+    m = O.Mesh(w["xy"], w["tri"], w["hv"], w["orders"], bc_tag=w.get("bc_tag"))
+    P = O.Params(g=w["g"], cfl=w["cfl"], rk_order=3, tide_amp=tide[0], tide_period=tide[1], tide_phase=tide[2])
+    return m, P
+
+
 def make_solver(w, precision, stream):
     from paper_2311_11348_gb300 import swedg
-    s = swedg.Solver(g=w["g"], cfl=w["cfl"], rk_order=3, precision=precision, stream=stream)
-    s.set_mesh(w["xy"], w["tri"])
+    s = swedg.Solver(g=w["g"], cfl=w["cfl"], rk_order=3, precision=precision, stream=stream,
+                     tide=w.get("tide", (0.0, 0.0, 0.0)))
+    s.set_mesh(w["xy"], w["tri"], w.get("bc_tag"))
     s.set_bathymetry(w["hv"])
     s.set_orders(w["orders"])
     return s
@@ -108,7 +130,7 @@ def run_ours(args, rank, world):
     import torch
     from paper_2311_11348_gb300 import swedg
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-    w = inputs.ocean_p123(args.n)
+    w, _ = single_mesh_workload(args)
     ne = len(w["tri"])
     dps = dofs_per_step(w["orders"])
     stream = torch.cuda.Stream()
@@ -169,13 +191,12 @@ def run_ours(args, rank, world):
 
 def accuracy(w, res, nsteps=2):
     """relative L2 error of nsteps CFL steps against the FP64 oracle (same input)"""
-    sys.path.insert(0, os.path.join(ROOT, "oracle"))
-    import oracle as O
-    m = O.Mesh(w["xy"], w["tri"], w["hv"], w["orders"])
-    P = O.Params(g=w["g"], cfl=w["cfl"], rk_order=3)
+    m, P = oracle_mesh_params(w)
     out = {}
     c0 = res["fp64"]["c0"]
+    t0 = time.perf_counter()
     c_o, t_o = m.run(P, c0, 0.0, nsteps)
+    accuracy.oracle_s_per_step = (time.perf_counter() - t0) / nsteps
     for name in res:
         s = res[name]["solver"]
         s.set_state(c0, 0.0)
@@ -208,10 +229,7 @@ def e2e(w, res, name, steps, stream):
 
 def oracle_rate(w, steps, warmup):
     """the FP64 oracle (single thread) on the same workload: full-mesh RK3 steps"""
-    sys.path.insert(0, os.path.join(ROOT, "oracle"))
-    import oracle as O
-    m = O.Mesh(w["xy"], w["tri"], w["hv"], w["orders"])
-    P = O.Params(g=w["g"], cfl=w["cfl"], rk_order=3)
+    m, P = oracle_mesh_params(w)
     xi_v = w["ic"](w["xy"][:, 0], w["xy"][:, 1])[0]
     c = np.zeros((3, 15, len(w["tri"])))
     c[0, :3] = m.p1_modes(xi_v)
@@ -458,7 +476,8 @@ def main():
                     help="headline mode: FP32 correction, FP64 throughout, or tensor-core (TF32 x3) correction")
     ap.add_argument("--n", type=int, default=256, help="split-square grid size (256: 131,072 triangles)")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle accuracy and cpu_baseline legs")
-    ap.add_argument("--workload", default="ocean", choices=["ocean", "ensemble", "serving"])
+    ap.add_argument("--workload", default="ocean", choices=["ocean", "shelf", "ensemble", "serving"])
+    ap.add_argument("--n-shelf", type=int, default=1024, help="shelf workload grid size (1024: 2,097,152 triangles)")
     ap.add_argument("--members", type=int, default=64, help="ensemble members")
     ap.add_argument("--rate", type=float, default=4.0, help="serving: arrivals per second")
     ap.add_argument("--duration", type=float, default=30.0, help="serving: seconds of arrivals")
@@ -474,13 +493,13 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
-    workload = f"ocean_p123: 256x256 split squares ({2 * args.n * args.n} triangles), p in {{1,2,3}} 70/20/10, SSP-RK3, CFL 0.1"
+    workload = single_mesh_workload(args)[1] if args.workload in ("ocean", "shelf") else args.workload
 
     if args.impl == "reference":
         if rank != 0:
             return
-        w = inputs.ocean_p123(args.n)
-        steps = max(1, min(args.steps, 8))
+        w, _ = single_mesh_workload(args)
+        steps = max(1, min(args.steps, 8 if args.workload != "shelf" else 1))
         warm = min(args.warmup, 1)
         sec = oracle_rate(w, steps, warm)
         dps = dofs_per_step(w["orders"])
@@ -498,7 +517,7 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
-    if args.workload != "ocean":
+    if args.workload in ("ensemble", "serving"):
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         line = bench_ensemble(args, world) if args.workload == "ensemble" else bench_serving(args, world)
         if rank == 0:
@@ -509,7 +528,7 @@ def main():
     w, dps, res, clk, stream, flush = run_ours(args, rank, world)
     head = args.precision
     others = [k for k in res if k != head]
-    acc, acc_steps = ({}, 0) if args.no_oracle else accuracy(w, res)
+    acc, acc_steps = ({}, 0) if args.no_oracle else accuracy(w, res, nsteps=1 if args.workload == "shelf" else 2)
     units = dps * args.steps * world
     value = units / (res[head]["total_ms"] / 1e3)
     rate = {k: units / (res[k]["total_ms"] / 1e3) for k in res}
@@ -541,7 +560,7 @@ def main():
                 "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
     }
     line["roofline"] = roofline(w, res[head], dom, args.steps, pk, head)
-    if not args.no_serving:
+    if not args.no_serving and args.workload == "ocean":
         r = serving_run(rate=3.0, duration=8.0, tri_lo=5e3, tri_hi=1e5, steps_lo=100, steps_hi=300, budget_gb=150.0,
                         chunk=50, warmup=args.warmup)
         line["serving"] = {"p50_s": r["p50_s"], "p99_s": r["p99_s"], "value": r["value"], "unit": "DOF-stage/s",
@@ -550,7 +569,8 @@ def main():
                            "workload": "Poisson 3/s for 8 s, triangles log-uniform [5k, 100k], steps U[100, 300], "
                                        "p in {1..4} 40/30/20/10, mixed, wall clock end to end"}
     if rank == 0 and not args.no_oracle:
-        sec = oracle_rate(w, 1, 0)
+        # the large shelf mesh reuses the oracle step of the accuracy check
+        sec = accuracy.oracle_s_per_step if args.workload == "shelf" else oracle_rate(w, 1, 0)
         line["cpu_baseline"] = {"value": dps / sec, "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
                                 "sample": "1 full-mesh SSP-RK3 step of the single-threaded FP64 C oracle"}
     if rank == 0:

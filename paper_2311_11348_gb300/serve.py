@@ -12,7 +12,8 @@ compacted (rebuilt with the continuing requests, states moved device to
 device) when requests wait for memory or less than half of it is still live,
 and the two smallest cohorts are merged when there are more than max_cohorts.
 Admitting a request therefore costs one context build of its own cohort, not
-of everything on the GPU.
+of everything on the GPU, and that build runs on the host while the running
+cohorts take their next chunk (the new cohort joins at the following one).
 
 This module is host-side scheduling only; every step runs in the CUDA library.
 """
@@ -146,7 +147,7 @@ class Server:
         self.rebuilds = 0
         self.rebuild_s = 0.0    # host time spent building cohort contexts
         self.launches = 0       # kernels launched by closed cohort contexts
-        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=max_cohorts + 1)
+        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=max_cohorts + 2)
 
     @property
     def active(self):
@@ -199,11 +200,17 @@ class Server:
             r.admitted = self.clock()
             admitted.append(r)
             used += f
+        pending = None
         if admitted:
-            self.cohorts.append(self._build(admitted, {}))
+            if self.cohorts:  # build the new cohort on the host while the running ones take their chunk
+                pending = self.pool.submit(self._build, admitted, {})
+            else:
+                self.cohorts.append(self._build(admitted, {}))
         active = self.active
         if not active:
-            return False
+            if pending is not None:
+                self.cohorts.append(pending.result())
+            return bool(self.cohorts)
         chunk = min(self.max_chunk, min(r.steps - r.done_steps for r in active))
         list(self.pool.map(lambda c: c.ens.run(chunk), self.cohorts))
         for r in active:
@@ -233,6 +240,8 @@ class Server:
             else:
                 keep_cohorts.append(c)
         self.cohorts = keep_cohorts
+        if pending is not None:  # the new cohort joins for the next chunk
+            self.cohorts.append(pending.result())
         while len(self.cohorts) > self.max_cohorts:
             a, b = sorted(self.cohorts, key=lambda c: c.nbytes)[:2]
             self.cohorts = [c for c in self.cohorts if c is not a and c is not b]

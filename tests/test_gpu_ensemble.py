@@ -41,8 +41,10 @@ def alone(mesh, c, steps, **kw):
     return out, t, nbytes
 
 
-@pytest.mark.parametrize("precision", [swedg.PREC_FP64, swedg.PREC_MIXED_FP32])
+@pytest.mark.parametrize("precision", [swedg.PREC_FP64, swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32])
 def test_ensemble_member_equals_alone(precision):
+    """(in the tensor-core mode the union puts other members' elements into the same 128-element MMA
+    tiles; every output row of an MMA depends only on its own row of A)"""
     kw = dict(g=9.81, cfl=0.2, rk_order=3, precision=precision, tide=(0.2, 900.0, 0.0))
     specs = [member(8, 2e3, 1, 1, 2), member(14, 5e3, 2, 1, 3, open_west=True), member(5, 1e3, 3, 2, 4)]
     ens = ensemble.Ensemble([m for m, _ in specs], **kw)

@@ -271,6 +271,35 @@ def test_full_size_shelf_rhs_p1234_open_sea():
     s.close()
 
 
+@pytest.mark.parametrize("precision", [swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32])
+def test_dynamic_adaptivity_mixed_modes(precision):
+    """swe_run_adaptive in the mixed modes: the same order decisions as the FP64
+    oracle (no indicator value within 1e-5 of a threshold, far above the mixed
+    modes' error) and the state within 1e-6."""
+    w = mixed_workload(seed=7, pmin=1, pmax=2, open_west=False)
+    up, down, pmin, pmax = 5e-2, 1e-3, 1, 4
+    m, P, s = make_pair(w, precision=precision)
+    c = m.project_state(w["ic"])
+    s.set_state(c, 0.0)
+    dt = 0.25
+    co = c.copy()
+    for rnd in range(3):
+        co, _ = m.run(P, co, 0.0, 10, dt=dt)
+        new, sv, n = m.indicator(co, up, down, pmin, pmax)
+        for th in (up, down):
+            assert np.all(np.abs(sv - th) > 1e-5 * th)
+        co = m.adapt_state(co, new)
+    s.run_adaptive(30, 10, up, down, pmin, pmax, dt_fixed=dt)
+    cg, _ = s.get_state()
+    err = rel_l2(cg, co)
+    print("adaptive, precision", precision, "rel L2", err, "orders", np.bincount(new, minlength=5))
+    assert err < 1e-6, err
+    po, _, _ = m.indicator(co, up, down, pmin, pmax)
+    o2, _ = s.adapt(up, down, pmin, pmax)
+    assert np.array_equal(o2, po)
+    s.close()
+
+
 def test_dynamic_adaptivity_matches_oracle():
     """swe_run_adaptive (indicator every 10 steps, hierarchical order changes)
     against the oracle doing the same: orders bit-exact, state to 1e-11."""
