@@ -43,6 +43,22 @@ from paper_2311_11348_gb300 import inputs  # noqa: E402
 METRIC = "DOF-stage updates/s, mixed vs FP64 at stated L2 error; p50/p99 solve latency"
 
 
+def max_over_ranks(value, world, device="cuda"):
+    """the maximum of a per-rank number over all ranks (the timed region's
+    wall time of the slowest replica); the identity on one rank"""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, max_seconds):
+    """whole-job throughput of N independent replicas: all ranks' units over the slowest rank's time"""
+    return units_per_rank * world / max_seconds
+
+
 def dofs_per_step(orders, stages=3):
     K = np.array([1, 3, 6, 10, 15])[orders.astype(np.int64)]
     return stages * 3 * int(K.sum())
@@ -166,11 +182,7 @@ def run_ours(args, rank, world):
         ms = [a.elapsed_time(b) for a, b in times]
         if name == prec_list[0][0]:
             clk = clocks.stop()
-        tot = sum(ms)
-        if world > 1:
-            t = torch.tensor([tot], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(sum(ms), world)
         # per-family timing (separate profiled pass over the same steps)
         s.set_state(c0, 0.0)
         s.profile(True)
@@ -292,11 +304,7 @@ def bench_ensemble(args, world):
         torch.cuda.synchronize()
         if clk is None:
             clk = clocks.stop()
-        tot = sum(a.elapsed_time(b) for a, b in times)
-        if world > 1:
-            t = torch.tensor([tot], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            tot = float(t.item())
+        tot = max_over_ranks(sum(a.elapsed_time(b) for a, b in times), world)
         ens.solver.set_state(c0, 0.0)
         ens.solver.set_member_times(np.zeros(ens.n))
         ens.solver.profile(True)
@@ -344,10 +352,9 @@ def bench_ensemble(args, world):
         res[name] = dict(total_ms=tot, prof=prof, launches=launches, err=err, build_s=t_build,
                          bytes=ens.solver.memory_bytes(), shape=shape, e2e=e2e_rate, e2e_bytes=e2e_bytes)
         ens.close()
-    units = dps * args.steps * world
-    value = units / (res["mixed"]["total_ms"] / 1e3)
-    fp64 = units / (res["fp64"]["total_ms"] / 1e3)
-    tf32 = units / (res["tf32"]["total_ms"] / 1e3)
+    value = job_rate(dps * args.steps, world, res["mixed"]["total_ms"] / 1e3)
+    fp64 = job_rate(dps * args.steps, world, res["fp64"]["total_ms"] / 1e3)
+    tf32 = job_rate(dps * args.steps, world, res["tf32"]["total_ms"] / 1e3)
     fams = {k: v for k, v in res["mixed"]["prof"].items() if k != "kernels"}
     dom = max(fams, key=lambda k: fams[k][0])
     ne = len(orders)
@@ -444,6 +451,8 @@ def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, c
 def bench_serving(args, world):
     r = serving_run(args.rate, args.duration, args.tri_lo, args.tri_hi, args.steps_lo, args.steps_hi,
                     args.budget_gb, args.chunk, args.warmup)
+    r["makespan_s"] = max_over_ranks(r["makespan_s"], world)
+    r["value"] = r["dof_stage_updates"] / r["makespan_s"]
     line = {
         "metric": METRIC, "value": r["value"] * world, "unit": "DOF-stage/s", "n_gpus": world,
         "steps": r["total_steps"], "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
@@ -529,10 +538,10 @@ def main():
     head = args.precision
     others = [k for k in res if k != head]
     acc, acc_steps = ({}, 0) if args.no_oracle else accuracy(w, res, nsteps=1 if args.workload == "shelf" else 2)
-    units = dps * args.steps * world
-    value = units / (res[head]["total_ms"] / 1e3)
-    rate = {k: units / (res[k]["total_ms"] / 1e3) for k in res}
+    value = job_rate(dps * args.steps, world, res[head]["total_ms"] / 1e3)
+    rate = {k: job_rate(dps * args.steps, world, res[k]["total_ms"] / 1e3) for k in res}
     e2e_s, e2e_bytes = e2e(w, res, head, max(3, args.steps // 2), stream)
+    e2e_s = max_over_ranks(e2e_s, world)
     e2e_steps = max(3, args.steps // 2)
     pk = peaks()
     # dominant kernel family of the headline mode (profiled pass)
