@@ -258,6 +258,14 @@ int swe_set_launch_shape(swe_ctx* ctx, const int32_t* shape);
  * stay valid for the trial steps (errors of swe_run are returned). */
 int swe_autotune(swe_ctx* ctx, int steps, int32_t* shape_out, double* ms_out);
 
+/* Self-test of the device-side failure path (the paper has no counterpart):
+ * every device wait of the library is bounded and, when it runs out, sets a
+ * status bit that the next status read turns into SWE_ETIMEOUT, leaving the
+ * context usable.  This call launches one block that waits `spins` times
+ * (1..2^20) on an mbarrier nothing arrives on, so it returns SWE_ETIMEOUT;
+ * the state is untouched. */
+int swe_selftest_wait(swe_ctx* ctx, int64_t spins);
+
 /* Per-kernel-family timing (ms, CUDA events on the context stream around
  * each family) accumulated while swe_profile(ctx, 1) is on; swe_run then
  * launches the steps directly instead of replaying its CUDA graph.  Families:

@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/swedg.h"
 #include "common.h"
 #include "kernels.h"
@@ -219,10 +221,18 @@ static void prof_collect(swe_ctx* ctx) {
   ctx->evs.clear();
 }
 
+// A kernel family's launches: an NVTX range on the host timeline (for Nsight
+// tools; free without one) and, while profiling, CUDA events on the stream.
 struct ProfScope {
   swe_ctx* c; int f;
-  ProfScope(swe_ctx* c_, int f_) : c(c_), f(f_) { prof_mark(c, f, true); }
-  ~ProfScope() { prof_mark(c, f, false); }
+  ProfScope(swe_ctx* c_, int f_) : c(c_), f(f_) {
+    nvtxRangePushA(kFamilies[f]);
+    prof_mark(c, f, true);
+  }
+  ~ProfScope() {
+    prof_mark(c, f, false);
+    nvtxRangePop();
+  }
 };
 
 // ------------------------------------------------------------------ mesh
@@ -1187,6 +1197,15 @@ int swe_autotune(swe_ctx* ctx, int steps, int32_t* shape_out, double* ms_out) {
   if (shape_out) swe_get_launch_shape(ctx, shape_out);
   if (ms_out) *ms_out = best_ms;
   return 0;
+}
+
+int swe_selftest_wait(swe_ctx* ctx, int64_t spins) {
+  if (!ctx || !ctx->have_mesh || spins < 1 || spins > (int64_t)1 << 20)
+    return fail(ctx, SWE_EINVAL, "swe_selftest_wait: no mesh or spins out of 1..2^20");
+  CK(ensure_built(ctx));
+  LaunchScope ls(ctx);
+  CK(corrtc::launch_wait_selftest(ctx->stream, spins, ctx->d_status));
+  return read_status(ctx, false);
 }
 
 int swe_profile(swe_ctx* ctx, int enable) {

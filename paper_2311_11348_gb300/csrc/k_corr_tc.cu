@@ -475,6 +475,38 @@ int launch_vol_tc(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys
   return r;
 }
 
+// Self-test of the bounded waits: an mbarrier that nothing arrives on, waited
+// for `spins` times; the wait runs out, the kernel sets ST_TIMEOUT and returns.
+__global__ void k_wait_selftest(int64_t spins, unsigned* status) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t a = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(a, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool ok = false;
+    for (int64_t it = 0; it < spins && !ok; ++it) {
+      uint32_t r;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(r)
+          : "r"(a), "r"(0u)
+          : "memory");
+      ok = r != 0;
+    }
+    if (!ok) atomicOr(status, (unsigned)ST_TIMEOUT);
+  }
+}
+
+int launch_wait_selftest(cudaStream_t st, int64_t spins, unsigned* status) {
+  k_wait_selftest<<<1, 32, 0, st>>>(spins, status);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
 // B images and kernel attributes of the current device (once per context creation)
 int upload_tc_tables() {
   static float img[TC_BTOTAL];

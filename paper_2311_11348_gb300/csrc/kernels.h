@@ -106,6 +106,8 @@ int launch_vol_tc(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys
                   float* vol, unsigned* status);
 // host: the shared-memory image of the B operands for K = 6, 10, 15 (floats written, or needed when out is NULL)
 int64_t tc_operand_image(int K, float* out, int64_t cap);
+// a bounded wait on an mbarrier that nothing arrives on: sets ST_TIMEOUT
+int launch_wait_selftest(cudaStream_t st, int64_t spins, unsigned* status);
 }  // namespace corrtc
 
 }  // namespace swedg

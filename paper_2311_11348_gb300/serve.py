@@ -101,6 +101,22 @@ class Request:
     t_final: float = 0.0
     done_steps: int = 0
     nbytes: int = None
+    error: str = None   # set when the request was evicted after a failed step
+
+
+def member_state_ok(mesh, c, h_min):
+    """finite coefficients and every element mean depth above h_min (the
+    conditions the library's status word checks), for one request's state"""
+    c = np.asarray(c)
+    if not np.isfinite(c).all():
+        return False
+    xy = np.asarray(mesh["xy"], np.float64)
+    tri = np.asarray(mesh["tri"], np.int64)
+    a, b, d = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
+    area = 0.5 * np.abs((b[:, 0] - a[:, 0]) * (d[:, 1] - a[:, 1]) - (d[:, 0] - a[:, 0]) * (b[:, 1] - a[:, 1]))
+    hb = np.asarray(mesh["hv"], np.float64)[tri].mean(axis=1)
+    H = c[0, 0] / np.sqrt(area) + hb
+    return bool((H > h_min).all())
 
 
 def footprint(req: Request, precision: int) -> int:
@@ -132,10 +148,10 @@ class Cohort:
 
 class Server:
     def __init__(self, budget_bytes: int, precision=swedg.PREC_MIXED_FP32, g=9.81, cfl=0.1, rk_order=3,
-                 max_chunk=50, clock=time.perf_counter, device_resident=True, max_cohorts=8):
+                 max_chunk=50, clock=time.perf_counter, device_resident=True, max_cohorts=8, h_min=1e-8):
         self.budget = budget_bytes
         self.device_resident = device_resident
-        self.kw = dict(g=g, cfl=cfl, rk_order=rk_order, precision=precision)
+        self.kw = dict(g=g, cfl=cfl, rk_order=rk_order, precision=precision, h_min=h_min)
         self.precision = precision
         self.max_chunk = max_chunk
         self.max_cohorts = max_cohorts
@@ -143,6 +159,8 @@ class Server:
         self.waiting: list[Request] = []
         self.cohorts: list[Cohort] = []
         self.done: list[Request] = []
+        self.failed: list[Request] = []
+        self.h_min = h_min
         self.dof_stage_updates = 0
         self.rebuilds = 0
         self.rebuild_s = 0.0    # host time spent building cohort contexts
@@ -187,6 +205,32 @@ class Server:
             self._close(c)
         return self._build(reqs, keep) if reqs else None
 
+    @staticmethod
+    def _run_cohort(c, chunk):
+        try:
+            c.ens.run(chunk)
+            return None
+        except swedg.SweError as err:
+            return err
+
+    def _evict_failed(self, c, err):
+        """A cohort's run reported an error (a non-finite state or a depth at or
+        below h_min in some member).  The members evolve independently, so
+        the ones whose state is still valid keep the chunk they just ran; the
+        others are evicted with the error, without touching other requests.
+        Without a member to blame, the whole cohort is evicted."""
+        states = c.ens.states(device=False)
+        bad = [i for i, r in enumerate(c.reqs) if c.live[i] and not member_state_ok(r.mesh, states[i], self.h_min)]
+        if not bad:
+            bad = [i for i in range(len(c.reqs)) if c.live[i]]
+        now = self.clock()
+        for i in bad:
+            r = c.reqs[i]
+            c.live[i] = False
+            r.error = f"{err}"
+            r.finished = now
+            self.failed.append(r)
+
     def step(self):
         """One scheduling round: admit, run a chunk on every cohort, retire.  Returns False when idle."""
         admitted = []
@@ -212,7 +256,13 @@ class Server:
                 self.cohorts.append(pending.result())
             return bool(self.cohorts)
         chunk = min(self.max_chunk, min(r.steps - r.done_steps for r in active))
-        list(self.pool.map(lambda c: c.ens.run(chunk), self.cohorts))
+        errors = list(self.pool.map(lambda c: self._run_cohort(c, chunk), self.cohorts))
+        failed = set()
+        for c, err in zip(self.cohorts, errors):
+            if err is not None:
+                self._evict_failed(c, err)
+                failed.add(id(c))
+        active = self.active
         for r in active:
             r.done_steps += chunk
             K = np.array(KP)[np.asarray(r.mesh["orders"], np.int64)]
@@ -235,7 +285,7 @@ class Server:
                     self.done.append(r)
             if not any(c.live):
                 self._close(c)
-            elif fin and (self.waiting or c.live_fraction() < 0.5):
+            elif id(c) in failed or (fin and (self.waiting or c.live_fraction() < 0.5)):  # evicted: always compact
                 keep_cohorts.append(self._rebuild([c]))
             else:
                 keep_cohorts.append(c)

@@ -44,7 +44,7 @@ SYMBOLS = ("swe_default_params", "swe_create", "swe_destroy", "swe_last_error", 
            "swe_edge_table", "swe_profile", "swe_profile_read", "swe_rhs_p1_noalloc", "swe_adapt",
            "swe_run_adaptive", "swe_set_members", "swe_set_member_times", "swe_get_member_times",
            "swe_memory_bytes", "swe_tc_operand_image", "swe_get_launch_shape", "swe_set_launch_shape",
-           "swe_autotune")
+           "swe_autotune", "swe_selftest_wait")
 
 
 def library_path() -> str:
@@ -294,6 +294,10 @@ class Solver:
         ms = C.c_double(0.0)
         self._ck(self._lib.swe_autotune(self.h, int(steps), v.ctypes.data_as(C.c_void_p), C.byref(ms)))
         return tuple(int(x) for x in v), ms.value
+
+    def selftest_wait(self, spins=1000):
+        """run the bounded-wait self-test (raises SweError SWE_ETIMEOUT by design)"""
+        self._ck(self._lib.swe_selftest_wait(self.h, C.c_int64(int(spins))))
 
     def memory_bytes(self):
         b = C.c_int64(0)

@@ -83,3 +83,28 @@ def test_serving_results_equal_alone_with_admission_by_footprint():
         assert np.array_equal(done[i].result, ref)
     lat = srv.latencies()
     assert np.all(lat > 0)
+
+
+def test_serving_evicts_a_failing_request_and_finishes_the_others():
+    """One request starts with a negative depth (xi = -500 m on a 30..300 m
+    sea): its cohort's run reports the error, the server evicts that request
+    and the others finish exactly as alone."""
+    kw = dict(g=9.81, cfl=0.2, rk_order=3, precision=swedg.PREC_MIXED_FP32)
+    specs = [member(8, 2e3, 21, 1, 2), member(6, 1e3, 22, 1, 3), member(7, 2e3, 23, 1, 2)]
+    bad_mesh, bad_c = specs[1]
+    bad_c = bad_c.copy()
+    bad_c[0, 0] = -500.0 * np.sqrt(0.5 * (1e3 / 6) ** 2)  # mean elevation -500 m everywhere
+    srv = serve.Server(1 << 40, precision=kw["precision"], g=9.81, cfl=0.2, rk_order=3, max_chunk=10)
+    for i, (m, c) in enumerate(specs):
+        srv.submit(serve.Request(rid=i, mesh=m, state=bad_c if i == 1 else c, steps=20))
+    srv.run_until_idle()
+    srv.close()
+    assert [r.rid for r in srv.failed] == [1]
+    assert srv.failed[0].error
+    done = {r.rid: r for r in srv.done}
+    assert set(done) == {0, 2}
+    for i in (0, 2):
+        m, c = specs[i]
+        ref, t, _ = alone(m, c, 20, **kw)
+        assert done[i].t_final == t
+        assert np.array_equal(done[i].result, ref)

@@ -242,6 +242,28 @@ def test_errors_are_reported_not_faulted():
     assert ei.value.code in (-3, -4)
 
 
+def test_device_wait_timeout_is_reported_and_the_context_survives():
+    """The failure path of the bounded device waits, without a GPU fault: a
+    wait that nothing completes runs out, the call returns SWE_ETIMEOUT, and
+    the same context then steps exactly like a fresh one."""
+    w = mixed_workload(seed=9, pmin=1, pmax=4)
+    m, P, s = make_pair(w, precision=swedg.PREC_MIXED_TF32)
+    c = m.project_state(w["ic"])
+    s.set_state(c, 0.0)
+    with pytest.raises(swedg.SweError) as ei:
+        s.selftest_wait(1000)
+    assert ei.value.code == -6
+    s.run(5)
+    a, _ = s.get_state()
+    _, _, f = make_pair(w, precision=swedg.PREC_MIXED_TF32)
+    f.set_state(c, 0.0)
+    f.run(5)
+    b, _ = f.get_state()
+    assert np.array_equal(a, b)
+    s.close()
+    f.close()
+
+
 def test_full_size_shelf_rhs_p1234_open_sea():
     """The paper's mesh size (2,097,152 triangles) with p in {1..4} and the M2
     open-sea boundary on x = 0: one rhs, all outputs, against the oracle."""

@@ -107,3 +107,40 @@ def test_device_bytes_counts_edges_orders_and_precision():
     alone = b64 + serve.device_bytes([p3], swedg.PREC_FP64)
     assert 0 < alone - both < 1024
     assert serve.device_bytes([p3], swedg.PREC_MIXED_TF32) > serve.device_bytes([p3], swedg.PREC_MIXED_FP32)
+
+
+class PoisonUnion(FakeUnion):
+    """a fake whose run fails when a member's mesh is marked poisoned: that
+    member's state turns non-finite, the others advance as usual"""
+
+    def run(self, n, dt_fixed=0.0):
+        super().run(n, dt_fixed)
+        bad = [i for i, m in enumerate(self.meshes) if m.get("poison")]
+        for i in bad:
+            self.c[i][:] = np.nan
+        if bad:
+            raise swedg.SweError(-4, "non-finite value in the state")
+
+
+def test_a_failing_request_is_evicted_without_the_others(monkeypatch):
+    monkeypatch.setattr(serve, "Ensemble", PoisonUnion)
+    FakeUnion.log = []
+    srv = serve.Server(budget_bytes=1 << 40, max_chunk=25, clock=lambda: 0.0, device_resident=False)
+    reqs = []
+    for rid in range(3):
+        r = make_req(rid, 20, 60)
+        # a valid mesh for the depth check: vertices far apart, deep water
+        r.mesh["xy"] = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+        r.mesh["hv"] = np.full(3, 10.0)
+        r.mesh["tri"] = np.tile(np.array([[0, 1, 2]], np.int32), (20, 1))
+        reqs.append(r)
+    reqs[1].mesh["poison"] = True
+    for r in reqs:
+        srv.submit(r)
+    srv.run_until_idle()
+    srv.close()
+    assert [r.rid for r in srv.failed] == [1] and "non-finite" in srv.failed[0].error
+    done = {r.rid: r for r in srv.done}
+    assert set(done) == {0, 2}
+    for r in done.values():
+        assert np.all(r.result == r.steps) and r.t_final == r.steps
