@@ -481,7 +481,7 @@ __host__ __device__ constexpr bool tc_vol(int K) { return false; }
 // edge fluxes, and the SSP-RK combination of that higher mode.
 // ---------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(128, kF32 ? 3 : 2) k_elem_corr(DevMesh m, CorrEdges ce, int64_t g0, int64_t n,
+__global__ void __launch_bounds__(128, kF32 ? 4 : 2) k_elem_corr(DevMesh m, CorrEdges ce, int64_t g0, int64_t n,
                                                             int64_t rc_off, int64_t nrc, Phys ph, Stage stg,
                                                             const T* __restrict__ cbS,
                                                             const T* __restrict__ chS, const T* __restrict__ chN,
