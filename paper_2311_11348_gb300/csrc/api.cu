@@ -461,10 +461,10 @@ static int build_device(swe_ctx* ctx) {
     return cuda_err(ctx, rc);
   cudaMemset(ctx->fx.Fbc, 0, sizeof(double) * 6 * nE);
   for (int pm = 0; pm < 5; ++pm) {
-    ctx->fx.Ff[pm] = nullptr;
+    ctx->fx.Pf[pm] = nullptr;
     if (pm < 2) continue;
-    const size_t sz = ts * 3 * npts_for(pm) * ctx->ce.n[pm];
-    if ((rc = dalloc(ctx, &ctx->fx.Ff[pm], sz))) return cuda_err(ctx, rc);
+    const size_t sz = ts * 2 * 3 * (Kof(pm) - 3) * ctx->ce.n[pm];
+    if ((rc = dalloc(ctx, &ctx->fx.Pf[pm], sz))) return cuda_err(ctx, rc);
   }
   // correction of the base modes from the volume terms: [U,V][q = 2,3][elements with p >= 2]
   const int64_t nrc = ne - ctx->G.start[2];

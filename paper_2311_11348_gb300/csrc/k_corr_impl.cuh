@@ -275,8 +275,8 @@ __device__ __forceinline__ void side_traces(const DevMesh& m, const Groups& G, S
 template <int PM>
 __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __restrict__ list, int64_t nl, Groups G,
                                                    Phys ph, Stage stg, StateDev c, VelDev u,
-                                                   double* __restrict__ Fbc, T* __restrict__ Ff) {
-  constexpr int N = npts_for(PM), GI = PM - 2;
+                                                   double* __restrict__ Fbc, T* __restrict__ Pf) {
+  constexpr int N = npts_for(PM), GI = PM - 2, KQ = Kof(PM) - 3;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= nl) return;
   const int64_t ed = list[idx], nE = m.nedge;
@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
   // zeroth and first moments (in the left element's edge parameter s) of the
   // weighted correction flux: they are all the test modes of degree <= 1 see
   T M0[3] = {0, 0, 0}, M1[3] = {0, 0, 0};
+  T Ffull[3][N];
   sfor<0, N>([&](auto q) {
     const T hb = hA + cES[GI][q] * (hB - hA);
     const Tr& x = a[q];
@@ -345,10 +346,29 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
     const T h0 = wgt * Fh0, h1 = wgt * Fh1, h2 = wgt * Fh2;
     M0[0] += h0; M0[1] += h1; M0[2] += h2;
     M1[0] += h0 * cES[GI][q]; M1[1] += h1 * cES[GI][q]; M1[2] += h2 * cES[GI][q];
-    Ff[(0 * N + q) * nl + idx] = wgt * (Fb0 + Fh0);
-    Ff[(1 * N + q) * nl + idx] = wgt * (Fb1 + Fh1);
-    Ff[(2 * N + q) * nl + idx] = wgt * (Fb2 + Fh2);
+    Ffull[0][q] = wgt * (Fb0 + Fh0);
+    Ffull[1][q] = wgt * (Fb1 + Fh1);
+    Ffull[2][q] = wgt * (Fb2 + Fh2);
   });
+  // the full flux projected onto the higher test modes of each side once here,
+  //   P[side][f][q] = -+ (1/s) sum_g F_f(s_g) phihat_q(gamma_k(s_g)),
+  // (left: minus, points in its own direction; right: plus, points reversed),
+  // so that the element kernel reads one value per edge, field and mode
+  auto project = [&](int side, int k, int Kside, T sg) {
+    sfor<3, Kof(PM)>([&](auto q) {
+      if (q < Kside) {
+        sfor<0, 3>([&](auto f) {
+          T acc = 0;
+          sfor<0, N>([&](auto g) {
+            acc += Ffull[f][g] * (side ? cEB[GI][k][q][N - 1 - g] : cEB[GI][k][q][g]);
+          });
+          Pf[((side * 3 + f) * KQ + (q - 3)) * nl + idx] = sg * acc;
+        });
+      }
+    });
+  };
+  if (m.p[L] >= 2) project(0, kL, Kof(m.p[L]), -geo[G_RS * ne + L]);
+  if (R >= 0 && m.p[R] >= 2) project(1, kR, Kof(m.p[R]), geo[G_RS * ne + R]);
   // Degree-<=1 test functions are linear along the edge, so the correction's
   // share of the base modes is fixed by (M0, M1); the two-point flux with the
   // same moments is stored next to the base flux of this edge, and both sides
@@ -368,7 +388,7 @@ static int edge_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
   if (nl == 0) return 0;
   const int ct = launch_shape().corr_threads;
   k_edge_corr<PM><<<nblocks(nl, ct), ct, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc,
-                                                    (T*)fx.Ff[PM]);
+                                                    (T*)fx.Pf[PM]);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -383,23 +403,19 @@ int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, con
 }
 
 // ---------------------------------------------------------------------------
-// projection of the full flux of one correction edge onto test mode Q >= 3:
-//   r_f -= sgn (1/s) sum_g F_g phihat_Q(gamma_k(s_g))
+// the projected full flux of one correction edge for test mode q >= 3 of an
+// element (written by the edge kernel for both sides)
 // ---------------------------------------------------------------------------
-// (q is warp-uniform: one constant-cache broadcast per trace value; a
-// runtime q keeps one copy of this code per pmax and edge instead of one per
-// test mode, which kept the higher-order kernels out of the instruction cache)
-template <int PM>
-__device__ __forceinline__ void project_edge(T (&r)[3], const EdgeFlux& fx, const CorrEdges& ce, int64_t sl, int k,
-                                             bool right, T rs, int q) {
-  constexpr int N = npts_for(PM), GI = PM - 2;
-  const int64_t nl = ce.n[PM];
-  const T* Ff = (const T*)fx.Ff[PM];
-  const T sg = right ? rs : -rs;
-  sfor<0, N>([&](auto g) {
-    const T bq = sg * (right ? cEB[GI][k][q][N - 1 - g] : cEB[GI][k][q][g]);
-    sfor<0, 3>([&](auto f) { r[f] += Ff[(f * N + g) * nl + sl] * bq; });
-  });
+__device__ __forceinline__ void add_edge_projection(T (&r)[3], const EdgeFlux& fx, const CorrEdges& ce, int pm,
+                                                    int64_t sl, bool right, int q) {
+  // selects rather than a runtime index into the kernel parameters (which
+  // would copy them to local memory)
+  const T* P = (const T*)(pm == 2 ? fx.Pf[2] : pm == 3 ? fx.Pf[3] : fx.Pf[4]);
+  const int KQ = Kof(pm) - 3;
+  const int64_t nl = pm == 2 ? ce.n[2] : pm == 3 ? ce.n[3] : ce.n[4];
+  const int side = right ? 1 : 0;
+#pragma unroll
+  for (int f = 0; f < 3; ++f) r[f] += P[((side * 3 + f) * KQ + (q - 3)) * nl + sl];
 }
 
 // ---------------------------------------------------------------------------
@@ -563,9 +579,7 @@ __global__ void __launch_bounds__(128, kF32 ? 4 : 2) k_elem_corr(DevMesh m, Corr
     const bool right = (cs >> 27) & 1;
     const int pm = cs >> 28;
     const int64_t sl = cs & 0x07ffffff;
-    if (pm == 2) project_edge<2>(r, fx, ce, sl, k, right, rs, q);
-    else if (pm == 3) project_edge<3>(r, fx, ce, sl, k, right, rs, q);
-    else project_edge<4>(r, fx, ce, sl, k, right, rs, q);
+    add_edge_projection(r, fx, ce, pm, sl, right, q);
   }
   const T dt = (T)stage_dt(stg, m.mem[e]), a = (T)stg.a, b = (T)stg.b;
   const T cs3[3] = {xq, Uq, Vq};

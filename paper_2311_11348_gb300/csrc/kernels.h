@@ -25,7 +25,8 @@ struct EdgeFlux {
   double* Fb;        // [3][2][nedge] base flux (weighted by |E| w_g) at the 2-point rule
   double* Fbc;       // [3][2][nedge] two-point equivalent of the correction flux's share of the
                      // base modes (zero on edges without a p >= 2 side)
-  void* Ff[5];       // per pmax = 2..4: [3][N][n] full flux at the npts(pmax) points
+  void* Pf[5];       // per pmax = 2..4: [2 sides][3 fields][K(pmax)-3][n]: the full flux of each correction
+                     // edge projected onto the higher test modes (q >= 3) of its left (0) and right (1) element
 };
 
 // every kernel launch of the library is counted (for launch accounting)

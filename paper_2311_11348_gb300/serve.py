@@ -33,18 +33,14 @@ KP = (1, 3, 6, 10, 15)
 NGEO, NEGEO = 19, 9  # rows of the element and edge geometry tables
 
 
-def _npts(pm):
-    return 2 if pm <= 1 else (3 * pm + 2) // 2
-
-
 def device_bytes(meshes, precision):
     """Device bytes a context holds after swe_set_mesh + swe_set_orders (+
     swe_set_members) of the disjoint union of `meshes`: the same allocations
     the library makes (swe_memory_bytes reports them), counted on the host so
     that admission needs no context.  Per element: FP64 geometry and its FP32
     copy, topology, three RK states, velocity, the user-layout staging; per
-    edge: geometry, base fluxes and the correction flux buffers of its max
-    order; the correction arrays scale with K(p) - 3 at the correction type's
+    edge: geometry, base fluxes and the projections of its correction flux
+    onto both sides' higher modes; the correction arrays scale with K - 3 at the correction type's
     width (4 bytes in the mixed mode, 8 in FP64)."""
     corr32 = precision in (swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32)
     ts = 4 if corr32 else 8
@@ -77,7 +73,7 @@ def device_bytes(meshes, precision):
     for _ in range(3):                                                                        # RK states
         allocs += [72 * ne] + ([36 * ne] if corr32 else []) + [ts * 3 * (KP[q] - 3) * n[q] for q in (2, 3, 4)]
     allocs += [48 * ne] + ([24 * ne] if corr32 else []) + [ts * 2 * (KP[q] - 3) * n[q] for q in (2, 3, 4)]
-    allocs += [48 * nE, 48 * nE] + [ts * 3 * _npts(q) * ncl[q] for q in (2, 3, 4)]         # fluxes
+    allocs += [48 * nE, 48 * nE] + [ts * 2 * 3 * (KP[q] - 3) * ncl[q] for q in (2, 3, 4)]  # fluxes, projections
     allocs += [32 * max(nrc, 1)]
     if precision == swedg.PREC_MIXED_TF32:
         allocs += [32 * 4 * max(nrc, 1)]                                                      # tensor-core volume terms
