@@ -485,6 +485,7 @@ static int build_device(swe_ctx* ctx) {
       (rc = dalloc(ctx, &ctx->d_status, sizeof(unsigned))))
     return cuda_err(ctx, rc);
   cudaMemset(ctx->d_dt, 0, sizeof(double) * nm);
+  if ((rc = launch_reset_min(ctx->stream, ctx->d_dmin, ctx->nmem))) return cuda_err(ctx, rc);
   ctx->nred = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (ne + 255) / 256));
   if ((rc = dalloc(ctx, &ctx->d_partial, sizeof(double) * ctx->nred)) || (rc = dalloc(ctx, &ctx->d_red, sizeof(double) * 2)))
     return cuda_err(ctx, rc);
@@ -505,10 +506,12 @@ static Phys phys(const swe_ctx* ctx) {
 static int usolve_all(swe_ctx* ctx, StateDev in) {
   ProfScope ps(ctx, F_USOLVE);
   const Phys ph = phys(ctx);
-  CK(launch_usolve_base(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status));
-  if (ctx->tc) CK(corrtc::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
-  else if (ctx->corr32) CK(corr32::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
-  else CK(corr64::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
+  CK(launch_usolve_base(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status, nullptr));
+  if (ctx->tc)
+    CK(corrtc::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, nullptr, nullptr));
+  else if (ctx->corr32)
+    CK(corr32::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, nullptr, nullptr));
+  else CK(corr64::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, nullptr, nullptr));
   return 0;
 }
 
@@ -517,10 +520,12 @@ static int usolve_all(swe_ctx* ctx, StateDev in) {
 // The base kernels (FP64 pipe bound) run on stream A, the correction kernels
 // on stream B, concurrently on the same SMs -- the GB300 counterpart of the
 // paper's base/correction distribution over CPU and GPU (Sect. 3-5):
-//   A: usolve_base ---------> [dt] edge_base ------------------> elem_base
-//   B: usolve_corr --------->      edge_corr -> elem_corr --------^
-// (each edge kernel needs both u-solves; elem_base needs elem_corr's rc and
-// edge_corr's share of the base-mode flux).  Profiling runs everything on A.
+//   A: usolve_base --------> [dt] edge_base -------------------------> elem_base
+//   B: usolve_corr (+ rc) -->      edge_corr -> elem_corr(q >= 3) ---^
+// (each edge kernel needs both u-solves; elem_base needs the rc of the base
+// test modes, which the velocity solve forms, and edge_corr's share of the
+// base-mode flux).  The tensor-core mode runs edge_corr -> vol_tc ->
+// elem_corr(every q) on B.  Profiling runs everything on A.
 static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, const Stage& stg, bool cfl_dt,
                      double dt_fixed) {
   const Phys ph = phys(ctx);
@@ -531,11 +536,15 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
     CU(cudaStreamWaitEvent(B, ctx->ev_fork, 0));
   }
   {
+    // the first stage of a CFL step folds the elements' CFL bounds into d_dmin
     ProfScope ps(ctx, F_USOLVE);
-    CK(launch_usolve_base(A, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status));
-    if (ctx->tc) CK(corrtc::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
-    else if (ctx->corr32) CK(corr32::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
-    else CK(corr64::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status));
+    unsigned long long* dmin = cfl_dt ? ctx->d_dmin : nullptr;
+    CK(launch_usolve_base(A, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status, dmin));
+    // the CUDA-core modes form rc in the velocity solve; the tensor-core mode in elem_corr (from vol)
+    if (ctx->tc) CK(corrtc::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, dmin, nullptr));
+    else if (ctx->corr32)
+      CK(corr32::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, dmin, ctx->rc));
+    else CK(corr64::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, dmin, ctx->rc));
   }
   if (conc) {
     CU(cudaEventRecord(ctx->ev_u1, A));
@@ -544,9 +553,7 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
     CU(cudaStreamWaitEvent(B, ctx->ev_u1, 0));
   }
   if (cfl_dt) {
-    ProfScope ps(ctx, F_DT);
-    CK(launch_reset_min(A, ctx->d_dmin, ctx->nmem));
-    CK(launch_dt(A, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->d_dmin));
+    ProfScope ps(ctx, F_DT);  // dt = cfl * min, and the minimum reset for the next step
     CK(launch_advance_time(A, nullptr, ctx->d_dmin, ctx->prm.cfl, dt_fixed, ctx->d_dt, ctx->nmem));
     if (conc) {  // the correction branch reads dt (stage time, RK update)
       CU(cudaEventRecord(ctx->ev_dt, A));
@@ -557,6 +564,19 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
     ProfScope ps(ctx, F_EDGEB);
     CK(launch_edge_base(A, ctx->dm, ph, stg, in.cb, ctx->vel.ub, ctx->fx));
   }
+  auto elem_corr = [&](int part) -> int {
+    ProfScope ps(ctx, F_ELEMC);
+    if (ctx->tc)
+      CK(corrtc::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
+                                  part, ctx->vol));
+    else if (ctx->corr32)
+      CK(corr32::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
+                                  part));
+    else
+      CK(corr64::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
+                                  part));
+    return 0;
+  };
   if (!stg.base_only) {
     {
       ProfScope ps(ctx, F_EDGEC);
@@ -564,19 +584,14 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
       else if (ctx->corr32) CK(corr32::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
       else CK(corr64::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
     }
-    if (ctx->tc) {
-      ProfScope ps(ctx, F_VOLTC);
-      CK(corrtc::launch_vol_tc(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->vol, ctx->d_status));
-    }
-    {
-      ProfScope ps(ctx, F_ELEMC);
-      if (ctx->tc)
-        CK(corrtc::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
-                                    ctx->vol));
-      else if (ctx->corr32)
-        CK(corr32::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc));
-      else
-        CK(corr64::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc));
+    if (ctx->tc) {  // every test mode (rc comes from the tensor-core volume terms)
+      {
+        ProfScope ps(ctx, F_VOLTC);
+        CK(corrtc::launch_vol_tc(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->vol, ctx->d_status));
+      }
+      CK(elem_corr(0));
+    } else {
+      CK(elem_corr(1));  // the higher test modes (the velocity solve formed rc)
     }
   }
   if (conc) {
@@ -904,9 +919,7 @@ static int rhs_impl(swe_ctx* ctx, const double* c_in, double* out0, double* out1
   CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->corr32, ctx->st[2], ctx->d_user));
   s.base_only = 1;
   CK(run_stage(ctx, ctx->st[1], ctx->st[1], ctx->st[2], s, false, 0.0));
-  StateDev b = ctx->st[2];
-  for (int p = 0; p < 5; ++p) b.ch[p] = nullptr;  // the base part has no higher modes
-  for (int p = 2; p < 5; ++p)
+  for (int p = 2; p < 5; ++p)  // the base part has no higher modes
     if (ctx->st[2].ch[p]) {
       const int64_t np = ctx->G.start[p + 1] - ctx->G.start[p];
       CU(cudaMemsetAsync(ctx->st[2].ch[p], 0, (ctx->corr32 ? 4 : 8) * 3 * (Kof(p) - 3) * np, ctx->stream));
@@ -919,7 +932,6 @@ static int rhs_impl(swe_ctx* ctx, const double* c_in, double* out0, double* out1
   CK(launch_sub(ctx->stream, ctx->d_user, base_dev, corr_dev, n));
   if (!dev1) CU(cudaMemcpyAsync(out1, corr_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
-  (void)b;
   return 0;
 }
 

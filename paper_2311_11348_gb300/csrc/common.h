@@ -126,6 +126,37 @@ struct CorrEdges {
 };
 
 __device__ __forceinline__ double stage_dt(const Stage& st, int mem) { return st.dt ? st.dt[mem] : st.dt_host; }
+
+// CFL bound of one element, d_e / ((|u_bar| + sqrt(g H_bar)) (2p+1)), in FP64
+// from mode 0 of u and v and of the depth H = xi + h_b; an element mean is
+// its mode 0 times sqrt 2 * rs (rs = 1 / sqrt(2 |Omega_e|)).  DBL_MAX where
+// the bound is not a positive number (NaN never wins the minimum; the state
+// checks report it).
+__device__ __forceinline__ double cfl_bound(double u0, double v0, double H0, double rs, double g, double diam,
+                                            int p) {
+  const double r = 1.4142135623730951 * rs;
+  const double ubar = u0 * r, vbar = v0 * r, Hbar = H0 * r;
+  const double sp = sqrt(ubar * ubar + vbar * vbar) + sqrt(g * Hbar);
+  const double dd = diam / (sp * (2.0 * p + 1.0));
+  return (dd > 0.0 && dd < 1.7976931348623157e308) ? dd : 1.7976931348623157e308;
+}
+
+// min of d into dmin[mem] over the whole grid: positive doubles order like
+// their bit patterns, so an integer atomicMin gives the exact minimum
+// independent of the order of the blocks.  Every lane of the warp calls it
+// (lanes without an element pass DBL_MAX); one atomic per warp when the
+// warp's elements share a member (the usual case).
+__device__ __forceinline__ void cfl_min_store(unsigned long long* dmin, int mem, double d) {
+  const unsigned full = 0xffffffffu;
+  const double dmax = 1.7976931348623157e308;
+  const int mem0 = __shfl_sync(full, mem, 0);
+  if (__all_sync(full, mem == mem0)) {
+    for (int o = 16; o > 0; o >>= 1) d = fmin(d, __shfl_xor_sync(full, d, o));
+    if ((threadIdx.x & 31) == 0 && d < dmax) atomicMin(dmin + mem0, (unsigned long long)__double_as_longlong(d));
+  } else if (d < dmax) {
+    atomicMin(dmin + mem, (unsigned long long)__double_as_longlong(d));
+  }
+}
 __device__ __forceinline__ double stage_time(const Stage& st, int mem) {
   return (st.t_dev ? st.t_dev[mem] : st.t) + st.tau * stage_dt(st, mem);
 }

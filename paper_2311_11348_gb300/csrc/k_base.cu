@@ -5,7 +5,8 @@
 //
 // Kernels (one thread per element or per edge, FP64-pipe bound on GB300):
 //   k_usolve_base  auxiliary system uH = q (Sect. 3) for p <= 1 elements
-//   k_dt           CFL step: min over elements, exact (order independent)
+//                  (and, in the first stage of a step, the CFL bounds of its
+//                  elements: min over elements, exact, order independent)
 //   k_edge_base    Lax-Friedrichs flux (Sect. 2) of the P1 traces at the two
 //                  Gauss points of every edge, lambda of Eq. (10) from means
 //   k_elem_base    volume + source terms (Eq. 13 with the degree-1 tensors in
@@ -141,90 +142,64 @@ int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int3
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_usolve_base(DevMesh m, int64_t n_end, Phys ph, const double* __restrict__ cb,
                                                      double* __restrict__ ub, float* __restrict__ ub32,
-                                                     unsigned* status) {
+                                                     unsigned* status, unsigned long long* dmin) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= n_end) return;
-  const int64_t ne = m.ne;
-  const double rs = m.geo[G_RS * ne + e];
-  const double H0 = cb[0 * ne + e] + m.geo[G_HB0 * ne + e];
-  const double U0 = cb[3 * ne + e], V0 = cb[6 * ne + e];
-  if (!(H0 * cPhi0 * rs > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
-  if (m.p[e] == 0) {
-    const double r = 1.0 / (H0 * cT1[0][0][0] * rs);
-    const double v[6] = {U0 * r, 0.0, 0.0, V0 * r, 0.0, 0.0};
+  double dcfl = DBL_MAX;
+  int mem = 0;
+  if (e < n_end) {
+    const int64_t ne = m.ne;
+    const double rs = m.geo[G_RS * ne + e];
+    const double H0 = cb[0 * ne + e] + m.geo[G_HB0 * ne + e];
+    const double U0 = cb[3 * ne + e], V0 = cb[6 * ne + e];
+    if (!(H0 * cPhi0 * rs > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
+    double v[6];
+    if (m.p[e] == 0) {
+      const double r = 1.0 / (H0 * cT1[0][0][0] * rs);
+      v[0] = U0 * r; v[1] = 0.0; v[2] = 0.0;
+      v[3] = V0 * r; v[4] = 0.0; v[5] = 0.0;
+    } else {
+      const double H1 = cb[1 * ne + e] + m.geo[G_HB1 * ne + e];
+      const double H2 = cb[2 * ne + e] + m.geo[G_HB2 * ne + e];
+      const double U1 = cb[4 * ne + e], U2 = cb[5 * ne + e];
+      const double V1 = cb[7 * ne + e], V2 = cb[8 * ne + e];
+      // entries (scaled by s: the 1/s factor cancels in the adjugate solve up to a final scale)
+      const double a = H0 * cT1[0][0][0];
+      const double b = H0 * cT1[0][0][1] + H1 * cT1[1][0][1] + H2 * cT1[2][0][1];
+      const double c = H0 * cT1[0][0][2] + H1 * cT1[1][0][2] + H2 * cT1[2][0][2];
+      const double d = H0 * cT1[0][1][1] + H1 * cT1[1][1][1] + H2 * cT1[2][1][1];
+      const double f = H0 * cT1[0][1][2] + H1 * cT1[1][1][2] + H2 * cT1[2][1][2];
+      const double h = H0 * cT1[0][2][2] + H1 * cT1[1][2][2] + H2 * cT1[2][2][2];
+      // M = (1/s) [[a b c][b d f][c f h]];  u = s * adj(S) U / det(S), S = s M
+      const double C00 = d * h - f * f, C01 = c * f - b * h, C02 = b * f - c * d;
+      const double C11 = a * h - c * c, C12 = b * c - a * f, C22 = a * d - b * b;
+      const double det = a * C00 + b * C01 + c * C02;
+      const double r = 1.0 / (det * rs);
+      v[0] = (C00 * U0 + C01 * U1 + C02 * U2) * r; v[1] = (C01 * U0 + C11 * U1 + C12 * U2) * r;
+      v[2] = (C02 * U0 + C12 * U1 + C22 * U2) * r; v[3] = (C00 * V0 + C01 * V1 + C02 * V2) * r;
+      v[4] = (C01 * V0 + C11 * V1 + C12 * V2) * r; v[5] = (C02 * V0 + C12 * V1 + C22 * V2) * r;
+    }
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
       ub[i * ne + e] = v[i];
       if (ub32) ub32[i * ne + e] = (float)v[i];
     }
-    return;
+    if (dmin) {
+      mem = m.mem[e];
+      dcfl = cfl_bound(v[0], v[3], H0, rs, ph.g, m.geo[G_DIAM * ne + e], m.p[e]);
+    }
   }
-  const double H1 = cb[1 * ne + e] + m.geo[G_HB1 * ne + e];
-  const double H2 = cb[2 * ne + e] + m.geo[G_HB2 * ne + e];
-  const double U1 = cb[4 * ne + e], U2 = cb[5 * ne + e];
-  const double V1 = cb[7 * ne + e], V2 = cb[8 * ne + e];
-  // entries (scaled by s: the 1/s factor cancels in the adjugate solve up to a final scale)
-  const double a = H0 * cT1[0][0][0];
-  const double b = H0 * cT1[0][0][1] + H1 * cT1[1][0][1] + H2 * cT1[2][0][1];
-  const double c = H0 * cT1[0][0][2] + H1 * cT1[1][0][2] + H2 * cT1[2][0][2];
-  const double d = H0 * cT1[0][1][1] + H1 * cT1[1][1][1] + H2 * cT1[2][1][1];
-  const double f = H0 * cT1[0][1][2] + H1 * cT1[1][1][2] + H2 * cT1[2][1][2];
-  const double h = H0 * cT1[0][2][2] + H1 * cT1[1][2][2] + H2 * cT1[2][2][2];
-  // M = (1/s) [[a b c][b d f][c f h]];  u = s * adj(S) U / det(S), S = s M
-  const double C00 = d * h - f * f, C01 = c * f - b * h, C02 = b * f - c * d;
-  const double C11 = a * h - c * c, C12 = b * c - a * f, C22 = a * d - b * b;
-  const double det = a * C00 + b * C01 + c * C02;
-  const double r = 1.0 / (det * rs);
-  const double v[6] = {(C00 * U0 + C01 * U1 + C02 * U2) * r, (C01 * U0 + C11 * U1 + C12 * U2) * r,
-                       (C02 * U0 + C12 * U1 + C22 * U2) * r, (C00 * V0 + C01 * V1 + C02 * V2) * r,
-                       (C01 * V0 + C11 * V1 + C12 * V2) * r, (C02 * V0 + C12 * V1 + C22 * V2) * r};
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    ub[i * ne + e] = v[i];
-    if (ub32) ub32[i * ne + e] = (float)v[i];
-  }
+  if (dmin) cfl_min_store(dmin, mem, dcfl);  // uniform over the grid: every lane of the warp is here
 }
 
 int launch_usolve_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
-                       double* ub, float* ub32, unsigned* status) {
+                       double* ub, float* ub32, unsigned* status, unsigned long long* dmin) {
   const int64_t n = G.start[2];
   if (n == 0) return 0;
   const int ut = launch_shape().usolve_threads;
-  k_usolve_base<<<nblocks(n, ut), ut, 0, s>>>(m, n, ph, cb, ub, ub32, status);
+  k_usolve_base<<<nblocks(n, ut), ut, 0, s>>>(m, n, ph, cb, ub, ub32, status, dmin);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
-}
-
-// ---------------------------------------------------------------------------
-// CFL reduction: min_e d_e / ((|u_bar| + sqrt(g H_bar)) (2p+1)).  Positive
-// doubles order like their bit patterns, so an integer atomicMin gives the
-// exact minimum independent of the order of the blocks.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_dt(DevMesh m, Phys ph, const double* __restrict__ cb,
-                                            const double* __restrict__ ub, unsigned long long* dmin) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t ne = m.ne;
-  double d = DBL_MAX;
-  int mem = 0;
-  if (e < ne) {
-    mem = m.mem[e];
-    const double r = cPhi0 * m.geo[G_RS * ne + e];
-    const double ubar = ub[0 * ne + e] * r, vbar = ub[3 * ne + e] * r;
-    const double Hbar = (cb[e] + m.geo[G_HB0 * ne + e]) * r;
-    const double sp = sqrt(ubar * ubar + vbar * vbar) + sqrt(ph.g * Hbar);
-    const double dd = m.geo[G_DIAM * ne + e] / (sp * (2.0 * m.p[e] + 1.0));
-    if (dd > 0.0 && dd < d) d = dd;  // NaN never wins; it is reported by the status checks
-  }
-  // one atomic per warp when its elements share a member (the usual case)
-  const unsigned full = 0xffffffffu;
-  const int mem0 = __shfl_sync(full, mem, 0);
-  if (__all_sync(full, mem == mem0)) {
-    for (int o = 16; o > 0; o >>= 1) d = fmin(d, __shfl_xor_sync(full, d, o));
-    if ((threadIdx.x & 31) == 0 && d < DBL_MAX) atomicMin(dmin + mem0, (unsigned long long)__double_as_longlong(d));
-  } else if (d < DBL_MAX) {
-    atomicMin(dmin + mem, (unsigned long long)__double_as_longlong(d));
-  }
 }
 
 __global__ void k_reset_min(unsigned long long* dmin, int n) {
@@ -239,27 +214,23 @@ int launch_reset_min(cudaStream_t s, unsigned long long* dmin, int nmem) {
   return 0;
 }
 
-int launch_dt(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
-              const double* ub, unsigned long long* dmin) {
-  (void)G;
-  if (m.ne == 0) return 0;
-  k_dt<<<nblocks(m.ne, 256), 256, 0, s>>>(m, ph, cb, ub, dmin);
-  count_launch();
-  SWE_CUDA_OK(cudaGetLastError());
-  return 0;
-}
-
-// per member: dt = dt_fixed > 0 ? dt_fixed : cfl * min (before the step); t += dt (after it)
-__global__ void k_set_dt(double* dt_dev, const unsigned long long* dmin, double cfl, double dt_fixed, int n) {
+// per member: dt = dt_fixed > 0 ? dt_fixed : cfl * min (before the step), and
+// the minimum back to DBL_MAX for the next step's reduction (the velocity
+// solves of the first stage fold their elements' CFL bounds into it);
+// t += dt (after the step)
+__global__ void k_set_dt(double* dt_dev, unsigned long long* dmin, double cfl, double dt_fixed, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dt_dev[i] = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)dmin[i]);
+  if (i < n) {
+    dt_dev[i] = dt_fixed > 0.0 ? dt_fixed : cfl * __longlong_as_double((long long)dmin[i]);
+    dmin[i] = (unsigned long long)__double_as_longlong(DBL_MAX);
+  }
 }
 __global__ void k_advance_time(double* t_dev, const double* dt_dev, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) t_dev[i] += dt_dev[i];
 }
 
-int launch_advance_time(cudaStream_t s, double* t_dev, const unsigned long long* dmin, double cfl, double dt_fixed,
+int launch_advance_time(cudaStream_t s, double* t_dev, unsigned long long* dmin, double cfl, double dt_fixed,
                         double* dt_dev, int nmem) {
   if (t_dev == nullptr) k_set_dt<<<nblocks(nmem, 128), 128, 0, s>>>(dt_dev, dmin, cfl, dt_fixed, nmem);
   else k_advance_time<<<nblocks(nmem, 128), 128, 0, s>>>(t_dev, dt_dev, nmem);

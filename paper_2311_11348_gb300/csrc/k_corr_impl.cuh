@@ -14,12 +14,14 @@
 //                      tensors D and G of Eq. (13) (compile-time sparsity),
 //                      source, projection of the correction edge fluxes, the
 //                      correction of the base modes (rc) and the SSP-RK
-//                      update of the higher modes
-//   k_elem_corr_lo     p <= 1 elements touching a correction edge: rc only
+//                      update of the higher modes (or, when the velocity
+//                      solve has formed rc, of the higher test modes only,
+//                      overlapping the base element kernel)
 //
 // With CORR_TC defined (k_corr_tc.cu) the volume terms of the momentum rows
 // come from a buffer that the tensor-core contraction k_vol_tc<K> wrote;
 // k_elem_corr then computes only the elevation row's volume term itself.
+#include <cfloat>
 #include <cstdio>
 
 #include "kernels.h"
@@ -129,94 +131,206 @@ __device__ __forceinline__ void load_modes(T (&out)[K], const T* __restrict__ ba
 }
 
 // ---------------------------------------------------------------------------
+// Volume terms of Eq. (13) for one test mode Q (non-base index triples only),
+// with J^{-1} folded into the contravariant coefficients
+//   Uc_i = (J^-1 q_i)_xhat, Vc_i = (J^-1 q_i)_yhat, uc_j, vc_j likewise, pp_j = xi_j/2 + hb_j:
+//   r_xi = sum_i Uc_i D_x[Q][i] + Vc_i D_y[Q][i]
+//   r_U  = (1/s) [ sum_ij U_i (uc_j G_x[Q][i][j] + vc_j G_y[Q][i][j]) + g (J00 P_x + J10 P_y) ]
+//   r_V  = (1/s) [ sum_ij V_i (...) + g (J01 P_x + J11 P_y) ]
+//   P_k  = sum_ij xi_i pp_j G_k[Q][i][j]
+// ---------------------------------------------------------------------------
+template <int K, int Q, int KL>
+__device__ __forceinline__ void volume_q(T (&r)[3], const T (&xi)[K], const T (&U)[K], const T (&V)[K],
+                                         const T (&uc)[K], const T (&vc)[K], const T (&pp)[K], const T (&Uc)[KL],
+                                         const T (&Vc)[KL], T rs, T J0, T J1, T J2, T J3, T g) {
+  T am = 0;
+  sfor<0, KL>([&](auto i) {
+    if constexpr (dnz(Q, i) && !base2(Q, i)) am += Uc[i] * cD[0][Q][i] + Vc[i] * cD[1][Q][i];
+  });
+  T aU = 0, aV = 0, Px = 0, Py = 0;
+  sfor<0, K>([&](auto i) {
+    constexpr bool any = [] {
+      for (int j = 0; j < K; ++j)
+        if (gnz(Q, decltype(i)::value, j) && !base3(Q, decltype(i)::value, j)) return true;
+      return false;
+    }();
+    if constexpr (any) {
+      T w = 0, px = 0, py = 0;
+      sfor<0, K>([&](auto j) {
+        if constexpr (gnz(Q, i, j) && !base3(Q, i, j)) {
+          const T gx = cG[0][Q][pk(i, j)], gy = cG[1][Q][pk(i, j)];
+          w += uc[j] * gx + vc[j] * gy;
+          px += pp[j] * gx;
+          py += pp[j] * gy;
+        }
+      });
+      aU += U[i] * w; aV += V[i] * w;
+      Px += xi[i] * px; Py += xi[i] * py;
+    }
+  });
+  r[0] = am;
+  r[1] = rs * (aU + g * (J0 * Px + J2 * Py));
+  r[2] = rs * (aV + g * (J1 * Px + J3 * Py));
+}
+
+// the elevation row of volume_q alone
+template <int K, int Q, int KL>
+__device__ __forceinline__ T volume_xi(const T (&Uc)[KL], const T (&Vc)[KL]) {
+  T am = 0;
+  sfor<0, KL>([&](auto i) {
+    if constexpr (dnz(Q, i) && !base2(Q, i)) am += Uc[i] * cD[0][Q][i] + Vc[i] * cD[1][Q][i];
+  });
+  return am;
+}
+
+#ifdef CORR_TC
+#define CORR_VOL_PARAM , const float* __restrict__ vol
+#define CORR_VOL_ARG , vol
+// orders whose momentum volume terms come from the tensor cores; for K = 6
+// the CUDA-core contraction measured as fast as the tensor-core kernel plus
+// the buffer round trip, so it stays here
+__host__ __device__ constexpr bool tc_vol(int K) { return K >= 10; }
+#else
+#define CORR_VOL_PARAM
+#define CORR_VOL_ARG
+__host__ __device__ constexpr bool tc_vol(int K) { return false; }
+#endif
+
+// ---------------------------------------------------------------------------
 // auxiliary system of one order group:  M u = U, M v = V,
 //   M[i][j] = (1/s) sum_{n < K(max deg)} H_n T[n][i][j],  H = xi + h_b.
 // Solved as S u = s U with S = s M by an unpivoted LDL^T factorisation.
+// With rc given, the same thread then forms the correction of the base modes
+// (the volume terms of the degree-1 test modes with a coefficient of degree
+// >= 2) from the velocity it has just solved for, so that the base element
+// kernel can take it without waiting for the correction element kernel.
 // ---------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int64_t n, Phys ph, StateDev c,
                                                      const T* __restrict__ ch, double* __restrict__ ub,
                                                      float* __restrict__ ub32, T* __restrict__ uh,
-                                                     unsigned* status) {
+                                                     unsigned* status, unsigned long long* dmin,
+                                                     double* __restrict__ rc, int64_t rc_off, int64_t nrc) {
   const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (l >= n) return;
-  const int64_t e = g0 + l, ne = m.ne;
-  constexpr int KH = K - 3, NP = K * (K + 1) / 2;
-  const T* cb = base_c(c);
-  const T* geo = geo_t(m);
-  T H[K];
-  load_modes<K>(H, cb, ne, e, ch, n, l, 0);
-  H[0] += geo[G_HB0 * ne + e];
-  H[1] += geo[G_HB1 * ne + e];
-  H[2] += geo[G_HB2 * ne + e];
-  // depth check on the FP64 mean (base modes are FP64 in every mode)
-  const double H0d = c.cb[e] + m.geo[G_HB0 * ne + e];
-  if (!(H0d * m.geo[G_RS * ne + e] * 1.4142135623730951 > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
-  const T sv = geo[G_S * ne + e];
-  T A[NP];
-  sfor<0, K>([&](auto j) {
-    sfor<0, j + 1>([&](auto i) {
-      T acc = 0;
-      sfor<0, ktr(i, j)>([&](auto nn) {
-        if constexpr (tnz(nn, i, j)) acc += H[nn] * cT[nn][pk(i, j)];
+  double dcfl = DBL_MAX;
+  int mem = 0;
+  if (l < n) {
+    const int64_t e = g0 + l, ne = m.ne;
+    constexpr int KH = K - 3, NP = K * (K + 1) / 2;
+    const T* cb = base_c(c);
+    const T* geo = geo_t(m);
+    T H[K];
+    load_modes<K>(H, cb, ne, e, ch, n, l, 0);
+    H[0] += geo[G_HB0 * ne + e];
+    H[1] += geo[G_HB1 * ne + e];
+    H[2] += geo[G_HB2 * ne + e];
+    // depth check on the FP64 mean (base modes are FP64 in every mode)
+    const double H0d = c.cb[e] + m.geo[G_HB0 * ne + e];
+    if (!(H0d * m.geo[G_RS * ne + e] * 1.4142135623730951 > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
+    const T sv = geo[G_S * ne + e];
+    T A[NP];
+    sfor<0, K>([&](auto j) {
+      sfor<0, j + 1>([&](auto i) {
+        T acc = 0;
+        sfor<0, ktr(i, j)>([&](auto nn) {
+          if constexpr (tnz(nn, i, j)) acc += H[nn] * cT[nn][pk(i, j)];
+        });
+        A[pk(i, j)] = acc;
       });
-      A[pk(i, j)] = acc;
     });
-  });
-  // LDL^T: A[pk(i,j)] (i > j) <- L_ij;  dg[j] = d_j, rd[j] = 1/d_j
-  T dg[K], rd[K];
-  sfor<0, K>([&](auto j) {
-    T dj = A[pk(j, j)];
-    sfor<0, j>([&](auto k) { dj -= A[pk(j, k)] * A[pk(j, k)] * dg[k]; });
-    dg[j] = dj;
-    rd[j] = (T)1 / dj;
-    sfor<j + 1, K>([&](auto i) {
-      T w = A[pk(i, j)];
-      sfor<0, j>([&](auto k) { w -= A[pk(i, k)] * A[pk(j, k)] * dg[k]; });
-      A[pk(i, j)] = w * rd[j];
+    // LDL^T: A[pk(i,j)] (i > j) <- L_ij;  dg[j] = d_j, rd[j] = 1/d_j
+    T dg[K], rd[K];
+    sfor<0, K>([&](auto j) {
+      T dj = A[pk(j, j)];
+      sfor<0, j>([&](auto k) { dj -= A[pk(j, k)] * A[pk(j, k)] * dg[k]; });
+      dg[j] = dj;
+      rd[j] = (T)1 / dj;
+      sfor<j + 1, K>([&](auto i) {
+        T w = A[pk(i, j)];
+        sfor<0, j>([&](auto k) { w -= A[pk(i, k)] * A[pk(j, k)] * dg[k]; });
+        A[pk(i, j)] = w * rd[j];
+      });
     });
-  });
-  T x[2][K];
-  load_modes<K>(x[0], cb, ne, e, ch, n, l, 1);
-  load_modes<K>(x[1], cb, ne, e, ch, n, l, 2);
-  const T s = sv;
-  sfor<0, 2>([&](auto r) {
-    sfor<0, K>([&](auto i) { sfor<0, i>([&](auto k) { x[r][i] -= A[pk(i, k)] * x[r][k]; }); });
-    sfor<0, K>([&](auto i) { x[r][i] *= rd[i]; });
-    sfor<0, K>([&](auto ii) {
-      constexpr int i = K - 1 - ii;
-      sfor<i + 1, K>([&](auto k) { x[r][i] -= A[pk(k, i)] * x[r][k]; });
+    T x[2][K];
+    load_modes<K>(x[0], cb, ne, e, ch, n, l, 1);
+    load_modes<K>(x[1], cb, ne, e, ch, n, l, 2);
+    const T s = sv;
+    double u00 = 0.0, v00 = 0.0;  // mode 0 of u and v as stored (FP64)
+    sfor<0, 2>([&](auto r) {
+      sfor<0, K>([&](auto i) { sfor<0, i>([&](auto k) { x[r][i] -= A[pk(i, k)] * x[r][k]; }); });
+      sfor<0, K>([&](auto i) { x[r][i] *= rd[i]; });
+      sfor<0, K>([&](auto ii) {
+        constexpr int i = K - 1 - ii;
+        sfor<i + 1, K>([&](auto k) { x[r][i] -= A[pk(k, i)] * x[r][k]; });
+      });
+      sfor<0, K>([&](auto i) {
+        const T v = x[r][i] * s;
+        if constexpr (i < 3) {
+          ub[(r * 3 + i) * ne + e] = (double)v;
+          if constexpr (kF32) ub32[(r * 3 + i) * ne + e] = v;
+          if constexpr (i == 0) {
+            if constexpr (r == 0) u00 = (double)v; else v00 = (double)v;
+          }
+        } else {
+          uh[(r * KH + (i - 3)) * n + l] = v;
+        }
+      });
     });
-    sfor<0, K>([&](auto i) {
-      const T v = x[r][i] * s;
-      if constexpr (i < 3) {
-        ub[(r * 3 + i) * ne + e] = (double)v;
-        if constexpr (kF32) ub32[(r * 3 + i) * ne + e] = v;
-      } else {
-        uh[(r * KH + (i - 3)) * n + l] = v;
-      }
-    });
-  });
+    if (dmin) {
+      mem = m.mem[e];
+      dcfl = cfl_bound(u00, v00, H0d, m.geo[G_RS * ne + e], ph.g, m.geo[G_DIAM * ne + e], m.p[e]);
+    }
+    if (rc) {
+      constexpr int KL = Kof(deg_of(K - 1) - 1);  // modes of degree < p (the only ones D couples)
+      T xi[K], U[K], V[K], uc[K], vc[K], pp[K], Uc[KL], Vc[KL];
+      load_modes<K>(xi, cb, ne, e, ch, n, l, 0);
+      load_modes<K>(U, cb, ne, e, ch, n, l, 1);
+      load_modes<K>(V, cb, ne, e, ch, n, l, 2);
+      const T J0 = geo[G_JI0 * ne + e], J1 = geo[G_JI1 * ne + e];
+      const T J2 = geo[G_JI2 * ne + e], J3 = geo[G_JI3 * ne + e];
+      sfor<0, K>([&](auto j) {
+        const T uu = x[0][j] * s, vv = x[1][j] * s;  // the velocity modes as stored above
+        uc[j] = J0 * uu + J1 * vv;
+        vc[j] = J2 * uu + J3 * vv;
+        if constexpr (j < 3) pp[j] = (T)0.5 * xi[j] + geo[(G_HB0 + j) * ne + e];
+        else pp[j] = (T)0.5 * xi[j];
+        if constexpr (j < KL) {
+          Uc[j] = J0 * U[j] + J1 * V[j];
+          Vc[j] = J2 * U[j] + J3 * V[j];
+        }
+      });
+      const T rs = geo[G_RS * ne + e], g = (T)ph.g;
+      T r1[3], r2[3];
+      volume_q<K, 1, KL>(r1, xi, U, V, uc, vc, pp, Uc, Vc, rs, J0, J1, J2, J3, g);
+      volume_q<K, 2, KL>(r2, xi, U, V, uc, vc, pp, Uc, Vc, rs, J0, J1, J2, J3, g);
+      rc[0 * nrc + rc_off + l] = (double)r1[1];
+      rc[1 * nrc + rc_off + l] = (double)r2[1];
+      rc[2 * nrc + rc_off + l] = (double)r1[2];
+      rc[3 * nrc + rc_off + l] = (double)r2[2];
+    }
+  }
+  if (dmin) cfl_min_store(dmin, mem, dcfl);  // uniform over the grid: every lane of the warp is here
 }
 
 template <int K>
 static int usolve_group(cudaStream_t st, const DevMesh& m, const Groups& G, int p, const Phys& ph, StateDev c,
-                        VelDev u, unsigned* status) {
+                        VelDev u, unsigned* status, unsigned long long* dmin, void* rc) {
   const int64_t g0 = G.start[p], n = G.start[p + 1] - g0;
   if (n == 0) return 0;
+  const int64_t nrc = G.start[5] - G.start[2], rc_off = g0 - G.start[2];
   const int ct = launch_shape().corr_threads;
   k_usolve_corr<K><<<nblocks(n, ct), ct, 0, st>>>(m, g0, n, ph, c, (const T*)c.ch[p], u.ub, u.ub32,
-                                                    (T*)u.uh[p], status);
+                                                    (T*)u.uh[p], status, dmin, (double*)rc, rc_off, nrc);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
 }
 
 int launch_usolve_corr(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u,
-                       unsigned* status) {
-  int r = usolve_group<6>(st, m, G, 2, ph, c, u, status);
-  if (!r) r = usolve_group<10>(st, m, G, 3, ph, c, u, status);
-  if (!r) r = usolve_group<15>(st, m, G, 4, ph, c, u, status);
+                       unsigned* status, unsigned long long* dmin, void* rc) {
+  int r = usolve_group<6>(st, m, G, 2, ph, c, u, status, dmin, rc);
+  if (!r) r = usolve_group<10>(st, m, G, 3, ph, c, u, status, dmin, rc);
+  if (!r) r = usolve_group<15>(st, m, G, 4, ph, c, u, status, dmin, rc);
   return r;
 }
 
@@ -235,19 +349,22 @@ struct Tr { T xb, Ub, Vb, ub, vb, xh, Uh, Vh, uh, vh; };
 
 template <int PM>
 __device__ __forceinline__ void side_traces(const DevMesh& m, const Groups& G, StateDev c, VelDev u, int64_t e,
-                                            int k, bool reverse, Tr (&tr)[npts_for(PM)]) {
+                                            int p, int k, bool reverse, Tr (&tr)[npts_for(PM)]) {
   constexpr int N = npts_for(PM), KM = Kof(PM), GI = PM - 2;
   const int64_t ne = m.ne;
-  const int p = m.p[e], K = Kof(p);
+  const int K = Kof(p);
   const T rs = geo_t(m)[G_RS * ne + e];
   const T* cbt = base_c(c);
   const T* ubt = base_u(u);
   int64_t l = 0, n = 1;
   const T* hc = nullptr;
   const T* hu = nullptr;
-  if (p >= 2) {
-    l = e - G.start[p]; n = G.start[p + 1] - G.start[p];
-    hc = (const T*)c.ch[p]; hu = (const T*)u.uh[p];
+  if (p >= 2) {  // selects, not a runtime index into the parameter arrays (that would copy them to the stack)
+    const int64_t s0 = p == 2 ? G.start[2] : p == 3 ? G.start[3] : G.start[4];
+    const int64_t s1 = p == 2 ? G.start[3] : p == 3 ? G.start[4] : G.start[5];
+    l = e - s0; n = s1 - s0;
+    hc = (const T*)(p == 2 ? c.ch[2] : p == 3 ? c.ch[3] : c.ch[4]);
+    hu = (const T*)(p == 2 ? u.uh[2] : p == 3 ? u.uh[3] : u.uh[4]);
   }
   sfor<0, N>([&](auto g) { tr[g] = Tr{0, 0, 0, 0, 0, 0, 0, 0, 0, 0}; });
   sfor<0, KM>([&](auto i) {
@@ -282,6 +399,7 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
   const int64_t ed = list[idx], nE = m.nedge;
   const int L = m.eL[ed], R = m.eR[ed], info = m.einfo[ed];
   const int kL = info & 3, kR = (info >> 2) & 3, bc = info >> 4;
+  const int pL = m.p[L], pR = R >= 0 ? m.p[R] : 0;
   const T* eg = egeo_t(m);
   const T len = eg[E_LEN * nE + ed], nx = eg[E_NX * nE + ed], ny = eg[E_NY * nE + ed];
   const T hA = eg[E_HA * nE + ed], hB = eg[E_HB * nE + ed];
@@ -297,9 +415,9 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
   const T HL = cbt[L] * mL + hmid;
   T unR, HR;
   Tr a[N], b[N];
-  side_traces<PM>(m, G, c, u, L, kL, false, a);
+  side_traces<PM>(m, G, c, u, L, pL, kL, false, a);
   if (R >= 0) {
-    side_traces<PM>(m, G, c, u, R, kR, true, b);
+    side_traces<PM>(m, G, c, u, R, pR, kR, true, b);
     const T mR = (T)1.4142135623730951 * geo[G_RS * ne + R];
     unR = (ubt[R] * nx + ubt[3 * ne + R] * ny) * mR;
     HR = cbt[R] * mR + hmid;
@@ -367,8 +485,8 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
       }
     });
   };
-  if (m.p[L] >= 2) project(0, kL, Kof(m.p[L]), -geo[G_RS * ne + L]);
-  if (R >= 0 && m.p[R] >= 2) project(1, kR, Kof(m.p[R]), geo[G_RS * ne + R]);
+  if (pL >= 2) project(0, kL, Kof(pL), -geo[G_RS * ne + L]);
+  if (R >= 0 && pR >= 2) project(1, kR, Kof(pR), geo[G_RS * ne + R]);
   // Degree-<=1 test functions are linear along the edge, so the correction's
   // share of the base modes is fixed by (M0, M1); the two-point flux with the
   // same moments is stored next to the base flux of this edge, and both sides
@@ -418,71 +536,6 @@ __device__ __forceinline__ void add_edge_projection(T (&r)[3], const EdgeFlux& f
   for (int f = 0; f < 3; ++f) r[f] += P[((side * 3 + f) * KQ + (q - 3)) * nl + sl];
 }
 
-// ---------------------------------------------------------------------------
-// Volume terms of Eq. (13) for one test mode Q (non-base index triples only),
-// with J^{-1} folded into the contravariant coefficients
-//   Uc_i = (J^-1 q_i)_xhat, Vc_i = (J^-1 q_i)_yhat, uc_j, vc_j likewise, pp_j = xi_j/2 + hb_j:
-//   r_xi = sum_i Uc_i D_x[Q][i] + Vc_i D_y[Q][i]
-//   r_U  = (1/s) [ sum_ij U_i (uc_j G_x[Q][i][j] + vc_j G_y[Q][i][j]) + g (J00 P_x + J10 P_y) ]
-//   r_V  = (1/s) [ sum_ij V_i (...) + g (J01 P_x + J11 P_y) ]
-//   P_k  = sum_ij xi_i pp_j G_k[Q][i][j]
-// ---------------------------------------------------------------------------
-template <int K, int Q, int KL>
-__device__ __forceinline__ void volume_q(T (&r)[3], const T (&xi)[K], const T (&U)[K], const T (&V)[K],
-                                         const T (&uc)[K], const T (&vc)[K], const T (&pp)[K], const T (&Uc)[KL],
-                                         const T (&Vc)[KL], T rs, T J0, T J1, T J2, T J3, T g) {
-  T am = 0;
-  sfor<0, KL>([&](auto i) {
-    if constexpr (dnz(Q, i) && !base2(Q, i)) am += Uc[i] * cD[0][Q][i] + Vc[i] * cD[1][Q][i];
-  });
-  T aU = 0, aV = 0, Px = 0, Py = 0;
-  sfor<0, K>([&](auto i) {
-    constexpr bool any = [] {
-      for (int j = 0; j < K; ++j)
-        if (gnz(Q, decltype(i)::value, j) && !base3(Q, decltype(i)::value, j)) return true;
-      return false;
-    }();
-    if constexpr (any) {
-      T w = 0, px = 0, py = 0;
-      sfor<0, K>([&](auto j) {
-        if constexpr (gnz(Q, i, j) && !base3(Q, i, j)) {
-          const T gx = cG[0][Q][pk(i, j)], gy = cG[1][Q][pk(i, j)];
-          w += uc[j] * gx + vc[j] * gy;
-          px += pp[j] * gx;
-          py += pp[j] * gy;
-        }
-      });
-      aU += U[i] * w; aV += V[i] * w;
-      Px += xi[i] * px; Py += xi[i] * py;
-    }
-  });
-  r[0] = am;
-  r[1] = rs * (aU + g * (J0 * Px + J2 * Py));
-  r[2] = rs * (aV + g * (J1 * Px + J3 * Py));
-}
-
-// the elevation row of volume_q alone
-template <int K, int Q, int KL>
-__device__ __forceinline__ T volume_xi(const T (&Uc)[KL], const T (&Vc)[KL]) {
-  T am = 0;
-  sfor<0, KL>([&](auto i) {
-    if constexpr (dnz(Q, i) && !base2(Q, i)) am += Uc[i] * cD[0][Q][i] + Vc[i] * cD[1][Q][i];
-  });
-  return am;
-}
-
-#ifdef CORR_TC
-#define CORR_VOL_PARAM , const float* __restrict__ vol
-#define CORR_VOL_ARG , vol
-// orders whose momentum volume terms come from the tensor cores; for K = 6
-// the CUDA-core contraction measured as fast as the tensor-core kernel plus
-// the buffer round trip, so it stays here
-__host__ __device__ constexpr bool tc_vol(int K) { return K >= 10; }
-#else
-#define CORR_VOL_PARAM
-#define CORR_VOL_ARG
-__host__ __device__ constexpr bool tc_vol(int K) { return false; }
-#endif
 
 // ---------------------------------------------------------------------------
 // correction element update of one order group (K = K(p), p >= 2).
@@ -494,25 +547,23 @@ __host__ __device__ constexpr bool tc_vol(int K) { return false; }
 // warps of a block each ran a different q).  q = 1, 2: the correction of the base
 // modes (volume terms with a higher coefficient index) -> rc;  q >= 3: the
 // full volume term, the source g grad h_b xi_q, the projections of the full
-// edge fluxes, and the SSP-RK combination of that higher mode.
+// edge fluxes, and the SSP-RK combination of that higher mode.  One launch
+// covers the test modes qlo .. qlo + gridDim.x / nb - 1.
 // ---------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(128, kF32 ? 4 : 2) k_elem_corr(DevMesh m, CorrEdges ce, int64_t g0, int64_t n,
-                                                            int64_t rc_off, int64_t nrc, Phys ph, Stage stg,
+                                                            int64_t rc_off, int64_t nrc, int qlo, Phys ph, Stage stg,
                                                             const T* __restrict__ cbS,
                                                             const T* __restrict__ chS, const T* __restrict__ chN,
                                                             T* __restrict__ chO, const T* __restrict__ ub,
                                                             const T* __restrict__ uh, EdgeFlux fx,
                                                             double* __restrict__ rc CORR_VOL_PARAM) {
   const int64_t nb = (n + 127) / 128;
-  const int q = 1 + (int)(blockIdx.x / nb);
+  const int q = qlo + (int)(blockIdx.x / nb);
   const int64_t l = (blockIdx.x % nb) * 128 + threadIdx.x;
   if (l >= n) return;
   const int64_t e = g0 + l, ne = m.ne;
   constexpr int KH = K - 3;
-  uint32_t ecs[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) ecs[k] = ce.ecs[k * nrc + rc_off + l];
   constexpr int KL = Kof(deg_of(K - 1) - 1);  // modes of degree < p (the only ones D couples)
   const T* geo = geo_t(m);
   T xi[K], U[K], V[K], uc[K], vc[K], pp[K], Uc[KL], Vc[KL];
@@ -575,7 +626,7 @@ __global__ void __launch_bounds__(128, kF32 ? 4 : 2) k_elem_corr(DevMesh m, Corr
   // edges: every edge of a p >= 2 element is a correction edge
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const uint32_t cs = ecs[k];
+    const uint32_t cs = ce.ecs[k * nrc + rc_off + l];
     const bool right = (cs >> 27) & 1;
     const int pm = cs >> 28;
     const int64_t sl = cs & 0x07ffffff;
@@ -600,11 +651,13 @@ static const T* base_u_host(const VelDev& u) {
 template <int K>
 static int elem_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, int p, const Phys& ph,
                       const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx,
-                      void* rc CORR_VOL_PARAM) {
+                      void* rc, int part CORR_VOL_PARAM) {
   const int64_t g0 = G.start[p], n = G.start[p + 1] - g0;
   if (n == 0) return 0;
   const int64_t nrc = G.start[5] - G.start[2], rc_off = g0 - G.start[2];
-  k_elem_corr<K><<<(unsigned)(((n + 127) / 128) * (K - 1)), 128, 0, st>>>(m, ce, g0, n, rc_off, nrc, ph, stg, base_c_host(cS),
+  // part 0: every test mode 1 .. K - 1 (rc included); part 1: the higher test modes 3 .. K - 1
+  const int qlo = part == 0 ? 1 : 3, nq = part == 0 ? K - 1 : K - 3;
+  k_elem_corr<K><<<(unsigned)(((n + 127) / 128) * nq), 128, 0, st>>>(m, ce, g0, n, rc_off, nrc, qlo, ph, stg, base_c_host(cS),
                                                            (const T*)cS.ch[p], (const T*)cN.ch[p], (T*)cO.ch[p],
                                                            base_u_host(u), (const T*)u.uh[p], fx,
                                                            (double*)rc CORR_VOL_ARG);
@@ -615,10 +668,10 @@ static int elem_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
 
 int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
                      const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx,
-                     void* rc CORR_VOL_PARAM) {
-  int r = elem_group<6>(st, m, ce, G, 2, ph, stg, cS, cN, cO, u, fx, rc CORR_VOL_ARG);
-  if (!r) r = elem_group<10>(st, m, ce, G, 3, ph, stg, cS, cN, cO, u, fx, rc CORR_VOL_ARG);
-  if (!r) r = elem_group<15>(st, m, ce, G, 4, ph, stg, cS, cN, cO, u, fx, rc CORR_VOL_ARG);
+                     void* rc, int part CORR_VOL_PARAM) {
+  int r = elem_group<6>(st, m, ce, G, 2, ph, stg, cS, cN, cO, u, fx, rc, part CORR_VOL_ARG);
+  if (!r) r = elem_group<10>(st, m, ce, G, 3, ph, stg, cS, cN, cO, u, fx, rc, part CORR_VOL_ARG);
+  if (!r) r = elem_group<15>(st, m, ce, G, 4, ph, stg, cS, cN, cO, u, fx, rc, part CORR_VOL_ARG);
   return r;
 }
 

@@ -55,16 +55,17 @@ int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int3
                    StateDev st, double* cu);
 int launch_sub(cudaStream_t s, const double* a, const double* b, double* out, int64_t n);
 
+// dmin (or nullptr): per member, the running minimum of the elements' CFL
+// bounds (DBL_MAX bits before the first stage of a step), folded in by the
+// velocity solves of that stage and read (and reset) by launch_advance_time
 int launch_usolve_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
-                       double* ub, float* ub32, unsigned* status);
-int launch_dt(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
-              const double* ub, unsigned long long* dmin);
+                       double* ub, float* ub32, unsigned* status, unsigned long long* dmin);
 int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Stage& stg, const double* cb,
                      const double* ub, EdgeFlux fx);
 int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
                      int corr_fp32, const double* cbS, const double* cbN, double* cbO, float* cbO32,
                      const double* ub, EdgeFlux fx, const void* rc, double cfl);
-int launch_advance_time(cudaStream_t s, double* t_dev, const unsigned long long* dmin, double cfl,
+int launch_advance_time(cudaStream_t s, double* t_dev, unsigned long long* dmin, double cfl,
                         double dt_fixed, double* dt_dev, int nmem);
 int launch_reset_min(cudaStream_t s, unsigned long long* dmin, int nmem);
 int launch_indicator(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
@@ -81,11 +82,12 @@ int launch_energy(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp
   namespace NS {                                                                                                 \
   void upload_tables();                                                                                          \
   int launch_usolve_corr(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u, \
-                         unsigned* status);                                                                      \
+                         unsigned* status, unsigned long long* dmin, void* rc);                                  \
   int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,   \
                        const Stage& stg, StateDev c, VelDev u, EdgeFlux fx);                                      \
   int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,   \
-                       const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc); \
+                       const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc,  \
+                       int part);                                                                                 \
   }
 SWE_CORR_DECL(corr64)
 SWE_CORR_DECL(corr32)
@@ -97,12 +99,12 @@ namespace corrtc {
 void upload_tables();
 int upload_tc_tables();
 int launch_usolve_corr(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u,
-                       unsigned* status);
+                       unsigned* status, unsigned long long* dmin, void* rc);
 int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
                      const Stage& stg, StateDev c, VelDev u, EdgeFlux fx);
 int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
                      const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc,
-                     const float* vol);
+                     int part, const float* vol);
 int launch_vol_tc(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u,
                   float* vol, unsigned* status);
 // host: the shared-memory image of the B operands for K = 6, 10, 15 (floats written, or needed when out is NULL)

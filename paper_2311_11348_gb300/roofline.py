@@ -7,18 +7,21 @@ loads, conversions and selects count 0.  They are the "algorithmic flops per
 unit" of the roofline that bench.py reports:
 
   family      unit                         arithmetic       count per unit
-  usolve      element (p<=1 / p>=2)        FP64 / corr      USOLVE_P1 / usolve_flops(K)
-  dt          element                      FP64             DT
+  usolve      element (p<=1 / p>=2)        FP64 / corr      USOLVE_P1 / usolve_flops(K, rc)
   edge_base   edge                         FP64             EDGE_BASE
   elem_base   element                      FP64             ELEM_BASE
   edge_corr   edge with max(p_L,p_R) >= 2  corr type        edge_corr_flops(K_L, K_R, pmax)
-  elem_corr   element p >= 2               corr type        elem_corr_flops(K, tc)
+  elem_corr   element p >= 2               corr type        elem_corr_flops(K, tc, rc)
   vol_tc      element p >= 2               TF32 tensor      vol_tc_flops(K)
 
 "corr type" is FP64 in the FP64 mode and FP32 in both mixed modes.  In the
-tensor-core mode ("tf32") elem_corr leaves the momentum volume terms to
-vol_tc, whose count is the MMA work it issues: three TF32 passes (head x
-head, tail x head, head x tail) over the padded K x 16 product blocks.
+FP64 and mixed modes the velocity solve of a p >= 2 element also forms the
+volume terms of the degree-1 test modes (rc), and elem_corr covers the test
+modes of degree >= 2; in the tensor-core mode ("tf32") elem_corr covers every
+test mode and leaves the momentum volume terms of p >= 3 to vol_tc, whose
+count is the MMA work it issues: three TF32 passes (head x head, tail x head,
+head x tail) over the padded K x 16 product blocks.  The CFL bounds (DT per
+element, first stage of a step) are part of the usolve family.
 """
 from __future__ import annotations
 
@@ -67,8 +70,9 @@ def ktr(i, j):
     return KP[max(DEG[i], DEG[j])]
 
 
-def usolve_flops(K):
-    """truncated K x K assembly, LDL^T, two right-hand sides"""
+def usolve_flops(K, rc=False):
+    """truncated K x K assembly, LDL^T, two right-hand sides (and, with rc,
+    the volume terms of test modes 1 and 2)"""
     f = 3
     for j in range(K):
         for i in range(j + 1):
@@ -76,25 +80,39 @@ def usolve_flops(K):
     for j in range(K):
         f += 3 * j + 1 + (K - 1 - j) * (3 * j + 1)
     f += 2 * (K * (K - 1) + K + K * (K - 1) + K)
+    if rc:
+        f += setup_flops(K) + sum(volume_flops(K, q) for q in (1, 2))
     return f
 
 
-def elem_corr_flops(K, tc=False):
-    """volume contraction (non-base triples), source, edge projections, RK;
-    with tc the momentum rows' volume terms are vol_tc's"""
+def setup_flops(K, tc=False):
+    """contravariant coefficients (J^-1 applied to u, v and to U, V of degree < p) and xi/2 + h_b"""
     KL = KP[DEG[K - 1] - 1]
-    f = KL * 6 if tc else K * 6 + KL * 6  # contravariant coefficients and xi/2 + h_b
-    for q in range(1, K):
-        for i in range(K):
-            if dnz(q, i) and not (q < 3 and i < 3):
-                f += 4
-            if tc:
-                continue
-            inner = sum(1 for j in range(K) if gnz(q, i, j) and not (q < 3 and i < 3 and j < 3))
-            f += 8 * inner + (8 if inner else 0)
-        f += 0 if tc else 10
+    return KL * 6 if tc else K * 6 + KL * 6
+
+
+def volume_flops(K, q, tc=False):
+    """the volume contraction of test mode q (non-base triples); with tc only the elevation row"""
+    f = 0
+    for i in range(K):
+        if dnz(q, i) and not (q < 3 and i < 3):
+            f += 4
+        if tc:
+            continue
+        inner = sum(1 for j in range(K) if gnz(q, i, j) and not (q < 3 and i < 3 and j < 3))
+        f += 8 * inner + (8 if inner else 0)
+    return f + (0 if tc else 10)
+
+
+def elem_corr_flops(K, tc=False, rc=True):
+    """volume contraction (non-base triples), source, the three edges'
+    projected fluxes and the RK combination of the higher test modes; with rc
+    also test modes 1 and 2; with tc the momentum rows' volume terms are vol_tc's"""
+    f = setup_flops(K, tc)
+    for q in range(1 if rc else 3, K):
+        f += volume_flops(K, q, tc)
         if q >= 3:
-            f += 4 + 3 * npts(DEG[K - 1]) * (1 + 3 * 2) + 3 * 5
+            f += 4 + 3 * 3 + 3 * 5
     return f
 
 
@@ -106,8 +124,14 @@ def vol_tc_flops(K):
 
 
 def edge_corr_flops(KL, KR, pm):
+    """traces of both sides (5 fields), lambda, the flux at npts(pm) points and
+    its two moments, the projections onto the higher test modes of each side"""
     N = npts(pm)
-    return 12 + N * (2 * 10 * (KL + KR) + 95)
+    f = 12 + N * (2 * 10 * (KL + KR) + (KL + KR) + 95)
+    for K in (KL, KR):
+        if K >= 6:
+            f += (K - 3) * 3 * (2 * N + 1)
+    return f
 
 
 def family_flops(orders, fam, nedge=None, mode="mixed"):
@@ -122,11 +146,13 @@ def family_flops(orders, fam, nedge=None, mode="mixed"):
     if fam == "edge_base":
         return st * EDGE_BASE * nedge
     if fam == "dt":
-        return DT * ne
+        return 0
     if fam == "usolve":
-        return st * (n[1] * USOLVE_P1 + n[0] * 6 + sum(n[q] * usolve_flops(KP[q]) for q in (2, 3, 4)))
+        rc = mode != "tf32"
+        return st * (n[1] * USOLVE_P1 + n[0] * 6 + sum(n[q] * usolve_flops(KP[q], rc) for q in (2, 3, 4))) + DT * ne
     if fam == "elem_corr":
-        return st * sum(n[q] * elem_corr_flops(KP[q], tc=(mode == "tf32" and q >= 3)) for q in (2, 3, 4))
+        return st * sum(n[q] * elem_corr_flops(KP[q], tc=(mode == "tf32" and q >= 3), rc=(mode == "tf32"))
+                        for q in (2, 3, 4))
     if fam == "vol_tc":  # orders 3 and 4 (order 2 stays on the CUDA cores)
         return st * sum(n[q] * vol_tc_flops(KP[q]) for q in (3, 4))
     if fam == "edge_corr":
