@@ -590,8 +590,9 @@ def main():
 
 # DRAM bytes (read + write) per launch of the base kernels on the default
 # ocean workload (256x256), from the full ncu capture summarised in
-# profiles/ocean_p123_kernels_ncu_full.md (cold cache); None elsewhere
-MEASURED_TRAFFIC = {"edge_base": 28.632576e6 + 6.4e3, "elem_base": 59.157248e6 + 777.216e3}
+# profiles/ocean_p123_kernels_ncu_full.md (cold cache; elem_base's is a first
+# stage's, which does not read the step's start state); None elsewhere
+MEASURED_TRAFFIC = {"edge_base": 28.632832e6 + 24.576e3, "elem_base": 49.723904e6 + 572.928e3}
 
 
 def roofline(w, r, dom, steps, pk, head):
