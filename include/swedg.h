@@ -236,14 +236,18 @@ int swe_edge_table(int npts, double* s, double* w, double* B);
 int64_t swe_tc_operand_image(int K, float* out, int64_t cap);
 
 /* Launch shapes (the paper has no counterpart: they tune the GPU kernels to
- * the mesh, orders and device).  shape[4]:
+ * the mesh, orders and device).  shape[5]:
  *   [0] resident blocks per SM of the grid-stride base edge and element
  *       kernels, 0..32 (0: no cap, one block per base_threads units of work)
  *   [1] threads per block of those kernels, 32..128, a multiple of 32
  *   [2] threads per block of the base u-solve, 32..256, a multiple of 32
  *   [3] threads per block of the correction u-solve and edge kernels,
  *       32..128, a multiple of 32
- * Defaults {2, 128, 256, 128}.  Results do not depend on the shape (every
+ *   [4] schedule of the correction element kernel (FP64 and mixed modes;
+ *       ignored in SWE_PREC_MIXED_TF32): 0 = its higher test modes run
+ *       before the base element kernel, 1 = beside it (on the correction
+ *       stream, joined at the end of the stage)
+ * Defaults {2, 128, 256, 128, 0}.  Results do not depend on the shape (every
  * unit of work is computed by one thread in the same order).  SWE_EINVAL for
  * a shape out of range. */
 int swe_get_launch_shape(swe_ctx* ctx, int32_t* shape);
@@ -251,9 +255,9 @@ int swe_set_launch_shape(swe_ctx* ctx, const int32_t* shape);
 
 /* Autotuner: for candidate launch shapes (coordinate descent: blocks per SM
  * in {1,2,3,4,6,0}, then base threads {64,128}, u-solve threads {128,256},
- * correction threads {64,128}), runs `steps` CFL steps of the context's own
+ * correction threads {64,128}, schedule {0,1}), runs `steps` CFL steps of the context's own
  * mesh and state, times them with CUDA events on the context stream, keeps
- * the fastest shape and restores the state and member times.  shape_out[4]
+ * the fastest shape and restores the state and member times.  shape_out[5]
  * and ms_out (time per step of the choice) may be NULL.  Needs the state to
  * stay valid for the trial steps (errors of swe_run are returned). */
 int swe_autotune(swe_ctx* ctx, int steps, int32_t* shape_out, double* ms_out);

@@ -28,7 +28,7 @@ namespace swedg {
 static thread_local std::string g_cuda_err;
 static thread_local int64_t* g_launch_counter = nullptr;
 static thread_local const LaunchShape* g_shape = nullptr;
-static const LaunchShape kDefaultShape{2, 128, 256, 128};
+static const LaunchShape kDefaultShape{2, 128, 256, 128, 0};
 void count_launch(int n) {
   if (g_launch_counter) *g_launch_counter += n;
 }
@@ -55,7 +55,7 @@ struct swe_ctx {
   swe_params prm{};
   cudaStream_t stream = nullptr;   // the caller's (or our) stream: base branch and ordering
   cudaStream_t stream2 = nullptr;  // the correction branch runs here, concurrently with the base
-  cudaEvent_t ev_fork = nullptr, ev_u1 = nullptr, ev_u2 = nullptr, ev_c = nullptr, ev_dt = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_u1 = nullptr, ev_u2 = nullptr, ev_c = nullptr, ev_dt = nullptr, ev_c2 = nullptr;
   bool own_stream = false;
   int device = 0;
   std::string err;
@@ -326,7 +326,16 @@ static int build_device(swe_ctx* ctx) {
     G_(G_GDHX) = ctx->prm.g * G_(G_DHX);
     G_(G_GDHY) = ctx->prm.g * G_(G_DHY);
     G_(G_SQA) = std::sqrt(0.5 * det);
+    G_(G_M0) = R.phi0 * rs;
   }
+  std::vector<double> etb((size_t)12 * ne);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int k = 0; k < 3; ++k) {
+      const double rs = geo[(size_t)G_RS * ne + e];
+      double* t = &etb[(size_t)(3 * e + k) * 4];
+      t[0] = rs * R.EB[2][k][1][0]; t[1] = rs * R.EB[2][k][2][0];
+      t[2] = rs * R.EB[2][k][1][1]; t[3] = rs * R.EB[2][k][2][1];
+    }
   // edges
   struct E { int32_t L, R, info; double len, nx, ny, hA, hB; };
   std::vector<E> ed;
@@ -373,6 +382,8 @@ static int build_device(swe_ctx* ctx) {
     E_(E_HG1) = ed[i].hA + R.es[2][1] * (ed[i].hB - ed[i].hA);
     E_(E_HMID) = 0.5 * (ed[i].hA + ed[i].hB);
     E_(E_WLEN) = 0.5 * ed[i].len * R.ew[2][0];  // the two weights of the base rule are equal
+    E_(E_NXW) = E_(E_WLEN) * ed[i].nx;
+    E_(E_NYW) = E_(E_WLEN) * ed[i].ny;
     if (ed[i].R >= 0) ++nint;
     eedge[(size_t)(ed[i].info & 3) * ne + ed[i].L] = (int32_t)(i << 1);
     if (ed[i].R >= 0) eedge[(size_t)((ed[i].info >> 2) & 3) * ne + ed[i].R] = (int32_t)((i << 1) | 1);
@@ -415,7 +426,9 @@ static int build_device(swe_ctx* ctx) {
   for (int64_t i = 0; i < nE; ++i) emem[i] = mem[eL[i]];
   int32_t *d_mem, *d_emem;
   if ((rc = upload(ctx, &d_mem, mem)) || (rc = upload(ctx, &d_emem, emem))) return cuda_err(ctx, rc);
-  ctx->dm = DevMesh{ne, nE, nint, d_geo, d_p, d_eedge, d_eL, d_eR, d_einfo, d_egeo, d_geo32, d_egeo32,
+  double* d_etb;
+  if ((rc = upload(ctx, &d_etb, etb))) return cuda_err(ctx, rc);
+  ctx->dm = DevMesh{ne, nE, nint, d_geo, d_p, d_eedge, d_eL, d_eR, d_einfo, d_egeo, d_geo32, d_egeo32, d_etb,
                     d_mem, d_emem, ctx->nmem};
   std::memset(&ctx->ce, 0, sizeof ctx->ce);
   ctx->ce.slot = d_slot;
@@ -524,12 +537,18 @@ static int usolve_all(swe_ctx* ctx, StateDev in) {
 //   B: usolve_corr (+ rc) -->      edge_corr -> elem_corr(q >= 3) ---^
 // (each edge kernel needs both u-solves; elem_base needs the rc of the base
 // test modes, which the velocity solve forms, and edge_corr's share of the
-// base-mode flux).  The tensor-core mode runs edge_corr -> vol_tc ->
-// elem_corr(every q) on B.  Profiling runs everything on A.
+// base-mode flux).  With the split schedule (a launch-shape choice) the
+// higher test modes, which write only the correction part of the state, run
+// beside elem_base instead:
+//   B: usolve_corr (+ rc) -->      edge_corr ----> elem_corr(q >= 3) --> (join)
+//   A:                        ... edge_base --^--> elem_base ------------^
+// The tensor-core mode runs edge_corr -> vol_tc -> elem_corr(every q) on B
+// before the join.  Profiling runs everything on A.
 static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, const Stage& stg, bool cfl_dt,
                      double dt_fixed) {
   const Phys ph = phys(ctx);
   const bool conc = !ctx->prof;
+  const bool split = ctx->shape.split && !ctx->tc && !stg.base_only;
   cudaStream_t A = ctx->stream, B = conc ? ctx->stream2 : ctx->stream;
   if (conc) {
     CU(cudaEventRecord(ctx->ev_fork, A));
@@ -590,7 +609,7 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
         CK(corrtc::launch_vol_tc(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->vol, ctx->d_status));
       }
       CK(elem_corr(0));
-    } else {
+    } else if (!split) {
       CK(elem_corr(1));  // the higher test modes (the velocity solve formed rc)
     }
   }
@@ -598,10 +617,15 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
     CU(cudaEventRecord(ctx->ev_c, B));
     CU(cudaStreamWaitEvent(A, ctx->ev_c, 0));
   }
+  if (split) CK(elem_corr(1));  // the higher test modes, beside elem_base
   {
     ProfScope ps(ctx, F_ELEMB);
     CK(launch_elem_base(A, ctx->dm, ctx->G, ph, stg, ctx->corr32, in.cb, nst.cb, out.cb, out.cb32, ctx->vel.ub,
                         ctx->fx, ctx->rc, ctx->prm.cfl));
+  }
+  if (conc && split) {
+    CU(cudaEventRecord(ctx->ev_c2, B));
+    CU(cudaStreamWaitEvent(A, ctx->ev_c2, 0));
   }
   return 0;
 }
@@ -723,6 +747,7 @@ int swe_create(swe_ctx** out, const swe_params* params) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_u2, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_c, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_dt, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_c2, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     g_create_err = "stream/event creation failed";
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -762,7 +787,7 @@ void swe_destroy(swe_ctx* ctx) {
   free_all(ctx);
   for (auto& ev : ctx->evs) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
   for (auto ev : ctx->pool) cudaEventDestroy(ev);
-  for (cudaEvent_t ev : {ctx->ev_fork, ctx->ev_u1, ctx->ev_u2, ctx->ev_c, ctx->ev_dt})
+  for (cudaEvent_t ev : {ctx->ev_fork, ctx->ev_u1, ctx->ev_u2, ctx->ev_c, ctx->ev_dt, ctx->ev_c2})
     if (ev) cudaEventDestroy(ev);
   if (ctx->stream2) { cudaStreamSynchronize(ctx->stream2); cudaStreamDestroy(ctx->stream2); }
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -1131,19 +1156,19 @@ int64_t swe_tc_operand_image(int K, float* out, int64_t cap) {
 
 static bool shape_ok(const int32_t* v) {
   return v[0] >= 0 && v[0] <= 32 && v[1] >= 32 && v[1] <= 128 && v[1] % 32 == 0 && v[2] >= 32 && v[2] <= 256 &&
-         v[2] % 32 == 0 && v[3] >= 32 && v[3] <= 128 && v[3] % 32 == 0;
+         v[2] % 32 == 0 && v[3] >= 32 && v[3] <= 128 && v[3] % 32 == 0 && (v[4] == 0 || v[4] == 1);
 }
 
 int swe_get_launch_shape(swe_ctx* ctx, int32_t* shape) {
   if (!ctx || !shape) return SWE_EINVAL;
   shape[0] = ctx->shape.base_bpsm; shape[1] = ctx->shape.base_threads;
-  shape[2] = ctx->shape.usolve_threads; shape[3] = ctx->shape.corr_threads;
+  shape[2] = ctx->shape.usolve_threads; shape[3] = ctx->shape.corr_threads; shape[4] = ctx->shape.split;
   return 0;
 }
 
 int swe_set_launch_shape(swe_ctx* ctx, const int32_t* shape) {
   if (!ctx || !shape || !shape_ok(shape)) return fail(ctx, SWE_EINVAL, "swe_set_launch_shape: shape out of range");
-  ctx->shape = LaunchShape{shape[0], shape[1], shape[2], shape[3]};
+  ctx->shape = LaunchShape{shape[0], shape[1], shape[2], shape[3], shape[4]};
   if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }  // captured with the old shape
   return 0;
 }
@@ -1187,11 +1212,13 @@ int swe_autotune(swe_ctx* ctx, int steps, int32_t* shape_out, double* ms_out) {
   LaunchShape best = ctx->shape;
   double best_ms = 0.0;
   if (!rc) rc = measure(best, &best_ms);
-  const std::vector<int> cand[4] = {{1, 2, 3, 4, 6, 0}, {64, 128}, {128, 256}, {64, 128}};
-  for (int k = 0; k < 4 && !rc; ++k)
+  const std::vector<int> cand[5] = {{1, 2, 3, 4, 6, 0}, {64, 128}, {128, 256}, {64, 128}, {0, 1}};
+  for (int k = 0; k < 5 && !rc; ++k)
     for (int v : cand[k]) {
+      if (k == 4 && ctx->tc) break;  // the tensor-core mode has one schedule
       LaunchShape sh = best;
-      int* f = k == 0 ? &sh.base_bpsm : k == 1 ? &sh.base_threads : k == 2 ? &sh.usolve_threads : &sh.corr_threads;
+      int* f = k == 0 ? &sh.base_bpsm : k == 1 ? &sh.base_threads : k == 2 ? &sh.usolve_threads
+             : k == 3 ? &sh.corr_threads : &sh.split;
       if (*f == v) continue;
       *f = v;
       double ms = 0.0;

@@ -62,6 +62,7 @@ enum {
   G_GDHX,    // g grad h_b (source term of Eq. 5)
   G_GDHY,
   G_SQA,     // sqrt|Omega_e| = int phi_{e,1}
+  G_M0,      // phihat_1 / s_e = sqrt 2 / s_e: the (constant) value of phi_{e,1}
   NGEO
 };
 
@@ -76,6 +77,8 @@ enum {
   E_HG1,
   E_HMID,     // h_b at the midpoint x_E (lambda, Eq. 10)
   E_WLEN,     // |E| w_g / 2 of the two-point rule (both weights are 1/2)
+  E_NXW,      // E_WLEN * the normal: the base flux comes out pre-weighted
+  E_NYW,
   NEGEO
 };
 
@@ -112,6 +115,9 @@ struct DevMesh {
   const double* egeo;     // [NEGEO][nedge] (rows E_*), in the left element's direction
   const float* geo32;     // FP32 copies of geo and egeo for the FP32 correction kernels
   const float* egeo32;
+  const double* etb;      // [ne][3 local edges][4]: the degree-1 basis on the edge at the two
+                          // points of the base rule, times 1/s_e: phi_{e,2}(g0), phi_{e,3}(g0),
+                          // phi_{e,2}(g1), phi_{e,3}(g1) (points in the element's own direction)
   const int32_t* mem;     // [ne] ensemble member of each element (all 0 for a single mesh)
   const int32_t* emem;    // [nedge] member of each edge
   int32_t nmem;

@@ -256,19 +256,24 @@ __device__ __forceinline__ double tide_value(const Phys& ph, double t) {
 // points.  Mode 1 is the constant sqrt 2 on every edge, so its trace is shared.
 struct Tr2 { double xi[2], U[2], V[2], w[2]; double xi0, w0; };
 
-__device__ __forceinline__ void p1_traces(const double* __restrict__ cb, const double* __restrict__ ub, int64_t ne,
-                                          int64_t e, int k, bool reverse, double rs, double nx, double ny, Tr2& t) {
-  const int g0 = reverse ? 1 : 0, g1 = reverse ? 0 : 1;
-  const double m0 = cPhi0 * rs;
-  const double b10 = rs * cB2[k][1][g0], b20 = rs * cB2[k][2][g0];
-  const double b11 = rs * cB2[k][1][g1], b21 = rs * cB2[k][2][g1];
+// P1 traces of one side at the two points of the base rule (edge direction of
+// the left element), from the scaled basis table: no FP64 multiply for the
+// basis values.  w is u . (|E| w_g / 2) n, the weighted normal velocity.
+__device__ __forceinline__ void p1_traces(const DevMesh& m, const double* __restrict__ cb,
+                                          const double* __restrict__ ub, int64_t ne, int64_t e, int k, bool reverse,
+                                          double nxw, double nyw, Tr2& t) {
+  const double m0 = m.geo[G_M0 * ne + e];
+  const double2 p0 = *reinterpret_cast<const double2*>(m.etb + (3 * e + k) * 4);
+  const double2 p1 = *reinterpret_cast<const double2*>(m.etb + (3 * e + k) * 4 + 2);
+  const double b10 = reverse ? p1.x : p0.x, b20 = reverse ? p1.y : p0.y;
+  const double b11 = reverse ? p0.x : p1.x, b21 = reverse ? p0.y : p1.y;
   double c[3][3], w[3];
 #pragma unroll
   for (int f = 0; f < 3; ++f)
 #pragma unroll
     for (int i = 0; i < 3; ++i) c[f][i] = cb[(f * 3 + i) * ne + e];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) w[i] = ub[i * ne + e] * nx + ub[(3 + i) * ne + e] * ny;
+  for (int i = 0; i < 3; ++i) w[i] = ub[i * ne + e] * nxw + ub[(3 + i) * ne + e] * nyw;
   double* out[3] = {t.xi, t.U, t.V};
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
@@ -288,14 +293,16 @@ __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg
   const int64_t ne = m.ne, nE = m.nedge;
   const int L = m.eL[ed], R = m.eR[ed], info = m.einfo[ed];
   const int kL = info & 3, kR = (info >> 2) & 3, bc = info >> 4;
-  const double nx = m.egeo[E_NX * nE + ed], ny = m.egeo[E_NY * nE + ed];
+  // the flux comes out weighted by wl = |E| w_g / 2 through the weighted
+  // normal (nxw, nyw) = wl n, which also weights w = u.n and so lambda
+  const double nxw = m.egeo[E_NXW * nE + ed], nyw = m.egeo[E_NYW * nE + ed];
   const double hmid = m.egeo[E_HMID * nE + ed];
   Tr2 a, b;
-  p1_traces(cb, ub, ne, L, kL, false, m.geo[G_RS * ne + L], nx, ny, a);
+  p1_traces(m, cb, ub, ne, L, kL, false, nxw, nyw, a);
   const double unL = a.w0, HL = a.xi0 + hmid;
   double unR, HR;
   if (R >= 0) {
-    p1_traces(cb, ub, ne, R, kR, true, m.geo[G_RS * ne + R], nx, ny, b);
+    p1_traces(m, cb, ub, ne, R, kR, true, nxw, nyw, b);
     unR = b.w0;
     HR = b.xi0 + hmid;
   } else if (bc == 2) {
@@ -306,6 +313,7 @@ __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg
     HR = xh + hmid;
   } else {
     // mirror state: q+ = q - 2 (q.n) n, (u.n)+ = -(u.n), xi+ = xi
+    const double nx = m.egeo[E_NX * nE + ed], ny = m.egeo[E_NY * nE + ed];
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
       const double qn2 = -2.0 * (a.U[g] * nx + a.V[g] * ny);
@@ -317,19 +325,16 @@ __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg
     unR = -unL;
     HR = HL;
   }
-  // lambda of Eq. (10) from the means (Sect. 3); max sqrt = sqrt max
-  const double lam = fmax(fabs(unL), fabs(unR)) + sqrt(ph.g * fmax(HL, HR));
+  // lambda of Eq. (10) from the means (Sect. 3); max sqrt = sqrt max; times wl
   const double wl = m.egeo[E_WLEN * nE + ed];
+  const double lam = fmax(fabs(unL), fabs(unR)) + wl * sqrt(ph.g * fmax(HL, HR));
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
     const double hb = m.egeo[(E_HG0 + g) * nE + ed];
     const double P = ph.g * (a.xi[g] * (0.5 * a.xi[g] + hb) + b.xi[g] * (0.5 * b.xi[g] + hb));
-    const double F0 = (a.U[g] + b.U[g]) * nx + (a.V[g] + b.V[g]) * ny + lam * (a.xi[g] - b.xi[g]);
-    const double F1 = a.U[g] * a.w[g] + b.U[g] * b.w[g] + P * nx + lam * (a.U[g] - b.U[g]);
-    const double F2 = a.V[g] * a.w[g] + b.V[g] * b.w[g] + P * ny + lam * (a.V[g] - b.V[g]);
-    Fb[(0 * 2 + g) * nE + ed] = wl * F0;
-    Fb[(1 * 2 + g) * nE + ed] = wl * F1;
-    Fb[(2 * 2 + g) * nE + ed] = wl * F2;
+    Fb[(0 * 2 + g) * nE + ed] = (a.U[g] + b.U[g]) * nxw + (a.V[g] + b.V[g]) * nyw + lam * (a.xi[g] - b.xi[g]);
+    Fb[(1 * 2 + g) * nE + ed] = a.U[g] * a.w[g] + b.U[g] * b.w[g] + P * nxw + lam * (a.U[g] - b.U[g]);
+    Fb[(2 * 2 + g) * nE + ed] = a.V[g] * a.w[g] + b.V[g] * b.w[g] + P * nyw + lam * (a.V[g] - b.V[g]);
   }
   }
 }
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
   for (int f = 0; f < 2; ++f)
 #pragma unroll
     for (int i = 0; i < 3; ++i) u[f][i] = ub[(f * 3 + i) * ne + e];
-  const double rs = geo[G_RS * ne + e], sqa = geo[G_SQA * ne + e];
+  const double rs = geo[G_RS * ne + e], sqa = geo[G_SQA * ne + e], m0 = geo[G_M0 * ne + e];
   const double hb[3] = {geo[G_HB0 * ne + e], geo[G_HB1 * ne + e], geo[G_HB2 * ne + e]};
   double r[3][3];
   // volume terms
@@ -425,11 +430,16 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
         F[f][1] += Fbc[(f * 2 + 1) * nE + ed];
       }
     }
-    const double sg = right ? rs : -rs;
-    const double s0 = sg * cPhi0;  // mode 1 is the constant sqrt 2
-    const int g0 = right ? 1 : 0, g1 = right ? 0 : 1;
-    const double b10 = sg * cB2[k][1][g0], b11 = sg * cB2[k][1][g1];
-    const double b20 = sg * cB2[k][2][g0], b21 = sg * cB2[k][2][g1];
+    // the basis at the edge's two points, times -1/s_e (left side) or +1/s_e
+    // (right side, whose own direction is reversed): table values with the
+    // sign bit set by an integer xor, no FP64 multiply
+    const unsigned long long neg = right ? 0ull : 0x8000000000000000ull;
+    auto sgn = [neg](double x) { return __longlong_as_double(__double_as_longlong(x) ^ neg); };
+    const double2 p0 = *reinterpret_cast<const double2*>(m.etb + (3 * e + k) * 4);
+    const double2 p1 = *reinterpret_cast<const double2*>(m.etb + (3 * e + k) * 4 + 2);
+    const double s0 = sgn(m0);  // mode 1 is the constant phi_{e,1}
+    const double b10 = sgn(right ? p1.x : p0.x), b11 = sgn(right ? p0.x : p1.x);
+    const double b20 = sgn(right ? p1.y : p0.y), b21 = sgn(right ? p0.y : p1.y);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
       r[f][0] += s0 * (F[f][0] + F[f][1]);

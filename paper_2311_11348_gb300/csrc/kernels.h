@@ -42,6 +42,8 @@ struct LaunchShape {
   int base_threads;    // threads per block of those kernels (32..128)
   int usolve_threads;  // threads per block of the base u-solve (32..256)
   int corr_threads;    // threads per block of the correction u-solve and edge kernels (32..128)
+  int split;           // 1: the correction element kernel's higher test modes run beside the base
+                       // element kernel instead of before it (FP64 and mixed modes)
 };
 const LaunchShape& launch_shape();
 

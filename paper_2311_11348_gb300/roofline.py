@@ -39,8 +39,8 @@ FP32_PEAK_TFLOPS = SM_COUNT * 256 * SM_MAX_GHZ / 1e3
 TF32_OVER_BF16 = 1.1 / 2.25
 
 USOLVE_P1 = 92
-EDGE_BASE = 175
-ELEM_BASE = 241
+EDGE_BASE = 160
+ELEM_BASE = 226
 DT = 12
 
 

@@ -30,7 +30,7 @@ from .ensemble import Ensemble
 
 KMAX = swedg.KMAX
 KP = (1, 3, 6, 10, 15)
-NGEO, NEGEO = 19, 9  # rows of the element and edge geometry tables
+NGEO, NEGEO = 20, 11  # rows of the element and edge geometry tables
 
 
 def device_bytes(meshes, precision):
@@ -68,7 +68,7 @@ def device_bytes(meshes, precision):
     nm = max(len(meshes), 1)
     nrc = n[2] + n[3] + n[4]
     allocs = [NGEO * 8 * ne, ne, 12 * ne, 4 * nE, 4 * nE, 4 * nE, NEGEO * 8 * nE, 4 * nE, 4 * ne,  # geo .. perm
-              NGEO * 4 * ne, NEGEO * 4 * nE, 4 * ne, 4 * nE,                                  # FP32 copies, members
+              NGEO * 4 * ne, NEGEO * 4 * nE, 96 * ne, 4 * ne, 4 * nE,                         # FP32 copies, basis, members
               12 * max(nrc, 1)] + [4 * ncl[q] for q in (2, 3, 4)]                             # correction edges
     for _ in range(3):                                                                        # RK states
         allocs += [72 * ne] + ([36 * ne] if corr32 else []) + [ts * 3 * (KP[q] - 3) * n[q] for q in (2, 3, 4)]

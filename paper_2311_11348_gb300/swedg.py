@@ -280,17 +280,20 @@ class Solver:
         self._ck(self._lib.swe_set_member_times(self.h, t.ctypes.data_as(C.c_void_p)))
 
     def launch_shape(self):
-        v = np.zeros(4, np.int32)
+        """(base blocks per SM, base threads, u-solve threads, correction threads, schedule)"""
+        v = np.zeros(5, np.int32)
         self._ck(self._lib.swe_get_launch_shape(self.h, v.ctypes.data_as(C.c_void_p)))
         return tuple(int(x) for x in v)
 
     def set_launch_shape(self, shape):
         v = np.ascontiguousarray(shape, dtype=np.int32)
+        if v.shape != (5,):
+            raise ValueError("a launch shape has 5 entries")
         self._ck(self._lib.swe_set_launch_shape(self.h, v.ctypes.data_as(C.c_void_p)))
 
     def autotune(self, steps=5):
         """choose the launch shape by timing trial steps; returns (shape, ms per step)"""
-        v = np.zeros(4, np.int32)
+        v = np.zeros(5, np.int32)
         ms = C.c_double(0.0)
         self._ck(self._lib.swe_autotune(self.h, int(steps), v.ctypes.data_as(C.c_void_p), C.byref(ms)))
         return tuple(int(x) for x in v), ms.value

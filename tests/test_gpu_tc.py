@@ -124,13 +124,15 @@ def test_tc_cfl_run_and_graph_replay_match_step_by_step():
     b.close()
 
 
-def test_autotuned_shape_gives_the_same_state():
-    """the launch shape changes no result: every unit is computed by one thread in the same order"""
+@pytest.mark.parametrize("prec", [swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32])
+def test_autotuned_shape_gives_the_same_state(prec):
+    """the launch shape (schedule included) changes no result: every unit is
+    computed by one thread in the same order"""
     w = workload(30, 6)
     m = O.Mesh(w["xy"], w["tri"], w["hv"], w["orders"], bc_tag=w["bc_tag"])
     c = m.project_state(w["ic"])
-    a = solver(w, swedg.PREC_MIXED_TF32)
-    b = solver(w, swedg.PREC_MIXED_TF32)
+    a = solver(w, prec)
+    b = solver(w, prec)
     a.set_state(c, 0.0)
     b.set_state(c, 0.0)
     c0, _ = a.get_state()
@@ -139,11 +141,15 @@ def test_autotuned_shape_gives_the_same_state():
     assert a.launch_shape() == shape and ms > 0
     c_a, t_a = a.get_state()
     assert t_a == 0.0 and np.array_equal(c_a, c0)  # the trial steps left no trace
-    b.set_launch_shape((1, 64, 128, 64))
+    b.set_launch_shape((1, 64, 128, 64, 1 - shape[4]))  # the other schedule
     a.run(10)
     b.run(10)
     assert np.array_equal(a.get_state()[0], b.get_state()[0])
     with pytest.raises(swedg.SweError):
-        a.set_launch_shape((2, 100, 256, 128))
+        a.set_launch_shape((2, 100, 256, 128, 0))
+    with pytest.raises(swedg.SweError):
+        a.set_launch_shape((2, 128, 256, 128, 2))
+    with pytest.raises(ValueError):
+        a.set_launch_shape((2, 128, 256, 128))
     a.close()
     b.close()
