@@ -220,20 +220,21 @@ def accuracy(w, res, nsteps=2):
 
 def e2e(w, res, name, steps, stream):
     """the same step through the C ABI with pinned host buffers: state in, one
-    step, state out (host<->device copies inside the timed region)"""
+    step, state out (host<->device copies inside the timed region), in the
+    packed state layout (the modes each element's order has)"""
     import torch
     s = res[name]["solver"]
-    c0 = res[name]["c0"]
-    hin = torch.from_numpy(c0.copy()).pin_memory()
+    s.set_state(res[name]["c0"], 0.0)
+    hin = torch.from_numpy(s.get_state_packed()[0]).pin_memory()
     hout = torch.empty_like(hin).pin_memory()
-    s.set_state(hin, 0.0)
+    s.set_state_packed(hin, 0.0)
     s.run(1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        s.set_state(hin, 0.0)
+        s.set_state_packed(hin, 0.0)
         s.run(1)
-        s.get_state(hout)
+        s.get_state_packed(hout)
     dt = time.perf_counter() - t0
     nbytes = hin.numel() * 8
     return dt, nbytes
@@ -333,19 +334,20 @@ def bench_ensemble(args, world):
             ref, _ = om.run(O.Params(g=9.81, cfl=0.1, rk_order=3), c0[:, :, ens.e0[small]:ens.e0[small + 1]], 0.0, 2)
             err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         e2e_rate = e2e_bytes = None
-        if name == "mixed":  # end to end through the API: pinned host state in, one step, state out
-            hin = torch.from_numpy(c0).pin_memory()
+        if name == "mixed":  # end to end through the API: pinned host state in (packed), one step, state out
+            ens.solver.set_state(c0, 0.0)
+            hin = torch.from_numpy(ens.solver.get_state_packed()[0]).pin_memory()
             hout = torch.empty_like(hin).pin_memory()
-            ens.solver.set_state(hin, 0.0)
+            ens.solver.set_state_packed(hin, 0.0)
             ens.run(1)
             torch.cuda.synchronize()
             n_e2e = 3
             t0 = time.perf_counter()
             for _ in range(n_e2e):
-                ens.solver.set_state(hin, 0.0)
+                ens.solver.set_state_packed(hin, 0.0)
                 ens.solver.set_member_times(np.zeros(ens.n))
                 ens.run(1)
-                ens.solver.get_state(hout)
+                ens.solver.get_state_packed(hout)
             e2e_rate = dps * n_e2e / (time.perf_counter() - t0)
             e2e_bytes = hin.numel() * 8
             del hin, hout

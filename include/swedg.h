@@ -122,6 +122,16 @@ int swe_set_state(swe_ctx* ctx, const double* c, double t);
 /* Copy the modal state out (host or device c_out[3][15][ne]); t_out may be NULL. */
 int swe_get_state(swe_ctx* ctx, double* c_out, double* t_out);
 
+/* The same state in the packed layout (the paper has no counterpart; it moves
+ * only the modes each element's order has): element by element in the
+ * caller's order, element u's 3 K(p_u) coefficients field-major (xi, then U,
+ * then V; modes 0 .. K(p_u)-1 each), K(p) = (p+1)(p+2)/2.  swe_packed_size
+ * gives the number of doubles (sum of 3 K(p_u)) for the current orders, or
+ * a negative error code.  Host or device buffers; SWE_EINVAL for NULL. */
+int64_t swe_packed_size(swe_ctx* ctx);
+int swe_set_state_packed(swe_ctx* ctx, const double* c, double t);
+int swe_get_state_packed(swe_ctx* ctx, double* c_out, double* t_out);
+
 /* Modal coefficients of the continuous piecewise-linear interpolant of vertex
  * values (host vals[nv]) -> host or device modes_out[3][ne] (modes 1..3).
  * This is how the bathymetry enters the scheme; it also gives P1 initial

@@ -91,6 +91,8 @@ struct swe_ctx {
   float* vol = nullptr;  // tensor-core volume terms [32][elements of order >= 2]
   double* d_user = nullptr;
   double* d_user2 = nullptr;
+  int64_t* d_off = nullptr;  // packed caller layout: offset of each caller element's 3 K(p) values
+  int64_t packed_n = 0;      // doubles in the packed layout
   double* d_dt = nullptr;
   double* d_t = nullptr;
   unsigned long long* d_dmin = nullptr;
@@ -492,6 +494,13 @@ static int build_device(swe_ctx* ctx) {
       (rc = dalloc(ctx, &ctx->d_user2, sizeof(double) * 3 * KMAX * ne)))
     return cuda_err(ctx, rc);
   if ((rc = dalloc(ctx, &ctx->d_newp, (size_t)ne))) return cuda_err(ctx, rc);
+  {
+    std::vector<int64_t> off((size_t)ne);
+    int64_t o = 0;
+    for (int64_t u = 0; u < ne; ++u) { off[u] = o; o += 3 * Kof(ctx->p_user[u]); }
+    ctx->packed_n = o;
+    if ((rc = upload(ctx, &ctx->d_off, off))) return cuda_err(ctx, rc);
+  }
   const size_t nm = (size_t)ctx->nmem;
   if ((rc = dalloc(ctx, &ctx->d_dt, sizeof(double) * nm)) || (rc = dalloc(ctx, &ctx->d_t, sizeof(double) * nm)) ||
       (rc = dalloc(ctx, &ctx->d_dmin, sizeof(unsigned long long) * nm)) ||
@@ -672,22 +681,24 @@ static int read_status(swe_ctx* ctx, bool check_state) {
 }
 
 // caller layout (host or device) -> state A (or the scratch state s)
-static int state_in(swe_ctx* ctx, const double* c, int s) {
-  const size_t bytes = sizeof(double) * 3 * KMAX * ctx->ne;
+static int state_in(swe_ctx* ctx, const double* c, int s, bool packed = false) {
+  const size_t bytes = sizeof(double) * (packed ? (size_t)ctx->packed_n : (size_t)3 * KMAX * ctx->ne);
   const double* src = c;
   if (!is_device_ptr(c)) {
     CU(cudaMemcpyAsync(ctx->d_user, c, bytes, cudaMemcpyHostToDevice, ctx->stream));
     src = ctx->d_user;
   }
-  CK(launch_from_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->corr32, src, ctx->st[s]));
+  CK(launch_from_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, packed ? ctx->d_off : nullptr, ctx->corr32, src,
+                      ctx->st[s]));
   return 0;
 }
 
-static int state_out(swe_ctx* ctx, StateDev st, double* c) {
-  const size_t bytes = sizeof(double) * 3 * KMAX * ctx->ne;
+static int state_out(swe_ctx* ctx, StateDev st, double* c, bool packed = false) {
+  const size_t bytes = sizeof(double) * (packed ? (size_t)ctx->packed_n : (size_t)3 * KMAX * ctx->ne);
   const bool dev = is_device_ptr(c);
   double* dst = dev ? c : ctx->d_user2;
-  CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->corr32, st, dst));
+  CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, packed ? ctx->d_off : nullptr, ctx->corr32, st,
+                    dst));
   if (!dev) CU(cudaMemcpyAsync(c, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   return 0;
@@ -901,6 +912,35 @@ int swe_get_state(swe_ctx* ctx, double* c_out, double* t_out) {
   return 0;
 }
 
+int64_t swe_packed_size(swe_ctx* ctx) {
+  if (!ctx || !ctx->have_mesh) return fail(ctx, SWE_EINVAL, "swe_packed_size: no mesh");
+  CK(ensure_built(ctx));
+  return ctx->packed_n;
+}
+
+int swe_set_state_packed(swe_ctx* ctx, const double* c, double t) {
+  if (!ctx || !ctx->have_mesh || !c) return fail(ctx, SWE_EINVAL, "swe_set_state_packed: no mesh or NULL");
+  CK(ensure_built(ctx));
+  LaunchScope ls(ctx);
+  CK(state_in(ctx, c, 0, true));
+  const std::vector<double> tv((size_t)ctx->nmem, t);
+  CU(cudaMemcpyAsync(ctx->d_t, tv.data(), sizeof(double) * tv.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return 0;
+}
+
+int swe_get_state_packed(swe_ctx* ctx, double* c_out, double* t_out) {
+  if (!ctx || !ctx->have_mesh || !c_out) return fail(ctx, SWE_EINVAL, "swe_get_state_packed: no mesh or NULL");
+  CK(ensure_built(ctx));
+  LaunchScope ls(ctx);
+  CK(state_out(ctx, ctx->st[0], c_out, true));
+  if (t_out) {
+    CU(cudaMemcpyAsync(t_out, ctx->d_t, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+  }
+  return 0;
+}
+
 int swe_p1_modes(swe_ctx* ctx, const double* vals, double* modes_out) {
   if (!ctx || !ctx->have_mesh || !vals || !modes_out) return fail(ctx, SWE_EINVAL, "swe_p1_modes: no mesh or NULL");
   const RefTables& R = tables();
@@ -941,7 +981,7 @@ static int rhs_impl(swe_ctx* ctx, const double* c_in, double* out0, double* out1
   if (!out1) return state_out(ctx, ctx->st[2], out0);
   // order separation: the whole rhs, then the base part alone; corr = whole - base
   const int64_t n = 3 * KMAX * ctx->ne;
-  CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->corr32, ctx->st[2], ctx->d_user));
+  CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, nullptr, ctx->corr32, ctx->st[2], ctx->d_user));
   s.base_only = 1;
   CK(run_stage(ctx, ctx->st[1], ctx->st[1], ctx->st[2], s, false, 0.0));
   for (int p = 2; p < 5; ++p)  // the base part has no higher modes

@@ -58,17 +58,24 @@ template <typename T>
 __device__ __forceinline__ T* chp(void* p) { return reinterpret_cast<T*>(p); }
 
 // ---------------------------------------------------------------------------
-// layout conversion: caller layout c[3][15][ne_user] <-> internal state
+// layout conversion: caller layout <-> internal state.  Caller layouts: the
+// full c[3][15][ne_user] (off == nullptr), or packed element by element,
+// element u's 3 K(p_u) values (field-major) from off[u] (modes < K(p_u) only).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t user_at(const int64_t* off, int64_t ne, int64_t u, int K, int f, int i) {
+  return off ? off[u] + f * K + i : (f * KMAX + i) * ne + u;
+}
+
 template <typename TC>
-__global__ void k_from_user(DevMesh m, Groups G, const int32_t* perm, const double* __restrict__ cu, StateDev st) {
+__global__ void k_from_user(DevMesh m, Groups G, const int32_t* perm, const int64_t* off,
+                            const double* __restrict__ cu, StateDev st) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m.ne) return;
   const int64_t ne = m.ne, u = perm[e];
   const int p = m.p[e], K = Kof(p);
   for (int f = 0; f < 3; ++f)
     for (int i = 0; i < 3; ++i) {
-      const double v = i < K ? cu[(f * KMAX + i) * ne + u] : 0.0;
+      const double v = i < K ? cu[user_at(off, ne, u, K, f, i)] : 0.0;
       st.cb[(f * 3 + i) * ne + e] = v;
       if (st.cb32) st.cb32[(f * 3 + i) * ne + e] = (float)v;
     }
@@ -76,25 +83,27 @@ __global__ void k_from_user(DevMesh m, Groups G, const int32_t* perm, const doub
     const int64_t n = G.start[p + 1] - G.start[p], l = e - G.start[p];
     TC* h = chp<TC>(st.ch[p]);
     for (int f = 0; f < 3; ++f)
-      for (int i = 3; i < K; ++i) h[(f * (K - 3) + (i - 3)) * n + l] = (TC)cu[(f * KMAX + i) * ne + u];
+      for (int i = 3; i < K; ++i) h[(f * (K - 3) + (i - 3)) * n + l] = (TC)cu[user_at(off, ne, u, K, f, i)];
   }
 }
 
 template <typename TC>
-__global__ void k_to_user(DevMesh m, Groups G, const int32_t* perm, StateDev st, double* __restrict__ cu) {
+__global__ void k_to_user(DevMesh m, Groups G, const int32_t* perm, const int64_t* off, StateDev st,
+                          double* __restrict__ cu) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= m.ne) return;
   const int64_t ne = m.ne, u = perm[e];
   const int p = m.p[e], K = Kof(p);
+  const int KO = off ? K : KMAX;  // the packed layout holds the modes < K only
   for (int f = 0; f < 3; ++f) {
-    for (int i = 0; i < 3; ++i) cu[(f * KMAX + i) * ne + u] = i < K ? st.cb[(f * 3 + i) * ne + e] : 0.0;
-    for (int i = 3; i < KMAX; ++i) {
+    for (int i = 0; i < 3 && i < KO; ++i) cu[user_at(off, ne, u, K, f, i)] = i < K ? st.cb[(f * 3 + i) * ne + e] : 0.0;
+    for (int i = 3; i < KO; ++i) {
       double v = 0.0;
       if (i < K) {
         const int64_t n = G.start[p + 1] - G.start[p], l = e - G.start[p];
         v = (double)chp<TC>(st.ch[p])[(f * (K - 3) + (i - 3)) * n + l];
       }
-      cu[(f * KMAX + i) * ne + u] = v;
+      cu[user_at(off, ne, u, K, f, i)] = v;
     }
   }
 }
@@ -113,23 +122,23 @@ int launch_sub(cudaStream_t s, const double* a, const double* b, double* out, in
   return 0;
 }
 
-int launch_from_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
-                     const double* cu, StateDev st) {
+int launch_from_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, const int64_t* off,
+                     int corr_fp32, const double* cu, StateDev st) {
   if (m.ne == 0) return 0;
-  if (corr_fp32) k_from_user<float><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, cu, st);
-  else k_from_user<double><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, cu, st);
+  if (corr_fp32) k_from_user<float><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, off, cu, st);
+  else k_from_user<double><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, off, cu, st);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
 }
 
-int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
-                   StateDev st, double* cu) {
+int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, const int64_t* off,
+                   int corr_fp32, StateDev st, double* cu) {
   if (m.ne == 0) return 0;
   if (corr_fp32)
-    k_to_user<float><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, st, cu);
+    k_to_user<float><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, off, st, cu);
   else
-    k_to_user<double><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, st, cu);
+    k_to_user<double><<<nblocks(m.ne, 256), 256, 0, s>>>(m, G, perm, off, st, cu);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;

@@ -51,10 +51,12 @@ const LaunchShape& launch_shape();
 void upload_base_tables();
 void set_sm_count(int n);
 
-int launch_from_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
-                     const double* cu, StateDev st);
-int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
-                   StateDev st, double* cu);
+// off == nullptr: the caller layout c[3][15][ne]; else packed, element u's
+// 3 K(p_u) values (field-major) from off[u]
+int launch_from_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, const int64_t* off,
+                     int corr_fp32, const double* cu, StateDev st);
+int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, const int64_t* off,
+                   int corr_fp32, StateDev st, double* cu);
 int launch_sub(cudaStream_t s, const double* a, const double* b, double* out, int64_t n);
 
 // dmin (or nullptr): per member, the running minimum of the elements' CFL

@@ -44,7 +44,8 @@ SYMBOLS = ("swe_default_params", "swe_create", "swe_destroy", "swe_last_error", 
            "swe_edge_table", "swe_profile", "swe_profile_read", "swe_rhs_p1_noalloc", "swe_adapt",
            "swe_run_adaptive", "swe_set_members", "swe_set_member_times", "swe_get_member_times",
            "swe_memory_bytes", "swe_tc_operand_image", "swe_get_launch_shape", "swe_set_launch_shape",
-           "swe_autotune", "swe_selftest_wait")
+           "swe_autotune", "swe_selftest_wait", "swe_packed_size", "swe_set_state_packed",
+           "swe_get_state_packed")
 
 
 def library_path() -> str:
@@ -73,6 +74,9 @@ def load():
     lib.swe_set_orders.argtypes = [P, P]
     lib.swe_set_state.argtypes = [P, P, d]
     lib.swe_get_state.argtypes = [P, P, C.POINTER(d)]
+    lib.swe_packed_size.argtypes = [P]
+    lib.swe_set_state_packed.argtypes = [P, P, d]
+    lib.swe_get_state_packed.argtypes = [P, P, C.POINTER(d)]
     lib.swe_p1_modes.argtypes = [P, P, P]
     lib.swe_rhs.argtypes = [P, P, P]
     lib.swe_rhs_parts.argtypes = [P, P, P, P]
@@ -95,6 +99,7 @@ def load():
         if s not in ("swe_destroy", "swe_default_params", "swe_last_error"):
             getattr(lib, s).restype = C.c_int
     lib.swe_tc_operand_image.restype = C.c_int64
+    lib.swe_packed_size.restype = C.c_int64
     _lib = lib
     return lib
 
@@ -216,6 +221,32 @@ class Solver:
         p, k = _ptr(out)
         t = C.c_double(0.0)
         self._ck(self._lib.swe_get_state(self.h, p, C.byref(t)))
+        return out, t.value
+
+    def packed_size(self):
+        """doubles in the packed state layout (sum over elements of 3 K(p))"""
+        n = self._lib.swe_packed_size(self.h)
+        if n < 0:
+            self._ck(int(n))
+        return int(n)
+
+    def set_state_packed(self, c, t=0.0):
+        """state in the packed layout: element by element, 3 K(p) values (xi, U, V modes)"""
+        n = c.numel() if hasattr(c, "numel") else np.size(c)
+        if n != self.packed_size():
+            raise ValueError(f"packed state has {n} values, the orders need {self.packed_size()}")
+        p, k = _ptr(c)
+        self._ck(self._lib.swe_set_state_packed(self.h, p, float(t)))
+
+    def get_state_packed(self, out=None):
+        if out is None:
+            out = np.zeros(self.packed_size())
+        n = out.numel() if hasattr(out, "numel") else np.size(out)
+        if n != self.packed_size():
+            raise ValueError(f"packed state buffer has {n} values, the orders need {self.packed_size()}")
+        p, k = _ptr(out)
+        t = C.c_double(0.0)
+        self._ck(self._lib.swe_get_state_packed(self.h, p, C.byref(t)))
         return out, t.value
 
     def p1_modes(self, vals, out=None):
