@@ -594,7 +594,7 @@ def main():
 # ocean workload (256x256), from the full ncu capture summarised in
 # profiles/ocean_p123_kernels_ncu_full.md (cold cache; elem_base's is a first
 # stage's, which does not read the step's start state); None elsewhere
-MEASURED_TRAFFIC = {"edge_base": 28.632832e6 + 24.576e3, "elem_base": 49.723904e6 + 572.928e3}
+MEASURED_TRAFFIC = {"edge_base": 41.230848e6 + 152.064e3, "elem_base": 62.508544e6 + 2397.184e3}
 
 
 def roofline(w, r, dom, steps, pk, head):

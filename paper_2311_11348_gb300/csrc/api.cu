@@ -55,6 +55,8 @@ struct swe_ctx {
   swe_params prm{};
   cudaStream_t stream = nullptr;   // the caller's (or our) stream: base branch and ordering
   cudaStream_t stream2 = nullptr;  // the correction branch runs here, concurrently with the base
+  cudaStream_t sg[2] = {nullptr, nullptr};  // its order groups p = 3, 4 (p = 2 stays on stream2)
+  cudaEvent_t ev_gf = nullptr, ev_gj[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_u1 = nullptr, ev_u2 = nullptr, ev_c = nullptr, ev_dt = nullptr, ev_c2 = nullptr;
   bool own_stream = false;
   int device = 0;
@@ -530,10 +532,13 @@ static int usolve_all(swe_ctx* ctx, StateDev in) {
   const Phys ph = phys(ctx);
   CK(launch_usolve_base(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status, nullptr));
   if (ctx->tc)
-    CK(corrtc::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, nullptr, nullptr));
+    CK(corrtc::launch_usolve_corr(GroupStreams{{ctx->stream, ctx->stream, ctx->stream}}, ctx->dm, ctx->G, ph, in, ctx->vel,
+                                  ctx->d_status, nullptr, nullptr));
   else if (ctx->corr32)
-    CK(corr32::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, nullptr, nullptr));
-  else CK(corr64::launch_usolve_corr(ctx->stream, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, nullptr, nullptr));
+    CK(corr32::launch_usolve_corr(GroupStreams{{ctx->stream, ctx->stream, ctx->stream}}, ctx->dm, ctx->G, ph, in, ctx->vel,
+                                  ctx->d_status, nullptr, nullptr));
+  else CK(corr64::launch_usolve_corr(GroupStreams{{ctx->stream, ctx->stream, ctx->stream}}, ctx->dm, ctx->G, ph, in, ctx->vel,
+                                  ctx->d_status, nullptr, nullptr));
   return 0;
 }
 
@@ -559,6 +564,24 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
   const bool conc = !ctx->prof;
   const bool split = ctx->shape.split && !ctx->tc && !stg.base_only;
   cudaStream_t A = ctx->stream, B = conc ? ctx->stream2 : ctx->stream;
+  // the order groups of each correction launch run concurrently: forked from
+  // B onto the group streams and joined back before B's next launch
+  const GroupStreams gs = conc ? GroupStreams{{B, ctx->sg[0], ctx->sg[1]}} : GroupStreams{{A, A, A}};
+  auto fork_groups = [&]() -> int {
+    if (!conc) return 0;
+    CU(cudaEventRecord(ctx->ev_gf, B));
+    CU(cudaStreamWaitEvent(ctx->sg[0], ctx->ev_gf, 0));
+    CU(cudaStreamWaitEvent(ctx->sg[1], ctx->ev_gf, 0));
+    return 0;
+  };
+  auto join_groups = [&]() -> int {
+    if (!conc) return 0;
+    for (int i = 0; i < 2; ++i) {
+      CU(cudaEventRecord(ctx->ev_gj[i], ctx->sg[i]));
+      CU(cudaStreamWaitEvent(B, ctx->ev_gj[i], 0));
+    }
+    return 0;
+  };
   if (conc) {
     CU(cudaEventRecord(ctx->ev_fork, A));
     CU(cudaStreamWaitEvent(B, ctx->ev_fork, 0));
@@ -568,11 +591,13 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
     ProfScope ps(ctx, F_USOLVE);
     unsigned long long* dmin = cfl_dt ? ctx->d_dmin : nullptr;
     CK(launch_usolve_base(A, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status, dmin));
+    CK(fork_groups());
     // the CUDA-core modes form rc in the velocity solve; the tensor-core mode in elem_corr (from vol)
-    if (ctx->tc) CK(corrtc::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, dmin, nullptr));
+    if (ctx->tc) CK(corrtc::launch_usolve_corr(gs, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, dmin, nullptr));
     else if (ctx->corr32)
-      CK(corr32::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, dmin, ctx->rc));
-    else CK(corr64::launch_usolve_corr(B, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, dmin, ctx->rc));
+      CK(corr32::launch_usolve_corr(gs, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, dmin, ctx->rc));
+    else CK(corr64::launch_usolve_corr(gs, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, dmin, ctx->rc));
+    CK(join_groups());
   }
   if (conc) {
     CU(cudaEventRecord(ctx->ev_u1, A));
@@ -594,23 +619,27 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
   }
   auto elem_corr = [&](int part) -> int {
     ProfScope ps(ctx, F_ELEMC);
+    CK(fork_groups());
     if (ctx->tc)
-      CK(corrtc::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
+      CK(corrtc::launch_elem_corr(gs, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
                                   part, ctx->vol));
     else if (ctx->corr32)
-      CK(corr32::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
+      CK(corr32::launch_elem_corr(gs, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
                                   part));
     else
-      CK(corr64::launch_elem_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
+      CK(corr64::launch_elem_corr(gs, ctx->dm, ctx->ce, ctx->G, ph, stg, in, nst, out, ctx->vel, ctx->fx, ctx->rc,
                                   part));
+    CK(join_groups());
     return 0;
   };
   if (!stg.base_only) {
     {
       ProfScope ps(ctx, F_EDGEC);
-      if (ctx->tc) CK(corrtc::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
-      else if (ctx->corr32) CK(corr32::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
-      else CK(corr64::launch_edge_corr(B, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+      CK(fork_groups());
+      if (ctx->tc) CK(corrtc::launch_edge_corr(gs, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+      else if (ctx->corr32) CK(corr32::launch_edge_corr(gs, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+      else CK(corr64::launch_edge_corr(gs, ctx->dm, ctx->ce, ctx->G, ph, stg, in, ctx->vel, ctx->fx));
+      CK(join_groups());
     }
     if (ctx->tc) {  // every test mode (rc comes from the tensor-core volume terms)
       {
@@ -752,6 +781,8 @@ int swe_create(swe_ctx** out, const swe_params* params) {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     e = cudaStreamCreateWithPriority(&ctx->stream2, cudaStreamNonBlocking, hi);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+      e = cudaStreamCreateWithPriority(&ctx->sg[i], cudaStreamNonBlocking, hi);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_u1, cudaEventDisableTiming);
@@ -759,6 +790,8 @@ int swe_create(swe_ctx** out, const swe_params* params) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_c, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_dt, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_c2, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_gf, cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ctx->ev_gj[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     g_create_err = "stream/event creation failed";
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -798,9 +831,12 @@ void swe_destroy(swe_ctx* ctx) {
   free_all(ctx);
   for (auto& ev : ctx->evs) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
   for (auto ev : ctx->pool) cudaEventDestroy(ev);
-  for (cudaEvent_t ev : {ctx->ev_fork, ctx->ev_u1, ctx->ev_u2, ctx->ev_c, ctx->ev_dt, ctx->ev_c2})
+  for (cudaEvent_t ev : {ctx->ev_fork, ctx->ev_u1, ctx->ev_u2, ctx->ev_c, ctx->ev_dt, ctx->ev_c2, ctx->ev_gf,
+                         ctx->ev_gj[0], ctx->ev_gj[1]})
     if (ev) cudaEventDestroy(ev);
   if (ctx->stream2) { cudaStreamSynchronize(ctx->stream2); cudaStreamDestroy(ctx->stream2); }
+  for (cudaStream_t sgi : ctx->sg)
+    if (sgi) { cudaStreamSynchronize(sgi); cudaStreamDestroy(sgi); }
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

@@ -326,11 +326,11 @@ static int usolve_group(cudaStream_t st, const DevMesh& m, const Groups& G, int 
   return 0;
 }
 
-int launch_usolve_corr(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u,
+int launch_usolve_corr(GroupStreams gs, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u,
                        unsigned* status, unsigned long long* dmin, void* rc) {
-  int r = usolve_group<6>(st, m, G, 2, ph, c, u, status, dmin, rc);
-  if (!r) r = usolve_group<10>(st, m, G, 3, ph, c, u, status, dmin, rc);
-  if (!r) r = usolve_group<15>(st, m, G, 4, ph, c, u, status, dmin, rc);
+  int r = usolve_group<6>(gs.s[0], m, G, 2, ph, c, u, status, dmin, rc);
+  if (!r) r = usolve_group<10>(gs.s[1], m, G, 3, ph, c, u, status, dmin, rc);
+  if (!r) r = usolve_group<15>(gs.s[2], m, G, 4, ph, c, u, status, dmin, rc);
   return r;
 }
 
@@ -512,11 +512,11 @@ static int edge_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
   return 0;
 }
 
-int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
+int launch_edge_corr(GroupStreams gs, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
                      const Stage& stg, StateDev c, VelDev u, EdgeFlux fx) {
-  int r = edge_group<2>(st, m, ce, G, ph, stg, c, u, fx);
-  if (!r) r = edge_group<3>(st, m, ce, G, ph, stg, c, u, fx);
-  if (!r) r = edge_group<4>(st, m, ce, G, ph, stg, c, u, fx);
+  int r = edge_group<2>(gs.s[0], m, ce, G, ph, stg, c, u, fx);
+  if (!r) r = edge_group<3>(gs.s[1], m, ce, G, ph, stg, c, u, fx);
+  if (!r) r = edge_group<4>(gs.s[2], m, ce, G, ph, stg, c, u, fx);
   return r;
 }
 
@@ -666,12 +666,12 @@ static int elem_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
   return 0;
 }
 
-int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
+int launch_elem_corr(GroupStreams gs, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
                      const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx,
                      void* rc, int part CORR_VOL_PARAM) {
-  int r = elem_group<6>(st, m, ce, G, 2, ph, stg, cS, cN, cO, u, fx, rc, part CORR_VOL_ARG);
-  if (!r) r = elem_group<10>(st, m, ce, G, 3, ph, stg, cS, cN, cO, u, fx, rc, part CORR_VOL_ARG);
-  if (!r) r = elem_group<15>(st, m, ce, G, 4, ph, stg, cS, cN, cO, u, fx, rc, part CORR_VOL_ARG);
+  int r = elem_group<6>(gs.s[0], m, ce, G, 2, ph, stg, cS, cN, cO, u, fx, rc, part CORR_VOL_ARG);
+  if (!r) r = elem_group<10>(gs.s[1], m, ce, G, 3, ph, stg, cS, cN, cO, u, fx, rc, part CORR_VOL_ARG);
+  if (!r) r = elem_group<15>(gs.s[2], m, ce, G, 4, ph, stg, cS, cN, cO, u, fx, rc, part CORR_VOL_ARG);
   return r;
 }
 

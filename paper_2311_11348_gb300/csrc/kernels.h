@@ -82,14 +82,21 @@ int launch_energy(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp
                   VelDev u, double* partial, int nblk, double* out);
 
 // correction kernels, one namespace per arithmetic type (FP64 / FP32)
+// Streams of the order groups p = 2, 3, 4 in the correction launchers: the
+// groups are independent (disjoint elements, edges and outputs), so they may
+// run concurrently; all three the same stream when serial.
+struct GroupStreams {
+  cudaStream_t s[3];
+};
+
 #define SWE_CORR_DECL(NS)                                                                                        \
   namespace NS {                                                                                                 \
   void upload_tables();                                                                                          \
-  int launch_usolve_corr(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u, \
+  int launch_usolve_corr(GroupStreams gs, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u, \
                          unsigned* status, unsigned long long* dmin, void* rc);                                  \
-  int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,   \
+  int launch_edge_corr(GroupStreams gs, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,   \
                        const Stage& stg, StateDev c, VelDev u, EdgeFlux fx);                                      \
-  int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,   \
+  int launch_elem_corr(GroupStreams gs, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,   \
                        const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc,  \
                        int part);                                                                                 \
   }
@@ -102,11 +109,11 @@ SWE_CORR_DECL(corr32)
 namespace corrtc {
 void upload_tables();
 int upload_tc_tables();
-int launch_usolve_corr(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u,
+int launch_usolve_corr(GroupStreams gs, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u,
                        unsigned* status, unsigned long long* dmin, void* rc);
-int launch_edge_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
+int launch_edge_corr(GroupStreams gs, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
                      const Stage& stg, StateDev c, VelDev u, EdgeFlux fx);
-int launch_elem_corr(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
+int launch_elem_corr(GroupStreams gs, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
                      const Stage& stg, StateDev cS, StateDev cN, StateDev cO, VelDev u, EdgeFlux fx, void* rc,
                      int part, const float* vol);
 int launch_vol_tc(cudaStream_t st, const DevMesh& m, const Groups& G, const Phys& ph, StateDev c, VelDev u,
