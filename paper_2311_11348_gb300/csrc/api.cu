@@ -469,10 +469,13 @@ static int build_device(swe_ctx* ctx) {
   ctx->vel.ub32 = nullptr;
   if (ctx->corr32 && (rc = dalloc(ctx, &ctx->vel.ub32, sizeof(float) * 6 * ne))) return cuda_err(ctx, rc);
   for (int p = 0; p < 5; ++p) {
-    ctx->vel.uh[p] = nullptr;
+    ctx->vel.uh[p] = ctx->vel.tr[p] = ctx->vel.trv[p] = nullptr;
     if (p < 2) continue;
     const int64_t n = ctx->G.start[p + 1] - ctx->G.start[p];
-    if ((rc = dalloc(ctx, &ctx->vel.uh[p], ts * 2 * (Kof(p) - 3) * n))) return cuda_err(ctx, rc);
+    if ((rc = dalloc(ctx, &ctx->vel.uh[p], ts * 2 * (Kof(p) - 3) * n)) ||
+        (rc = dalloc(ctx, &ctx->vel.tr[p], ts * 4 * Kof(p) * n)) ||
+        (rc = dalloc(ctx, &ctx->vel.trv[p], ts * Kof(p) * n)))
+      return cuda_err(ctx, rc);
   }
   if ((rc = dalloc(ctx, &ctx->fx.Fb, sizeof(double) * 6 * nE)) || (rc = dalloc(ctx, &ctx->fx.Fbc, sizeof(double) * 6 * nE)))
     return cuda_err(ctx, rc);

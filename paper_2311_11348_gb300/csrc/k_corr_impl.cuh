@@ -119,6 +119,23 @@ __device__ __forceinline__ double tide_value(const Phys& ph, double t) {
   return ph.tide_amp * sin(2.0 * 3.14159265358979323846 * t / ph.tide_period + ph.tide_phase);
 }
 
+// 16-byte accesses to 4 consecutive values (FP64: two of them)
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
+}
+__device__ __forceinline__ void ld4(const float* p, float& a, float& b, float& c, float& d) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double& a, double& b, double& c, double& d) {
+  const double2 v = *reinterpret_cast<const double2*>(p), w = *reinterpret_cast<const double2*>(p + 2);
+  a = v.x; b = v.y; c = w.x; d = w.y;
+}
+
 // Load all K modes of field f (base rows from the FP64 base state, higher rows
 // from the group's correction array).
 template <int K>
@@ -209,6 +226,7 @@ template <int K>
 __global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int64_t n, Phys ph, StateDev c,
                                                      const T* __restrict__ ch, double* __restrict__ ub,
                                                      float* __restrict__ ub32, T* __restrict__ uh,
+                                                     T* __restrict__ tr, T* __restrict__ trv,
                                                      unsigned* status, unsigned long long* dmin,
                                                      double* __restrict__ rc, int64_t rc_off, int64_t nrc) {
   const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -280,12 +298,18 @@ __global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int6
       mem = m.mem[e];
       dcfl = cfl_bound(u00, v00, H0d, m.geo[G_RS * ne + e], ph.g, m.geo[G_DIAM * ne + e], m.p[e]);
     }
+    T xi[K], U[K], V[K];
+    load_modes<K>(xi, cb, ne, e, ch, n, l, 0);
+    load_modes<K>(U, cb, ne, e, ch, n, l, 1);
+    load_modes<K>(V, cb, ne, e, ch, n, l, 2);
+    // this element's trace record for the correction edges (VelDev::tr)
+    sfor<0, K>([&](auto i) {
+      st4(tr + (l * K + i) * 4, xi[i], U[i], V[i], x[0][i] * s);
+      trv[l * K + i] = x[1][i] * s;
+    });
     if (rc) {
       constexpr int KL = Kof(deg_of(K - 1) - 1);  // modes of degree < p (the only ones D couples)
-      T xi[K], U[K], V[K], uc[K], vc[K], pp[K], Uc[KL], Vc[KL];
-      load_modes<K>(xi, cb, ne, e, ch, n, l, 0);
-      load_modes<K>(U, cb, ne, e, ch, n, l, 1);
-      load_modes<K>(V, cb, ne, e, ch, n, l, 2);
+      T uc[K], vc[K], pp[K], Uc[KL], Vc[KL];
       const T J0 = geo[G_JI0 * ne + e], J1 = geo[G_JI1 * ne + e];
       const T J2 = geo[G_JI2 * ne + e], J3 = geo[G_JI3 * ne + e];
       sfor<0, K>([&](auto j) {
@@ -320,7 +344,8 @@ static int usolve_group(cudaStream_t st, const DevMesh& m, const Groups& G, int 
   const int64_t nrc = G.start[5] - G.start[2], rc_off = g0 - G.start[2];
   const int ct = launch_shape().corr_threads;
   k_usolve_corr<K><<<nblocks(n, ct), ct, 0, st>>>(m, g0, n, ph, c, (const T*)c.ch[p], u.ub, u.ub32,
-                                                    (T*)u.uh[p], status, dmin, (double*)rc, rc_off, nrc);
+                                                    (T*)u.uh[p], (T*)u.tr[p], (T*)u.trv[p], status, dmin,
+                                                    (double*)rc, rc_off, nrc);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -356,27 +381,26 @@ __device__ __forceinline__ void side_traces(const DevMesh& m, const Groups& G, S
   const T rs = geo_t(m)[G_RS * ne + e];
   const T* cbt = base_c(c);
   const T* ubt = base_u(u);
-  int64_t l = 0, n = 1;
-  const T* hc = nullptr;
-  const T* hu = nullptr;
+  // an element of order >= 2 reads its trace record (16 + 4 bytes per mode),
+  // an element of order <= 1 its base modes from the base state and velocity
+  const T* r4 = nullptr;
+  const T* rv = nullptr;
   if (p >= 2) {  // selects, not a runtime index into the parameter arrays (that would copy them to the stack)
     const int64_t s0 = p == 2 ? G.start[2] : p == 3 ? G.start[3] : G.start[4];
-    const int64_t s1 = p == 2 ? G.start[3] : p == 3 ? G.start[4] : G.start[5];
-    l = e - s0; n = s1 - s0;
-    hc = (const T*)(p == 2 ? c.ch[2] : p == 3 ? c.ch[3] : c.ch[4]);
-    hu = (const T*)(p == 2 ? u.uh[2] : p == 3 ? u.uh[3] : u.uh[4]);
+    const int64_t l = e - s0;
+    r4 = (const T*)(p == 2 ? u.tr[2] : p == 3 ? u.tr[3] : u.tr[4]) + l * K * 4;
+    rv = (const T*)(p == 2 ? u.trv[2] : p == 3 ? u.trv[3] : u.trv[4]) + l * K;
   }
   sfor<0, N>([&](auto g) { tr[g] = Tr{0, 0, 0, 0, 0, 0, 0, 0, 0, 0}; });
   sfor<0, KM>([&](auto i) {
     if (i >= K) return;
     T cx, cU, cV, cu, cv;
-    if constexpr (i < 3) {
+    if (p >= 2) {
+      ld4(r4 + i * 4, cx, cU, cV, cu);
+      cv = rv[i];
+    } else if constexpr (i < 3) {
       cx = cbt[(0 * 3 + i) * ne + e]; cU = cbt[(1 * 3 + i) * ne + e]; cV = cbt[(2 * 3 + i) * ne + e];
       cu = ubt[(0 * 3 + i) * ne + e]; cv = ubt[(1 * 3 + i) * ne + e];
-    } else {
-      const int Kh = K - 3;
-      cx = hc[(0 * Kh + i - 3) * n + l]; cU = hc[(1 * Kh + i - 3) * n + l]; cV = hc[(2 * Kh + i - 3) * n + l];
-      cu = hu[(0 * Kh + i - 3) * n + l]; cv = hu[(1 * Kh + i - 3) * n + l];
     }
     sfor<0, N>([&](auto g) {
       const T b = rs * (reverse ? cEB[GI][k][i][N - 1 - g] : cEB[GI][k][i][g]);

@@ -15,6 +15,13 @@ struct VelDev {
   double* ub;        // [2][3][ne]
   void* uh[5];       // per p = 2..4: [2][K(p)-3][n_p]
   float* ub32;       // FP32 copy of ub (FP32 correction mode only)
+  // per p = 2..4, element by element, every mode i < K(p) of the stage's state
+  // and velocity as the correction kernels read them: tr = [n_p][K][4]
+  // (xi, U, V, u), trv = [n_p][K] (v); written by the correction velocity
+  // solve, read by the correction edge kernel (one 16-byte and one 4-byte
+  // load per mode instead of five scattered loads)
+  void* tr[5];
+  void* trv[5];
 };
 
 struct Groups {

@@ -72,7 +72,9 @@ def device_bytes(meshes, precision):
               12 * max(nrc, 1)] + [4 * ncl[q] for q in (2, 3, 4)]                             # correction edges
     for _ in range(3):                                                                        # RK states
         allocs += [72 * ne] + ([36 * ne] if corr32 else []) + [ts * 3 * (KP[q] - 3) * n[q] for q in (2, 3, 4)]
-    allocs += [48 * ne] + ([24 * ne] if corr32 else []) + [ts * 2 * (KP[q] - 3) * n[q] for q in (2, 3, 4)]
+    allocs += [48 * ne] + ([24 * ne] if corr32 else [])
+    for q in (2, 3, 4):                                                                       # velocity, trace records
+        allocs += [ts * 2 * (KP[q] - 3) * n[q], ts * 4 * KP[q] * n[q], ts * KP[q] * n[q]]
     allocs += [48 * nE, 48 * nE] + [ts * 2 * 3 * (KP[q] - 3) * ncl[q] for q in (2, 3, 4)]  # fluxes, projections
     allocs += [32 * max(nrc, 1)]
     if precision == swedg.PREC_MIXED_TF32:
