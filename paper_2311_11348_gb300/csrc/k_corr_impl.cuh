@@ -4,19 +4,23 @@
 // (FP32 correction), which define CORR_T and CORR_NS before including it.
 //
 //   k_usolve_corr<K>   truncated auxiliary system uH = q for one order group
-//                      (K x K symmetric, LDL^T), also writes the degree-1 modes
+//                      (K x K symmetric, LDL^T), also writes the degree-1
+//                      modes, the element's trace record for the edge kernel,
+//                      in the first stage of a CFL step its CFL bound, and
+//                      (FP64 and mixed modes) the correction of the base
+//                      modes rc (volume terms of the degree-1 test modes)
 //   k_edge_corr<PM>    edges with max(p_L, p_R) = PM >= 2: traces of the P1
 //                      and higher parts at npts_for(PM) Gauss points, the LF
 //                      flux of the higher part written as a sum of products
-//                      (no cancellation against the base flux), plus the full
-//                      flux for the higher test modes
+//                      (no cancellation against the base flux), the full flux
+//                      projected onto both sides' higher test modes, and the
+//                      two-point equivalent of the correction flux for the
+//                      base modes (Fbc)
 //   k_elem_corr<K>     volume terms as contractions with the reference
 //                      tensors D and G of Eq. (13) (compile-time sparsity),
-//                      source, projection of the correction edge fluxes, the
-//                      correction of the base modes (rc) and the SSP-RK
-//                      update of the higher modes (or, when the velocity
-//                      solve has formed rc, of the higher test modes only,
-//                      overlapping the base element kernel)
+//                      source, the edges' projected fluxes and the SSP-RK
+//                      update of the higher modes (test modes q >= 3); in the
+//                      tensor-core mode also the test modes 1, 2 (rc)
 //
 // With CORR_TC defined (k_corr_tc.cu) the volume terms of the momentum rows
 // come from a buffer that the tensor-core contraction k_vol_tc<K> wrote;
