@@ -216,7 +216,7 @@ def test_lake_at_rest(xi0):
         assert np.all(r == 0.0)
     else:
         assert np.abs(r).max() <= 1e-12 * scale
-    c1, t = m.run(P, c, 0.0, 100)
+    c1, t = m.run(P, c, 0.0, 1000)
     assert np.abs(c1 - c).max() <= 1e-12 * max(xi0, 1.0)
 
 
@@ -294,7 +294,7 @@ def test_mass_conservation_walls():
     M0 = m.mass(c)
     area = m.geometry()["area"]
     Mref = M0 + np.sum(m.geometry()["hb"][:, 0] * np.sqrt(area))  # total water volume int H
-    steps = 200
+    steps = 1000
     c1, t = m.run(P, c, 0.0, steps)
     assert t > 0
     assert abs(m.mass(c1) - M0) / Mref <= 1e-13 * math.sqrt(steps)
