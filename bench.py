@@ -21,6 +21,10 @@ Other workloads (one JSON line each):
     --workload serving    Poisson arrivals of such members (5k..200k
                           triangles, 100..500 steps by default), continuous
                           batching, p50/p99 latency and throughput
+    --workload shelf      2,097,152 triangles, tanh shelf, M2 tide, p in {1..4}
+    --workload sweep      the paper's statically adaptive p1-2 dam break
+                          (2,097,152 triangles), fraction of p = 2 elements
+                          0, 1/64, 1/32, 1/16, 1/8, 1; mixed and FP64
 """
 from __future__ import annotations
 
@@ -450,6 +454,56 @@ def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, c
                 mean_triangles=float(np.mean([len(r.mesh["tri"]) for _, r in prepared])), clocks=clk)
 
 
+def bench_sweep(args, world):
+    """The paper's statically adaptive p1-2 study (Sect. 5, radial dam break on
+    a perturbed uniform mesh of 2,097,152 triangles): every nth element at p = 2,
+    fractions 0, 1/64, 1/32, 1/16, 1/8, 1; mixed and FP64 modes with the default
+    launch shape, W warm-up and K timed steps each (CUDA events, L2 flushed)."""
+    import torch
+    from paper_2311_11348_gb300 import swedg
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    n = args.n_shelf
+    rows = []
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", 0)))
+    for nth, frac in ((0, "0"), (64, "1/64"), (32, "1/32"), (16, "1/16"), (8, "1/8"), (1, "1")):
+        w = inputs.dam_break_p12(n, nth)
+        dps = dofs_per_step(w["orders"])
+        row = {"fraction_p2": frac, "triangles": len(w["tri"]), "dof_stage_per_step": dps}
+        for name, prec in (("mixed", swedg.PREC_MIXED_FP32), ("fp64", swedg.PREC_FP64)):
+            s = make_solver(w, prec, stream.cuda_stream)
+            c0 = initial_state(s, w)
+            s.set_state(c0, 0.0)
+            s.run(args.warmup)
+            torch.cuda.synchronize()
+            times = []
+            with torch.cuda.stream(stream):
+                for _ in range(args.steps):
+                    flush.add_(1.0)
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    s.run(1)
+                    b.record(stream)
+                    times.append((a, b))
+            torch.cuda.synchronize()
+            tot = max_over_ranks(sum(a.elapsed_time(b) for a, b in times), world)
+            row[name] = {"value": job_rate(dps * args.steps, world, tot / 1e3),
+                         "ms_per_stage": tot / args.steps / 3.0}
+            s.close()
+        rows.append(row)
+    clk = clocks.stop()
+    head = next(r for r in rows if r["fraction_p2"] == "1/32")
+    return {"metric": METRIC, "value": head["mixed"]["value"], "unit": "DOF-stage/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 3.0 * head["mixed"]["ms_per_stage"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": f"dam break p1-2 sweep: {n}x{n} perturbed split squares ({2 * n * n} triangles), "
+                                   "flat 10 m bottom, radial dam, walls, every nth element at p = 2; value = the mixed "
+                                   "mode at 1/32", "l2": "flushed between timed steps (256 MB write)", "replicas": world},
+            "sweep": rows, "clocks": clk}
+
+
 def bench_serving(args, world):
     r = serving_run(args.rate, args.duration, args.tri_lo, args.tri_hi, args.steps_lo, args.steps_hi,
                     args.budget_gb, args.chunk, args.warmup)
@@ -487,7 +541,7 @@ def main():
                     help="headline mode: FP32 correction, FP64 throughout, or tensor-core (TF32 x3) correction")
     ap.add_argument("--n", type=int, default=256, help="split-square grid size (256: 131,072 triangles)")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle accuracy and cpu_baseline legs")
-    ap.add_argument("--workload", default="ocean", choices=["ocean", "shelf", "ensemble", "serving"])
+    ap.add_argument("--workload", default="ocean", choices=["ocean", "shelf", "ensemble", "serving", "sweep"])
     ap.add_argument("--n-shelf", type=int, default=1024, help="shelf workload grid size (1024: 2,097,152 triangles)")
     ap.add_argument("--members", type=int, default=64, help="ensemble members")
     ap.add_argument("--rate", type=float, default=4.0, help="serving: arrivals per second")
@@ -543,9 +597,9 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
-    if args.workload in ("ensemble", "serving"):
+    if args.workload in ("ensemble", "serving", "sweep"):
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-        line = bench_ensemble(args, world) if args.workload == "ensemble" else bench_serving(args, world)
+        line = {"ensemble": bench_ensemble, "serving": bench_serving, "sweep": bench_sweep}[args.workload](args, world)
         if rank == 0:
             print(json.dumps(line))
         if world > 1:

@@ -160,6 +160,28 @@ def shelf_p1234(n: int = 1024):
                 tide=(1.0, 44714.0, 0.0))
 
 
+def dam_break_p12(n: int = 1024, nth: int = 32, L: float = 1e4, seed: int = 9):
+    """The paper's radial dam break setting (Sect. 5): a randomly perturbed
+    uniform mesh of 2 n^2 triangles (2,097,152 at n = 1024) over a flat bottom
+    (10 m), a circular dam of radius L/8 holding 1 m of extra water (a smooth
+    tanh step 20 m wide), walls; static adaptivity p1-2 with every nth element
+    at p = 2 (nth = 0: p = 1 everywhere, nth = 1: p = 2 everywhere)."""
+    xy, tri = split_square_mesh(n, L, jitter=0.2, seed=seed)
+    hv = np.full(len(xy), 10.0)
+    ne = len(tri)
+    if nth == 0:
+        orders = np.full(ne, 1, dtype=np.int8)
+    else:
+        orders = orders_every_nth(ne, nth, 1, 2)
+
+    def ic(x, y):
+        r = np.sqrt((x - 0.5 * L) ** 2 + (y - 0.5 * L) ** 2)
+        return 0.5 * (1.0 - np.tanh((r - L / 8) / 20.0)), 0.0 * x, 0.0 * x
+
+    return dict(name=f"dam_break_p12_n{n}_nth{nth}", xy=xy, tri=tri, hv=hv, orders=orders, ic=ic,
+                bc_tag=None, g=9.81, rk_order=3, cfl=0.1)
+
+
 # ---------------- many-mesh workloads ----------------
 
 def _member(T: float, seed: int, L: float = 1e5, fractions=None):
