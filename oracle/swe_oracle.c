@@ -22,7 +22,7 @@
  *                            ("quadrature-free"); base/correction split.
  *   Sect. 3 (end)          : truncated auxiliary system uH = q with K(p,i,j).
  *
- * Readings where the paper is silent or garbled (all restated in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - basis: orthonormal Dubiner polynomials on the reference triangle,
  *     ordered by total degree, then by the Jacobi index;
  *   - K(p,i,j) = K(max(deg i, deg j));
