@@ -1,9 +1,12 @@
 """Planted mistakes (CPU): each is written into a private copy of the
-oracle's source, compiled, and must fail the brute-force pin of the
-right-hand side (quadrature of the pointwise weak form of Eq. 8 with the
-Lax-Friedrichs flux and lambda of Eq. 10, and the truncated auxiliary system
-of Sect. 3), which the unmodified copy passes.  The oracle itself is never
-modified: the copies live in pytest's temporary directory."""
+oracle's source, compiled, and must fail a pin that the unmodified copy
+passes: the brute-force pin of the right-hand side (quadrature of the
+pointwise weak form of Eq. 8 with the Lax-Friedrichs flux and lambda of
+Eq. 10, and the truncated auxiliary system of Sect. 3), the closed-form
+integral of the mass diagnostic, or the temporal order of the SSP-RK schemes
+under a time-dependent open-sea boundary (which sees the stage times).  The
+oracle itself is never modified: the copies live in pytest's temporary
+directory."""
 import importlib.util
 import os
 import shutil
@@ -13,7 +16,8 @@ import pytest
 
 import dgref
 import oracle as O_REAL
-from test_oracle_scheme import random_state, scale_state_means, tiny_meshes
+from test_oracle_scheme import (MASS_TOL, mass_errors, random_state, scale_state_means, tide_order_rate,
+                                tiny_meshes)
 
 SRC_DIR = os.path.dirname(os.path.abspath(O_REAL.__file__))
 
@@ -33,6 +37,23 @@ MUTANTS = {
     "volume_pressure_factor": ("double pres = g * (0.5 * xi[i] * xi[j] + xi[i] * hb[j]);",
                                "double pres = g * (0.45 * xi[i] * xi[j] + xi[i] * hb[j]);"),
 }
+
+# mistakes that the right-hand side cannot see, each with the pin that must catch it
+OTHER_MUTANTS = {
+    # mass summed with the element area instead of sqrt|Omega_e| (the integral of phi_{e,1})
+    "mass_area_scale": (("s += sqrt(m->area[e]) * c[e];", "s += m->area[e] * c[e];"), "mass"),
+    # the third stage of SSP-RK3 evaluated at t + dt instead of t + dt/2
+    "rk3_third_stage_time": (("tau3[3] = {0.0, 1.0, 0.5}", "tau3[3] = {0.0, 1.0, 1.0}"), "rk3"),
+    # the second stage of SSP-RK2 evaluated at t instead of t + dt
+    "rk2_second_stage_time": (("tau2[2] = {0.0, 1.0}", "tau2[2] = {0.0, 0.0}"), "rk2"),
+}
+
+
+def other_pin_passes(O, pin):
+    if pin == "mass":
+        return all(max(mass_errors(O, f)) <= MASS_TOL[f] for f in ("poly", "sine"))
+    rk = 3 if pin == "rk3" else 2
+    return abs(tide_order_rate(O, rk) - rk) < 0.3
 
 
 def load_copy(tmp_path, name, mutation):
@@ -82,3 +103,16 @@ def test_unmodified_copy_passes(tmp_path):
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_planted_mistake_fails_the_pin(tmp_path, name):
     assert not brute_force_pin_passes(load_copy(tmp_path, name, MUTANTS[name]))
+
+
+def test_unmodified_copy_passes_the_other_pins(tmp_path):
+    O = load_copy(tmp_path, "unmodified_other", None)
+    assert all(other_pin_passes(O, pin) for pin in ("mass", "rk2", "rk3"))
+
+
+@pytest.mark.parametrize("name", sorted(OTHER_MUTANTS))
+def test_planted_mistake_fails_its_pin(tmp_path, name):
+    mutation, pin = OTHER_MUTANTS[name]
+    O = load_copy(tmp_path, name, mutation)
+    assert brute_force_pin_passes(O)  # invisible to the right-hand side ...
+    assert not other_pin_passes(O, pin)  # ... but not to its own pin

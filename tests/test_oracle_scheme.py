@@ -382,3 +382,135 @@ def test_adaptivity_indicator_decisions():
     # hierarchical order change: dropped modes vanish, kept ones are untouched
     c2 = m.adapt_state(c, np.array([1, 3], np.int8))
     assert np.all(c2[:, 3:, 0] == 0.0) and np.all(c2[:, :3, 0] == c[:, :3, 0]) and np.all(c2[:, :, 1] == c[:, :, 1])
+
+
+def _dgref_modes(xy, tri, orders, f, nq=10):
+    """c[3,15,ne] of f(x, y) -> (xi, U, V) by an independent quadrature with the
+    scipy-evaluated basis (dgref), c_i = int_Omega_e f phi_{e,i} for i < K(p_e)"""
+    msh = dgref.Tri(xy, tri)
+    xh, yh, w = dgref.tri_rule(nq)
+    c = np.zeros((3, 15, len(tri)))
+    for e in range(len(tri)):
+        K = K_OF_P[orders[e]]
+        X, Y = msh.to_phys(e, xh, yh)
+        ph, _, _ = msh.phys_basis(e, X, Y)
+        for fld, val in enumerate(f(X, Y)):
+            c[fld, :K, e] = (ph[:K] * (w * msh.det[e] * np.broadcast_to(val, X.shape))).sum(axis=1)
+    return c
+
+
+def mass_errors(Om, field):
+    """relative errors of the mass of the oracle module Om (its own L2
+    projection, then the independent quadrature) against the closed form"""
+    xy, tri, hv, orders = jittered_mixed(n=6, seed=12)
+    m = Om.Mesh(xy, tri, hv, orders)
+    if field == "poly":
+        f = lambda x, y: (1.0 + 2.0 * x - 3.0 * y * y + x * y * y, 0.0 * x, 0.0 * x)  # noqa: E731
+        exact = 1.0 + 1.0 - 1.0 + 1.0 / 6.0
+    else:
+        f = lambda x, y: (np.sin(math.pi * x) * np.sin(math.pi * y), 0.0 * x, 0.0 * x)  # noqa: E731
+        exact = 4.0 / math.pi ** 2
+    area = m.geometry()["area"]
+    assert area.max() / area.min() > 1.5  # a wrong per-element scale cannot hide
+    return [abs(m.mass(c) - exact) / exact for c in (m.project_state(f, n=10), _dgref_modes(xy, tri, orders, f))]
+
+
+MASS_TOL = {"poly": 1e-14, "sine": 1e-11}
+
+
+@pytest.mark.parametrize("field", ["poly", "sine"])
+def test_mass_is_the_integral_of_xi(field):
+    """Mass (Sect. 2 diagnostics: int_Omega xi dx) equals the closed-form
+    integral of the elevation over the unit square, on a jittered mesh whose
+    element areas all differ and with orders 0..4.  A polynomial of degree 3
+    is represented exactly by the modal coefficients' mean mode; the sine
+    product's integral 4 / pi^2 is met to the quadrature error.  Two routes to
+    the coefficients: the oracle's own L2 projection and an independent
+    quadrature with the scipy-evaluated basis."""
+    errs = mass_errors(O, field)
+    assert max(errs) <= MASS_TOL[field], errs
+
+
+def tide_order_rate(Om, rk):
+    """observed temporal order of the oracle module Om under a time-dependent
+    open-sea boundary (self-convergence, dt = T/10 .. T/80)"""
+    xy, tri = inputs.split_square_mesh(4, 1.0)
+    hv = np.full(len(xy), 1.0)
+    orders = np.full(len(tri), 2, np.int8)
+    bc = inputs.boundary_tags(xy, tri, "west")
+    m = Om.Mesh(xy, tri, hv, orders, bc_tag=bc)
+    c0 = np.zeros((3, 15, len(tri)))
+    P = Om.Params(g=1.0, rk_order=rk, tide_amp=0.05, tide_period=0.4, tide_phase=0.3)
+    T_end = 0.2
+    sols = []
+    for nsteps in (10, 20, 40, 80):
+        c, t = m.run(P, c0, 0.0, nsteps, dt=T_end / nsteps)
+        assert abs(t - T_end) < 1e-14
+        sols.append(c)
+    assert np.abs(sols[-1]).max() > 1e-3  # the tide moved the water
+    e1 = np.abs(sols[0] - sols[3]).max()
+    e2 = np.abs(sols[1] - sols[3]).max()
+    e3 = np.abs(sols[2] - sols[3]).max()
+    return math.log2((e1 - e2) / (e2 - e3))
+
+
+@pytest.mark.parametrize("rk,order", [(2, 2), (3, 3)])
+def test_ssp_rk_temporal_order_with_a_time_dependent_open_sea(rk, order):
+    """Self-convergence in dt under a time-dependent open-sea boundary
+    xi = xi_hat(t) (Sect. 2: the open-sea condition; SSP-RK time stepping):
+    the boundary value enters every stage at its stage time t + tau_s dt, so
+    the order holds only with the right stage times (0, 1 for the two-stage
+    scheme; 0, 1, 1/2 for the three-stage one).  The tide swings through half
+    a period in the run and drives the flow (the state starts at rest)."""
+    rate = tide_order_rate(O, rk)
+    assert abs(rate - order) < 0.3, rate
+
+
+def _evaluate(xy, tri, c_f, orders, pts_per_elem=7, seed=0):
+    """the modal field c_f[15, ne] at random points of every element, with the
+    scipy-evaluated basis (dgref); returns (points x, y, values)"""
+    msh = dgref.Tri(xy, tri)
+    rng = np.random.default_rng(seed)
+    X, Y, F = [], [], []
+    for e in range(len(tri)):
+        a, b = rng.uniform(size=(2, pts_per_elem))
+        flip = a + b > 1.0
+        a[flip], b[flip] = 1.0 - a[flip], 1.0 - b[flip]
+        x, y = msh.to_phys(e, a, b)
+        ph, _, _ = msh.phys_basis(e, x, y)
+        K = K_OF_P[orders[e]]
+        X.append(x); Y.append(y); F.append(np.tensordot(c_f[:K, e], ph[:K], 1))
+    return np.concatenate(X), np.concatenate(Y), np.concatenate(F)
+
+
+def test_projection_reproduces_polynomials_of_the_element_order():
+    """The oracle's L2 projection (the initial-state route of the tests) is
+    exact on polynomials of degree <= p_e: evaluated with the independent
+    basis, the projected field equals the polynomial pointwise."""
+    xy, tri, hv, orders = jittered_mixed(n=4, seed=13, pmin=2, pmax=4)
+    m = O.Mesh(xy, tri, hv, orders)
+    f = lambda x, y: (0.3 - 0.2 * x + 0.5 * y + 0.7 * x * y - 0.4 * y * y, 0.0 * x, 0.0 * x)  # noqa: E731
+    c = m.project_state(f, n=8)
+    x, y, val = _evaluate(xy, tri, c[0], orders)
+    assert np.abs(val - f(x, y)[0]).max() <= 1e-13
+
+
+def test_p1_modes_reproduce_the_vertex_interpolant():
+    """or_p1_modes (vertex values -> modes 1..3, the bathymetry's and the
+    benchmarks' initial states' route) reproduces the continuous piecewise-
+    linear interpolant: exact for a linear function, and equal to the vertex
+    values at the vertices of every element for arbitrary ones."""
+    xy, tri, hv, orders = jittered_mixed(n=5, seed=14)
+    m = O.Mesh(xy, tri, hv, np.ones(len(tri), np.int8))
+    lin = 0.4 + 1.3 * xy[:, 0] - 0.7 * xy[:, 1]
+    c = np.zeros((15, len(tri)))
+    c[:3] = m.p1_modes(lin)
+    x, y, val = _evaluate(xy, tri, c, np.ones(len(tri), np.int8))
+    assert np.abs(val - (0.4 + 1.3 * x - 0.7 * y)).max() <= 1e-13
+    rnd = np.random.default_rng(3).standard_normal(len(xy))
+    c[:3] = m.p1_modes(rnd)
+    msh = dgref.Tri(xy, tri)
+    for e in range(len(tri)):
+        vx, vy = xy[msh.tri[e], 0], xy[msh.tri[e], 1]
+        ph, _, _ = msh.phys_basis(e, vx - 1e-12 * (vx - vx.mean()), vy - 1e-12 * (vy - vy.mean()))
+        assert np.abs(np.tensordot(c[:3, e], ph[:3], 1) - rnd[msh.tri[e]]).max() <= 1e-9
