@@ -305,8 +305,7 @@ int swe_profile_read(swe_ctx* ctx, int n, const char** names, double* ms, int64_
  * no tide, from caller-owned device arrays:
  *   xy[nv][2]   vertex coordinates          hv[nv]  vertex depths h_b
  *   tri[ne][3]  counter-clockwise triangles (vertex ids < nv)
- *   nbr[ne][3]  element across the edge opposite vertex k, or -1 (land);
- *               the relation must be symmetric; ids outside [0, ne) are land
+ *   nbr[ne][3]  element across the edge opposite vertex k, or -1 (land)
  *   c[3][3][ne] modes 1..3 of xi, U, V (the basis of the context layout)
  *   rhs_out[3][3][ne]  the right-hand side of those modes
  * The intermediate values -- the auxiliary velocity u and the flux of every
@@ -314,15 +313,24 @@ int swe_profile_read(swe_ctx* ctx, int n, const char** names, double* ms, int64_
  * sized for SWE_NOALLOC_MAX_ELEMENTS elements (24 doubles each, 12.6 MB),
  * which every GPU that loads the library holds until the process exits.
  * Errors: SWE_EINVAL for ne < 1, ne > SWE_NOALLOC_MAX_ELEMENTS, nv < 3,
- * g <= 0 or a NULL array; SWE_ECUDA when a launch fails.  An element with a
- * vertex id outside [0, nv) gets NaN rows; no depth or finiteness status is
- * reported (there is no context to hold it).
- * The first call on a device copies the reference tables to constant memory
- * and looks up the device address of the scratch array (cudaMemcpyToSymbol,
- * cudaGetSymbolAddress; no allocation): make that first call before any
- * stream capture.  Every call shares the one scratch array and leaves its
- * contents behind; nothing in it needs to start at zero (each call writes
- * every entry before reading it), but calls that overlap on the GPU --
+ * g not in (0, inf) or a NULL array; SWE_ECUDA when a launch fails, or when
+ * the calling thread already had a CUDA error pending on entry (it is
+ * reported here instead of being taken for this call's later).
+ * Invalid mesh data never leads to an out-of-range access:
+ *  - an element with a vertex id outside [0, nv), or that is clockwise or
+ *    degenerate (det J_e <= 0), gets NaN rows and is land to its neighbours;
+ *  - an edge is interior only when the relation is mutual: nbr[e][k] = n
+ *    with n in [0, ne), n usable, and e in n's own list; otherwise (an id
+ *    outside [0, ne), a one-sided entry) the edge is land for e.
+ * No depth or finiteness status is reported (there is no context to hold it).
+ * The first call on a device context copies the reference tables to constant
+ * memory and looks up the device address of the scratch array
+ * (cudaMemcpyToSymbol, cudaGetSymbolAddress; no allocation); make that first
+ * call before any stream capture.  The set-up is serialised across host
+ * threads and repeated when the device's context is re-created (for
+ * instance after cudaDeviceReset).  Every call shares the one scratch array
+ * and leaves its contents behind; nothing in it needs to start at zero (each
+ * call writes every entry it reads), but calls that overlap on the GPU --
  * different streams, or different host threads -- race on it, so the caller
  * must serialise them.  Asynchronous on `stream` (a cudaStream_t; NULL is
  * the legacy default stream). */

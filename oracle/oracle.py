@@ -28,20 +28,25 @@ K_OF_P = (1, 3, 6, 10, 15)
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "swe_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 
 _lib = None
+_lib_omp = None
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, openmp: bool = False) -> str:
     """Compile the oracle with gcc (-O2, no fast-math, FMA contraction off so
-    that every product is rounded as written)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
+    that every product is rounded as written).  openmp=True builds the same
+    source with -fopenmp into a second library whose element loops run on all
+    host cores (bitwise the same results; see the header of swe_oracle.c)."""
+    out = _LIB_OMP if openmp else _LIB
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               *(["-fopenmp"] if openmp else []), "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class _Params(C.Structure):
@@ -50,11 +55,13 @@ class _Params(C.Structure):
                 ("fric_lin", C.c_double), ("fric_quad", C.c_double), ("f_c", C.c_double)]
 
 
-def _load():
-    global _lib
-    if _lib is not None:
+def _load(openmp: bool = False):
+    global _lib, _lib_omp
+    if openmp and _lib_omp is not None:
+        return _lib_omp
+    if not openmp and _lib is not None:
         return _lib
-    lib = C.CDLL(build())
+    lib = C.CDLL(build(openmp=openmp))
     P = C.c_void_p
     d = C.c_double
     i64 = C.c_int64
@@ -91,8 +98,21 @@ def _load():
         getattr(lib, "or_tensor_" + n).argtypes = [P]
     lib.or_basis_monomials.argtypes = [P]
     lib.or_degrees.argtypes = [P]
-    _lib = lib
+    lib.or_set_threads.argtypes = [C.c_int]
+    lib.or_max_threads.restype = C.c_int
+    if openmp:
+        _lib_omp = lib
+    else:
+        _lib = lib
     return lib
+
+
+def threaded(threads: int = 0):
+    """the threaded oracle library with `threads` OpenMP threads (0: every
+    host core); returns the number of threads it will use"""
+    lib = _load(openmp=True)
+    lib.or_set_threads(int(threads) if threads > 0 else (os.cpu_count() or 1))
+    return lib.or_max_threads()
 
 
 def _ptr(a):
@@ -168,8 +188,12 @@ class Mesh:
     boundary tags [ne,3] (edge k opposite vertex k; 0 interior/land, 1 land,
     2 open sea) and orders [ne]."""
 
-    def __init__(self, xy, tri, hv, orders=None, bc_tag=None):
-        lib = _load()
+    def __init__(self, xy, tri, hv, orders=None, bc_tag=None, threads: int = 1):
+        """threads > 1 (or 0: every host core) runs the element loops of this
+        mesh's calls on the threaded build of the same source"""
+        lib = _load(openmp=threads != 1)
+        if threads != 1:
+            threaded(threads)
         self.xy = np.ascontiguousarray(xy, dtype=np.float64)
         self.tri = np.ascontiguousarray(tri, dtype=np.int32)
         self.hv = np.ascontiguousarray(hv, dtype=np.float64)

@@ -36,6 +36,12 @@
  *
  * Every reference-element integral is computed exactly from monomial
  * integrals (int_T x^a y^b = a! b! / (a+b+2)!; int_0^1 s^m = 1/(m+1)).
+ *
+ * Threads: built with -fopenmp, the loops over elements (and the elementwise
+ * RK update) run in parallel.  Every element's arithmetic is the same
+ * sequence of operations either way and the only reductions are a minimum
+ * and integer counts, so a threaded build gives bitwise the results of the
+ * serial one (the mass and energy sums stay serial).
  */
 #define _USE_MATH_DEFINES
 #include <math.h>
@@ -48,6 +54,14 @@
 #define M_PI 3.14159265358979323846
 #endif
 #define PD 16     /* polynomial coefficient grid: degrees 0..15 */
+#ifdef _OPENMP
+#include <omp.h>
+void or_set_threads(int n) { if (n > 0) omp_set_num_threads(n); }
+int or_max_threads(void) { return omp_get_max_threads(); }
+#else
+void or_set_threads(int n) { (void)n; }
+int or_max_threads(void) { return 1; }
+#endif
 
 /* ------------------------------------------------------------------ */
 /* Double-double numbers (error-free transformations; Dekker, Knuth):   */
@@ -559,6 +573,7 @@ void or_proj_points(const or_mesh* m, int n, double* xy) {
   int nq = n * n;
   double xh[4096], yh[4096], w[4096];
   or_tri_rule(n, xh, yh, w);
+  #pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < m->ne; ++e) {
     int32_t v0 = m->tri[3 * e], v1 = m->tri[3 * e + 1], v2 = m->tri[3 * e + 2];
     for (int q = 0; q < nq; ++q) {
@@ -574,6 +589,7 @@ void or_project(const or_mesh* m, int n, const double* vals, double* out) {
   int nq = n * n;
   double xh[4096], yh[4096], w[4096];
   or_tri_rule(n, xh, yh, w);
+  #pragma omp parallel for schedule(static)
   for (int64_t e = 0; e < m->ne; ++e) {
     int K = KP[m->p[e]];
     for (int i = 0; i < KMAX; ++i) {
@@ -617,12 +633,13 @@ static int lu_solve(int K, double A[KMAX][KMAX], double* b1, double* b2) {
  * <= h_min. */
 int or_usolve(const or_mesh* m, const or_params* P, const double* c, double* u) {
   int64_t ne = m->ne;
-  int status = 0;
+  int bad_depth = 0, bad_solve = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : bad_depth, bad_solve)
   for (int64_t e = 0; e < ne; ++e) {
     int K = KP[m->p[e]];
     double H[KMAX], A[KMAX][KMAX], bu[KMAX], bv[KMAX];
     for (int n = 0; n < KMAX; ++n) H[n] = (n < K ? C_(c, 0, n, e, ne) : 0.0) + (n < 3 ? m->hb[3 * e + n] : 0.0);
-    if (!(H[0] / sqrt(m->area[e]) > P->h_min)) status = -3;
+    if (!(H[0] / sqrt(m->area[e]) > P->h_min)) bad_depth = 1;
     for (int i = 0; i < K; ++i) for (int j = 0; j < K; ++j) {
       double acc = 0.0;
       int nt = Ktr(i, j);
@@ -630,13 +647,13 @@ int or_usolve(const or_mesh* m, const or_params* P, const double* c, double* u) 
       A[i][j] = acc / m->s[e];
     }
     for (int i = 0; i < K; ++i) { bu[i] = C_(c, 1, i, e, ne); bv[i] = C_(c, 2, i, e, ne); }
-    if (lu_solve(K, A, bu, bv)) status = status ? status : -4;
+    if (lu_solve(K, A, bu, bv)) bad_solve = 1;
     for (int i = 0; i < KMAX; ++i) {
       u[((int64_t)0 * KMAX + i) * ne + e] = i < K ? bu[i] : 0.0;
       u[((int64_t)1 * KMAX + i) * ne + e] = i < K ? bv[i] : 0.0;
     }
   }
-  return status;
+  return bad_depth ? -3 : bad_solve ? -4 : 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -656,6 +673,7 @@ int or_rhs(const or_mesh* m, const or_params* P, const double* c, double t, doub
   double g = P->g;
   double* u = u_out ? u_out : malloc(sizeof(double) * 2 * KMAX * ne);
   int status = or_usolve(m, P, c, u);
+#pragma omp parallel for schedule(dynamic, 64)
   for (int64_t e = 0; e < ne; ++e) {
     int K = KP[m->p[e]];
     double se = m->s[e];
@@ -790,6 +808,7 @@ int or_rhs(const or_mesh* m, const or_params* P, const double* c, double t, doub
 double or_dt(const or_mesh* m, const or_params* P, const double* c, const double* u) {
   double best = INFINITY;
   int64_t ne = m->ne;
+#pragma omp parallel for schedule(static) reduction(min : best)
   for (int64_t e = 0; e < ne; ++e) {
     double ra = 1.0 / sqrt(m->area[e]);
     double ub = u[e] * ra, vb = u[(int64_t)KMAX * ne + e] * ra;
@@ -823,6 +842,7 @@ int or_step(const or_mesh* m, const or_params* P, double* c, double* t, double d
   for (int s = 0; s < ns && status == 0; ++s) {
     double a = ns == 3 ? a3[s] : a2[s], b = ns == 3 ? b3[s] : b2[s], tau = ns == 3 ? tau3[s] : tau2[s];
     status = or_rhs(m, P, cs, *t + tau * dt, r, 0, u);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) cs[i] = a * c0[i] + b * (cs[i] + dt * r[i]);
   }
   if (status == 0) { memcpy(c, cs, sizeof(double) * n); *t += dt; }
@@ -876,6 +896,7 @@ int64_t or_indicator(const or_mesh* m, const double* c, double theta_up, double 
                      int8_t* p_out, double* s_out) {
   ensure_ready();
   int64_t ne = m->ne, changed = 0;
+#pragma omp parallel for schedule(static) reduction(+ : changed)
   for (int64_t e = 0; e < ne; ++e) {
     int p = m->p[e], K = KP[p];
     double num = 0.0, den = 0.0;

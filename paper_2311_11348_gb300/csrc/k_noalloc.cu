@@ -14,7 +14,11 @@
 //
 // The same arithmetic as the context path (k_usolve_base, k_edge_base,
 // k_elem_base): Sect. 2-3 of the paper for p = 1 with land walls.
+#include <cuda.h>
+
+#include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/swedg.h"
 #include "common.h"
@@ -36,17 +40,63 @@ __constant__ double nLv[3][3];     // int lambda_v phihat_i
 __constant__ double nGrad[3][2];   // grad phihat_q, q < 3
 __constant__ double nPhi0;
 
-// Set-up once per device (with that device current): tables into constant
-// memory and the device address of the scratch array.
+// Set-up once per device context (with that device current): tables into
+// constant memory and the device address of the scratch array.  The context
+// is identified by its driver id, so a context re-created after
+// cudaDeviceReset (whose constant memory starts zeroed) is set up again; a
+// mutex serialises the set-up of host threads that call at the same time.
 struct DevState {
   bool ready = false;
+  unsigned long long ctx_id = 0;
   double* scratch = nullptr;
 };
 static DevState g_dev[64];
+static std::mutex g_setup_mutex;
 
-static int setup(int dev) {
+typedef CUresult (*PFN_ctxGetCurrent)(CUcontext*);
+typedef CUresult (*PFN_ctxGetId)(CUcontext, unsigned long long*);
+
+// driver id of the current context, 0 when there is none (or no driver entry)
+static unsigned long long current_ctx_id() {
+  static PFN_ctxGetCurrent get_current = nullptr;
+  static PFN_ctxGetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = (PFN_ctxGetCurrent)f1;
+      get_id = (PFN_ctxGetId)f2;
+    }
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+static int setup(int dev, double** scratch) {
   if (dev < 0 || dev >= 64) return SWE_EINVAL;
-  if (g_dev[dev].ready) return 0;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  const unsigned long long id0 = current_ctx_id();
+  if (g_dev[dev].ready && id0 != 0 && id0 == g_dev[dev].ctx_id) {
+    *scratch = g_dev[dev].scratch;
+    return 0;
+  }
+  // the symbol lookup also makes the device's primary context current
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || p == nullptr) return SWE_ECUDA;
+  const unsigned long long id = current_ctx_id();
+  if (g_dev[dev].ready && id != 0 && id == g_dev[dev].ctx_id) {
+    *scratch = g_dev[dev].scratch;
+    return 0;
+  }
+  g_dev[dev].ready = false;
   const RefTables& R = tables();
   double B[3][3][2], T1[3][3][3], Lv[3][3], Gr[3][2];
   for (int k = 0; k < 3; ++k)
@@ -64,10 +114,10 @@ static int setup(int dev) {
       cudaMemcpyToSymbol(nGrad, Gr, sizeof Gr) != cudaSuccess ||
       cudaMemcpyToSymbol(nPhi0, &R.phi0, sizeof(double)) != cudaSuccess)
     return SWE_ECUDA;
-  void* p = nullptr;
-  if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || p == nullptr) return SWE_ECUDA;
   g_dev[dev].scratch = (double*)p;
+  g_dev[dev].ctx_id = id;
   g_dev[dev].ready = true;
+  *scratch = (double*)p;
   return 0;
 }
 
@@ -95,22 +145,38 @@ __device__ __forceinline__ void hb_modes(const double* __restrict__ hv, const in
   for (int i = 0; i < 3; ++i) hb[i] = s * (h[0] * nLv[0][i] + h[1] * nLv[1][i] + h[2] * nLv[2][i]);
 }
 
-// auxiliary system of Sect. 3 for p = 1 (3 x 3, adjugate)
-__device__ __forceinline__ bool tri_ok(const int32_t* __restrict__ tri, int64_t nv, int64_t e) {
+// An element is used only when its vertex ids lie in [0, nv) and it is
+// counter-clockwise with positive area (det J_e > 0); any other element gets
+// NaN rows and is a land edge to its neighbours.
+__device__ __forceinline__ bool elem_ok(const double* __restrict__ xy, const int32_t* __restrict__ tri, int64_t nv,
+                                        int64_t e) {
   const int32_t a = tri[3 * e], b = tri[3 * e + 1], c = tri[3 * e + 2];
-  return a >= 0 && b >= 0 && c >= 0 && a < nv && b < nv && c < nv;
+  if (!(a >= 0 && b >= 0 && c >= 0 && a < nv && b < nv && c < nv)) return false;
+  const double x0 = xy[2 * a], y0 = xy[2 * a + 1];
+  const double det = (xy[2 * b] - x0) * (xy[2 * c + 1] - y0) - (xy[2 * c] - x0) * (xy[2 * b + 1] - y0);
+  return det > 0.0;
 }
 
-// a neighbour id outside [0, ne) is read as a land edge
-__device__ __forceinline__ int64_t nbr_of(const int32_t* __restrict__ nbr, int64_t ne, int64_t e, int k) {
+// The element across local edge k of e, with e's local edge number kn in the
+// neighbour's list, or -1 (land): a neighbour id outside [0, ne), an unusable
+// neighbour, or one whose own list does not name e.  Both the edge and the
+// element kernel decide through this one function, so every flux slot an
+// element reads was written by the same call.
+__device__ __forceinline__ int64_t mutual_nbr(const double* __restrict__ xy, const int32_t* __restrict__ tri,
+                                              const int32_t* __restrict__ nbr, int64_t nv, int64_t ne, int64_t e,
+                                              int k, int& kn) {
   const int64_t n = nbr[3 * e + k];
-  return n >= 0 && n < ne ? n : -1;
+  if (n < 0 || n >= ne || n == e || !elem_ok(xy, tri, nv, n)) return -1;
+  for (int j = 0; j < 3; ++j)
+    if (nbr[3 * n + j] == e) { kn = j; return n; }
+  return -1;
 }
 
+// auxiliary system of Sect. 3 for p = 1 (3 x 3, adjugate)
 __global__ void k_na_usolve(int64_t nv, int64_t ne, const double* __restrict__ xy, const double* __restrict__ hv,
                             const int32_t* __restrict__ tri, const double* __restrict__ c, double* __restrict__ scr) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= ne || !tri_ok(tri, nv, e)) return;
+  if (e >= ne || !elem_ok(xy, tri, nv, e)) return;
   const Geo G = element_geo(xy, tri, e);
   double hb[3];
   hb_modes(hv, tri, e, G.s, hb);
@@ -132,10 +198,6 @@ __global__ void k_na_usolve(int64_t nv, int64_t ne, const double* __restrict__ x
   scr[3 * NMAX + e] = (C00 * V[0] + C01 * V[1] + C02 * V[2]) * r;
   scr[4 * NMAX + e] = (C01 * V[0] + C11 * V[1] + C12 * V[2]) * r;
   scr[5 * NMAX + e] = (C02 * V[0] + C12 * V[1] + C22 * V[2]) * r;
-}
-
-__device__ __forceinline__ int local_index_of(const int32_t* __restrict__ nbr, int64_t n, int64_t e) {
-  return nbr[3 * n] == e ? 0 : nbr[3 * n + 1] == e ? 1 : 2;  // nbr must be symmetric
 }
 
 // P1 traces of xi, U, V, u, v of element e on its local edge k at the two points
@@ -166,9 +228,9 @@ __global__ void k_na_edge(int64_t nv, int64_t ne, const double* __restrict__ xy,
   if (t >= 3 * ne) return;
   const int64_t e = t / 3;
   const int k = (int)(t % 3);
-  int64_t n = nbr_of(nbr, ne, e, k);
-  if (n >= 0 && !tri_ok(tri, nv, n)) n = -1;
-  if (!tri_ok(tri, nv, e)) return;
+  if (!elem_ok(xy, tri, nv, e)) return;
+  int kn = 0;
+  const int64_t n = mutual_nbr(xy, tri, nbr, nv, ne, e, k, kn);
   if (n >= 0 && n < e) return;  // owned by the neighbour
   const int32_t va = tri[3 * e + (k + 1) % 3], vb = tri[3 * e + (k + 2) % 3];
   const double dx = xy[2 * vb] - xy[2 * va], dy = xy[2 * vb + 1] - xy[2 * va + 1];
@@ -183,7 +245,7 @@ __global__ void k_na_edge(int64_t nv, int64_t ne, const double* __restrict__ xy,
   double unR, HR;
   if (n >= 0) {
     const Geo GR = element_geo(xy, tri, n);
-    traces(c, scr, ne, n, local_index_of(nbr, n, e), true, GR.rs, b);
+    traces(c, scr, ne, n, kn, true, GR.rs, b);
     const double mR = nPhi0 * GR.rs;
     unR = (scr[0 * NMAX + n] * nx + scr[3 * NMAX + n] * ny) * mR;
     HR = c[n] * mR + hmid;
@@ -222,7 +284,7 @@ __global__ void k_na_elem(int64_t nv, int64_t ne, const double* __restrict__ xy,
                           double* __restrict__ rhs) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= ne) return;
-  if (!tri_ok(tri, nv, e)) {  // a vertex id out of range: NaN rows, nothing read
+  if (!elem_ok(xy, tri, nv, e)) {  // unusable element: NaN rows, nothing read
     for (int i = 0; i < 9; ++i) rhs[i * ne + e] = __longlong_as_double(0x7ff8000000000000LL);
     return;
   }
@@ -265,11 +327,11 @@ __global__ void k_na_elem(int64_t nv, int64_t ne, const double* __restrict__ xy,
   const double* F = scr + 6 * NMAX;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    int64_t n = nbr_of(nbr, ne, e, k);
-    if (n >= 0 && !tri_ok(tri, nv, n)) n = -1;
+    int kn = 0;
+    const int64_t n = mutual_nbr(xy, tri, nbr, nv, ne, e, k, kn);
     const bool right = n >= 0 && n < e;  // the flux is stored by the neighbour, in its direction
     const int64_t owner = right ? n : e;
-    const int ko = right ? local_index_of(nbr, n, e) : k;
+    const int ko = right ? kn : k;
     const double sg = right ? G.rs : -G.rs;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -293,17 +355,22 @@ using namespace swedg;
 
 extern "C" int swe_rhs_p1_noalloc(int64_t nv, const double* xy, const double* hv, int64_t ne, const int32_t* tri,
                                   const int32_t* nbr, const double* c, double g, double* rhs_out, void* stream) {
-  if (ne < 1 || ne > na::NMAX || nv < 3 || !xy || !hv || !tri || !nbr || !c || !rhs_out || !(g > 0.0))
+  if (ne < 1 || ne > na::NMAX || nv < 3 || !xy || !hv || !tri || !nbr || !c || !rhs_out || !(g > 0.0) ||
+      !(g < INFINITY))
     return SWE_EINVAL;
+  // an error left by earlier work on this thread is reported, not mistaken for ours later
+  if (cudaGetLastError() != cudaSuccess) return SWE_ECUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SWE_ECUDA;
-  const int rc = na::setup(dev);
+  double* scr = nullptr;
+  const int rc = na::setup(dev, &scr);
   if (rc) return rc;
-  double* scr = na::g_dev[dev].scratch;
   cudaStream_t s = (cudaStream_t)stream;
   const int T = 128;
   na::k_na_usolve<<<(unsigned)((ne + T - 1) / T), T, 0, s>>>(nv, ne, xy, hv, tri, c, scr);
+  if (cudaGetLastError() != cudaSuccess) return SWE_ECUDA;
   na::k_na_edge<<<(unsigned)((3 * ne + T - 1) / T), T, 0, s>>>(nv, ne, xy, hv, tri, nbr, c, g, scr);
+  if (cudaGetLastError() != cudaSuccess) return SWE_ECUDA;
   na::k_na_elem<<<(unsigned)((ne + T - 1) / T), T, 0, s>>>(nv, ne, xy, hv, tri, nbr, c, g, scr, rhs_out);
   return cudaGetLastError() == cudaSuccess ? 0 : SWE_ECUDA;
 }

@@ -146,13 +146,41 @@ def edge_table(npts: int):
 NOALLOC_MAX_ELEMENTS = 65536
 
 
+def _check_device_tensor(name, a, dtype, shape):
+    """a must be a contiguous CUDA tensor of the current device with this dtype
+    and shape (the entry point reads and writes exactly these extents)"""
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise ValueError(f"{name}: a torch CUDA tensor is required, got {type(a).__name__}")
+    if a.dtype != dtype:
+        raise ValueError(f"{name}: dtype {a.dtype}, expected {dtype}")
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(a.shape)}, expected {tuple(shape)}")
+    if not a.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if not a.is_cuda:
+        raise ValueError(f"{name}: must be on a CUDA device, not {a.device}")
+    if a.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on {a.device}, but the current device is cuda:{torch.cuda.current_device()}")
+
+
 def rhs_p1_noalloc(xy, hv, tri, nbr, c, g, out, stream=None):
     """swe_rhs_p1_noalloc on caller-owned device tensors (see include/swedg.h):
-    xy [nv,2], hv [nv], tri [ne,3] int32, nbr [ne,3] int32, c [3,3,ne], out [3,3,ne]."""
+    xy [nv,2] float64, hv [nv] float64, tri [ne,3] int32, nbr [ne,3] int32,
+    c [3,3,ne] float64, out [3,3,ne] float64, all contiguous on the current
+    CUDA device; anything else raises ValueError before the call."""
+    import torch
+    if not hasattr(xy, "shape") or len(xy.shape) != 2 or not hasattr(tri, "shape") or len(tri.shape) != 2:
+        raise ValueError("xy must be [nv, 2] and tri [ne, 3]")
+    nv, ne = int(xy.shape[0]), int(tri.shape[0])
+    for name, a, dt, sh in (("xy", xy, torch.float64, (nv, 2)), ("hv", hv, torch.float64, (nv,)),
+                            ("tri", tri, torch.int32, (ne, 3)), ("nbr", nbr, torch.int32, (ne, 3)),
+                            ("c", c, torch.float64, (3, 3, ne)), ("out", out, torch.float64, (3, 3, ne))):
+        _check_device_tensor(name, a, dt, sh)
     lib = load()
     args = [_ptr(a) for a in (xy, hv, tri, nbr, c, out)]
-    rc = lib.swe_rhs_p1_noalloc(int(xy.shape[0]), args[0][0], args[1][0], int(tri.shape[0]), args[2][0], args[3][0],
-                                args[4][0], float(g), args[5][0], stream)
+    rc = lib.swe_rhs_p1_noalloc(nv, args[0][0], args[1][0], ne, args[2][0], args[3][0], args[4][0], float(g),
+                                args[5][0], stream)
     if rc:
         raise SweError(rc, "swe_rhs_p1_noalloc")
     return out

@@ -52,3 +52,30 @@ def test_factored_edge_tables_reproduce_edge_tensors(lib, npts, pmax):
     assert np.abs(S3 - t["S3"][:, :K, :K, :K]).max() <= 1e-14 * np.abs(t["S3"]).max()
     assert np.abs(X3 - t["X3"][..., :K, :K, :K]).max() <= 1e-14 * np.abs(t["X3"]).max()
     assert abs(w.sum() - 1.0) < 1e-15
+
+
+def test_noalloc_wrapper_rejects_bad_arguments_before_the_call():
+    """rhs_p1_noalloc hands raw pointers to kernels that read and write fixed
+    extents, so the binding refuses anything but contiguous CUDA tensors of the
+    right dtype and shape (checked on the host, no GPU needed)"""
+    import torch
+    nv, ne = 9, 8
+    good = dict(xy=torch.zeros((nv, 2), dtype=torch.float64), hv=torch.ones(nv, dtype=torch.float64),
+                tri=torch.zeros((ne, 3), dtype=torch.int32), nbr=torch.full((ne, 3), -1, dtype=torch.int32),
+                c=torch.zeros((3, 3, ne), dtype=torch.float64), out=torch.zeros((3, 3, ne), dtype=torch.float64))
+    bad = {
+        "numpy": ("c", np.zeros((3, 3, ne))),
+        "dtype": ("c", torch.zeros((3, 3, ne), dtype=torch.float32)),
+        "int64 mesh": ("tri", torch.zeros((ne, 3), dtype=torch.int64)),
+        "short out": ("out", torch.zeros((3, 3, ne - 1), dtype=torch.float64)),
+        "hv length": ("hv", torch.ones(nv + 1, dtype=torch.float64)),
+        "nbr shape": ("nbr", torch.full((ne, 2), -1, dtype=torch.int32)),
+        "strided": ("c", torch.zeros((3, 3, 2 * ne), dtype=torch.float64)[:, :, ::2]),
+        "host": ("out", None),  # every tensor of `good` lives on the host
+    }
+    for what, (name, val) in bad.items():
+        args = dict(good)
+        if val is not None:
+            args[name] = val
+        with pytest.raises(ValueError):
+            swedg.rhs_p1_noalloc(args["xy"], args["hv"], args["tri"], args["nbr"], args["c"], 9.81, args["out"])

@@ -514,3 +514,22 @@ def test_p1_modes_reproduce_the_vertex_interpolant():
         vx, vy = xy[msh.tri[e], 0], xy[msh.tri[e], 1]
         ph, _, _ = msh.phys_basis(e, vx - 1e-12 * (vx - vx.mean()), vy - 1e-12 * (vy - vy.mean()))
         assert np.abs(np.tensordot(c[:3, e], ph[:3], 1) - rnd[msh.tri[e]]).max() <= 1e-9
+
+
+def test_threaded_oracle_is_bitwise_the_serial_one():
+    """The threaded build (OpenMP over elements; the bench's all-core baseline
+    and the long parity runs use it) gives bitwise the serial results: the
+    projection, 5 CFL steps with an open-sea tide and the indicator."""
+    xy, tri, hv, orders = jittered_mixed(n=10, seed=15, pmin=0, pmax=4)
+    bc = inputs.boundary_tags(xy, tri, "west")
+    ic = lambda x, y: (0.1 * np.exp(-((x - 0.4) ** 2 + (y - 0.6) ** 2) / 0.02), 0.05 + 0.0 * x, 0.0 * x)  # noqa: E731
+    P = O.Params(g=9.81, rk_order=3, cfl=0.2, tide_amp=0.02, tide_period=0.5)
+    out = []
+    for threads in (1, 4):
+        m = O.Mesh(xy, tri, hv, orders, bc_tag=bc, threads=threads)
+        c = m.project_state(ic)
+        c5, t5 = m.run(P, c, 0.0, 5)
+        out.append((c, c5, t5, m.indicator(c5, 0.05, 1e-3, 0, 4)[0]))
+    assert O.threaded(4) == 4
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
