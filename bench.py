@@ -45,6 +45,9 @@ sys.path.insert(0, ROOT)
 from paper_2311_11348_gb300 import inputs  # noqa: E402
 
 METRIC = "DOF-stage updates/s, mixed vs FP64 at stated L2 error; p50/p99 solve latency"
+REPEATS, REPEAT_STEPS = 5, 34  # the median of 5 repeats of 34 SSP-RK3 steps (102 stages) each
+ACC_STEPS = 100  # CFL steps of the accuracy comparison against the oracle
+ADAPT = dict(up=0.05, down=1e-3, pmin=1, pmax=3, every=10, steps=100)  # the adaptive leg
 
 
 def max_over_ranks(value, world, device="cuda"):
@@ -120,11 +123,35 @@ def single_mesh_workload(args):
                f"p in {{1,2,3}} 70/20/10, SSP-RK3, CFL 0.1")
 
 
-def oracle_mesh_params(w):
+def host_cpu():
+    """(logical cores, CPU model) of this host, for the oracle baselines"""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def oracle_mesh_params(w, threads=1):
+    """the FP64 oracle on the workload's mesh; threads > 1 (0: every host core)
+    runs its element loops on the threaded build of the same source"""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
     tide = w.get("tide", (0.0, 0.0, 0.0))
-    m = O.Mesh(w["xy"], w["tri"], w["hv"], w["orders"], bc_tag=w.get("bc_tag"))
+    m = O.Mesh(w["xy"], w["tri"], w["hv"], w["orders"], bc_tag=w.get("bc_tag"), threads=threads)
     P = O.Params(g=w["g"], cfl=w["cfl"], rk_order=3, tide_amp=tide[0], tide_period=tide[1], tide_phase=tide[2])
     return m, P
 
@@ -164,7 +191,9 @@ def run_ours(args, rank, world):
         s = make_solver(w, prec, stream.cuda_stream)
         c0 = initial_state(s, w)
         s.set_state(c0, 0.0)
-        shape = s.autotune(steps=5)[0] if args.autotune else s.launch_shape()
+        if args.shape:
+            s.set_launch_shape(args.shape)
+        shape = s.autotune(steps=5)[0] if args.autotune and not args.shape else s.launch_shape()
         s.run(args.warmup)
         s.set_state(c0, 0.0)
         torch.cuda.synchronize()
@@ -187,6 +216,23 @@ def run_ours(args, rank, world):
         if name == prec_list[0][0]:
             clk = clocks.stop()
         tot = max_over_ranks(sum(ms), world)
+        reps = None
+        if name == prec_list[0][0]:  # 5 repeats of >= 100 stages each, for the median
+            reps = []
+            for _ in range(REPEATS):
+                s.set_state(c0, 0.0)
+                times = []
+                with torch.cuda.stream(stream):
+                    for _ in range(REPEAT_STEPS):
+                        flush.add_(1.0)
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        s.run(1)
+                        b.record(stream)
+                        times.append((a, b))
+                torch.cuda.synchronize()
+                reps.append(max_over_ranks(sum(a.elapsed_time(b) for a, b in times), world) / REPEAT_STEPS)
         # per-family timing (separate profiled pass over the same steps)
         s.set_state(c0, 0.0)
         s.profile(True)
@@ -201,13 +247,15 @@ def run_ours(args, rank, world):
         s.run(args.steps)
         launches = s.profile_read()["kernels"][1]
         s.profile(False)
-        res[name] = dict(ms_steps=ms, total_ms=tot, prof=prof, launches=launches, solver=s, c0=c0, shape=shape)
+        res[name] = dict(ms_steps=ms, total_ms=tot, prof=prof, launches=launches, solver=s, c0=c0, shape=shape,
+                         repeats=reps)
     return w, dps, res, clk, stream, flush
 
 
-def accuracy(w, res, nsteps=2):
-    """relative L2 error of nsteps CFL steps against the FP64 oracle (same input)"""
-    m, P = oracle_mesh_params(w)
+def accuracy(w, res, nsteps=100):
+    """relative L2 error of every mode after nsteps CFL steps against the FP64
+    oracle run from the same input (the threaded build, every host core)"""
+    m, P = oracle_mesh_params(w, threads=0)
     out = {}
     c0 = res["fp64"]["c0"]
     t0 = time.perf_counter()
@@ -222,6 +270,28 @@ def accuracy(w, res, nsteps=2):
     return out, nsteps
 
 
+def e2e_loop(s, hin, hout, steps, per_step=None):
+    """every step: the state in from pinned host memory, one SSP-RK3 step, the
+    state out to pinned host memory (packed layout), through the asynchronous
+    C ABI calls (copies double-buffered on copy streams, overlapping the
+    previous / next step); one swe_sync at the end.  Returns the wall time."""
+    import torch
+    s.set_state_packed_async(hin, 0.0)
+    s.run_async(1)
+    s.get_state_packed_async(hout[0])
+    s.sync()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        s.set_state_packed_async(hin, 0.0)
+        if per_step is not None:
+            per_step()
+        s.run_async(1)
+        s.get_state_packed_async(hout[k % 2])
+    s.sync()
+    return time.perf_counter() - t0
+
+
 def e2e(w, res, name, steps, stream):
     """the same step through the C ABI with pinned host buffers: state in, one
     step, state out (host<->device copies inside the timed region), in the
@@ -230,23 +300,16 @@ def e2e(w, res, name, steps, stream):
     s = res[name]["solver"]
     s.set_state(res[name]["c0"], 0.0)
     hin = torch.from_numpy(s.get_state_packed()[0]).pin_memory()
-    hout = torch.empty_like(hin).pin_memory()
-    s.set_state_packed(hin, 0.0)
-    s.run(1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        s.set_state_packed(hin, 0.0)
-        s.run(1)
-        s.get_state_packed(hout)
-    dt = time.perf_counter() - t0
+    hout = [torch.empty_like(hin).pin_memory() for _ in range(2)]
+    dt = e2e_loop(s, hin, hout, steps)
     nbytes = hin.numel() * 8
     return dt, nbytes
 
 
-def oracle_rate(w, steps, warmup):
-    """the FP64 oracle (single thread) on the same workload: full-mesh RK3 steps"""
-    m, P = oracle_mesh_params(w)
+def oracle_rate(w, steps, warmup, threads=1):
+    """seconds of `steps` full-mesh RK3 steps of the FP64 oracle on the
+    workload (after `warmup` untimed ones); threads as in oracle_mesh_params"""
+    m, P = oracle_mesh_params(w, threads=threads)
     xi_v = w["ic"](w["xy"][:, 0], w["xy"][:, 1])[0]
     c = np.zeros((3, 15, len(w["tri"])))
     c[0, :3] = m.p1_modes(xi_v)
@@ -257,6 +320,47 @@ def oracle_rate(w, steps, warmup):
     for _ in range(steps):
         c, t, _ = m.step(P, c, t)
     return time.perf_counter() - t0
+
+
+def adaptive_leg(w, res, stream):
+    """The adaptive run of the workload's recipe: ADAPT["steps"] SSP-RK3 CFL
+    steps with the modal-decay indicator every ADAPT["every"] steps (orders in
+    ADAPT["pmin"]..ADAPT["pmax"]), FP64 and mixed mode side by side from the
+    same initial state.  The FP64 context takes the decisions (swe_adapt) and
+    the mixed context is given the same order map, so that the two states are
+    compared on one trajectory of maps; reported: their relative L2 distance
+    at the end, and the wall time of one adaptation (indicator, order change
+    and the rebuild of the context's device description it triggers)."""
+    import torch
+    c0 = res["fp64"]["c0"]
+    ctx = {}
+    for name in ("fp64", "mixed"):
+        s = make_solver(w, {"fp64": 0, "mixed": 1}[name], stream.cuda_stream)
+        s.set_launch_shape(res[name]["shape"])
+        s.set_state(c0, 0.0)
+        ctx[name] = s
+    a = ADAPT
+    adapt_s, changed = [], []
+    for _ in range(a["steps"] // a["every"]):
+        for s in ctx.values():
+            s.run(a["every"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        orders, n = ctx["fp64"].adapt(a["up"], a["down"], a["pmin"], a["pmax"])
+        ctx["fp64"].packed_size()  # the rebuild the order change triggers
+        adapt_s.append(time.perf_counter() - t0)
+        changed.append(n)
+        ctx["mixed"].set_orders(orders)
+    cf, tf = ctx["fp64"].get_state()
+    cm, tm = ctx["mixed"].get_state()
+    for s in ctx.values():
+        s.close()
+    return {"steps": a["steps"], "adapt_every": a["every"], "theta_up": a["up"], "theta_down": a["down"],
+            "orders": [a["pmin"], a["pmax"]],
+            "mixed_vs_fp64_rel_l2": float(np.linalg.norm(cm - cf) / np.linalg.norm(cf)),
+            "t_end_s": tf, "adapt_ms_mean": 1e3 * float(np.mean(adapt_s)), "adapt_ms_max": 1e3 * float(np.max(adapt_s)),
+            "changed_per_pass_mean": float(np.mean(changed)),
+            "final_order_counts": np.bincount(orders, minlength=5)[1:4].tolist()}
 
 
 def ensemble_state(ens, members):
@@ -341,18 +445,9 @@ def bench_ensemble(args, world):
         if name == "mixed":  # end to end through the API: pinned host state in (packed), one step, state out
             ens.solver.set_state(c0, 0.0)
             hin = torch.from_numpy(ens.solver.get_state_packed()[0]).pin_memory()
-            hout = torch.empty_like(hin).pin_memory()
-            ens.solver.set_state_packed(hin, 0.0)
-            ens.run(1)
-            torch.cuda.synchronize()
-            n_e2e = 3
-            t0 = time.perf_counter()
-            for _ in range(n_e2e):
-                ens.solver.set_state_packed(hin, 0.0)
-                ens.solver.set_member_times(np.zeros(ens.n))
-                ens.run(1)
-                ens.solver.get_state_packed(hout)
-            e2e_rate = dps * n_e2e / (time.perf_counter() - t0)
+            hout = [torch.empty_like(hin).pin_memory() for _ in range(2)]
+            n_e2e = 5
+            e2e_rate = dps * n_e2e / e2e_loop(ens.solver, hin, hout, n_e2e)
             e2e_bytes = hin.numel() * 8
             del hin, hout
         res[name] = dict(total_ms=tot, prof=prof, launches=launches, err=err, build_s=t_build,
@@ -472,6 +567,8 @@ def bench_sweep(args, world):
         row = {"fraction_p2": frac, "triangles": len(w["tri"]), "dof_stage_per_step": dps}
         for name, prec in (("mixed", swedg.PREC_MIXED_FP32), ("fp64", swedg.PREC_FP64)):
             s = make_solver(w, prec, stream.cuda_stream)
+            if args.shape:
+                s.set_launch_shape(args.shape)
             c0 = initial_state(s, w)
             s.set_state(c0, 0.0)
             s.run(args.warmup)
@@ -500,7 +597,8 @@ def bench_sweep(args, world):
             "data": "synthetic",
             "config": {"workload": f"dam break p1-2 sweep: {n}x{n} perturbed split squares ({2 * n * n} triangles), "
                                    "flat 10 m bottom, radial dam, walls, every nth element at p = 2; value = the mixed "
-                                   "mode at 1/32", "l2": "flushed between timed steps (256 MB write)", "replicas": world},
+                                   "mode at 1/32", "l2": "flushed between timed steps (256 MB write)", "replicas": world,
+                       "launch_shape": list(args.shape) if args.shape else "default"},
             "sweep": rows, "clocks": clk}
 
 
@@ -553,43 +651,59 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--chunk", type=int, default=50, help="serving: max steps between scheduling points")
     ap.add_argument("--no-serving", action="store_true", help="skip the short serving leg of the ocean workload")
+    ap.add_argument("--no-adaptive", action="store_true", help="skip the adaptive leg of the ocean workload")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shape instead of autotuning it per mode")
+    ap.add_argument("--shape", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
+                    help="launch shape to use instead of the autotuner's (6 comma-separated integers, see swedg.h)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     workload = single_mesh_workload(args)[1] if args.workload in ("ocean", "shelf") else args.workload
 
+    def config_of(w, replicas):
+        """the workload's config, the same dict in both arms"""
+        return {"workload": workload, "triangles": len(w["tri"]), "dof_stage_per_step": dofs_per_step(w["orders"]),
+                "l2": "GPU arm: flushed between timed steps (256 MB write)", "replicas": replicas}
+
     if args.impl == "reference":
         if rank != 0:
             return
-        # every step a bounded sample of the workload: the same recipe on a grid
-        # small enough that the W warm-up and K timed oracle steps end within
-        # about two minutes (cost per element-step calibrated on 32x32)
+        # every step a bounded sample of the workload: the same recipe, on the
+        # full grid unless the W warm-up and K timed steps of the threaded
+        # oracle (every host core) would take more than about two minutes
+        # (cost per element-step calibrated on 32x32), else on a smaller grid
         import copy
+        sys.path.insert(0, os.path.join(ROOT, "oracle"))
+        import oracle as O
+        threads = O.threaded(0)
+        cores, model = host_cpu()
         steps, warm = max(1, args.steps), max(0, args.warmup)
         n_full = args.n_shelf if args.workload == "shelf" else args.n
         probe = copy.copy(args)
         probe.n = probe.n_shelf = 32
         wp, _ = single_mesh_workload(probe)
-        per_elem = oracle_rate(wp, 1, 0) / len(wp["tri"])
+        per_elem = oracle_rate(wp, 2, 1, threads=0) / 2 / len(wp["tri"])
         n = n_full
         while n > 32 and per_elem * 2 * n * n * (steps + warm) > 120.0:
             n //= 2
         sample = copy.copy(args)
         sample.n = sample.n_shelf = n
         w, _ = single_mesh_workload(sample)
-        sec = oracle_rate(w, steps, warm)
+        sec = oracle_rate(w, steps, warm, threads=0)
         dps = dofs_per_step(w["orders"])
         v = dps * steps / sec
         what = "the full workload" if n == n_full else f"the same recipe at {n}x{n}"
+        w_full = single_mesh_workload(args)[0] if n != n_full else w
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "DOF-stage/s", "n_gpus": args.gpus,
                 "steps": steps, "warmup": warm, "ms_per_step": 1e3 * sec / steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload, "triangles": 2 * n_full * n_full},
-                "cpu_baseline": {"value": v, "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
-                                 "sample": f"{steps} SSP-RK3 steps (after {warm} warm-up steps) of the single-threaded "
-                                           f"FP64 C oracle on {what} ({len(w['tri'])} triangles)"},
+                "config": config_of(w_full, args.gpus),
+                "cpu_baseline": {"value": v, "unit": "DOF-stage/s", "cores": threads, "kind": "oracle",
+                                 "nproc": cores, "cpu_model": model,
+                                 "sample": f"{steps} SSP-RK3 steps (after {warm} warm-up steps) of the FP64 C oracle, "
+                                           f"threaded build ({threads} OpenMP threads over elements), on {what} "
+                                           f"({len(w['tri'])} triangles)"},
                 "e2e": {"value": v, "unit": "DOF-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -608,12 +722,12 @@ def main():
     w, dps, res, clk, stream, flush = run_ours(args, rank, world)
     head = args.precision
     others = [k for k in res if k != head]
-    acc, acc_steps = ({}, 0) if args.no_oracle else accuracy(w, res, nsteps=1 if args.workload == "shelf" else 2)
+    acc, acc_steps = ({}, 0) if args.no_oracle else accuracy(w, res, nsteps=2 if args.workload == "shelf" else ACC_STEPS)
     value = job_rate(dps * args.steps, world, res[head]["total_ms"] / 1e3)
     rate = {k: job_rate(dps * args.steps, world, res[k]["total_ms"] / 1e3) for k in res}
-    e2e_s, e2e_bytes = e2e(w, res, head, max(3, args.steps // 2), stream)
+    e2e_steps = max(5, args.steps)
+    e2e_s, e2e_bytes = e2e(w, res, head, e2e_steps, stream)
     e2e_s = max_over_ranks(e2e_s, world)
-    e2e_steps = max(3, args.steps // 2)
     pk = peaks()
     # dominant kernel family of the headline mode (profiled pass)
     prof = res[head]["prof"]
@@ -624,14 +738,17 @@ def main():
         "warmup": args.warmup, "ms_per_step": res[head]["total_ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"mixed": "f64+f32", "fp64": "f64", "tf32": "f64+f32+tf32"}[head],
         "data": "synthetic",
-        "config": {"workload": workload, "triangles": len(w["tri"]), "dof_stage_per_step": dps,
-                   "precision": head, "l2": "flushed between timed steps (256 MB write)",
-                   "replicas": world},
+        "config": config_of(w, world),
+        "precision": head,
         "modes": {k: {"value": rate[k], "ms_per_step": res[k]["total_ms"] / args.steps,
                       "rel_l2_vs_oracle": acc.get(k), "oracle_steps": acc_steps,
                       "launch_shape": res[k]["shape"]} for k in res},
         "mixed_over_fp64": rate["mixed"] / rate["fp64"],
         "tf32_over_fp64": rate["tf32"] / rate["fp64"],
+        "repeats": {"n": REPEATS, "steps_each": REPEAT_STEPS, "stages_each": 3 * REPEAT_STEPS,
+                    "ms_per_step_median": statistics.median(res[head]["repeats"]),
+                    "ms_per_step_min": min(res[head]["repeats"]), "ms_per_step_max": max(res[head]["repeats"]),
+                    "value_median": job_rate(dps, world, statistics.median(res[head]["repeats"]) / 1e3)},
         "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in fams.items()},
         "dominant_kernel": dom,
         "gpu_launches": int(res[head]["launches"]),
@@ -648,11 +765,26 @@ def main():
                            "rebuild_s": r["rebuild_s"], "makespan_s": r["makespan_s"],
                            "workload": "Poisson 3/s for 8 s, triangles log-uniform [5k, 100k], steps U[100, 300], "
                                        "p in {1..4} 40/30/20/10, mixed, wall clock end to end"}
+    if args.workload == "ocean" and not args.no_adaptive:
+        line["adaptive"] = adaptive_leg(w, res, stream)
     if rank == 0 and not args.no_oracle:
-        # the large shelf mesh reuses the oracle step of the accuracy check
-        sec = accuracy.oracle_s_per_step if args.workload == "shelf" else oracle_rate(w, 1, 0)
-        line["cpu_baseline"] = {"value": dps / sec, "unit": "DOF-stage/s", "cores": 1, "kind": "oracle",
-                                "sample": "1 full-mesh SSP-RK3 step of the single-threaded FP64 C oracle"}
+        # the threaded oracle on every host core (the large shelf mesh reuses
+        # the timing of the accuracy check), and one step single-threaded
+        import oracle as O
+        threads = O.threaded(0)
+        cores, model = host_cpu()
+        if args.workload == "shelf":
+            sec_n, n_steps = accuracy.oracle_s_per_step, 1
+        else:
+            n_steps = 3
+            sec_n = oracle_rate(w, n_steps, 1, threads=0) / n_steps
+        sec_1 = oracle_rate(w, 1, 0, threads=1)
+        line["cpu_baseline"] = {"value": dps / sec_n, "unit": "DOF-stage/s", "cores": threads, "kind": "oracle",
+                                "nproc": cores, "cpu_model": model,
+                                "sample": f"{n_steps} full-mesh SSP-RK3 steps of the FP64 C oracle, threaded build "
+                                          f"({threads} OpenMP threads over elements)",
+                                "single_core": {"value": dps / sec_1, "cores": 1,
+                                                "sample": "1 full-mesh SSP-RK3 step of the serial build"}}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -132,6 +132,31 @@ int64_t swe_packed_size(swe_ctx* ctx);
 int swe_set_state_packed(swe_ctx* ctx, const double* c, double t);
 int swe_get_state_packed(swe_ctx* ctx, double* c_out, double* t_out);
 
+/* Asynchronous variants (the paper has no counterpart: they let a caller
+ * overlap the host<->device copies of one step's state with the computation
+ * of the previous step).  The three calls only enqueue work on the context's
+ * streams and return; swe_sync waits for everything enqueued on the context
+ * and reports the first error, including the depth and finiteness checks of
+ * the steps run since the previous status read.
+ *   swe_set_state_packed_async  state (packed layout) and time t of every
+ *                               member from c, host or device
+ *   swe_run_async               nsteps CFL steps (dt_fixed <= 0) or fixed
+ *                               steps of dt_fixed, as swe_run
+ *   swe_get_state_packed_async  the current state (packed layout) into c_out,
+ *                               host or device
+ * Host buffers are copied on a copy stream per direction through two staging
+ * buffers each (4 x swe_packed_size doubles of device memory, allocated by the
+ * first asynchronous call and counted by swe_memory_bytes); they overlap with
+ * the steps only when pinned (cudaHostAlloc / cudaHostRegister).  A buffer
+ * passed to swe_set_state_packed_async must not be modified, and one passed
+ * to swe_get_state_packed_async not be read, before swe_sync returns.
+ * Order changes (swe_set_orders, swe_adapt) and the other calls may be mixed
+ * in; they synchronise as documented for each. */
+int swe_set_state_packed_async(swe_ctx* ctx, const double* c, double t);
+int swe_run_async(swe_ctx* ctx, int64_t nsteps, double dt_fixed);
+int swe_get_state_packed_async(swe_ctx* ctx, double* c_out);
+int swe_sync(swe_ctx* ctx);
+
 /* Modal coefficients of the continuous piecewise-linear interpolant of vertex
  * values (host vals[nv]) -> host or device modes_out[3][ne] (modes 1..3).
  * This is how the bathymetry enters the scheme; it also gives P1 initial
@@ -246,7 +271,7 @@ int swe_edge_table(int npts, double* s, double* w, double* B);
 int64_t swe_tc_operand_image(int K, float* out, int64_t cap);
 
 /* Launch shapes (the paper has no counterpart: they tune the GPU kernels to
- * the mesh, orders and device).  shape[5]:
+ * the mesh, orders and device).  shape[6]:
  *   [0] resident blocks per SM of the grid-stride base edge and element
  *       kernels, 0..32 (0: no cap, one block per base_threads units of work)
  *   [1] threads per block of those kernels, 32..128, a multiple of 32
@@ -257,7 +282,12 @@ int64_t swe_tc_operand_image(int K, float* out, int64_t cap);
  *       ignored in SWE_PREC_MIXED_TF32): 0 = its higher test modes run
  *       before the base element kernel, 1 = beside it (on the correction
  *       stream, joined at the end of the stage)
- * Defaults {2, 128, 256, 128, 0}.  Results do not depend on the shape (every
+ *   [5] work distribution of the capped base grids ([0] > 0), 0..16:
+ *       0 = equal grid-stride shares per block; c > 0 = dynamic tiles: a
+ *       block takes c * [1] consecutive edges (elements) at a time from a
+ *       ticket counter until none are left, so blocks that share their SM
+ *       with the concurrent correction kernels take fewer tiles
+ * Defaults {2, 128, 256, 128, 0, 2}.  Results do not depend on the shape (every
  * unit of work is computed by one thread in the same order).  SWE_EINVAL for
  * a shape out of range. */
 int swe_get_launch_shape(swe_ctx* ctx, int32_t* shape);
@@ -265,9 +295,9 @@ int swe_set_launch_shape(swe_ctx* ctx, const int32_t* shape);
 
 /* Autotuner: for candidate launch shapes (coordinate descent: blocks per SM
  * in {1,2,3,4,6,0}, then base threads {64,128}, u-solve threads {128,256},
- * correction threads {64,128}, schedule {0,1}), runs `steps` CFL steps of the context's own
+ * correction threads {64,128}, schedule {0,1}, base tiles {0,1,2,4}), runs `steps` CFL steps of the context's own
  * mesh and state, times them with CUDA events on the context stream, keeps
- * the fastest shape and restores the state and member times.  shape_out[5]
+ * the fastest shape and restores the state and member times.  shape_out[6]
  * and ms_out (time per step of the choice) may be NULL.  Needs the state to
  * stay valid for the trial steps (errors of swe_run are returned). */
 int swe_autotune(swe_ctx* ctx, int steps, int32_t* shape_out, double* ms_out);

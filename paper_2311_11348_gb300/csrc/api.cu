@@ -28,7 +28,7 @@ namespace swedg {
 static thread_local std::string g_cuda_err;
 static thread_local int64_t* g_launch_counter = nullptr;
 static thread_local const LaunchShape* g_shape = nullptr;
-static const LaunchShape kDefaultShape{2, 128, 256, 128, 0};
+static const LaunchShape kDefaultShape{2, 128, 256, 128, 0, 2};
 void count_launch(int n) {
   if (g_launch_counter) *g_launch_counter += n;
 }
@@ -59,6 +59,14 @@ struct swe_ctx {
   cudaEvent_t ev_gf = nullptr, ev_gj[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_u1 = nullptr, ev_u2 = nullptr, ev_c = nullptr, ev_dt = nullptr, ev_c2 = nullptr;
   bool own_stream = false;
+  // asynchronous packed transfers: one copy stream per direction, two staging
+  // buffers per direction (allocated on first use), events that order them
+  // against the compute stream
+  cudaStream_t cin = nullptr, cout = nullptr;
+  cudaEvent_t ev_in[2] = {}, ev_conv[2] = {}, ev_oready[2] = {}, ev_d2h[2] = {};
+  double* d_stage_in[2] = {nullptr, nullptr};
+  double* d_stage_out[2] = {nullptr, nullptr};
+  int in_slot = 0, out_slot = 0;
   int device = 0;
   std::string err;
   bool have_mesh = false;   // a valid host mesh (topology built)
@@ -102,6 +110,7 @@ struct swe_ctx {
   double* d_partial = nullptr;
   double* d_red = nullptr;
   int8_t* d_newp = nullptr;  // orders proposed by the adaptivity indicator (caller order)
+  unsigned* d_work = nullptr;  // ticket counters of the dynamic base schedule: edge kernel [0,1], element kernel [2,3]
   int nred = 0;
   // profiling
   bool prof = false;
@@ -274,6 +283,7 @@ static int build_topology(swe_ctx* ctx) {
 // reset to zero (callers that keep it go through the caller layout).
 static int build_device(swe_ctx* ctx) {
   free_all(ctx);
+  for (int k = 0; k < 2; ++k) ctx->d_stage_in[k] = ctx->d_stage_out[k] = nullptr;  // freed with the rest
   const int64_t ne = ctx->ne;
   const RefTables& R = tables();
   // internal order: stable sort by p
@@ -518,6 +528,8 @@ static int build_device(swe_ctx* ctx) {
     return cuda_err(ctx, rc);
   cudaMemset(ctx->d_t, 0, sizeof(double) * nm);
   cudaMemset(ctx->d_status, 0, sizeof(unsigned));
+  if ((rc = dalloc(ctx, &ctx->d_work, sizeof(unsigned) * 4))) return cuda_err(ctx, rc);
+  cudaMemset(ctx->d_work, 0, sizeof(unsigned) * 4);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_err(ctx, cuda_fail(e, "build_device", __FILE__, __LINE__));
   return 0;
@@ -618,7 +630,7 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
   }
   {
     ProfScope ps(ctx, F_EDGEB);
-    CK(launch_edge_base(A, ctx->dm, ph, stg, in.cb, ctx->vel.ub, ctx->fx));
+    CK(launch_edge_base(A, ctx->dm, ph, stg, in.cb, ctx->vel.ub, ctx->fx, ctx->d_work));
   }
   auto elem_corr = [&](int part) -> int {
     ProfScope ps(ctx, F_ELEMC);
@@ -662,7 +674,7 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
   {
     ProfScope ps(ctx, F_ELEMB);
     CK(launch_elem_base(A, ctx->dm, ctx->G, ph, stg, ctx->corr32, in.cb, nst.cb, out.cb, out.cb32, ctx->vel.ub,
-                        ctx->fx, ctx->rc, ctx->prm.cfl));
+                        ctx->fx, ctx->rc, ctx->prm.cfl, ctx->d_work + 2));
   }
   if (conc && split) {
     CU(cudaEventRecord(ctx->ev_c2, B));
@@ -838,6 +850,11 @@ void swe_destroy(swe_ctx* ctx) {
                          ctx->ev_gj[0], ctx->ev_gj[1]})
     if (ev) cudaEventDestroy(ev);
   if (ctx->stream2) { cudaStreamSynchronize(ctx->stream2); cudaStreamDestroy(ctx->stream2); }
+  for (cudaStream_t cs : {ctx->cin, ctx->cout})
+    if (cs) { cudaStreamSynchronize(cs); cudaStreamDestroy(cs); }
+  for (int k = 0; k < 2; ++k)
+    for (cudaEvent_t ev : {ctx->ev_in[k], ctx->ev_conv[k], ctx->ev_oready[k], ctx->ev_d2h[k]})
+      if (ev) cudaEventDestroy(ev);
   for (cudaStream_t sgi : ctx->sg)
     if (sgi) { cudaStreamSynchronize(sgi); cudaStreamDestroy(sgi); }
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -1081,10 +1098,8 @@ static int build_graph(swe_ctx* ctx, double dt_fixed) {
   return 0;
 }
 
-int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out) {
-  if (!ctx || !ctx->have_mesh || nsteps < 0) return fail(ctx, SWE_EINVAL, "swe_run: no mesh or negative count");
-  CK(ensure_built(ctx));
-  LaunchScope ls(ctx);
+// nsteps steps enqueued on the context stream (graph replays when possible)
+static int enqueue_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed) {
   if (ctx->use_graph && !ctx->prof && nsteps > 0) {
     if (!ctx->graph || ctx->graph_dt != dt_fixed) CK(build_graph(ctx, dt_fixed));
   }
@@ -1096,6 +1111,14 @@ int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out) {
   } else {
     for (int64_t s = 0; s < nsteps; ++s) CK(enqueue_step(ctx, dt_fixed));
   }
+  return 0;
+}
+
+int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out) {
+  if (!ctx || !ctx->have_mesh || nsteps < 0) return fail(ctx, SWE_EINVAL, "swe_run: no mesh or negative count");
+  CK(ensure_built(ctx));
+  LaunchScope ls(ctx);
+  CK(enqueue_run(ctx, nsteps, dt_fixed));
   int rc = read_status(ctx, true);
   prof_collect(ctx);
   if (t_out) {
@@ -1103,6 +1126,91 @@ int swe_run(swe_ctx* ctx, int64_t nsteps, double dt_fixed, double* t_out) {
     CU(cudaStreamSynchronize(ctx->stream));
   }
   return rc;
+}
+
+// ---- asynchronous packed transfers and steps ----
+static int ensure_async(swe_ctx* ctx) {
+  if (!ctx->cin) {
+    CU(cudaStreamCreateWithFlags(&ctx->cin, cudaStreamNonBlocking));
+    CU(cudaStreamCreateWithFlags(&ctx->cout, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k)
+      for (cudaEvent_t* ev : {&ctx->ev_in[k], &ctx->ev_conv[k], &ctx->ev_oready[k], &ctx->ev_d2h[k]}) {
+        CU(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+        CU(cudaEventRecord(*ev, ctx->stream));  // every slot starts free
+      }
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (!ctx->d_stage_in[k]) {
+      int rc = dalloc(ctx, &ctx->d_stage_in[k], sizeof(double) * (size_t)std::max<int64_t>(ctx->packed_n, 1));
+      if (!rc) rc = dalloc(ctx, &ctx->d_stage_out[k], sizeof(double) * (size_t)std::max<int64_t>(ctx->packed_n, 1));
+      if (rc) return cuda_err(ctx, rc);
+    }
+  }
+  return 0;
+}
+
+int swe_set_state_packed_async(swe_ctx* ctx, const double* c, double t) {
+  if (!ctx || !ctx->have_mesh || !c) return fail(ctx, SWE_EINVAL, "swe_set_state_packed_async: no mesh or NULL");
+  CK(ensure_built(ctx));
+  CK(ensure_async(ctx));
+  LaunchScope ls(ctx);
+  const double* src = c;
+  if (!is_device_ptr(c)) {
+    const int k = ctx->in_slot;
+    ctx->in_slot ^= 1;
+    // the staging buffer is free once the conversion that last read it has run
+    CU(cudaStreamWaitEvent(ctx->cin, ctx->ev_conv[k], 0));
+    CU(cudaMemcpyAsync(ctx->d_stage_in[k], c, sizeof(double) * (size_t)ctx->packed_n, cudaMemcpyHostToDevice,
+                       ctx->cin));
+    CU(cudaEventRecord(ctx->ev_in[k], ctx->cin));
+    CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_in[k], 0));
+    src = ctx->d_stage_in[k];
+    CK(launch_from_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->d_off, ctx->corr32, src, ctx->st[0]));
+    CU(cudaEventRecord(ctx->ev_conv[k], ctx->stream));
+  } else {
+    CK(launch_from_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->d_off, ctx->corr32, src, ctx->st[0]));
+  }
+  CK(launch_fill(ctx->stream, ctx->d_t, t, ctx->nmem));
+  return 0;
+}
+
+int swe_run_async(swe_ctx* ctx, int64_t nsteps, double dt_fixed) {
+  if (!ctx || !ctx->have_mesh || nsteps < 0) return fail(ctx, SWE_EINVAL, "swe_run_async: no mesh or negative count");
+  CK(ensure_built(ctx));
+  LaunchScope ls(ctx);
+  return enqueue_run(ctx, nsteps, dt_fixed);
+}
+
+int swe_get_state_packed_async(swe_ctx* ctx, double* c_out) {
+  if (!ctx || !ctx->have_mesh || !c_out) return fail(ctx, SWE_EINVAL, "swe_get_state_packed_async: no mesh or NULL");
+  CK(ensure_built(ctx));
+  CK(ensure_async(ctx));
+  LaunchScope ls(ctx);
+  if (is_device_ptr(c_out)) {
+    CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->d_off, ctx->corr32, ctx->st[0], c_out));
+    return 0;
+  }
+  const int k = ctx->out_slot;
+  ctx->out_slot ^= 1;
+  // the staging buffer is free once its previous copy to the host has run
+  CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_d2h[k], 0));
+  CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->d_off, ctx->corr32, ctx->st[0],
+                    ctx->d_stage_out[k]));
+  CU(cudaEventRecord(ctx->ev_oready[k], ctx->stream));
+  CU(cudaStreamWaitEvent(ctx->cout, ctx->ev_oready[k], 0));
+  CU(cudaMemcpyAsync(c_out, ctx->d_stage_out[k], sizeof(double) * (size_t)ctx->packed_n, cudaMemcpyDeviceToHost,
+                     ctx->cout));
+  CU(cudaEventRecord(ctx->ev_d2h[k], ctx->cout));
+  return 0;
+}
+
+int swe_sync(swe_ctx* ctx) {
+  if (!ctx) return SWE_EINVAL;
+  if (!ctx->have_mesh || ctx->dirty) return 0;  // nothing was enqueued on a device description
+  LaunchScope ls(ctx);
+  for (cudaStream_t cs : {ctx->cin, ctx->cout})
+    if (cs) CU(cudaStreamSynchronize(cs));
+  return read_status(ctx, true);
 }
 
 int swe_adapt(swe_ctx* ctx, double theta_up, double theta_down, int p_min, int p_max, int64_t* n_changed,
@@ -1235,19 +1343,21 @@ int64_t swe_tc_operand_image(int K, float* out, int64_t cap) {
 
 static bool shape_ok(const int32_t* v) {
   return v[0] >= 0 && v[0] <= 32 && v[1] >= 32 && v[1] <= 128 && v[1] % 32 == 0 && v[2] >= 32 && v[2] <= 256 &&
-         v[2] % 32 == 0 && v[3] >= 32 && v[3] <= 128 && v[3] % 32 == 0 && (v[4] == 0 || v[4] == 1);
+         v[2] % 32 == 0 && v[3] >= 32 && v[3] <= 128 && v[3] % 32 == 0 && (v[4] == 0 || v[4] == 1) && v[5] >= 0 &&
+         v[5] <= 16;
 }
 
 int swe_get_launch_shape(swe_ctx* ctx, int32_t* shape) {
   if (!ctx || !shape) return SWE_EINVAL;
   shape[0] = ctx->shape.base_bpsm; shape[1] = ctx->shape.base_threads;
   shape[2] = ctx->shape.usolve_threads; shape[3] = ctx->shape.corr_threads; shape[4] = ctx->shape.split;
+  shape[5] = ctx->shape.base_chunk;
   return 0;
 }
 
 int swe_set_launch_shape(swe_ctx* ctx, const int32_t* shape) {
   if (!ctx || !shape || !shape_ok(shape)) return fail(ctx, SWE_EINVAL, "swe_set_launch_shape: shape out of range");
-  ctx->shape = LaunchShape{shape[0], shape[1], shape[2], shape[3], shape[4]};
+  ctx->shape = LaunchShape{shape[0], shape[1], shape[2], shape[3], shape[4], shape[5]};
   if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }  // captured with the old shape
   return 0;
 }
@@ -1291,13 +1401,14 @@ int swe_autotune(swe_ctx* ctx, int steps, int32_t* shape_out, double* ms_out) {
   LaunchShape best = ctx->shape;
   double best_ms = 0.0;
   if (!rc) rc = measure(best, &best_ms);
-  const std::vector<int> cand[5] = {{1, 2, 3, 4, 6, 0}, {64, 128}, {128, 256}, {64, 128}, {0, 1}};
-  for (int k = 0; k < 5 && !rc; ++k)
+  const std::vector<int> cand[6] = {{1, 2, 3, 4, 6, 0}, {64, 128}, {128, 256}, {64, 128}, {0, 1}, {0, 1, 2, 4}};
+  for (int k = 0; k < 6 && !rc; ++k)
     for (int v : cand[k]) {
-      if (k == 4 && ctx->tc) break;  // the tensor-core mode has one schedule
+      if (k == 4 && ctx->tc) break;   // the tensor-core mode has one schedule
+      if (k == 5 && best.base_bpsm == 0) break;  // an uncapped grid has no tile schedule
       LaunchShape sh = best;
       int* f = k == 0 ? &sh.base_bpsm : k == 1 ? &sh.base_threads : k == 2 ? &sh.usolve_threads
-             : k == 3 ? &sh.corr_threads : &sh.split;
+             : k == 3 ? &sh.corr_threads : k == 4 ? &sh.split : &sh.base_chunk;
       if (*f == v) continue;
       *f = v;
       double ms = 0.0;

@@ -57,6 +57,62 @@ static inline int capped_blocks(int64_t n, int t, int per_sm) {
 template <typename T>
 __device__ __forceinline__ T* chp(void* p) { return reinterpret_cast<T*>(p); }
 
+// Work distribution of the persistent base kernels over n units (edges or
+// elements).  chunk == 0 or work == nullptr: equal grid-stride shares.
+// Otherwise every block takes tiles of chunk * blockDim.x consecutive units
+// from an atomic ticket counter (work[0]) until none are left -- the next
+// ticket is fetched while the current tile runs -- so a block on an SM that
+// the concurrent correction kernels keep busy simply takes fewer tiles; the
+// last block to finish (counted in work[1]) resets both counters for the next
+// launch on the stream.  Every unit is computed by one thread with the same
+// arithmetic whatever the schedule, so results do not depend on it.
+template <typename F>
+__device__ __forceinline__ void for_units(int64_t n, int chunk, unsigned* work, F&& f) {
+  const bool dyn = chunk > 0 && work != nullptr;
+  __shared__ unsigned s_ticket;
+  const int64_t tile = dyn ? (int64_t)chunk * blockDim.x : (int64_t)gridDim.x * blockDim.x;
+  const int64_t ntiles = (n + tile - 1) / tile;
+  // static: tile t is the t-th grid-wide stride, every block takes each t
+  // with its own offset blockIdx.x * blockDim.x; dynamic: tile t is chunk *
+  // blockDim.x consecutive units, taken from the ticket counter
+  int64_t t = 0;
+  if (dyn) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(work, 1u);
+    __syncthreads();
+    t = s_ticket;
+  }
+  const int64_t off = dyn ? threadIdx.x : blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int per = dyn ? chunk : 1;
+#pragma unroll 1
+  while (t < ntiles) {
+    if (dyn) {
+      __syncthreads();  // every thread has read the ticket
+      if (threadIdx.x == 0) s_ticket = atomicAdd(work, 1u);
+    }
+    const int64_t base = t * tile + off;
+#pragma unroll 1
+    for (int k = 0; k < per; ++k) {
+      const int64_t i = base + (int64_t)k * blockDim.x;
+      if (i < n) f(i);
+    }
+    if (dyn) {
+      __syncthreads();  // the next ticket has arrived
+      t = s_ticket;
+    } else {
+      ++t;
+    }
+  }
+  if (dyn && threadIdx.x == 0) {
+    // this block takes no more tickets; the last one out resets the counters
+    __threadfence();
+    if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {
+      work[0] = 0u;
+      work[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // layout conversion: caller layout <-> internal state.  Caller layouts: the
 // full c[3][15][ne_user] (off == nullptr), or packed element by element,
@@ -234,6 +290,19 @@ __global__ void k_set_dt(double* dt_dev, unsigned long long* dmin, double cfl, d
     dmin[i] = (unsigned long long)__double_as_longlong(DBL_MAX);
   }
 }
+__global__ void k_fill(double* p, double v, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+int launch_fill(cudaStream_t s, double* p, double v, int n) {
+  if (n <= 0) return 0;
+  k_fill<<<nblocks(n, 128), 128, 0, s>>>(p, v, n);
+  count_launch();
+  SWE_CUDA_OK(cudaGetLastError());
+  return 0;
+}
+
 __global__ void k_advance_time(double* t_dev, const double* dt_dev, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) t_dev[i] += dt_dev[i];
@@ -297,8 +366,9 @@ __device__ __forceinline__ void p1_traces(const DevMesh& m, const double* __rest
 }
 
 __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cb,
-                                                   const double* __restrict__ ub, double* __restrict__ Fb) {
-  for (int64_t ed = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ed < m.nedge; ed += (int64_t)gridDim.x * blockDim.x) {
+                                                   const double* __restrict__ ub, double* __restrict__ Fb, int chunk,
+                                                   unsigned* work) {
+  for_units(m.nedge, chunk, work, [&](int64_t ed) {
   const int64_t ne = m.ne, nE = m.nedge;
   const int L = m.eL[ed], R = m.eR[ed], info = m.einfo[ed];
   const int kL = info & 3, kR = (info >> 2) & 3, bc = info >> 4;
@@ -345,14 +415,19 @@ __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg
     Fb[(1 * 2 + g) * nE + ed] = a.U[g] * a.w[g] + b.U[g] * b.w[g] + P * nxw + lam * (a.U[g] - b.U[g]);
     Fb[(2 * 2 + g) * nE + ed] = a.V[g] * a.w[g] + b.V[g] * b.w[g] + P * nyw + lam * (a.V[g] - b.V[g]);
   }
-  }
+  });
 }
 
+// the tile size of the dynamic schedule, 0 for the static one (an uncapped
+// grid of one block per base_threads units needs no schedule)
+static inline int base_chunk(const LaunchShape& L) { return L.base_bpsm > 0 ? L.base_chunk : 0; }
+
 int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Stage& stg, const double* cb,
-                     const double* ub, EdgeFlux fx) {
+                     const double* ub, EdgeFlux fx, unsigned* work) {
   if (m.nedge == 0) return 0;
   const LaunchShape& L = launch_shape();
-  k_edge_base<<<capped_blocks(m.nedge, L.base_threads, L.base_bpsm), L.base_threads, 0, s>>>(m, ph, stg, cb, ub, fx.Fb);
+  k_edge_base<<<capped_blocks(m.nedge, L.base_threads, L.base_bpsm), L.base_threads, 0, s>>>(m, ph, stg, cb, ub, fx.Fb,
+                                                                                             base_chunk(L), work);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -368,14 +443,15 @@ int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Sta
 // f_c U_q with bottom friction and Coriolis), and the edge terms are
 // -sum_g F_g phi_q(x_g) over the three edges (sign flipped for the right side).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cbS,
+__global__ void __launch_bounds__(128, 3) k_elem_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cbS,
                                                    const double* __restrict__ cbN, double* __restrict__ cbO,
                                                    float* __restrict__ cbO32, const double* __restrict__ ub,
                                                    const double* __restrict__ Fb, const double* __restrict__ Fbc,
-                                                   const double* __restrict__ rc, int64_t rc_start) {
+                                                   const double* __restrict__ rc, int64_t rc_start, int chunk,
+                                                   unsigned* work) {
   const int64_t ne = m.ne, nE = m.nedge;
   const double* geo = m.geo;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+  for_units(ne, chunk, work, [&](int64_t e) {
   double c[3][3], u[2][3];
 #pragma unroll
   for (int f = 0; f < 3; ++f)
@@ -479,18 +555,18 @@ __global__ void __launch_bounds__(128) k_elem_base(DevMesh m, Phys ph, Stage stg
       cbO[ix] = v;
       if (cbO32) cbO32[ix] = (float)v;
     }
-  }
+  });
 }
 
 int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
                      int corr_fp32, const double* cbS, const double* cbN, double* cbO, float* cbO32, const double* ub,
-                     EdgeFlux fx, const void* rc, double cfl) {
+                     EdgeFlux fx, const void* rc, double cfl, unsigned* work) {
   (void)cfl;
   if (m.ne == 0) return 0;
   (void)corr_fp32;
   const LaunchShape& L = launch_shape();
-  k_elem_base<<<capped_blocks(m.ne, L.base_threads, L.base_bpsm), L.base_threads, 0, s>>>(m, ph, stg, cbS, cbN, cbO, cbO32, ub, fx.Fb, fx.Fbc,
-                                                 (const double*)rc, G.start[2]);
+  k_elem_base<<<capped_blocks(m.ne, L.base_threads, L.base_bpsm), L.base_threads, 0, s>>>(
+      m, ph, stg, cbS, cbN, cbO, cbO32, ub, fx.Fb, fx.Fbc, (const double*)rc, G.start[2], base_chunk(L), work);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;

@@ -51,6 +51,8 @@ struct LaunchShape {
   int corr_threads;    // threads per block of the correction u-solve and edge kernels (32..128)
   int split;           // 1: the correction element kernel's higher test modes run beside the base
                        // element kernel instead of before it (FP64 and mixed modes)
+  int base_chunk;      // schedule of the capped base grids: 0 = equal grid-stride shares, c > 0 =
+                       // dynamic tiles of c * base_threads edges / elements taken from a ticket counter
 };
 const LaunchShape& launch_shape();
 
@@ -71,14 +73,18 @@ int launch_sub(cudaStream_t s, const double* a, const double* b, double* out, in
 // velocity solves of that stage and read (and reset) by launch_advance_time
 int launch_usolve_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const double* cb,
                        double* ub, float* ub32, unsigned* status, unsigned long long* dmin);
+// work: two zero-initialised counters per kernel for the dynamic schedule
+// (left at zero when the launch ends), used by one launch at a time
 int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Stage& stg, const double* cb,
-                     const double* ub, EdgeFlux fx);
+                     const double* ub, EdgeFlux fx, unsigned* work);
 int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
                      int corr_fp32, const double* cbS, const double* cbN, double* cbO, float* cbO32,
-                     const double* ub, EdgeFlux fx, const void* rc, double cfl);
+                     const double* ub, EdgeFlux fx, const void* rc, double cfl, unsigned* work);
 int launch_advance_time(cudaStream_t s, double* t_dev, unsigned long long* dmin, double cfl,
                         double dt_fixed, double* dt_dev, int nmem);
 int launch_reset_min(cudaStream_t s, unsigned long long* dmin, int nmem);
+// p[0 .. n) = v (member times set on the stream, without a host copy)
+int launch_fill(cudaStream_t s, double* p, double v, int n);
 int launch_indicator(cudaStream_t s, const DevMesh& m, const Groups& G, const int32_t* perm, int corr_fp32,
                      StateDev st, double up, double down, int pmin, int pmax, int8_t* p_user);
 int launch_check_state(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp32, StateDev st,

@@ -80,7 +80,7 @@ def device_bytes(meshes, precision):
     if precision == swedg.PREC_MIXED_TF32:
         allocs += [32 * 4 * max(nrc, 1)]                                                      # tensor-core volume terms
     allocs += [8 * 3 * KMAX * ne, 8 * 3 * KMAX * ne, ne, 8 * ne, 8 * nm, 8 * nm, 8 * nm, 4,  # staging, packed offsets
-               8 * min(1024, max(1, (ne + 255) // 256)), 16]
+               8 * min(1024, max(1, (ne + 255) // 256)), 16, 16]                           # ..., base tickets
     b = sum(a if a > 0 else 16 for a in allocs)  # the library allocates 16 bytes for an empty array
     return b
 

@@ -45,7 +45,8 @@ SYMBOLS = ("swe_default_params", "swe_create", "swe_destroy", "swe_last_error", 
            "swe_run_adaptive", "swe_set_members", "swe_set_member_times", "swe_get_member_times",
            "swe_memory_bytes", "swe_tc_operand_image", "swe_get_launch_shape", "swe_set_launch_shape",
            "swe_autotune", "swe_selftest_wait", "swe_packed_size", "swe_set_state_packed",
-           "swe_get_state_packed")
+           "swe_get_state_packed", "swe_set_state_packed_async", "swe_run_async", "swe_get_state_packed_async",
+           "swe_sync")
 
 
 def library_path() -> str:
@@ -77,6 +78,10 @@ def load():
     lib.swe_packed_size.argtypes = [P]
     lib.swe_set_state_packed.argtypes = [P, P, d]
     lib.swe_get_state_packed.argtypes = [P, P, C.POINTER(d)]
+    lib.swe_set_state_packed_async.argtypes = [P, P, d]
+    lib.swe_run_async.argtypes = [P, i64, d]
+    lib.swe_get_state_packed_async.argtypes = [P, P]
+    lib.swe_sync.argtypes = [P]
     lib.swe_p1_modes.argtypes = [P, P, P]
     lib.swe_rhs.argtypes = [P, P, P]
     lib.swe_rhs_parts.argtypes = [P, P, P, P]
@@ -277,6 +282,32 @@ class Solver:
         self._ck(self._lib.swe_get_state_packed(self.h, p, C.byref(t)))
         return out, t.value
 
+    # asynchronous variants: enqueue and return; sync() waits and reports errors.
+    # The caller keeps the buffers alive and untouched until sync() returns.
+    def set_state_packed_async(self, c, t=0.0):
+        n = c.numel() if hasattr(c, "numel") else np.size(c)
+        if n != self.packed_size():
+            raise ValueError(f"packed state has {n} values, the orders need {self.packed_size()}")
+        if not hasattr(c, "data_ptr"):
+            raise ValueError("asynchronous calls take torch tensors (pinned host or CUDA), which the caller keeps alive")
+        p, _ = _ptr(c)
+        self._ck(self._lib.swe_set_state_packed_async(self.h, p, float(t)))
+
+    def run_async(self, nsteps, dt_fixed=0.0):
+        self._ck(self._lib.swe_run_async(self.h, int(nsteps), float(dt_fixed)))
+
+    def get_state_packed_async(self, out):
+        n = out.numel() if hasattr(out, "numel") else np.size(out)
+        if n != self.packed_size():
+            raise ValueError(f"packed state buffer has {n} values, the orders need {self.packed_size()}")
+        if not hasattr(out, "data_ptr"):
+            raise ValueError("asynchronous calls take torch tensors (pinned host or CUDA), which the caller keeps alive")
+        p, _ = _ptr(out)
+        self._ck(self._lib.swe_get_state_packed_async(self.h, p))
+
+    def sync(self):
+        self._ck(self._lib.swe_sync(self.h))
+
     def p1_modes(self, vals, out=None):
         if out is None:
             out = np.zeros((3, self.ne))
@@ -339,20 +370,20 @@ class Solver:
         self._ck(self._lib.swe_set_member_times(self.h, t.ctypes.data_as(C.c_void_p)))
 
     def launch_shape(self):
-        """(base blocks per SM, base threads, u-solve threads, correction threads, schedule)"""
-        v = np.zeros(5, np.int32)
+        """(base blocks per SM, base threads, u-solve threads, correction threads, schedule, base tiles)"""
+        v = np.zeros(6, np.int32)
         self._ck(self._lib.swe_get_launch_shape(self.h, v.ctypes.data_as(C.c_void_p)))
         return tuple(int(x) for x in v)
 
     def set_launch_shape(self, shape):
         v = np.ascontiguousarray(shape, dtype=np.int32)
-        if v.shape != (5,):
-            raise ValueError("a launch shape has 5 entries")
+        if v.shape != (6,):
+            raise ValueError("a launch shape has 6 entries")
         self._ck(self._lib.swe_set_launch_shape(self.h, v.ctypes.data_as(C.c_void_p)))
 
     def autotune(self, steps=5):
         """choose the launch shape by timing trial steps; returns (shape, ms per step)"""
-        v = np.zeros(5, np.int32)
+        v = np.zeros(6, np.int32)
         ms = C.c_double(0.0)
         self._ck(self._lib.swe_autotune(self.h, int(steps), v.ctypes.data_as(C.c_void_p), C.byref(ms)))
         return tuple(int(x) for x in v), ms.value

@@ -21,8 +21,10 @@ def test_reference_arm_line():
     line = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
     assert line["impl"] == "reference" and line["unit"] == "DOF-stage/s" and line["value"] > 0
     assert line["steps"] == 3 and line["warmup"] == 3 and line["higher_is_better"] is True
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
-    assert line["cpu_baseline"]["value"] == line["value"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and 1 <= cb["cores"] <= cb["nproc"] == (os.cpu_count() or 1)
+    assert cb["cpu_model"] and cb["value"] == line["value"]
+    assert set(line["config"]) == {"workload", "triangles", "dof_stage_per_step", "l2", "replicas"}
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["config"]["triangles"] == 2 * 32 * 32
 

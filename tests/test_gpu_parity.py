@@ -386,3 +386,72 @@ def test_dynamic_adaptivity_matches_oracle():
     o2, _ = s.adapt(up, down, pmin, pmax)
     po, _, _ = m.indicator(co, up, down, pmin, pmax)
     assert np.array_equal(o2, po)
+
+
+@pytest.mark.parametrize("precision", [swedg.PREC_FP64, swedg.PREC_MIXED_FP32])
+def test_base_work_schedules_give_the_same_state(precision):
+    """Static grid-stride shares and dynamic tiles of 1, 3 and 16 x base
+    threads units (ticket counters that every launch leaves at zero for the
+    next one: 30 graph replays of 3 stages, then an rhs) give bitwise the same
+    state, the oracle's to 1e-11 in FP64"""
+    w = mixed_workload(n=20, seed=5, pmin=1, pmax=4)
+    m, P, _ = make_pair(w)
+    c = m.project_state(w["ic"])
+    got = []
+    for shape in ((1, 64, 256, 128, 0, 0), (1, 64, 256, 128, 0, 1), (3, 128, 256, 128, 1, 3), (1, 32, 256, 64, 0, 16)):
+        _, _, s = make_pair(w, precision=precision)
+        s.set_launch_shape(shape)
+        s.set_state(c, 0.0)
+        s.run(30)
+        cg, t = s.get_state()
+        got.append((cg, t, s.rhs(cg)))
+        s.close()
+    for g in got[1:]:
+        assert g[1] == got[0][1]
+        assert np.array_equal(g[0], got[0][0]) and np.array_equal(g[2], got[0][2])
+    if precision == swedg.PREC_FP64:
+        co, to = m.run(P, c, 0.0, 30)
+        assert rel_l2(got[0][0], co) < 1e-11 and abs(got[0][1] - to) <= 1e-12 * to
+
+
+@pytest.mark.parametrize("precision", [swedg.PREC_FP64, swedg.PREC_MIXED_FP32])
+def test_async_packed_pipeline_equals_the_synchronous_calls(precision):
+    """swe_set_state_packed_async / swe_run_async / swe_get_state_packed_async
+    with pinned host buffers, six different inputs in a row and one swe_sync
+    at the end (copies double-buffered on their own streams): every output is
+    bitwise the synchronous calls' result; a state with a negative depth
+    enqueued the same way is reported by swe_sync"""
+    import torch
+    w = mixed_workload(n=18, seed=6, pmin=1, pmax=4)
+    m, P, s = make_pair(w, precision=precision)
+    base = m.project_state(w["ic"])
+    n = s.packed_size()
+    ins, refs = [], []
+    for k in range(6):
+        c = base.copy()
+        c[1:] *= 1.0 + 0.1 * k
+        s.set_state(c, 0.0)
+        packed, _ = s.get_state_packed()
+        ins.append(torch.from_numpy(packed).pin_memory())
+        s.set_state_packed(packed, 10.0 * k)
+        s.run(2)
+        refs.append(s.get_state_packed()[0])
+    outs = [torch.zeros(n, dtype=torch.float64).pin_memory() for _ in range(6)]
+    for k in range(6):
+        s.set_state_packed_async(ins[k], 10.0 * k)
+        s.run_async(2)
+        s.get_state_packed_async(outs[k])
+    s.sync()
+    for k in range(6):
+        assert np.array_equal(outs[k].numpy(), refs[k]), k
+    bad = ins[0].clone()
+    bad_c = base.copy()
+    bad_c[0, 0] = -1e4 * np.sqrt(m.geometry()["area"])
+    s.set_state(bad_c, 0.0)
+    bad.copy_(torch.from_numpy(s.get_state_packed()[0]))
+    s.set_state_packed_async(bad, 0.0)
+    s.run_async(1)
+    with pytest.raises(swedg.SweError) as ei:
+        s.sync()
+    assert ei.value.code in (-3, -4)
+    s.close()

@@ -141,15 +141,17 @@ def test_autotuned_shape_gives_the_same_state(prec):
     assert a.launch_shape() == shape and ms > 0
     c_a, t_a = a.get_state()
     assert t_a == 0.0 and np.array_equal(c_a, c0)  # the trial steps left no trace
-    b.set_launch_shape((1, 64, 128, 64, 1 - shape[4]))  # the other schedule
+    b.set_launch_shape((1, 64, 128, 64, 1 - shape[4], 0 if shape[5] else 3))  # the other schedules
     a.run(10)
     b.run(10)
     assert np.array_equal(a.get_state()[0], b.get_state()[0])
     with pytest.raises(swedg.SweError):
-        a.set_launch_shape((2, 100, 256, 128, 0))
+        a.set_launch_shape((2, 100, 256, 128, 0, 2))
     with pytest.raises(swedg.SweError):
-        a.set_launch_shape((2, 128, 256, 128, 2))
+        a.set_launch_shape((2, 128, 256, 128, 2, 2))
+    with pytest.raises(swedg.SweError):
+        a.set_launch_shape((2, 128, 256, 128, 0, 17))
     with pytest.raises(ValueError):
-        a.set_launch_shape((2, 128, 256, 128))
+        a.set_launch_shape((2, 128, 256, 128, 0))
     a.close()
     b.close()
