@@ -491,26 +491,33 @@ def bench_ensemble(args, world):
     return line
 
 
-def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, chunk, warmup, seed=7):
+def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, chunk, warmup, seed=7, pool=0,
+                drain_s=None):
     """Continuous-batching serving loop against a wall clock: requests arrive
-    by a seeded Poisson process, are admitted by device footprint, share RK
-    launches with the running ones and leave when done.  Returns a summary."""
+    by a seeded Poisson process over `duration` seconds, are admitted by
+    device footprint, share RK launches with the running ones and leave when
+    done.  pool > 0 draws the requests' meshes from that many pre-generated
+    members (see inputs.serving_requests).  The loop ends when every request
+    is done, or drain_s seconds after the last arrival (then the unfinished
+    ones are the backlog).  Returns a summary."""
     import torch
     from paper_2311_11348_gb300 import serve, swedg
-    reqs = inputs.serving_requests(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, seed=seed)
-    prepared = []
+    reqs = inputs.serving_requests(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, seed=seed, pool=pool)
+    prepared, initial = [], {}
     for k, (t_arr, m, steps) in enumerate(reqs):  # client side: initial states, before the clock starts
-        s = swedg.Solver()
-        s.set_mesh(m["xy"], m["tri"])
-        c = np.zeros((3, 15, len(m["tri"])))
-        c[0, :3] = s.p1_modes(m["xi_vertex"])
-        s.close()
+        if id(m) not in initial:
+            s = swedg.Solver()
+            s.set_mesh(m["xy"], m["tri"])
+            c = np.zeros((3, 15, len(m["tri"])))
+            c[0, :3] = s.p1_modes(m["xi_vertex"])
+            s.close()
+            initial[id(m)] = c
         mesh = dict(xy=m["xy"], tri=m["tri"], hv=m["hv"], orders=m["orders"])
-        prepared.append((t_arr, serve.Request(rid=k, mesh=mesh, state=c, steps=steps)))
+        prepared.append((t_arr, serve.Request(rid=k, mesh=mesh, state=initial[id(m)], steps=steps)))
     kw = dict(precision=swedg.PREC_MIXED_FP32, g=9.81, cfl=0.1, rk_order=3, max_chunk=chunk)
     # warm-up: one small request through the same path (module load, graph capture)
     srv = serve.Server(int(budget_gb * 1e9), **kw)
-    w0 = prepared[0][1]
+    w0 = min((r for _, r in prepared), key=lambda r: len(r.mesh["tri"]))
     srv.submit(serve.Request(rid=-1, mesh=w0.mesh, state=w0.state, steps=max(3, warmup), arrival=1.0))
     srv.run_until_idle()
     srv.close()
@@ -520,8 +527,11 @@ def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, c
     t0 = time.perf_counter()
     pending = list(prepared)
     busy = 0.0
+    stop = None if drain_s is None else duration + drain_s
     while pending or srv.waiting or srv.active:
         now = time.perf_counter() - t0
+        if stop is not None and now >= stop:
+            break
         while pending and pending[0][0] <= now:
             t_arr, r = pending.pop(0)
             r.arrival = t0 + t_arr
@@ -534,15 +544,25 @@ def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, c
         busy += time.perf_counter() - tb
     makespan = time.perf_counter() - t0
     clk = clocks.stop()
+    backlog = len(pending) + len(srv.waiting) + len(srv.active)
     srv.close()
     lat = srv.latencies()
+    arr = np.array([r.arrival - t0 for r in srv.done])
     work = srv.dof_stage_updates
     offered = sum(r.steps * 3 * 3 * int(np.array([1, 3, 6, 10, 15])[r.mesh["orders"].astype(np.int64)].sum())
                   for _, r in prepared) / duration
     state_bytes = sum(r.state.nbytes for _, r in prepared)
-    return dict(value=work / makespan, requests=len(prepared), makespan_s=makespan,
-                p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
-                mean_s=float(lat.mean()), max_s=float(lat.max()), offered_dof_stage_per_s=offered,
+    pct = (lambda a, q: float(np.percentile(a, q)) if len(a) else None)
+    first, second = lat[arr < duration / 2], lat[(arr >= duration / 2) & (arr < duration)]
+    p99a, p99b = pct(first, 99), pct(second, 99)
+    # stable: every request of the window done in the drain time, and the p99 of
+    # the second half of the window no more than twice the first half's
+    stable = backlog == 0 and p99a is not None and p99b is not None and p99b <= 2.0 * p99a
+    return dict(value=work / makespan, requests=len(prepared), completed=len(srv.done), backlog=backlog,
+                failed=len(srv.failed), makespan_s=makespan, rate=rate,
+                p50_s=pct(lat, 50), p99_s=pct(lat, 99), mean_s=float(lat.mean()) if len(lat) else None,
+                max_s=float(lat.max()) if len(lat) else None, p99_first_half_s=p99a, p99_second_half_s=p99b,
+                stable=stable, offered_dof_stage_per_s=offered,
                 dof_stage_updates=work, rebuilds=srv.rebuilds, rebuild_s=srv.rebuild_s, busy_s=busy,
                 launches=srv.launches, state_bytes=state_bytes,
                 total_steps=sum(r.steps for _, r in prepared),
@@ -603,10 +623,20 @@ def bench_sweep(args, world):
 
 
 def bench_serving(args, world):
-    r = serving_run(args.rate, args.duration, args.tri_lo, args.tri_hi, args.steps_lo, args.steps_hi,
-                    args.budget_gb, args.chunk, args.warmup)
-    r["makespan_s"] = max_over_ranks(r["makespan_s"], world)
-    r["value"] = r["dof_stage_updates"] / r["makespan_s"]
+    """The serving loop at one offered rate (--rate), and with --rates a
+    sweep of rates for the highest one whose p99 stays stable."""
+    def one(rate):
+        r = serving_run(rate, args.duration, args.tri_lo, args.tri_hi, args.steps_lo, args.steps_hi,
+                        args.budget_gb, args.chunk, args.warmup, pool=args.pool, drain_s=args.drain_s)
+        r["makespan_s"] = max_over_ranks(r["makespan_s"], world)
+        r["value"] = r["dof_stage_updates"] / r["makespan_s"]
+        return r
+    r = one(args.rate)
+    sweep = [one(x) for x in args.rates] if args.rates else []
+    stable = [x["rate"] for x in sweep if x["stable"]]
+    pool = f", meshes drawn from a pool of {args.pool} seeded members" if args.pool else ""
+    drain = (f"; the loop stops {args.drain_s} s after the last arrival (unfinished requests: backlog)"
+             if args.drain_s is not None else "; every request runs to completion")
     line = {
         "metric": METRIC, "value": r["value"] * world, "unit": "DOF-stage/s", "n_gpus": world,
         "steps": r["total_steps"], "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
@@ -614,10 +644,12 @@ def bench_serving(args, world):
         "config": {"workload": f"serving: Poisson arrivals {args.rate}/s for {args.duration} s, triangles "
                                f"log-uniform [{int(args.tri_lo)}, {int(args.tri_hi)}], steps uniform "
                                f"[{args.steps_lo}, {args.steps_hi}], p in {{1..4}} 40/30/20/10, mixed, "
-                               f"{args.budget_gb} GB admission budget, chunks of <= {args.chunk} steps",
+                               f"{args.budget_gb} GB admission budget, chunks of <= {args.chunk} steps{pool}{drain}",
                    "requests": r["requests"], "mean_triangles": r["mean_triangles"], "replicas": world,
                    "l2": "wall clock, end to end (state in from host, result out to host)"},
-        "latency_s": {"p50": r["p50_s"], "p99": r["p99_s"], "mean": r["mean_s"], "max": r["max_s"]},
+        "latency_s": {"p50": r["p50_s"], "p99": r["p99_s"], "mean": r["mean_s"], "max": r["max_s"],
+                      "p99_first_half": r["p99_first_half_s"], "p99_second_half": r["p99_second_half_s"]},
+        "completed": r["completed"], "backlog": r["backlog"], "failed": r["failed"],
         "offered_dof_stage_per_s": r["offered_dof_stage_per_s"],
         "makespan_s": r["makespan_s"], "rebuilds": r["rebuilds"], "rebuild_s": r["rebuild_s"],
         "gpu_launches": r["launches"], "clocks": r["clocks"],
@@ -626,6 +658,11 @@ def bench_serving(args, world):
                 "d2h_bytes_per_step": r["state_bytes"] / max(r["total_steps"], 1)},
         "roofline": None,
     }
+    if sweep:
+        line["rate_sweep"] = [{k: x[k] for k in ("rate", "requests", "completed", "backlog", "p50_s", "p99_s",
+                                                "p99_first_half_s", "p99_second_half_s", "stable", "value",
+                                                "offered_dof_stage_per_s", "makespan_s")} for x in sweep]
+        line["highest_stable_rate_per_s"] = max(stable) if stable else None
     return line
 
 
@@ -650,6 +687,11 @@ def main():
     ap.add_argument("--steps-hi", type=int, default=500)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--chunk", type=int, default=50, help="serving: max steps between scheduling points")
+    ap.add_argument("--pool", type=int, default=0, help="serving: draw the meshes from this many members (0: one each)")
+    ap.add_argument("--drain-s", type=float, default=None,
+                    help="serving: stop this long after the last arrival (default: run every request to completion)")
+    ap.add_argument("--rates", type=lambda v: [float(x) for x in v.split(",")], default=None,
+                    help="serving: also sweep these arrival rates for the highest stable one")
     ap.add_argument("--no-serving", action="store_true", help="skip the short serving leg of the ocean workload")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the adaptive leg of the ocean workload")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",

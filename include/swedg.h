@@ -205,6 +205,19 @@ int swe_set_members(swe_ctx* ctx, int32_t nmembers, const int32_t* member);
 int swe_set_member_times(swe_ctx* ctx, const double* t);
 int swe_get_member_times(swe_ctx* ctx, double* t_out, double* dt_out);
 
+/* Status of every ensemble member (host [nmembers]): the SWE_STATUS_* bits
+ * that the steps since the last call (or since the last state upload) set
+ * for that member's elements -- a mean depth at or below h_min, a non-finite
+ * value in its state.  The paper has no counterpart: it lets a caller that
+ * runs independent simulations in one context (a serving loop) tell which of
+ * them failed when swe_run reports SWE_EDEPTH or SWE_ENONFINITE.  The bits
+ * come from the depth checks of the steps and from the state check that
+ * swe_run, swe_rk_step and swe_sync make before they return.  Reading clears
+ * them. */
+#define SWE_STATUS_DEPTH 1u
+#define SWE_STATUS_NONFINITE 2u
+int swe_member_status(swe_ctx* ctx, uint32_t* status_out);
+
 /* Device memory held by the context (bytes); a serving loop admits requests
  * by this footprint. */
 int swe_memory_bytes(swe_ctx* ctx, int64_t* bytes);

@@ -86,11 +86,17 @@ struct swe_ctx {
   std::vector<int64_t> nb;
   std::vector<int8_t> nbk;
   // internal numbering: perm[internal] = caller index
-  std::vector<int32_t> perm, inv;
   Groups G{};
   int64_t nedge = 0;
+  // the mesh in caller order and what the device regrouping writes
+  MeshStatic ms{};
+  DevMeshOut dout{};
+  RegroupScratch rw{};
+  // capacities (bytes) of the buffers sized by the order groups
+  size_t cap_ch[3][5] = {}, cap_uh[5] = {}, cap_tr[5] = {}, cap_trv[5] = {}, cap_pf[5] = {};
+  size_t cap_rc = 0, cap_vol = 0, cap_ecs = 0;
   // device
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;
   DevMesh dm{};
   CorrEdges ce{};
   int32_t* d_perm = nullptr;
@@ -107,6 +113,7 @@ struct swe_ctx {
   double* d_t = nullptr;
   unsigned long long* d_dmin = nullptr;
   unsigned* d_status = nullptr;
+  unsigned* d_mstatus = nullptr;  // [nmem] status bits per ensemble member
   double* d_partial = nullptr;
   double* d_red = nullptr;
   int8_t* d_newp = nullptr;  // orders proposed by the adaptivity indicator (caller order)
@@ -172,7 +179,7 @@ static std::string g_create_err_s;
 // ------------------------------------------------------------------ memory
 static void free_all(swe_ctx* ctx) {
   if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
-  for (void* p : ctx->allocs) cudaFree(p);
+  for (auto& a : ctx->allocs) cudaFree(a.first);
   ctx->allocs.clear();
   ctx->dev_bytes = 0;
 }
@@ -183,10 +190,36 @@ static int dalloc(swe_ctx* ctx, P** out, size_t bytes) {
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
-  ctx->allocs.push_back(p);
+  ctx->allocs.push_back({p, bytes});
   ctx->dev_bytes += (int64_t)bytes;
   *out = (P*)p;
   return 0;
+}
+
+static void dfree(swe_ctx* ctx, void* p) {
+  for (size_t i = 0; i < ctx->allocs.size(); ++i)
+    if (ctx->allocs[i].first == p) {
+      cudaFree(p);
+      ctx->dev_bytes -= (int64_t)ctx->allocs[i].second;
+      ctx->allocs.erase(ctx->allocs.begin() + (long)i);
+      return;
+    }
+}
+
+// *p holds at least `need` bytes: the first allocation is exact, a later
+// growth takes a quarter more so that repeated order changes rarely
+// reallocate.  The contents are not kept.
+template <typename P>
+static int ensure_buf(swe_ctx* ctx, P** p, size_t* cap, size_t need) {
+  if (need == 0) need = 16;
+  if (*p && need <= *cap) return 0;
+  const size_t bytes = *p ? need + need / 4 : need;
+  if (*p) dfree(ctx, (void*)*p);
+  *p = nullptr;
+  *cap = 0;
+  int rc = dalloc(ctx, p, bytes);
+  if (!rc) *cap = bytes;
+  return rc;
 }
 
 template <typename V>
@@ -279,42 +312,104 @@ static int build_topology(swe_ctx* ctx) {
   return 0;
 }
 
-// Build the internal order, geometry, edges and device buffers; the state is
-// reset to zero (callers that keep it go through the caller layout).
+// Buffers whose sizes follow the order groups (the current G and ce.n): the
+// correction parts of the three RK states, of the velocity and of the trace
+// records, the correction edges' projections, rc, the tensor-core volume
+// terms and the per-element correction edge slots.  Grown as needed (a new
+// buffer starts zeroed; the contents of a regrown one are not kept).
+static int alloc_group_buffers(swe_ctx* ctx) {
+  const size_t ts = ctx->corr32 ? sizeof(float) : sizeof(double);
+  auto grow = [&](auto** ptr, size_t* cap, size_t need) -> int {
+    void* before = (void*)*ptr;
+    int rc = ensure_buf(ctx, ptr, cap, need);
+    // zeroed on the context stream, ahead of the kernels that fill it
+    if (!rc && (void*)*ptr != before)
+      rc = cudaMemsetAsync((void*)*ptr, 0, *cap, ctx->stream) == cudaSuccess ? 0 : SWE_ECUDA;
+    return rc;
+  };
+  int rc = 0;
+  for (int p = 2; p < 5 && !rc; ++p) {
+    const size_t n = (size_t)(ctx->G.start[p + 1] - ctx->G.start[p]), K = (size_t)Kof(p);
+    for (int s = 0; s < 3 && !rc; ++s) rc = grow(&ctx->st[s].ch[p], &ctx->cap_ch[s][p], ts * 3 * (K - 3) * n);
+    if (!rc) rc = grow(&ctx->vel.uh[p], &ctx->cap_uh[p], ts * 2 * (K - 3) * n);
+    if (!rc) rc = grow(&ctx->vel.tr[p], &ctx->cap_tr[p], ts * 4 * K * n);
+    if (!rc) rc = grow(&ctx->vel.trv[p], &ctx->cap_trv[p], ts * K * n);
+    if (!rc) rc = grow(&ctx->fx.Pf[p], &ctx->cap_pf[p], ts * 2 * 3 * (K - 3) * (size_t)ctx->ce.n[p]);
+  }
+  const size_t nrc = (size_t)std::max<int64_t>(ctx->ne - ctx->G.start[2], 1);
+  if (!rc) rc = grow(&ctx->rc, &ctx->cap_rc, sizeof(double) * 4 * nrc);
+  if (!rc && ctx->tc) rc = grow(&ctx->vol, &ctx->cap_vol, sizeof(float) * 32 * nrc);
+  uint32_t* ecs = const_cast<uint32_t*>(ctx->ce.ecs);
+  if (!rc) rc = grow(&ecs, &ctx->cap_ecs, sizeof(uint32_t) * 3 * nrc);
+  ctx->ce.ecs = ecs;
+  return rc ? cuda_err(ctx, rc) : 0;
+}
+
+// Group the elements for the orders in d_newp (caller order) on the device:
+// the internal arrays, the group sizes (read back: one small copy and a
+// stream synchronisation) and the buffers that follow them.  keep_state
+// carries the state over hierarchically through the caller layout (modes
+// beyond an element's new order dropped, new modes zero).
+static int regroup(swe_ctx* ctx, bool keep_state) {
+  nvtxRangePushA("regroup");
+  const int64_t packed_before = ctx->packed_n;
+  if (keep_state)  // the state in the old internal order, out to the caller layout
+    CK(launch_to_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, nullptr, ctx->corr32, ctx->st[0], ctx->d_user));
+  CK(launch_regroup(ctx->stream, ctx->ms, ctx->d_newp, ctx->dout, ctx->rw));
+  int64_t info[11] = {};
+  CU(cudaMemcpyAsync(info, ctx->rw.info, sizeof info, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  for (int p = 0; p <= 5; ++p) ctx->G.start[p] = info[p];
+  for (int pm = 0; pm < 5; ++pm) ctx->ce.n[pm] = (pm >= 2 && ctx->nedge > 0) ? info[6 + pm - 1] - info[6 + pm - 2] : 0;
+  ctx->packed_n = info[10];
+  CK(alloc_group_buffers(ctx));
+  CK(launch_ecs(ctx->stream, ctx->ne, ctx->G.start[2], ctx->dout.eedge, ctx->dout.slot,
+                const_cast<uint32_t*>(ctx->ce.ecs)));
+  // edges that no longer touch a p >= 2 element carry no correction flux
+  CU(cudaMemsetAsync(ctx->fx.Fbc, 0, sizeof(double) * 6 * (size_t)std::max<int64_t>(ctx->nedge, 1), ctx->stream));
+  if (keep_state)
+    CK(launch_from_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, nullptr, ctx->corr32, ctx->d_user, ctx->st[0]));
+  if (ctx->packed_n != packed_before)  // the asynchronous staging buffers follow the packed size
+    for (int k = 0; k < 2; ++k) {
+      if (ctx->d_stage_in[k]) { CU(cudaStreamSynchronize(ctx->cin)); dfree(ctx, ctx->d_stage_in[k]); }
+      if (ctx->d_stage_out[k]) { CU(cudaStreamSynchronize(ctx->cout)); dfree(ctx, ctx->d_stage_out[k]); }
+      ctx->d_stage_in[k] = ctx->d_stage_out[k] = nullptr;
+    }
+  if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }  // sizes and grids changed
+  nvtxRangePop();
+  return 0;
+}
+
+// Build the mesh data in the caller's order on the host (geometry, edges),
+// the fixed-size device buffers, and the order-dependent ones through the
+// device regrouping; the state is reset to zero (callers that keep it go
+// through the caller layout).
 static int build_device(swe_ctx* ctx) {
   free_all(ctx);
   for (int k = 0; k < 2; ++k) ctx->d_stage_in[k] = ctx->d_stage_out[k] = nullptr;  // freed with the rest
+  for (int s = 0; s < 3; ++s)
+    for (int p = 0; p < 5; ++p) { ctx->st[s].ch[p] = nullptr; ctx->cap_ch[s][p] = 0; }
+  for (int p = 0; p < 5; ++p) {
+    ctx->vel.uh[p] = ctx->vel.tr[p] = ctx->vel.trv[p] = nullptr;
+    ctx->fx.Pf[p] = nullptr;
+    ctx->cap_uh[p] = ctx->cap_tr[p] = ctx->cap_trv[p] = ctx->cap_pf[p] = 0;
+  }
+  ctx->rc = nullptr; ctx->vol = nullptr; ctx->cap_rc = ctx->cap_vol = ctx->cap_ecs = 0;
+  std::memset(&ctx->ce, 0, sizeof ctx->ce);
   const int64_t ne = ctx->ne;
   const RefTables& R = tables();
-  // internal order: stable sort by p
-  ctx->perm.resize(ne);
-  std::iota(ctx->perm.begin(), ctx->perm.end(), 0);
-  std::stable_sort(ctx->perm.begin(), ctx->perm.end(),
-                   [&](int32_t a, int32_t b) { return ctx->p_user[a] < ctx->p_user[b]; });
-  ctx->inv.resize(ne);
-  for (int64_t e = 0; e < ne; ++e) ctx->inv[ctx->perm[e]] = (int32_t)e;
-  for (int p = 0; p <= 5; ++p) ctx->G.start[p] = 0;
-  {
-    int64_t cnt[5] = {0, 0, 0, 0, 0};
-    for (int64_t u = 0; u < ne; ++u) cnt[ctx->p_user[u]]++;
-    ctx->G.start[0] = 0;
-    for (int p = 0; p < 5; ++p) ctx->G.start[p + 1] = ctx->G.start[p] + cnt[p];
-  }
-  std::vector<int8_t> pint(ne);
-  for (int64_t e = 0; e < ne; ++e) pint[e] = ctx->p_user[ctx->perm[e]];
-  // geometry
+  // geometry, caller order
   std::vector<double> geo((size_t)NGEO * ne);
-  for (int64_t e = 0; e < ne; ++e) {
-    const int64_t u = ctx->perm[e];
+  for (int64_t u = 0; u < ne; ++u) {
     const int32_t* v = &ctx->tri[3 * u];
     const double x0 = ctx->xy[2 * v[0]], y0 = ctx->xy[2 * v[0] + 1];
     const double J00 = ctx->xy[2 * v[1]] - x0, J01 = ctx->xy[2 * v[2]] - x0;
     const double J10 = ctx->xy[2 * v[1] + 1] - y0, J11 = ctx->xy[2 * v[2] + 1] - y0;
     const double det = J00 * J11 - J01 * J10;
-    const double s = std::sqrt(det), rs = 1.0 / s;
+    const double sq = std::sqrt(det), rs = 1.0 / sq;
     const double Ji[4] = {J11 / det, -J01 / det, -J10 / det, J00 / det};
-    auto G_ = [&](int row) -> double& { return geo[(size_t)row * ne + e]; };
-    G_(G_RS) = rs; G_(G_S) = s;
+    auto G_ = [&](int row) -> double& { return geo[(size_t)row * ne + u]; };
+    G_(G_RS) = rs; G_(G_S) = sq;
     G_(G_JI0) = Ji[0]; G_(G_JI1) = Ji[1]; G_(G_JI2) = Ji[2]; G_(G_JI3) = Ji[3];
     for (int q = 1; q < 3; ++q) {
       const double gx = rs * (R.grad1[q][0] * Ji[0] + R.grad1[q][1] * Ji[2]);
@@ -329,7 +424,7 @@ static int build_device(swe_ctx* ctx) {
     for (int i = 0; i < 3; ++i) {
       double acc = 0.0;
       for (int w = 0; w < 3; ++w) acc += hvv[w] * R.Lv[w][i];
-      G_(G_HB0 + i) = s * acc;
+      G_(G_HB0 + i) = sq * acc;
     }
     double per = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -343,33 +438,33 @@ static int build_device(swe_ctx* ctx) {
     G_(G_M0) = R.phi0 * rs;
   }
   std::vector<double> etb((size_t)12 * ne);
-  for (int64_t e = 0; e < ne; ++e)
+  for (int64_t u = 0; u < ne; ++u)
     for (int k = 0; k < 3; ++k) {
-      const double rs = geo[(size_t)G_RS * ne + e];
-      double* t = &etb[(size_t)(3 * e + k) * 4];
+      const double rs = geo[(size_t)G_RS * ne + u];
+      double* t = &etb[(size_t)(3 * u + k) * 4];
       t[0] = rs * R.EB[2][k][1][0]; t[1] = rs * R.EB[2][k][2][0];
       t[2] = rs * R.EB[2][k][1][1]; t[3] = rs * R.EB[2][k][2][1];
     }
-  // edges
+  // edges: left element = the lower caller index, interior edges first, then
+  // sorted by the left element
   struct E { int32_t L, R, info; double len, nx, ny, hA, hB; };
   std::vector<E> ed;
   ed.reserve(3 * ne / 2 + 16);
   for (int64_t u = 0; u < ne; ++u)
     for (int k = 0; k < 3; ++k) {
       const int64_t n = ctx->nb[3 * u + k];
-      if (n >= 0 && ctx->inv[n] < ctx->inv[u]) continue;  // created from the other side
+      if (n >= 0 && n < u) continue;  // created from the other side
       E x;
-      int64_t uL = u; int kL = k;
-      int32_t R = -1, kR = 0, bc;
+      int32_t Rr = -1, kR = 0, bc;
       if (n >= 0) {
         bc = 0;
-        R = ctx->inv[n]; kR = ctx->nbk[3 * u + k];
+        Rr = (int32_t)n; kR = ctx->nbk[3 * u + k];
       } else {
         bc = ctx->tag[3 * u + k] == 2 ? 2 : 1;
       }
-      x.L = ctx->inv[uL]; x.R = R;
-      x.info = kL | (kR << 2) | (bc << 4);
-      const int32_t a = ctx->tri[3 * uL + (kL + 1) % 3], b = ctx->tri[3 * uL + (kL + 2) % 3];
+      x.L = (int32_t)u; x.R = Rr;
+      x.info = k | (kR << 2) | (bc << 4);
+      const int32_t a = ctx->tri[3 * u + (k + 1) % 3], b = ctx->tri[3 * u + (k + 2) % 3];
       const double dx = ctx->xy[2 * b] - ctx->xy[2 * a], dy = ctx->xy[2 * b + 1] - ctx->xy[2 * a + 1];
       x.len = std::hypot(dx, dy);
       x.nx = dy / x.len; x.ny = -dx / x.len;
@@ -383,12 +478,13 @@ static int build_device(swe_ctx* ctx) {
   });
   const int64_t nE = (int64_t)ed.size();
   ctx->nedge = nE;
-  if (nE >= (1ll << 30) || ne >= (1ll << 30)) return fail(ctx, SWE_EINVAL, "mesh too large for 30-bit edge ids");
-  std::vector<int32_t> eL(nE), eR(nE), einfo(nE), eedge(3 * ne, -1);
+  if (nE >= (1ll << 27) || ne >= (1ll << 30)) return fail(ctx, SWE_EINVAL, "mesh too large for 27-bit edge slots");
+  std::vector<int32_t> eLu(nE), eRu(nE), einfo(nE), eedge_u(3 * ne, -1), emem(nE);
   std::vector<double> egeo((size_t)NEGEO * nE);
   int64_t nint = 0;
   for (int64_t i = 0; i < nE; ++i) {
-    eL[i] = ed[i].L; eR[i] = ed[i].R; einfo[i] = ed[i].info;
+    eLu[i] = ed[i].L; eRu[i] = ed[i].R; einfo[i] = ed[i].info;
+    emem[i] = ctx->member_user[ed[i].L];
     auto E_ = [&](int row) -> double& { return egeo[(size_t)row * nE + i]; };
     E_(E_LEN) = ed[i].len; E_(E_NX) = ed[i].nx; E_(E_NY) = ed[i].ny;
     E_(E_HA) = ed[i].hA; E_(E_HB) = ed[i].hB;
@@ -399,66 +495,48 @@ static int build_device(swe_ctx* ctx) {
     E_(E_NXW) = E_(E_WLEN) * ed[i].nx;
     E_(E_NYW) = E_(E_WLEN) * ed[i].ny;
     if (ed[i].R >= 0) ++nint;
-    eedge[(size_t)(ed[i].info & 3) * ne + ed[i].L] = (int32_t)(i << 1);
-    if (ed[i].R >= 0) eedge[(size_t)((ed[i].info >> 2) & 3) * ne + ed[i].R] = (int32_t)((i << 1) | 1);
+    eedge_u[(size_t)(ed[i].info & 3) * ne + ed[i].L] = (int32_t)(i << 1);
+    if (ed[i].R >= 0) eedge_u[(size_t)((ed[i].info >> 2) & 3) * ne + ed[i].R] = (int32_t)((i << 1) | 1);
   }
-  // correction edges, grouped by max order of their sides
-  std::vector<int32_t> slot(nE, -1);
-  std::vector<int32_t> clist[5];
-  for (int64_t i = 0; i < nE; ++i) {
-    int pm = pint[eL[i]];
-    if (eR[i] >= 0) pm = std::max<int>(pm, pint[eR[i]]);
-    if (pm >= 2) {
-      slot[i] = (pm << 28) | (int32_t)clist[pm].size();
-      clist[pm].push_back((int32_t)i);
-    }
-  }
-  // per element of order >= 2: its three correction edges (pmax, side, slot)
-  const int64_t nrc_e = ne - ctx->G.start[2];
-  std::vector<uint32_t> ecs((size_t)3 * std::max<int64_t>(nrc_e, 1), 0u);
-  for (int64_t e = ctx->G.start[2]; e < ne; ++e)
-    for (int k = 0; k < 3; ++k) {
-      const int32_t ee = eedge[(size_t)k * ne + e];
-      const uint32_t cs = (uint32_t)slot[ee >> 1];
-      ecs[(size_t)k * nrc_e + (e - ctx->G.start[2])] = (cs & 0xf0000000u) | ((uint32_t)(ee & 1) << 27) | (cs & 0x07ffffffu);
-    }
-  for (int pm = 2; pm <= 4; ++pm)
-    if ((int64_t)clist[pm].size() >= (1ll << 27)) return fail(ctx, SWE_EINVAL, "too many correction edges");
-  // upload topology and geometry
-  double* d_geo; int8_t* d_p; int32_t *d_eedge, *d_eL, *d_eR, *d_einfo, *d_slot; double* d_egeo;
   int rc = 0;
-  if ((rc = upload(ctx, &d_geo, geo)) || (rc = upload(ctx, &d_p, pint)) || (rc = upload(ctx, &d_eedge, eedge)) ||
-      (rc = upload(ctx, &d_eL, eL)) || (rc = upload(ctx, &d_eR, eR)) || (rc = upload(ctx, &d_einfo, einfo)) ||
-      (rc = upload(ctx, &d_egeo, egeo)) || (rc = upload(ctx, &d_slot, slot)) ||
-      (rc = upload(ctx, &ctx->d_perm, ctx->perm)))
+  // the mesh in caller order (read by every regrouping) and the fixed edge data
+  double *d_geo_u, *d_etb_u, *d_egeo;
+  int32_t *d_eedge_u, *d_eLu, *d_eRu, *d_mem_u, *d_einfo, *d_emem;
+  std::vector<float> egeo32(egeo.begin(), egeo.end());
+  float* d_egeo32;
+  if ((rc = upload(ctx, &d_geo_u, geo)) || (rc = upload(ctx, &d_etb_u, etb)) || (rc = upload(ctx, &d_eedge_u, eedge_u)) ||
+      (rc = upload(ctx, &d_eLu, eLu)) || (rc = upload(ctx, &d_eRu, eRu)) || (rc = upload(ctx, &d_mem_u, ctx->member_user)) ||
+      (rc = upload(ctx, &d_einfo, einfo)) || (rc = upload(ctx, &d_egeo, egeo)) || (rc = upload(ctx, &d_egeo32, egeo32)) ||
+      (rc = upload(ctx, &d_emem, emem)))
     return cuda_err(ctx, rc);
-  std::vector<float> geo32(geo.begin(), geo.end()), egeo32(egeo.begin(), egeo.end());
-  float *d_geo32, *d_egeo32;
-  if ((rc = upload(ctx, &d_geo32, geo32)) || (rc = upload(ctx, &d_egeo32, egeo32))) return cuda_err(ctx, rc);
-  std::vector<int32_t> mem((size_t)ne), emem((size_t)nE);
-  for (int64_t e = 0; e < ne; ++e) mem[e] = ctx->member_user[ctx->perm[e]];
-  for (int64_t i = 0; i < nE; ++i) emem[i] = mem[eL[i]];
-  int32_t *d_mem, *d_emem;
-  if ((rc = upload(ctx, &d_mem, mem)) || (rc = upload(ctx, &d_emem, emem))) return cuda_err(ctx, rc);
-  double* d_etb;
-  if ((rc = upload(ctx, &d_etb, etb))) return cuda_err(ctx, rc);
-  ctx->dm = DevMesh{ne, nE, nint, d_geo, d_p, d_eedge, d_eL, d_eR, d_einfo, d_egeo, d_geo32, d_egeo32, d_etb,
-                    d_mem, d_emem, ctx->nmem};
-  std::memset(&ctx->ce, 0, sizeof ctx->ce);
-  ctx->ce.slot = d_slot;
+  ctx->ms = MeshStatic{ne, nE, d_geo_u, d_etb_u, d_eedge_u, d_eLu, d_eRu, d_mem_u};
+  // what the regrouping writes
+  DevMeshOut& D = ctx->dout;
+  if ((rc = dalloc(ctx, &D.perm, 4 * (size_t)ne)) || (rc = dalloc(ctx, &D.inv, 4 * (size_t)ne)) ||
+      (rc = dalloc(ctx, &D.p, (size_t)ne)) || (rc = dalloc(ctx, &D.geo, 8 * (size_t)NGEO * ne)) ||
+      (rc = dalloc(ctx, &D.geo32, 4 * (size_t)NGEO * ne)) || (rc = dalloc(ctx, &D.etb, 96 * (size_t)ne)) ||
+      (rc = dalloc(ctx, &D.mem, 4 * (size_t)ne)) || (rc = dalloc(ctx, &D.eedge, 12 * (size_t)ne)) ||
+      (rc = dalloc(ctx, &D.eL, 4 * (size_t)nE)) || (rc = dalloc(ctx, &D.eR, 4 * (size_t)nE)) ||
+      (rc = dalloc(ctx, &D.slot, 4 * (size_t)nE)) || (rc = dalloc(ctx, &D.lists, 12 * (size_t)nE)) ||
+      (rc = dalloc(ctx, &D.off, 8 * (size_t)ne)))
+    return cuda_err(ctx, rc);
   {
-    uint32_t* d_ecs = nullptr;
-    if ((rc = upload(ctx, &d_ecs, ecs))) return cuda_err(ctx, rc);
-    ctx->ce.ecs = d_ecs;
+    const int64_t be = regroup_blocks(ne), bg = regroup_blocks(nE);
+    RegroupScratch& W = ctx->rw;
+    if ((rc = dalloc(ctx, &W.ecnt, 4 * 5 * (size_t)be)) || (rc = dalloc(ctx, &W.eoff, 8 * 5 * (size_t)be)) ||
+        (rc = dalloc(ctx, &W.gcnt, 4 * 3 * (size_t)bg)) || (rc = dalloc(ctx, &W.goff, 8 * 3 * (size_t)bg)) ||
+        (rc = dalloc(ctx, &W.psum, 8 * (size_t)be)) || (rc = dalloc(ctx, &W.poff, 8 * (size_t)(be + 1))) ||
+        (rc = dalloc(ctx, &W.info, 8 * 16)))
+      return cuda_err(ctx, rc);
+    cudaMemset(W.info, 0, 8 * 16);
   }
-  for (int pm = 2; pm <= 4; ++pm) {
-    int32_t* d = nullptr;
-    if ((rc = upload(ctx, &d, clist[pm]))) return cuda_err(ctx, rc);
-    ctx->ce.list[pm] = d;
-    ctx->ce.n[pm] = (int64_t)clist[pm].size();
-  }
-  // state, velocity, fluxes
-  const size_t ts = ctx->corr32 ? sizeof(float) : sizeof(double);
+  ctx->d_perm = D.perm;
+  ctx->d_off = D.off;
+  ctx->dm = DevMesh{ne, nE, nint, D.geo, D.p, D.eedge, D.eL, D.eR, d_einfo, d_egeo, D.geo32, d_egeo32, D.etb,
+                    D.mem, d_emem, ctx->nmem, nullptr};
+  ctx->ce.slot = D.slot;
+  for (int pm = 2; pm <= 4; ++pm) ctx->ce.list[pm] = D.lists + (size_t)(pm - 2) * nE;
+  // base state, velocity and fluxes (sized by the mesh)
   for (int s = 0; s < 3; ++s) {
     if ((rc = dalloc(ctx, &ctx->st[s].cb, sizeof(double) * 9 * ne))) return cuda_err(ctx, rc);
     cudaMemset(ctx->st[s].cb, 0, sizeof(double) * 9 * ne);
@@ -467,60 +545,23 @@ static int build_device(swe_ctx* ctx) {
       if ((rc = dalloc(ctx, &ctx->st[s].cb32, sizeof(float) * 9 * ne))) return cuda_err(ctx, rc);
       cudaMemset(ctx->st[s].cb32, 0, sizeof(float) * 9 * ne);
     }
-    for (int p = 0; p < 5; ++p) {
-      ctx->st[s].ch[p] = nullptr;
-      if (p < 2) continue;
-      const int64_t n = ctx->G.start[p + 1] - ctx->G.start[p];
-      if ((rc = dalloc(ctx, &ctx->st[s].ch[p], ts * 3 * (Kof(p) - 3) * n))) return cuda_err(ctx, rc);
-      cudaMemset(ctx->st[s].ch[p], 0, ts * 3 * (Kof(p) - 3) * std::max<int64_t>(n, 0));
-    }
   }
   if ((rc = dalloc(ctx, &ctx->vel.ub, sizeof(double) * 6 * ne))) return cuda_err(ctx, rc);
   ctx->vel.ub32 = nullptr;
   if (ctx->corr32 && (rc = dalloc(ctx, &ctx->vel.ub32, sizeof(float) * 6 * ne))) return cuda_err(ctx, rc);
-  for (int p = 0; p < 5; ++p) {
-    ctx->vel.uh[p] = ctx->vel.tr[p] = ctx->vel.trv[p] = nullptr;
-    if (p < 2) continue;
-    const int64_t n = ctx->G.start[p + 1] - ctx->G.start[p];
-    if ((rc = dalloc(ctx, &ctx->vel.uh[p], ts * 2 * (Kof(p) - 3) * n)) ||
-        (rc = dalloc(ctx, &ctx->vel.tr[p], ts * 4 * Kof(p) * n)) ||
-        (rc = dalloc(ctx, &ctx->vel.trv[p], ts * Kof(p) * n)))
-      return cuda_err(ctx, rc);
-  }
   if ((rc = dalloc(ctx, &ctx->fx.Fb, sizeof(double) * 6 * nE)) || (rc = dalloc(ctx, &ctx->fx.Fbc, sizeof(double) * 6 * nE)))
     return cuda_err(ctx, rc);
-  cudaMemset(ctx->fx.Fbc, 0, sizeof(double) * 6 * nE);
-  for (int pm = 0; pm < 5; ++pm) {
-    ctx->fx.Pf[pm] = nullptr;
-    if (pm < 2) continue;
-    const size_t sz = ts * 2 * 3 * (Kof(pm) - 3) * ctx->ce.n[pm];
-    if ((rc = dalloc(ctx, &ctx->fx.Pf[pm], sz))) return cuda_err(ctx, rc);
-  }
-  // correction of the base modes from the volume terms: [U,V][q = 2,3][elements with p >= 2]
-  const int64_t nrc = ne - ctx->G.start[2];
-  if ((rc = dalloc(ctx, &ctx->rc, sizeof(double) * 4 * std::max<int64_t>(nrc, 1)))) return cuda_err(ctx, rc);
-  cudaMemset(ctx->rc, 0, sizeof(double) * 4 * std::max<int64_t>(nrc, 1));
-  ctx->vol = nullptr;
-  if (ctx->tc) {
-    if ((rc = dalloc(ctx, &ctx->vol, sizeof(float) * 32 * std::max<int64_t>(nrc, 1)))) return cuda_err(ctx, rc);
-    cudaMemset(ctx->vol, 0, sizeof(float) * 32 * std::max<int64_t>(nrc, 1));
-  }
   if ((rc = dalloc(ctx, &ctx->d_user, sizeof(double) * 3 * KMAX * ne)) ||
       (rc = dalloc(ctx, &ctx->d_user2, sizeof(double) * 3 * KMAX * ne)))
     return cuda_err(ctx, rc);
   if ((rc = dalloc(ctx, &ctx->d_newp, (size_t)ne))) return cuda_err(ctx, rc);
-  {
-    std::vector<int64_t> off((size_t)ne);
-    int64_t o = 0;
-    for (int64_t u = 0; u < ne; ++u) { off[u] = o; o += 3 * Kof(ctx->p_user[u]); }
-    ctx->packed_n = o;
-    if ((rc = upload(ctx, &ctx->d_off, off))) return cuda_err(ctx, rc);
-  }
   const size_t nm = (size_t)ctx->nmem;
   if ((rc = dalloc(ctx, &ctx->d_dt, sizeof(double) * nm)) || (rc = dalloc(ctx, &ctx->d_t, sizeof(double) * nm)) ||
       (rc = dalloc(ctx, &ctx->d_dmin, sizeof(unsigned long long) * nm)) ||
-      (rc = dalloc(ctx, &ctx->d_status, sizeof(unsigned))))
+      (rc = dalloc(ctx, &ctx->d_status, sizeof(unsigned))) ||
+      (rc = dalloc(ctx, &ctx->d_mstatus, sizeof(unsigned) * nm)))
     return cuda_err(ctx, rc);
+  cudaMemset(ctx->d_mstatus, 0, sizeof(unsigned) * nm);
   cudaMemset(ctx->d_dt, 0, sizeof(double) * nm);
   if ((rc = launch_reset_min(ctx->stream, ctx->d_dmin, ctx->nmem))) return cuda_err(ctx, rc);
   ctx->nred = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (ne + 255) / 256));
@@ -528,9 +569,16 @@ static int build_device(swe_ctx* ctx) {
     return cuda_err(ctx, rc);
   cudaMemset(ctx->d_t, 0, sizeof(double) * nm);
   cudaMemset(ctx->d_status, 0, sizeof(unsigned));
+  ctx->dm.mstatus = ctx->d_mstatus;
   if ((rc = dalloc(ctx, &ctx->d_work, sizeof(unsigned) * 4))) return cuda_err(ctx, rc);
   cudaMemset(ctx->d_work, 0, sizeof(unsigned) * 4);
   cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_err(ctx, cuda_fail(e, "build_device", __FILE__, __LINE__));
+  // the order-dependent part
+  CU(cudaMemcpy(ctx->d_newp, ctx->p_user.data(), (size_t)ne, cudaMemcpyHostToDevice));
+  ctx->packed_n = -1;
+  CK(regroup(ctx, false));
+  e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_err(ctx, cuda_fail(e, "build_device", __FILE__, __LINE__));
   return 0;
 }
@@ -734,6 +782,8 @@ static int state_in(swe_ctx* ctx, const double* c, int s, bool packed = false) {
   }
   CK(launch_from_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, packed ? ctx->d_off : nullptr, ctx->corr32, src,
                       ctx->st[s]));
+  if (s == 0)  // a new state: the members' status starts afresh
+    CU(cudaMemsetAsync(ctx->d_mstatus, 0, sizeof(unsigned) * (size_t)ctx->nmem, ctx->stream));
   return 0;
 }
 
@@ -939,10 +989,12 @@ int swe_set_orders(swe_ctx* ctx, const int8_t* p) {
   if (!ctx || !ctx->have_mesh || !p) return fail(ctx, SWE_EINVAL, "swe_set_orders: no mesh or NULL");
   for (int64_t e = 0; e < ctx->ne; ++e)
     if (p[e] < 0 || p[e] > 4) return fail(ctx, SWE_EINVAL, "order of element %lld is %d, not in 0..4", (long long)e, (int)p[e]);
-  int rc = mark_dirty_keep_state(ctx);
-  if (rc) return rc;
   ctx->p_user.assign(p, p + ctx->ne);
-  return 0;
+  if (ctx->dirty) return 0;  // the next build groups the elements
+  // a built context regroups on the device and carries the state over
+  LaunchScope ls(ctx);
+  CU(cudaMemcpyAsync(ctx->d_newp, p, (size_t)ctx->ne, cudaMemcpyHostToDevice, ctx->stream));
+  return regroup(ctx, true);
 }
 
 int swe_set_state(swe_ctx* ctx, const double* c, double t) {
@@ -1171,6 +1223,7 @@ int swe_set_state_packed_async(swe_ctx* ctx, const double* c, double t) {
     CK(launch_from_user(ctx->stream, ctx->dm, ctx->G, ctx->d_perm, ctx->d_off, ctx->corr32, src, ctx->st[0]));
   }
   CK(launch_fill(ctx->stream, ctx->d_t, t, ctx->nmem));
+  CU(cudaMemsetAsync(ctx->d_mstatus, 0, sizeof(unsigned) * (size_t)ctx->nmem, ctx->stream));
   return 0;
 }
 
@@ -1230,7 +1283,9 @@ int swe_adapt(swe_ctx* ctx, double theta_up, double theta_down, int p_min, int p
   if (n_changed) *n_changed = changed;
   if (orders_out) std::memcpy(orders_out, np.data(), (size_t)ctx->ne);
   if (changed == 0) return 0;
-  return swe_set_orders(ctx, np.data());
+  // the new orders are in d_newp already: regroup on the device
+  ctx->p_user.swap(np);
+  return regroup(ctx, true);
 }
 
 int swe_run_adaptive(swe_ctx* ctx, int64_t nsteps, int64_t every, double dt_fixed, double theta_up,
@@ -1282,6 +1337,18 @@ int swe_get_member_times(swe_ctx* ctx, double* t_out, double* dt_out) {
   CK(ensure_built(ctx));
   CU(cudaMemcpyAsync(t_out, ctx->d_t, sizeof(double) * ctx->nmem, cudaMemcpyDeviceToHost, ctx->stream));
   if (dt_out) CU(cudaMemcpyAsync(dt_out, ctx->d_dt, sizeof(double) * ctx->nmem, cudaMemcpyDeviceToHost, ctx->stream));
+  CU(cudaStreamSynchronize(ctx->stream));
+  return 0;
+}
+
+int swe_member_status(swe_ctx* ctx, uint32_t* status_out) {
+  if (!ctx || !ctx->have_mesh || !status_out) return fail(ctx, SWE_EINVAL, "swe_member_status: no mesh or NULL");
+  CK(ensure_built(ctx));
+  LaunchScope ls(ctx);
+  // set by the steps' depth checks and by the state check of swe_run / swe_rk_step / swe_sync
+  CU(cudaMemcpyAsync(status_out, ctx->d_mstatus, sizeof(unsigned) * (size_t)ctx->nmem, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CU(cudaMemsetAsync(ctx->d_mstatus, 0, sizeof(unsigned) * (size_t)ctx->nmem, ctx->stream));
   CU(cudaStreamSynchronize(ctx->stream));
   return 0;
 }

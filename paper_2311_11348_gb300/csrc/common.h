@@ -121,6 +121,7 @@ struct DevMesh {
   const int32_t* mem;     // [ne] ensemble member of each element (all 0 for a single mesh)
   const int32_t* emem;    // [nedge] member of each edge
   int32_t nmem;
+  unsigned* mstatus;      // [nmem] status bits per member (ST_DEPTH, ST_NONFINITE), set beside the global word
 };
 
 // Correction edges grouped by pmax = max(p_L, p_R) in 2..4.

@@ -216,7 +216,10 @@ __global__ void __launch_bounds__(256) k_usolve_base(DevMesh m, int64_t n_end, P
     const double rs = m.geo[G_RS * ne + e];
     const double H0 = cb[0 * ne + e] + m.geo[G_HB0 * ne + e];
     const double U0 = cb[3 * ne + e], V0 = cb[6 * ne + e];
-    if (!(H0 * cPhi0 * rs > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
+    if (!(H0 * cPhi0 * rs > ph.h_min)) {
+      atomicOr(status, (unsigned)ST_DEPTH);
+      atomicOr(m.mstatus + m.mem[e], (unsigned)ST_DEPTH);
+    }
     double v[6];
     if (m.p[e] == 0) {
       const double r = 1.0 / (H0 * cT1[0][0][0] * rs);
@@ -634,7 +637,10 @@ __global__ void k_check(DevMesh m, Groups G, StateDev st, unsigned* status) {
     const TC* h = chp<TC>(st.ch[p]);
     for (int i = 0; i < 3 * (K - 3); ++i) bad |= !isfinite((double)h[i * n + l]);
   }
-  if (bad) atomicOr(status, (unsigned)ST_NONFINITE);
+  if (bad) {
+    atomicOr(status, (unsigned)ST_NONFINITE);
+    atomicOr(m.mstatus + m.mem[e], (unsigned)ST_NONFINITE);
+  }
 }
 
 int launch_check_state(cudaStream_t s, const DevMesh& m, const Groups& G, int corr_fp32, StateDev st,

@@ -248,7 +248,10 @@ __global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int6
     H[2] += geo[G_HB2 * ne + e];
     // depth check on the FP64 mean (base modes are FP64 in every mode)
     const double H0d = c.cb[e] + m.geo[G_HB0 * ne + e];
-    if (!(H0d * m.geo[G_RS * ne + e] * 1.4142135623730951 > ph.h_min)) atomicOr(status, (unsigned)ST_DEPTH);
+    if (!(H0d * m.geo[G_RS * ne + e] * 1.4142135623730951 > ph.h_min)) {
+      atomicOr(status, (unsigned)ST_DEPTH);
+      atomicOr(m.mstatus + m.mem[e], (unsigned)ST_DEPTH);
+    }
     const T sv = geo[G_S * ne + e];
     T A[NP];
     sfor<0, K>([&](auto j) {

@@ -36,6 +36,53 @@ struct EdgeFlux {
                      // edge projected onto the higher test modes (q >= 3) of its left (0) and right (1) element
 };
 
+// The mesh in the caller's element order, independent of the orders: what
+// the device regrouping (k_regroup.cu) builds the internal arrays from.
+// Edges are fixed: left element = the lower caller index of the two,
+// interior edges first; eedge_u[k][u] = (edge << 1) | side of caller element
+// u's local edge k (side 1: u is the edge's right element).
+struct MeshStatic {
+  int64_t ne, nedge;
+  const double* geo_u;     // [NGEO][ne]
+  const double* etb_u;     // [ne][12]
+  const int32_t* eedge_u;  // [3][ne]
+  const int32_t* eLu;      // [nedge] caller index of the left element
+  const int32_t* eRu;      // [nedge] caller index of the right element or -1
+  const int32_t* mem_u;    // [ne] ensemble member
+};
+// what the regrouping writes (every pointer a device array of the context)
+struct DevMeshOut {
+  int32_t* perm;   // [ne] internal -> caller
+  int32_t* inv;    // [ne] caller -> internal
+  int8_t* p;       // [ne] orders, internal
+  double* geo;     // [NGEO][ne] internal
+  float* geo32;    // [NGEO][ne]
+  double* etb;     // [ne][12]
+  int32_t* mem;    // [ne]
+  int32_t* eedge;  // [3][ne]
+  int32_t* eL;     // [nedge] internal index of the left element
+  int32_t* eR;     // [nedge] internal index of the right element or -1
+  int32_t* slot;   // [nedge] (pmax << 28) | position in the correction group, or -1
+  int32_t* lists;  // [3][nedge] correction edge ids per pmax = 2, 3, 4
+  int64_t* off;    // [ne] packed caller layout offsets (caller order)
+};
+// scratch of the partitions (sizes from regroup_blocks of ne and nedge)
+struct RegroupScratch {
+  int32_t* ecnt;  // [be][5]
+  int64_t* eoff;  // [be][5]
+  int32_t* gcnt;  // [bg][3]
+  int64_t* goff;  // [bg][3]
+  int64_t* psum;  // [be]
+  int64_t* poff;  // [be + 1]
+  int64_t* info;  // [16]: order group starts [0..5], correction group starts [6..9], packed size [10]
+};
+int64_t regroup_blocks(int64_t n);
+// the internal arrays for the orders p_user (device, caller order); the
+// group sizes land in W.info (device), for the host to read
+int launch_regroup(cudaStream_t s, const MeshStatic& S, const int8_t* p_user, DevMeshOut D, RegroupScratch W);
+// ecs of every element of order >= 2 from the regrouped eedge and slot
+int launch_ecs(cudaStream_t s, int64_t ne, int64_t g2, const int32_t* eedge, const int32_t* slot, uint32_t* ecs);
+
 // every kernel launch of the library is counted (for launch accounting)
 void count_launch(int n = 1);
 

@@ -71,6 +71,10 @@ class Ensemble:
     def times(self):
         return self.solver.member_times()
 
+    def member_status(self):
+        """per member: the status bits its elements set since the last call (see swe_member_status)"""
+        return self.solver.member_status()
+
     def run(self, nsteps, dt_fixed=0.0):
         self.solver.run(nsteps, dt_fixed)
 

@@ -212,19 +212,28 @@ def ensemble_members(count: int = 64, lo: float = 8e3, hi: float = 6e5, seed: in
 
 
 def serving_requests(rate: float, duration: float, lo: float = 5e3, hi: float = 2e6, steps_lo: int = 100,
-                     steps_hi: int = 2000, seed: int = 7):
+                     steps_hi: int = 2000, seed: int = 7, pool: int = 0):
     """Poisson arrivals at `rate` per second over `duration` seconds; each
     request an ensemble-style member of log-uniform [lo, hi] triangles with a
     step count uniform in [steps_lo, steps_hi].  Returns a list of
-    (arrival offset in s, member dict, steps)."""
+    (arrival offset in s, member dict, steps).  pool > 0: the members are
+    drawn (uniformly, seeded) from `pool` members generated once with
+    log-uniform sizes, so that thousands of requests need no thousands of
+    mesh generations; the requests still run as independent simulations."""
     rng = np.random.default_rng(seed)
+    members = []
+    if pool > 0:
+        prng = np.random.default_rng(seed + 1)
+        sizes = np.exp(prng.uniform(math.log(lo), math.log(hi), size=pool))
+        members = [_member(T, 7000 + 10 * k) for k, T in enumerate(sizes)]
     out = []
     t = rng.exponential(1.0 / rate)
     k = 0
     while t < duration:
         T = math.exp(rng.uniform(math.log(lo), math.log(hi)))
         steps = int(rng.integers(steps_lo, steps_hi + 1))
-        out.append((t, _member(T, 7000 + 10 * k), steps))
+        m = members[int(rng.integers(pool))] if pool > 0 else _member(T, 7000 + 10 * k)
+        out.append((t, m, steps))
         t += rng.exponential(1.0 / rate)
         k += 1
     return out

@@ -37,11 +37,13 @@ def device_bytes(meshes, precision):
     """Device bytes a context holds after swe_set_mesh + swe_set_orders (+
     swe_set_members) of the disjoint union of `meshes`: the same allocations
     the library makes (swe_memory_bytes reports them), counted on the host so
-    that admission needs no context.  Per element: FP64 geometry and its FP32
-    copy, topology, three RK states, velocity, the user-layout staging; per
-    edge: geometry, base fluxes and the projections of its correction flux
-    onto both sides' higher modes; the correction arrays scale with K - 3 at the correction type's
-    width (4 bytes in the mixed mode, 8 in FP64)."""
+    that admission needs no context.  Per element: the mesh in caller order
+    and regrouped (geometry and its FP32 copy, topology), three RK states,
+    velocity, the user-layout staging; per edge: geometry, base fluxes and
+    the projections of its correction flux onto both sides' higher modes; the
+    correction arrays scale with K - 3 at the correction type's width (4 bytes
+    in the mixed mode, 8 in FP64).  After an order change the library may hold
+    more (its order-group buffers grow with a quarter to spare)."""
     corr32 = precision in (swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32)
     ts = 4 if corr32 else 8
     ne = nE = 0
@@ -67,20 +69,25 @@ def device_bytes(meshes, precision):
             ncl[q] += int((pm == q).sum())
     nm = max(len(meshes), 1)
     nrc = n[2] + n[3] + n[4]
-    allocs = [NGEO * 8 * ne, ne, 12 * ne, 4 * nE, 4 * nE, 4 * nE, NEGEO * 8 * nE, 4 * nE, 4 * ne,  # geo .. perm
-              NGEO * 4 * ne, NEGEO * 4 * nE, 96 * ne, 4 * ne, 4 * nE,                         # FP32 copies, basis, members
-              12 * max(nrc, 1)] + [4 * ncl[q] for q in (2, 3, 4)]                             # correction edges
-    for _ in range(3):                                                                        # RK states
-        allocs += [72 * ne] + ([36 * ne] if corr32 else []) + [ts * 3 * (KP[q] - 3) * n[q] for q in (2, 3, 4)]
-    allocs += [48 * ne] + ([24 * ne] if corr32 else [])
-    for q in (2, 3, 4):                                                                       # velocity, trace records
+    be, bg = -(-ne // 256), -(-nE // 256)
+    allocs = [NGEO * 8 * ne, 96 * ne, 12 * ne, 4 * nE, 4 * nE, 4 * ne,                    # mesh in caller order
+              4 * nE, NEGEO * 8 * nE, NEGEO * 4 * nE, 4 * nE,                                # edge info, geometry, members
+              4 * ne, 4 * ne, ne, NGEO * 8 * ne, NGEO * 4 * ne, 96 * ne, 4 * ne, 12 * ne,    # regrouped elements
+              4 * nE, 4 * nE, 4 * nE, 12 * nE, 8 * ne,                                       # regrouped edges, offsets
+              20 * be, 40 * be, 12 * bg, 24 * bg, 8 * be, 8 * (be + 1), 128]                # partition scratch
+    allocs += [72 * ne] * 3 + ([36 * ne] * 3 if corr32 else [])                             # base RK states
+    allocs += [48 * ne] + ([24 * ne] if corr32 else [])                                     # base velocity
+    allocs += [48 * nE, 48 * nE, 8 * 3 * KMAX * ne, 8 * 3 * KMAX * ne, ne,                  # fluxes, staging, orders
+               8 * nm, 8 * nm, 8 * nm, 4, 4 * nm,                                           # members, status words
+               8 * min(1024, max(1, (ne + 255) // 256)), 16, 16]                           # sums, tickets
+    for q in (2, 3, 4):                                                                     # order groups
+        allocs += [ts * 3 * (KP[q] - 3) * n[q]] * 3
         allocs += [ts * 2 * (KP[q] - 3) * n[q], ts * 4 * KP[q] * n[q], ts * KP[q] * n[q]]
-    allocs += [48 * nE, 48 * nE] + [ts * 2 * 3 * (KP[q] - 3) * ncl[q] for q in (2, 3, 4)]  # fluxes, projections
+        allocs += [ts * 2 * 3 * (KP[q] - 3) * ncl[q]]
     allocs += [32 * max(nrc, 1)]
     if precision == swedg.PREC_MIXED_TF32:
-        allocs += [32 * 4 * max(nrc, 1)]                                                      # tensor-core volume terms
-    allocs += [8 * 3 * KMAX * ne, 8 * 3 * KMAX * ne, ne, 8 * ne, 8 * nm, 8 * nm, 8 * nm, 4,  # staging, packed offsets
-               8 * min(1024, max(1, (ne + 255) // 256)), 16, 16]                           # ..., base tickets
+        allocs += [32 * 4 * max(nrc, 1)]                                                    # tensor-core volume terms
+    allocs += [12 * max(nrc, 1)]                                                            # correction edge slots
     b = sum(a if a > 0 else 16 for a in allocs)  # the library allocates 16 bytes for an empty array
     return b
 
@@ -100,21 +107,6 @@ class Request:
     done_steps: int = 0
     nbytes: int = None
     error: str = None   # set when the request was evicted after a failed step
-
-
-def member_state_ok(mesh, c, h_min):
-    """finite coefficients and every element mean depth above h_min (the
-    conditions the library's status word checks), for one request's state"""
-    c = np.asarray(c)
-    if not np.isfinite(c).all():
-        return False
-    xy = np.asarray(mesh["xy"], np.float64)
-    tri = np.asarray(mesh["tri"], np.int64)
-    a, b, d = xy[tri[:, 0]], xy[tri[:, 1]], xy[tri[:, 2]]
-    area = 0.5 * np.abs((b[:, 0] - a[:, 0]) * (d[:, 1] - a[:, 1]) - (d[:, 0] - a[:, 0]) * (b[:, 1] - a[:, 1]))
-    hb = np.asarray(mesh["hv"], np.float64)[tri].mean(axis=1)
-    H = c[0, 0] / np.sqrt(area) + hb
-    return bool((H > h_min).all())
 
 
 def footprint(req: Request, precision: int) -> int:
@@ -214,11 +206,12 @@ class Server:
     def _evict_failed(self, c, err):
         """A cohort's run reported an error (a non-finite state or a depth at or
         below h_min in some member).  The members evolve independently, so
-        the ones whose state is still valid keep the chunk they just ran; the
-        others are evicted with the error, without touching other requests.
-        Without a member to blame, the whole cohort is evicted."""
-        states = c.ens.states(device=False)
-        bad = [i for i, r in enumerate(c.reqs) if c.live[i] and not member_state_ok(r.mesh, states[i], self.h_min)]
+        the ones the library's per-member status words do not flag keep the
+        chunk they just ran; the flagged ones are evicted with the error,
+        without touching other requests.  Without a member to blame (a device
+        wait that timed out), the whole cohort is evicted."""
+        status = c.ens.member_status()
+        bad = [i for i in range(len(c.reqs)) if c.live[i] and status[i] != 0]
         if not bad:
             bad = [i for i in range(len(c.reqs)) if c.live[i]]
         now = self.clock()

@@ -17,6 +17,8 @@ KMAX = 15
 PREC_FP64 = 0
 PREC_MIXED_FP32 = 1
 PREC_MIXED_TF32 = 2
+STATUS_DEPTH = 1
+STATUS_NONFINITE = 2
 
 _ERRORS = {-1: "invalid argument", -2: "bad mesh", -3: "depth <= h_min", -4: "non-finite state",
            -5: "CUDA error", -6: "device wait timeout"}
@@ -46,7 +48,7 @@ SYMBOLS = ("swe_default_params", "swe_create", "swe_destroy", "swe_last_error", 
            "swe_memory_bytes", "swe_tc_operand_image", "swe_get_launch_shape", "swe_set_launch_shape",
            "swe_autotune", "swe_selftest_wait", "swe_packed_size", "swe_set_state_packed",
            "swe_get_state_packed", "swe_set_state_packed_async", "swe_run_async", "swe_get_state_packed_async",
-           "swe_sync")
+           "swe_sync", "swe_member_status")
 
 
 def library_path() -> str:
@@ -100,6 +102,7 @@ def load():
     lib.swe_set_member_times.argtypes = [P, P]
     lib.swe_get_member_times.argtypes = [P, P, P]
     lib.swe_memory_bytes.argtypes = [P, C.POINTER(i64)]
+    lib.swe_member_status.argtypes = [P, P]
     for s in SYMBOLS:
         if s not in ("swe_destroy", "swe_default_params", "swe_last_error"):
             getattr(lib, s).restype = C.c_int
@@ -391,6 +394,13 @@ class Solver:
     def selftest_wait(self, spins=1000):
         """run the bounded-wait self-test (raises SweError SWE_ETIMEOUT by design)"""
         self._ck(self._lib.swe_selftest_wait(self.h, C.c_int64(int(spins))))
+
+    def member_status(self):
+        """per ensemble member: STATUS_DEPTH | STATUS_NONFINITE bits set since the last call (cleared)"""
+        n = getattr(self, "nmembers", 1)
+        out = np.zeros(n, np.uint32)
+        self._ck(self._lib.swe_member_status(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def memory_bytes(self):
         b = C.c_int64(0)

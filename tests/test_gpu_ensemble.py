@@ -132,3 +132,25 @@ def test_serving_evicts_a_failing_request_and_finishes_the_others():
         assert done[i].t_final == t
         assert np.array_equal(done[i].result, ref)
         check_against_oracle(done[i].result, done[i].t_final, m, c, 20, **kw)
+
+
+def test_member_status_names_the_failing_member():
+    """swe_member_status: after a run that reports a depth failure, only the
+    member whose state went below h_min carries the status bit; reading clears
+    the bits, and a new state upload starts them afresh"""
+    kw = dict(g=9.81, cfl=0.2, rk_order=3, precision=swedg.PREC_MIXED_FP32)
+    specs = [member(6, 1e3, 31, 1, 2), member(7, 2e3, 32, 1, 3), member(5, 1e3, 33, 1, 2)]
+    ens = ensemble.Ensemble([m for m, _ in specs], **kw)
+    states = [c.copy() for _, c in specs]
+    states[1][0, 0] = -500.0 * np.sqrt(0.5 * (2e3 / 7) ** 2)  # mean elevation -500 m on a 30..300 m sea
+    ens.set_states(states)
+    with pytest.raises(swedg.SweError) as ei:
+        ens.run(2)
+    assert ei.value.code in (-3, -4)  # the negative depth also turns the state non-finite
+    st = ens.member_status()
+    assert st[1] & swedg.STATUS_DEPTH and st[0] == 0 and st[2] == 0
+    assert not np.any(ens.member_status())  # read and cleared
+    ens.set_states([c for _, c in specs])
+    ens.run(2)
+    assert not np.any(ens.member_status())
+    ens.close()

@@ -455,3 +455,36 @@ def test_async_packed_pipeline_equals_the_synchronous_calls(precision):
         s.sync()
     assert ei.value.code in (-3, -4)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [swedg.PREC_FP64, swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32])
+def test_order_change_on_the_device_equals_a_fresh_build(precision):
+    """swe_set_orders on a built context regroups the elements on the device
+    (stable partition by order, correction edges, packed offsets) and carries
+    the state over hierarchically: the steps that follow are bitwise those of
+    a context built afresh with the new orders from the truncated state, and
+    the footprint is at least the fresh build's"""
+    from paper_2311_11348_gb300 import serve
+    w = mixed_workload(n=14, seed=8, pmin=0, pmax=4)
+    m, P, s = make_pair(w, precision=precision)
+    c = m.project_state(w["ic"])
+    s.set_state(c, 0.0)
+    s.run(5)
+    c5, t5 = s.get_state()
+    new = np.random.default_rng(9).integers(0, 5, size=len(w["tri"])).astype(np.int8)
+    s.set_orders(new)
+    got_c, _ = s.get_state()
+    K = np.array([1, 3, 6, 10, 15])[new]
+    assert np.array_equal(got_c, np.where(np.arange(15)[None, :, None] < K[None, None, :], c5, 0.0))
+    s.run(5)
+    got, tg = s.get_state()
+    w2 = dict(w, orders=new)
+    _, _, f = make_pair(w2, precision=precision)
+    f.set_state(c5, t5)
+    f.run(5)
+    ref, tr = f.get_state()
+    assert tg == tr and np.array_equal(got, ref)
+    assert s.memory_bytes() >= f.memory_bytes() == serve.device_bytes([w2], precision)
+    assert s.packed_size() == f.packed_size()
+    s.close()
+    f.close()

@@ -116,10 +116,15 @@ class PoisonUnion(FakeUnion):
     def run(self, n, dt_fixed=0.0):
         super().run(n, dt_fixed)
         bad = [i for i, m in enumerate(self.meshes) if m.get("poison")]
+        self.status = np.zeros(len(self.meshes), np.uint32)
         for i in bad:
             self.c[i][:] = np.nan
+            self.status[i] = swedg.STATUS_NONFINITE
         if bad:
             raise swedg.SweError(-4, "non-finite value in the state")
+
+    def member_status(self):
+        return self.status
 
 
 def test_a_failing_request_is_evicted_without_the_others(monkeypatch):

@@ -1,9 +1,10 @@
 """Host-side checks of the tensor-core volume contraction (precision mode
 SWE_PREC_MIXED_TF32), no GPU: the library's constant operand images decode,
 by the layout the header documents, to the oracle's G tensors of Eq. (13),
-split into two TF32 parts; and the GEMM decomposition the
-kernel uses (symmetrised coefficient products against those images)
-reproduces the direct volume contraction of the momentum rows."""
+split into two TF32 parts; and the two-stage decomposition the kernel uses
+(GEMMs of per-element velocity and pressure rows against those images, then
+sums over the coefficient rows) reproduces the direct volume contraction of
+the momentum rows."""
 import numpy as np
 import pytest
 
@@ -19,39 +20,28 @@ def lib():
     return swedg.load()
 
 
-def pairs(K):
-    return [(i, j) for j in range(K) for i in range(j + 1)]  # pair index j(j+1)/2 + i
+def at(r, c):  # K-major, 128-byte swizzle: 16-byte unit c/4 of row r at unit (c/4) ^ (r%8)
+    return (r // 8) * 256 + (r % 8) * 32 + (((c // 4) ^ (r % 8)) * 4) + c % 4
 
 
 def decode(K, img):
-    """the two parts of the image as Gx, Gy [part][16][K][16] (from the U/V
-    operand) and Gp [part][2][16][K][16] (from the pressure operand)"""
-    C = (K + 1) // 2
-    bpart = C * (2 * 16 * 32 + 32 * 32)
-    assert len(img) == 2 * bpart
-
-    def at(r, c):  # K-major, 128-byte swizzle: 16-byte unit c/4 of row r at unit (c/4) ^ (r%8)
-        return (r // 8) * 256 + (r % 8) * 32 + (((c // 4) ^ (r % 8)) * 4) + c % 4
-
-    Gx = np.zeros((2, 16, K, 16), np.float32)
-    Gy = np.zeros((2, 16, K, 16), np.float32)
-    Gp = np.zeros((2, 2, 16, K, 16), np.float32)
+    """the two parts of the image as B[part][k][q][i][j]: row 16 i + q, column
+    k K + j of a [16 K][32] operand per part; every other entry zero"""
+    nb = 16 * K
+    assert len(img) == 2 * nb * 32
+    B = np.zeros((2, 2, 16, K, K), np.float32)
+    seen = np.zeros(len(img), bool)
     for part in range(2):
-        base = part * bpart
+        base = part * nb * 32
         for i in range(K):
-            c, col0 = i // 2, 16 * (i % 2)
             for q in range(16):
-                for j in range(16):
-                    Gx[part, q, i, j] = img[base + c * 512 + at(q, col0 + j)]
-                    Gy[part, q, i, j] = img[base + (C + c) * 512 + at(q, col0 + j)]
-                    for k in range(2):
-                        Gp[part, k, q, i, j] = img[base + 2 * C * 512 + c * 1024 + at(16 * k + q, col0 + j)]
-        if K % 2:  # the padding row of the last chunk is zero
-            c = K // 2
-            for q in range(16):
-                for j in range(16):
-                    assert img[base + c * 512 + at(q, 16 + j)] == 0
-    return Gx, Gy, Gp
+                for k in range(2):
+                    for j in range(K):
+                        o = base + at(16 * i + q, k * K + j)
+                        B[part, k, q, i, j] = img[o]
+                        seen[o] = True
+    assert not np.any(img[~seen])  # the padding (q >= K, columns >= 2 K) is zero
+    return B
 
 
 def used(q, i, j):
@@ -68,28 +58,28 @@ def used(q, i, j):
 
 @pytest.mark.parametrize("K", [6, 10, 15])
 def test_operand_images_hold_G_split_into_tf32_head_and_tail(lib, K):
-    Gx, Gy, Gp = decode(K, swedg.tc_operand_image(K))
+    B = decode(K, swedg.tc_operand_image(K))
     G = O.tensors()["G"]
-    for a in (Gx, Gy, Gp):  # every part is a TF32 value: no bits below the 10-bit mantissa
-        assert np.all(a.view(np.uint32) & 0x1FFF == 0)
-    S = [Gx.astype(np.float64).sum(0), Gy.astype(np.float64).sum(0)]
-    Pm = Gp.astype(np.float64).sum(0)
+    assert np.all(B.view(np.uint32) & 0x1FFF == 0)  # every part is a TF32 value: no bits below the 10-bit mantissa
+    S = B.astype(np.float64).sum(0)
     floor = 1e-14 * np.abs(G).max()  # the library's tables agree with the oracle's to this
     for k in range(2):
-        assert np.array_equal(Pm[k], S[k])  # both operands hold the same values
         for q in range(16):
             for i in range(K):
-                for j in range(16):
-                    want = G[k, q, i, j] if (q < K and j < K and used(q, i, j)) else 0.0
+                for j in range(K):
+                    want = G[k, q, i, j] if (q < K and used(q, i, j)) else 0.0
                     tol = 2.0 ** -21 * abs(want) + floor  # the parts sum to G within 2^-22 |G|
-                    assert abs(S[k][q, i, j] - want) <= tol, (k, q, i, j)
+                    assert abs(S[k, q, i, j] - want) <= tol, (k, q, i, j)
                     if want:  # part 0 is G rounded to 10 mantissa bits
-                        part0 = (Gx if k == 0 else Gy)[0, q, i, j]
-                        assert abs(part0 - want) <= 2.0 ** -11 * abs(want) + floor
+                        assert abs(B[0, k, q, i, j] - want) <= 2.0 ** -11 * abs(want) + floor
 
 
 @pytest.mark.parametrize("K", [6, 10, 15])
 def test_gemm_decomposition_reproduces_the_volume_contraction(lib, K):
+    """the kernel's two stages: GEMMs of per-element rows (2 K values: the
+    contravariant velocities, or g J^-1 times the pressure products without
+    h_b's mean) against the image, giving W, ZU, ZV [i][q]; then the sums over
+    i with the element's U, V, xi, and the mean-depth part added apart"""
     rng = np.random.default_rng(K)
     n = 7
     xi, U, V, u, v = (rng.standard_normal((n, K)) for _ in range(5))
@@ -97,9 +87,8 @@ def test_gemm_decomposition_reproduces_the_volume_contraction(lib, K):
     J = rng.standard_normal((n, 4))
     rs = rng.uniform(0.5, 2.0, n)
     g = 9.81
-    # the G values the images hold (sum of the parts)
-    Gx, Gy, Gp = decode(K, swedg.tc_operand_image(K))
-    Gm = np.stack([Gx.astype(np.float64).sum(0)[:K, :, :K], Gy.astype(np.float64).sum(0)[:K, :, :K]])
+    B = decode(K, swedg.tc_operand_image(K)).astype(np.float64).sum(0)  # [k][q][i][j], q < 16
+    Gm = B[:, :K]
     mask = np.array([[[used(q, i, j) for j in range(K)] for i in range(K)] for q in range(K)])
     assert not np.any(Gm[:, ~mask])
     # direct contraction (non-base triples only), physical gradients through J^-1
@@ -113,27 +102,24 @@ def test_gemm_decomposition_reproduces_the_volume_contraction(lib, K):
                         + g * (J[:, [0]] * Px + J[:, [2]] * Py))
     rV = rs[:, None] * (np.einsum("qij,ei,ej->eq", Gm[0], V, uc) + np.einsum("qij,ei,ej->eq", Gm[1], V, vc)
                         + g * (J[:, [1]] * Px + J[:, [3]] * Py))
-    # the kernel's GEMMs: rows i x 16 columns j of coefficient products against the images
-    def rows(a, b):
-        bb = np.zeros((n, 16))
-        bb[:, :K] = b
-        return (a[:, :, None] * bb[:, None, :]).reshape(n, K * 16)
-
-    BSx = Gx.astype(np.float64).sum(0)[:K].reshape(K, K * 16)
-    BSy = Gy.astype(np.float64).sum(0)[:K].reshape(K, K * 16)
-    BPx = Gp[:, 0].astype(np.float64).sum(0)[:K].reshape(K, K * 16)
-    BPy = Gp[:, 1].astype(np.float64).sum(0)[:K].reshape(K, K * 16)
-    DU = rows(U, uc) @ BSx.T + rows(U, vc) @ BSy.T
-    DV = rows(V, uc) @ BSx.T + rows(V, vc) @ BSy.T
-    # h_b's mean mode stays out of the pressure GEMM and is added as hb0 sum_i xi_i G_k[q][i][0]
-    pp_tc = pp.copy()
-    pp_tc[:, 0] -= hb[:, 0]
-    DPx = rows(xi, pp_tc) @ BPx.T + hb[:, [0]] * np.einsum("qi,ei->eq", Gm[0, :, :, 0], xi)
-    DPy = rows(xi, pp_tc) @ BPy.T + hb[:, [0]] * np.einsum("qi,ei->eq", Gm[1, :, :, 0], xi)
-    DP = np.zeros((n, 32))
-    DP[:, :K], DP[:, 16:16 + K] = DPx, DPy
-    gU = rs[:, None] * (DU + g * (J[:, [0]] * DP[:, :K] + J[:, [2]] * DP[:, 16:16 + K]))
-    gV = rs[:, None] * (DV + g * (J[:, [1]] * DP[:, :K] + J[:, [3]] * DP[:, 16:16 + K]))
+    # the kernel: the operand B[(i, q)][(k, j)] and three A operands of 2 K columns
+    Bop = np.zeros((16 * K, 2 * K))
+    for i in range(K):
+        for q in range(16):
+            Bop[16 * i + q, :K] = B[0, q, i, :]
+            Bop[16 * i + q, K:] = B[1, q, i, :]
+    pq = pp.copy()
+    pq[:, 0] -= hb[:, 0]  # h_b's mean mode stays out of the GEMM
+    Aw = np.hstack([uc, vc])
+    Au = g * np.hstack([J[:, [0]] * pq, J[:, [2]] * pq])
+    Av = g * np.hstack([J[:, [1]] * pq, J[:, [3]] * pq])
+    W, ZU, ZV = ((A @ Bop.T).reshape(n, K, 16) for A in (Aw, Au, Av))
+    ex = np.einsum("qi,ei->eq", Gm[0, :, :, 0], xi)
+    ey = np.einsum("qi,ei->eq", Gm[1, :, :, 0], xi)
+    gU = np.einsum("ei,eiq->eq", U, W) + np.einsum("ei,eiq->eq", xi, ZU)
+    gV = np.einsum("ei,eiq->eq", V, W) + np.einsum("ei,eiq->eq", xi, ZV)
+    gU = rs[:, None] * (gU[:, :K] + g * hb[:, [0]] * (J[:, [0]] * ex + J[:, [2]] * ey))
+    gV = rs[:, None] * (gV[:, :K] + g * hb[:, [0]] * (J[:, [1]] * ex + J[:, [3]] * ey))
     tol = 1e-9 * max(np.abs(rU).max(), np.abs(rV).max())
     assert np.abs(gU - rU).max() <= tol
     assert np.abs(gV - rV).max() <= tol
