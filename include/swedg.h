@@ -263,24 +263,22 @@ int swe_reference_tensors(double* D, double* G, double* T);
  * npts in 1..8; host pointers.  Needs no device. */
 int swe_edge_table(int npts, double* s, double* w, double* B);
 
-/* Shared-memory image of the constant tensor-core operands of the
+/* Shared-memory image of the constant tensor-core operand of the
  * SWE_PREC_MIXED_TF32 volume contraction for K = 6, 10 or 15 modes (the paper
  * has no counterpart: it is the GB300 layout of the G_k tensors of Eq. 13).
- * The reduction runs over coefficient rows i < K of 16 columns j (zero for
- * j >= K), two rows per chunk of 32 columns; with C = ceil(K/2) chunks per
- * row set, each of the two parts of the image holds, one after another,
- *   C chunks [16][32] for d/dxhat:  row q, column 16 (i % 2) + j of chunk i / 2
- *                                   = G_x[q][i][j]
- *   C chunks [16][32] for d/dyhat:  the same with G_y
- *   C chunks [32][32]:              row 16k + q, same columns = G_k[q][i][j]
- * (zero for the base triples q, i, j < 3 and for structural zeros).  The two
- * parts are TF32 values (10 mantissa bits): part 0 = G rounded to the nearest
- * TF32 value (ties away from zero), part 1 = G - part 0 rounded the same way,
- * so their sum equals G to within 2^-22 |G|.  A chunk of R rows stores (row r,
- * column c) at float offset (r / 8) * 256 + (r % 8) * 32 + ((c / 4) ^ (r % 8)) * 4
- * + c % 4 (rows of 128 bytes, 16-byte units XOR-swizzled by the row index).
- * Returns the number of floats (out may be NULL to query it), or SWE_EINVAL
- * for another K or cap too small.  Host pointer; needs no device. */
+ * The contraction runs as GEMMs of per-element rows of 2 K values (the
+ * velocities, or the pressure products, for k = x^ then y^) against one
+ * operand B with 16 K rows and 32 columns:
+ *   B[16 i + q][k K + j] = G_k[q][i][j]
+ * (zero for q >= K, for columns >= 2 K, for the base triples q, i, j < 3 and
+ * for structural zeros).  The image holds two parts one after the other, each
+ * 16 K x 32 floats: part 0 = G rounded to the nearest TF32 value (10 mantissa
+ * bits, ties away from zero), part 1 = G - part 0 rounded the same way, so
+ * their sum equals G to within 2^-22 |G|.  (row r, column c) of a part is at
+ * float offset (r / 8) * 256 + (r % 8) * 32 + ((c / 4) ^ (r % 8)) * 4 + c % 4
+ * (rows of 128 bytes, 16-byte units XOR-swizzled by the row index).  Returns
+ * the number of floats (out may be NULL to query it), or SWE_EINVAL for
+ * another K or cap too small.  Host pointer; needs no device. */
 int64_t swe_tc_operand_image(int K, float* out, int64_t cap);
 
 /* Launch shapes (the paper has no counterpart: they tune the GPU kernels to

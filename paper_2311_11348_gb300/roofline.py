@@ -19,9 +19,11 @@ FP64 and mixed modes the velocity solve of a p >= 2 element also forms the
 volume terms of the degree-1 test modes (rc), and elem_corr covers the test
 modes of degree >= 2; in the tensor-core mode ("tf32") elem_corr covers every
 test mode and leaves the momentum volume terms of p >= 3 to vol_tc, whose
-count is the MMA work it issues: three TF32 passes (head x head, tail x head,
-head x tail) over the padded K x 16 product blocks.  The CFL bounds (DT per
-element, first stage of a step) are part of the usolve family.
+count is the MMA work it issues: three GEMMs (velocities, and the pressure
+products for each momentum equation) against the 16 K x 2 K operand of G,
+each in three TF32 passes (head x head, head x tail, tail x head) over the
+reduction padded to a multiple of 8.  The CFL bounds (DT per element, first
+stage of a step) are part of the usolve family.
 """
 from __future__ import annotations
 
@@ -117,10 +119,10 @@ def elem_corr_flops(K, tc=False, rc=True):
 
 
 def vol_tc_flops(K):
-    """TF32 MMA flops per element: three products (hh, ht, th), four K = 8 steps
-    per 32-column chunk, ceil(K/2) chunks for each of the five product blocks
-    (four with N = 16 test modes, one with N = 32)"""
-    return 3 * 4 * 2 * 8 * (4 * 16 + 32) * ((K + 1) // 2)
+    """TF32 MMA flops per element (row of the GEMMs): three GEMMs of N = 16 K
+    columns (rows i, test modes q padded to 16) over ceil(2K / 8) steps of 8,
+    each in three passes (hh, ht, th); 2 flops per multiply-add"""
+    return 3 * 3 * 2 * (16 * K) * 8 * ((2 * K + 7) // 8)
 
 
 def edge_corr_flops(KL, KR, pm):
