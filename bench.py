@@ -833,11 +833,14 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-# DRAM bytes (read + write) per launch of the base kernels on the default
-# ocean workload (256x256), from the full ncu capture summarised in
-# profiles/ocean_p123_kernels_ncu_full.md (cold cache; elem_base's is a first
-# stage's, which does not read the step's start state); None elsewhere
-MEASURED_TRAFFIC = {"edge_base": 41.230848e6 + 152.064e3, "elem_base": 62.508544e6 + 2397.184e3}
+# DRAM bytes (read + write) per launch of the base kernels on the 131,072-
+# triangle ocean workload (default launch shape), from one ncu capture of the
+# current kernels (cold cache): TRAFFIC_CAPTURE below, run after the same
+# command exited 0 without ncu.  None for other workloads and kernels.
+MEASURED_TRAFFIC = {"edge_base": 41.235968e6 + 0.143360e6, "elem_base": 62.641920e6 + 1.718272e6}
+TRAFFIC_CAPTURE = ("ncu --section SpeedOfLight --section MemoryWorkloadAnalysis --metrics "
+                   "dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:'k_edge_base|k_elem_base' "
+                   "-s 6 -c 2 python bench.py --steps 2 --warmup 3 --no-oracle --no-serving --no-adaptive --no-autotune")
 
 
 def roofline(w, r, dom, steps, pk, head):
@@ -868,8 +871,11 @@ def roofline(w, r, dom, steps, pk, head):
             if pipe == "fp64" else "FP32 pipe, 152 SMs x 256 flop/clk x 2.07 GHz (nominal; measured FFMA loop 74.6 "
             "TFLOP/s at 1.92 GHz)")
     traffic = MEASURED_TRAFFIC.get(dom) if len(w["orders"]) == 131072 and pipe == "fp64" else None
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel": dom, "pipe": pipe, "flops_per_step": f, "peak_source": note}
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": traffic, "kernel": dom, "pipe": pipe, "flops_per_step": f, "peak_source": note}
+    if traffic is not None:
+        out["traffic_source"] = TRAFFIC_CAPTURE
+    return out
 
 
 if __name__ == "__main__":

@@ -94,7 +94,7 @@ struct swe_ctx {
   RegroupScratch rw{};
   // capacities (bytes) of the buffers sized by the order groups
   size_t cap_ch[3][5] = {}, cap_uh[5] = {}, cap_tr[5] = {}, cap_trv[5] = {}, cap_pf[5] = {};
-  size_t cap_rc = 0, cap_vol = 0, cap_ecs = 0;
+  size_t cap_rc = 0, cap_vol = 0;
   // device
   std::vector<std::pair<void*, size_t>> allocs;
   DevMesh dm{};
@@ -334,14 +334,11 @@ static int alloc_group_buffers(swe_ctx* ctx) {
     if (!rc) rc = grow(&ctx->vel.uh[p], &ctx->cap_uh[p], ts * 2 * (K - 3) * n);
     if (!rc) rc = grow(&ctx->vel.tr[p], &ctx->cap_tr[p], ts * 4 * K * n);
     if (!rc) rc = grow(&ctx->vel.trv[p], &ctx->cap_trv[p], ts * K * n);
-    if (!rc) rc = grow(&ctx->fx.Pf[p], &ctx->cap_pf[p], ts * 2 * 3 * (K - 3) * (size_t)ctx->ce.n[p]);
+    if (!rc) rc = grow(&ctx->fx.Pf[p], &ctx->cap_pf[p], ts * 3 * 3 * (K - 3) * n);
   }
   const size_t nrc = (size_t)std::max<int64_t>(ctx->ne - ctx->G.start[2], 1);
   if (!rc) rc = grow(&ctx->rc, &ctx->cap_rc, sizeof(double) * 4 * nrc);
   if (!rc && ctx->tc) rc = grow(&ctx->vol, &ctx->cap_vol, sizeof(float) * 32 * nrc);
-  uint32_t* ecs = const_cast<uint32_t*>(ctx->ce.ecs);
-  if (!rc) rc = grow(&ecs, &ctx->cap_ecs, sizeof(uint32_t) * 3 * nrc);
-  ctx->ce.ecs = ecs;
   return rc ? cuda_err(ctx, rc) : 0;
 }
 
@@ -363,8 +360,6 @@ static int regroup(swe_ctx* ctx, bool keep_state) {
   for (int pm = 0; pm < 5; ++pm) ctx->ce.n[pm] = (pm >= 2 && ctx->nedge > 0) ? info[6 + pm - 1] - info[6 + pm - 2] : 0;
   ctx->packed_n = info[10];
   CK(alloc_group_buffers(ctx));
-  CK(launch_ecs(ctx->stream, ctx->ne, ctx->G.start[2], ctx->dout.eedge, ctx->dout.slot,
-                const_cast<uint32_t*>(ctx->ce.ecs)));
   // edges that no longer touch a p >= 2 element carry no correction flux
   CU(cudaMemsetAsync(ctx->fx.Fbc, 0, sizeof(double) * 6 * (size_t)std::max<int64_t>(ctx->nedge, 1), ctx->stream));
   if (keep_state)
@@ -394,7 +389,7 @@ static int build_device(swe_ctx* ctx) {
     ctx->fx.Pf[p] = nullptr;
     ctx->cap_uh[p] = ctx->cap_tr[p] = ctx->cap_trv[p] = ctx->cap_pf[p] = 0;
   }
-  ctx->rc = nullptr; ctx->vol = nullptr; ctx->cap_rc = ctx->cap_vol = ctx->cap_ecs = 0;
+  ctx->rc = nullptr; ctx->vol = nullptr; ctx->cap_rc = ctx->cap_vol = 0;
   std::memset(&ctx->ce, 0, sizeof ctx->ce);
   const int64_t ne = ctx->ne;
   const RefTables& R = tables();

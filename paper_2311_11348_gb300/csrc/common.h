@@ -129,7 +129,6 @@ struct CorrEdges {
   int64_t n[5];           // per pmax
   const int32_t* list[5]; // edge ids
   const int32_t* slot;    // [nedge]: (pmax << 28) | slot within group, or -1
-  const uint32_t* ecs;    // [3][elements with p >= 2]: (pmax << 28) | (side << 27) | slot of each local edge
 };
 
 __device__ __forceinline__ double stage_dt(const Stage& st, int mem) { return st.dt ? st.dt[mem] : st.dt_host; }

@@ -423,8 +423,9 @@ __device__ __forceinline__ void side_traces(const DevMesh& m, const Groups& G, S
 template <int PM>
 __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __restrict__ list, int64_t nl, Groups G,
                                                    Phys ph, Stage stg, StateDev c, VelDev u,
-                                                   double* __restrict__ Fbc, T* __restrict__ Pf) {
-  constexpr int N = npts_for(PM), GI = PM - 2, KQ = Kof(PM) - 3;
+                                                   double* __restrict__ Fbc, EdgeFlux fx) {
+  constexpr int N = npts_for(PM), GI = PM - 2;
+  void* const* Pf = fx.Pf;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= nl) return;
   const int64_t ed = list[idx], nE = m.nedge;
@@ -500,10 +501,16 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
     Ffull[2][q] = wgt * (Fb2 + Fh2);
   });
   // the full flux projected onto the higher test modes of each side once here,
-  //   P[side][f][q] = -+ (1/s) sum_g F_f(s_g) phihat_q(gamma_k(s_g)),
+  //   P[k][f][q] = -+ (1/s) sum_g F_f(s_g) phihat_q(gamma_k(s_g)),
   // (left: minus, points in its own direction; right: plus, points reversed),
-  // so that the element kernel reads one value per edge, field and mode
-  auto project = [&](int side, int k, int Kside, T sg) {
+  // stored in the element's own slot of its order group (local edge k), so
+  // that the element kernel reads one value per edge, field and mode,
+  // consecutive elements contiguous
+  auto project = [&](int side, int64_t el, int k, int pside, T sg) {
+    const int Kside = Kof(pside), KH = Kside - 3;
+    const int64_t s0 = pside == 2 ? G.start[2] : pside == 3 ? G.start[3] : G.start[4];
+    const int64_t ns = (pside == 2 ? G.start[3] : pside == 3 ? G.start[4] : G.start[5]) - s0;
+    T* P = (T*)(pside == 2 ? Pf[2] : pside == 3 ? Pf[3] : Pf[4]) + (el - s0);
     sfor<3, Kof(PM)>([&](auto q) {
       if (q < Kside) {
         sfor<0, 3>([&](auto f) {
@@ -511,13 +518,13 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
           sfor<0, N>([&](auto g) {
             acc += Ffull[f][g] * (side ? cEB[GI][k][q][N - 1 - g] : cEB[GI][k][q][g]);
           });
-          Pf[((side * 3 + f) * KQ + (q - 3)) * nl + idx] = sg * acc;
+          P[((k * 3 + f) * KH + (q - 3)) * ns] = sg * acc;
         });
       }
     });
   };
-  if (pL >= 2) project(0, kL, Kof(pL), -geo[G_RS * ne + L]);
-  if (R >= 0 && pR >= 2) project(1, kR, Kof(pR), geo[G_RS * ne + R]);
+  if (pL >= 2) project(0, L, kL, pL, -geo[G_RS * ne + L]);
+  if (R >= 0 && pR >= 2) project(1, R, kR, pR, geo[G_RS * ne + R]);
   // Degree-<=1 test functions are linear along the edge, so the correction's
   // share of the base modes is fixed by (M0, M1); the two-point flux with the
   // same moments is stored next to the base flux of this edge, and both sides
@@ -536,8 +543,7 @@ static int edge_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
   const int64_t nl = ce.n[PM];
   if (nl == 0) return 0;
   const int ct = launch_shape().corr_threads;
-  k_edge_corr<PM><<<nblocks(nl, ct), ct, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc,
-                                                    (T*)fx.Pf[PM]);
+  k_edge_corr<PM><<<nblocks(nl, ct), ct, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc, fx);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -549,22 +555,6 @@ int launch_edge_corr(GroupStreams gs, const DevMesh& m, const CorrEdges& ce, con
   if (!r) r = edge_group<3>(gs.s[1], m, ce, G, ph, stg, c, u, fx);
   if (!r) r = edge_group<4>(gs.s[2], m, ce, G, ph, stg, c, u, fx);
   return r;
-}
-
-// ---------------------------------------------------------------------------
-// the projected full flux of one correction edge for test mode q >= 3 of an
-// element (written by the edge kernel for both sides)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void add_edge_projection(T (&r)[3], const EdgeFlux& fx, const CorrEdges& ce, int pm,
-                                                    int64_t sl, bool right, int q) {
-  // selects rather than a runtime index into the kernel parameters (which
-  // would copy them to local memory)
-  const T* P = (const T*)(pm == 2 ? fx.Pf[2] : pm == 3 ? fx.Pf[3] : fx.Pf[4]);
-  const int KQ = Kof(pm) - 3;
-  const int64_t nl = pm == 2 ? ce.n[2] : pm == 3 ? ce.n[3] : ce.n[4];
-  const int side = right ? 1 : 0;
-#pragma unroll
-  for (int f = 0; f < 3; ++f) r[f] += P[((side * 3 + f) * KQ + (q - 3)) * nl + sl];
 }
 
 
@@ -587,7 +577,7 @@ __global__ void __launch_bounds__(128, kF32 ? 4 : 2) k_elem_corr(DevMesh m, Corr
                                                             const T* __restrict__ cbS,
                                                             const T* __restrict__ chS, const T* __restrict__ chN,
                                                             T* __restrict__ chO, const T* __restrict__ ub,
-                                                            const T* __restrict__ uh, EdgeFlux fx,
+                                                            const T* __restrict__ uh, const T* __restrict__ pe,
                                                             double* __restrict__ rc CORR_VOL_PARAM) {
   const int64_t nb = (n + 127) / 128;
   const int q = qlo + (int)(blockIdx.x / nb);
@@ -597,10 +587,44 @@ __global__ void __launch_bounds__(128, kF32 ? 4 : 2) k_elem_corr(DevMesh m, Corr
   constexpr int KH = K - 3;
   constexpr int KL = Kof(deg_of(K - 1) - 1);  // modes of degree < p (the only ones D couples)
   const T* geo = geo_t(m);
-  T xi[K], U[K], V[K], uc[K], vc[K], pp[K], Uc[KL], Vc[KL];
   const T J0 = geo[G_JI0 * ne + e], J1 = geo[G_JI1 * ne + e];
   const T J2 = geo[G_JI2 * ne + e], J3 = geo[G_JI3 * ne + e];
-  {
+  const T rs = geo[G_RS * ne + e];
+  const T g = (T)ph.g;
+  T r[3] = {0, 0, 0};
+  // the test mode's own coefficients and the element's mean elevation
+  T xq = 0, Uq = 0, Vq = 0, xi0 = 0;
+  if constexpr (tc_vol(K)) {
+#ifdef CORR_TC
+    // the momentum volume terms come from the tensor cores: only the xi row's
+    // contravariant momenta (modes of degree < p) are needed here
+    T Uc[KL], Vc[KL];
+    sfor<0, KL>([&](auto j) {
+      T Uj, Vj;
+      if constexpr (j < 3) {
+        Uj = cbS[(1 * 3 + j) * ne + e];
+        Vj = cbS[(2 * 3 + j) * ne + e];
+      } else {
+        Uj = chS[(1 * KH + (j - 3)) * n + l];
+        Vj = chS[(2 * KH + (j - 3)) * n + l];
+      }
+      Uc[j] = J0 * Uj + J1 * Vj;
+      Vc[j] = J2 * Uj + J3 * Vj;
+    });
+    sfor<1, K>([&](auto Q) {
+      if (q == Q) r[0] = volume_xi<K, Q, KL>(Uc, Vc);
+    });
+    r[1] = (T)vol[q * nrc + rc_off + l];
+    r[2] = (T)vol[(16 + q) * nrc + rc_off + l];
+    if (q >= 3) {
+      xq = chS[(0 * KH + (q - 3)) * n + l];
+      Uq = chS[(1 * KH + (q - 3)) * n + l];
+      Vq = chS[(2 * KH + (q - 3)) * n + l];
+    }
+    xi0 = cbS[e];
+#endif
+  } else {
+    T xi[K], U[K], V[K], uc[K], vc[K], pp[K], Uc[KL], Vc[KL];
     T uu[K], vv[K];
     load_modes<K>(xi, cbS, ne, e, chS, n, l, 0);
     load_modes<K>(U, cbS, ne, e, chS, n, l, 1);
@@ -617,51 +641,38 @@ __global__ void __launch_bounds__(128, kF32 ? 4 : 2) k_elem_corr(DevMesh m, Corr
         Vc[j] = J2 * U[j] + J3 * V[j];
       }
     });
-  }
-  const T rs = geo[G_RS * ne + e];
-  const T g = (T)ph.g;
-  T r[3] = {0, 0, 0};
-  if constexpr (tc_vol(K)) {
-#ifdef CORR_TC
-    sfor<1, K>([&](auto Q) {
-      if (q == Q) r[0] = volume_xi<K, Q, KL>(Uc, Vc);
-    });
-    r[1] = (T)vol[q * nrc + rc_off + l];
-    r[2] = (T)vol[(16 + q) * nrc + rc_off + l];
-#endif
-  } else {
     sfor<1, K>([&](auto Q) {
       if (q == Q) volume_q<K, Q, KL>(r, xi, U, V, uc, vc, pp, Uc, Vc, rs, J0, J1, J2, J3, g);
     });
+    sfor<3, K>([&](auto Q) {
+      if (q == Q) { xq = xi[Q]; Uq = U[Q]; Vq = V[Q]; }
+    });
+    xi0 = xi[0];
   }
   if (q < 3) {
     rc[(0 * 2 + (q - 1)) * nrc + rc_off + l] = (double)r[1];
     rc[(1 * 2 + (q - 1)) * nrc + rc_off + l] = (double)r[2];
     return;
   }
-  T xq = 0, Uq = 0, Vq = 0;
-  sfor<3, K>([&](auto Q) {
-    if (q == Q) { xq = xi[Q]; Uq = U[Q]; Vq = V[Q]; }
-  });
   r[1] += geo[G_GDHX * ne + e] * xq;
   r[2] += geo[G_GDHY * ne + e] * xq;
   if (ph.src) {  // bottom friction (tau from the element means, Sect. 3) and Coriolis of Eq. (5)
     const T ra = (T)1.4142135623730951 * rs;
-    const T Hm = (xi[0] + geo[G_HB0 * ne + e]) * ra;
+    const T Hm = (xi0 + geo[G_HB0 * ne + e]) * ra;
     const T um = ub[0 * ne + e] * ra, vm = ub[3 * ne + e] * ra;  // mode 0 of u, v (layout [2][3][ne])
     const T tau = (T)ph.fric_lin * Hm + (T)ph.fric_quad * sqrt(um * um + vm * vm);
     const T uq = uh[(0 * KH + (q - 3)) * n + l], vq = uh[(1 * KH + (q - 3)) * n + l];
     r[1] += (T)ph.f_c * Vq - tau * uq;
     r[2] -= (T)ph.f_c * Uq + tau * vq;
   }
-  // edges: every edge of a p >= 2 element is a correction edge
+  // edges: every edge of a p >= 2 element is a correction edge, whose kernel
+  // left the projections in this element's slots
+  {
+    const T* P = pe + (q - 3) * n + l;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const uint32_t cs = ce.ecs[k * nrc + rc_off + l];
-    const bool right = (cs >> 27) & 1;
-    const int pm = cs >> 28;
-    const int64_t sl = cs & 0x07ffffff;
-    add_edge_projection(r, fx, ce, pm, sl, right, q);
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int f = 0; f < 3; ++f) r[f] += P[(k * 3 + f) * KH * n];
   }
   const T dt = (T)stage_dt(stg, m.mem[e]), a = (T)stg.a, b = (T)stg.b;
   const T cs3[3] = {xq, Uq, Vq};
@@ -690,7 +701,7 @@ static int elem_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
   const int qlo = part == 0 ? 1 : 3, nq = part == 0 ? K - 1 : K - 3;
   k_elem_corr<K><<<(unsigned)(((n + 127) / 128) * nq), 128, 0, st>>>(m, ce, g0, n, rc_off, nrc, qlo, ph, stg, base_c_host(cS),
                                                            (const T*)cS.ch[p], (const T*)cN.ch[p], (T*)cO.ch[p],
-                                                           base_u_host(u), (const T*)u.uh[p], fx,
+                                                           base_u_host(u), (const T*)u.uh[p], (const T*)fx.Pf[p],
                                                            (double*)rc CORR_VOL_ARG);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());

@@ -181,20 +181,6 @@ __global__ void k_gather_edges(MeshStatic S, const int32_t* __restrict__ inv, De
   D.eR[i] = r >= 0 ? inv[r] : -1;
 }
 
-// every element of order >= 2: its three local edges' (pmax, side, slot)
-__global__ void k_ecs(int64_t ne, int64_t g2, const int32_t* __restrict__ eedge, const int32_t* __restrict__ slot,
-                      uint32_t* ecs) {
-  const int64_t e = g2 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= ne) return;
-  const int64_t nrc = ne - g2;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int32_t ee = eedge[k * ne + e];
-    const uint32_t cs = (uint32_t)slot[ee >> 1];
-    ecs[k * nrc + (e - g2)] = (cs & 0xf0000000u) | ((uint32_t)(ee & 1) << 27) | (cs & 0x07ffffffu);
-  }
-}
-
 // packed caller layout: off[u] = sum_{u' < u} 3 K(p_u'), total in *total
 __global__ void __launch_bounds__(RG_T) k_packed_counts(const int8_t* p_user, int64_t ne, int64_t* bsum) {
   __shared__ int64_t s[RG_T];
@@ -280,14 +266,6 @@ int launch_regroup(cudaStream_t s, const MeshStatic& S, const int8_t* p_user, De
   SWE_CUDA_OK(cudaGetLastError());
   // the packed total (poff[be]) next to the group starts
   SWE_CUDA_OK(cudaMemcpyAsync(W.info + 10, W.poff + be, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-  return 0;
-}
-
-int launch_ecs(cudaStream_t s, int64_t ne, int64_t g2, const int32_t* eedge, const int32_t* slot, uint32_t* ecs) {
-  if (ne - g2 <= 0) return 0;
-  k_ecs<<<nb(ne - g2, 256), 256, 0, s>>>(ne, g2, eedge, slot, ecs);
-  count_launch();
-  SWE_CUDA_OK(cudaGetLastError());
   return 0;
 }
 

@@ -32,8 +32,9 @@ struct EdgeFlux {
   double* Fb;        // [3][2][nedge] base flux (weighted by |E| w_g) at the 2-point rule
   double* Fbc;       // [3][2][nedge] two-point equivalent of the correction flux's share of the
                      // base modes (zero on edges without a p >= 2 side)
-  void* Pf[5];       // per pmax = 2..4: [2 sides][3 fields][K(pmax)-3][n]: the full flux of each correction
-                     // edge projected onto the higher test modes (q >= 3) of its left (0) and right (1) element
+  void* Pf[5];       // per element order p = 2..4: [3 local edges][3 fields][K(p)-3][n_p]: the full flux of
+                     // each of the element's (correction) edges projected onto its higher test modes (q >= 3),
+                     // written by the correction edge kernel, read contiguously by the element kernel
 };
 
 // The mesh in the caller's element order, independent of the orders: what
@@ -80,8 +81,6 @@ int64_t regroup_blocks(int64_t n);
 // the internal arrays for the orders p_user (device, caller order); the
 // group sizes land in W.info (device), for the host to read
 int launch_regroup(cudaStream_t s, const MeshStatic& S, const int8_t* p_user, DevMeshOut D, RegroupScratch W);
-// ecs of every element of order >= 2 from the regrouped eedge and slot
-int launch_ecs(cudaStream_t s, int64_t ne, int64_t g2, const int32_t* eedge, const int32_t* slot, uint32_t* ecs);
 
 // every kernel launch of the library is counted (for launch accounting)
 void count_launch(int n = 1);

@@ -39,16 +39,15 @@ def device_bytes(meshes, precision):
     the library makes (swe_memory_bytes reports them), counted on the host so
     that admission needs no context.  Per element: the mesh in caller order
     and regrouped (geometry and its FP32 copy, topology), three RK states,
-    velocity, the user-layout staging; per edge: geometry, base fluxes and
-    the projections of its correction flux onto both sides' higher modes; the
-    correction arrays scale with K - 3 at the correction type's width (4 bytes
-    in the mixed mode, 8 in FP64).  After an order change the library may hold
+    velocity, the user-layout staging; per edge: geometry and base fluxes;
+    per element of order p >= 2 also the projections of its three edges'
+    fluxes onto its higher modes.  The correction arrays scale with K - 3 at
+    the correction type's width (4 bytes in the mixed mode, 8 in FP64).  After an order change the library may hold
     more (its order-group buffers grow with a quarter to spare)."""
     corr32 = precision in (swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32)
     ts = 4 if corr32 else 8
     ne = nE = 0
     n = [0] * 5
-    ncl = [0] * 5
     for m in meshes:
         tri = np.asarray(m["tri"], np.int64)
         p = np.asarray(m["orders"], np.int64)
@@ -58,15 +57,10 @@ def device_bytes(meshes, precision):
         a = tri.reshape(-1)
         b = tri[:, [1, 2, 0]].reshape(-1)
         key = np.minimum(a, b) * (int(tri.max(initial=0)) + 1) + np.maximum(a, b)
-        owner = np.repeat(np.arange(len(tri)), 3)
-        order = np.argsort(key, kind="stable")
-        key, owner = key[order], owner[order]
+        key = np.sort(key)
         first = np.ones(len(key), bool)
         first[1:] = key[1:] != key[:-1]
-        pm = np.maximum.reduceat(p[owner], np.flatnonzero(first)) if len(key) else np.zeros(0, np.int64)
         nE += int(first.sum())
-        for q in (2, 3, 4):
-            ncl[q] += int((pm == q).sum())
     nm = max(len(meshes), 1)
     nrc = n[2] + n[3] + n[4]
     be, bg = -(-ne // 256), -(-nE // 256)
@@ -83,11 +77,10 @@ def device_bytes(meshes, precision):
     for q in (2, 3, 4):                                                                     # order groups
         allocs += [ts * 3 * (KP[q] - 3) * n[q]] * 3
         allocs += [ts * 2 * (KP[q] - 3) * n[q], ts * 4 * KP[q] * n[q], ts * KP[q] * n[q]]
-        allocs += [ts * 2 * 3 * (KP[q] - 3) * ncl[q]]
+        allocs += [ts * 3 * 3 * (KP[q] - 3) * n[q]]                                        # projected edge fluxes
     allocs += [32 * max(nrc, 1)]
     if precision == swedg.PREC_MIXED_TF32:
         allocs += [32 * 4 * max(nrc, 1)]                                                    # tensor-core volume terms
-    allocs += [12 * max(nrc, 1)]                                                            # correction edge slots
     b = sum(a if a > 0 else 16 for a in allocs)  # the library allocates 16 bytes for an empty array
     return b
 
