@@ -79,6 +79,7 @@ __constant__ T cES[3][8];           // points on [0,1]
 __constant__ T cPhi0;
 __constant__ T cS2b[2];             // points of the two-point base rule on [0,1]
 __constant__ T cRS2b;               // 1 / (s_1 - s_0)
+__constant__ double cEV[3][2][3];   // phihat_i(gamma_k(a)), i < 3, at the edge ends a = 0, 1 (FP64 in every mode)
 
 void upload_tables() {
   const RefTables& R = tables();
@@ -114,6 +115,7 @@ void upload_tables() {
   cudaMemcpyToSymbol(cEW, ew, sizeof ew);
   cudaMemcpyToSymbol(cES, es, sizeof es);
   cudaMemcpyToSymbol(cPhi0, &phi0, sizeof phi0);
+  cudaMemcpyToSymbol(cEV, R.EV, sizeof R.EV);
 }
 
 static inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -154,16 +156,26 @@ __device__ __forceinline__ void load_modes(T (&out)[K], const T* __restrict__ ba
 // ---------------------------------------------------------------------------
 // Volume terms of Eq. (13) for one test mode Q (non-base index triples only),
 // with J^{-1} folded into the contravariant coefficients
-//   Uc_i = (J^-1 q_i)_xhat, Vc_i = (J^-1 q_i)_yhat, uc_j, vc_j likewise, pp_j = xi_j/2 + hb_j:
+//   Uc_i = (J^-1 q_i)_xhat, Vc_i = (J^-1 q_i)_yhat, uc_j, vc_j likewise, pp_j = xi_j/2:
 //   r_xi = sum_i Uc_i D_x[Q][i] + Vc_i D_y[Q][i]
 //   r_U  = (1/s) [ sum_ij U_i (uc_j G_x[Q][i][j] + vc_j G_y[Q][i][j]) + g (J00 P_x + J10 P_y) ]
 //   r_V  = (1/s) [ sum_ij V_i (...) + g (J01 P_x + J11 P_y) ]
-//   P_k  = sum_ij xi_i pp_j G_k[Q][i][j]
+//   P_k  = sum_ij xi_i pp_j G_k[Q][i][j] + sum_{i >= 3, j < 3} xi_i hb_j G_k[Q][i][j]
+// The bottom term g xi h_b keeps only the products with a higher elevation
+// mode i >= 3.  For Q < 3 the rest are base triples.  For Q >= 3 the rest,
+// g (xi_lin h_b) with xi_lin the degree-1 part of xi, integrates by parts to
+// its own boundary integral (the gradient of xi_lin h_b is linear, so phi_Q
+// of degree >= 2 is orthogonal to it): the correction edge kernel moves that
+// integral into the edge flux, where it meets the flux's own g xi_lin h_b
+// term and leaves g h_b times the jump of xi_lin, formed in FP64.  In FP32
+// the two O(g |xi| h_b) integrals otherwise cancel to a residual several
+// orders of magnitude smaller and carry their rounding error into it.
 // ---------------------------------------------------------------------------
 template <int K, int Q, int KL>
 __device__ __forceinline__ void volume_q(T (&r)[3], const T (&xi)[K], const T (&U)[K], const T (&V)[K],
-                                         const T (&uc)[K], const T (&vc)[K], const T (&pp)[K], const T (&Uc)[KL],
-                                         const T (&Vc)[KL], T rs, T J0, T J1, T J2, T J3, T g) {
+                                         const T (&uc)[K], const T (&vc)[K], const T (&pp)[K], const T (&hb)[3],
+                                         const T (&Uc)[KL], const T (&Vc)[KL], T rs, T J0, T J1, T J2, T J3,
+                                         T g) {
   T am = 0;
   sfor<0, KL>([&](auto i) {
     if constexpr (dnz(Q, i) && !base2(Q, i)) am += Uc[i] * cD[0][Q][i] + Vc[i] * cD[1][Q][i];
@@ -181,8 +193,10 @@ __device__ __forceinline__ void volume_q(T (&r)[3], const T (&xi)[K], const T (&
         if constexpr (gnz(Q, i, j) && !base3(Q, i, j)) {
           const T gx = cG[0][Q][pk(i, j)], gy = cG[1][Q][pk(i, j)];
           w += uc[j] * gx + vc[j] * gy;
-          px += pp[j] * gx;
-          py += pp[j] * gy;
+          T pj = pp[j];
+          if constexpr (i >= 3 && j < 3) pj += hb[j];
+          px += pj * gx;
+          py += pj * gy;
         }
       });
       aU += U[i] * w; aV += V[i] * w;
@@ -319,12 +333,12 @@ __global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int6
       T uc[K], vc[K], pp[K], Uc[KL], Vc[KL];
       const T J0 = geo[G_JI0 * ne + e], J1 = geo[G_JI1 * ne + e];
       const T J2 = geo[G_JI2 * ne + e], J3 = geo[G_JI3 * ne + e];
+      const T hb[3] = {geo[G_HB0 * ne + e], geo[G_HB1 * ne + e], geo[G_HB2 * ne + e]};
       sfor<0, K>([&](auto j) {
         const T uu = x[0][j] * s, vv = x[1][j] * s;  // the velocity modes as stored above
         uc[j] = J0 * uu + J1 * vv;
         vc[j] = J2 * uu + J3 * vv;
-        if constexpr (j < 3) pp[j] = (T)0.5 * xi[j] + geo[(G_HB0 + j) * ne + e];
-        else pp[j] = (T)0.5 * xi[j];
+        pp[j] = (T)0.5 * xi[j];
         if constexpr (j < KL) {
           Uc[j] = J0 * U[j] + J1 * V[j];
           Vc[j] = J2 * U[j] + J3 * V[j];
@@ -332,8 +346,8 @@ __global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int6
       });
       const T rs = geo[G_RS * ne + e], g = (T)ph.g;
       T r1[3], r2[3];
-      volume_q<K, 1, KL>(r1, xi, U, V, uc, vc, pp, Uc, Vc, rs, J0, J1, J2, J3, g);
-      volume_q<K, 2, KL>(r2, xi, U, V, uc, vc, pp, Uc, Vc, rs, J0, J1, J2, J3, g);
+      volume_q<K, 1, KL>(r1, xi, U, V, uc, vc, pp, hb, Uc, Vc, rs, J0, J1, J2, J3, g);
+      volume_q<K, 2, KL>(r2, xi, U, V, uc, vc, pp, hb, Uc, Vc, rs, J0, J1, J2, J3, g);
       rc[0 * nrc + rc_off + l] = (double)r1[1];
       rc[1 * nrc + rc_off + l] = (double)r2[1];
       rc[2 * nrc + rc_off + l] = (double)r1[2];
@@ -446,6 +460,7 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
   const T unL = (ubt[L] * nx + ubt[3 * ne + L] * ny) * mL;
   const T HL = cbt[L] * mL + hmid;
   T unR, HR;
+  double xt = 0.0;  // open sea elevation
   Tr a[N], b[N];
   side_traces<PM>(m, G, c, u, L, pL, kL, false, a);
   if (R >= 0) {
@@ -454,7 +469,8 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
     unR = (ubt[R] * nx + ubt[3 * ne + R] * ny) * mR;
     HR = cbt[R] * mR + hmid;
   } else if (bc == 2) {
-    const T xh = (T)tide_value(ph, stage_time(stg, m.emem[ed]));
+    xt = tide_value(ph, stage_time(stg, m.emem[ed]));
+    const T xh = (T)xt;
     sfor<0, N>([&](auto q) { b[q] = a[q]; b[q].xb = xh; b[q].xh = 0; });
     unR = unL;
     HR = xh + hmid;
@@ -470,17 +486,48 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
     });
   }
   const T lam = fmax(fabs(unL), fabs(unR)) + sqrt(g * fmax(HL, HR));
+  // jump xi_lin,R - xi_lin,L of the degree-1 elevations at the edge ends
+  // (s = 0, 1 of the left element's parameter; the right element runs the
+  // edge the other way) from the FP64 base modes: it carries the volume
+  // term g xi_lin h_b of the higher test modes (moved here, see volume_q),
+  // zero on land, where the mirror state has the same elevation
+  double JA = 0.0, JB = 0.0;
+  if (R >= 0 || bc == 2) {
+    const double rl = m.geo[G_RS * ne + L];
+    double lA = 0.0, lB = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      lA += c.cb[i * ne + L] * cEV[kL][0][i];
+      lB += c.cb[i * ne + L] * cEV[kL][1][i];
+    }
+    double rA = xt, rB = xt;
+    if (R >= 0) {
+      const double rr = m.geo[G_RS * ne + R];
+      rA = rB = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        rA += c.cb[i * ne + R] * cEV[kR][1][i];
+        rB += c.cb[i * ne + R] * cEV[kR][0][i];
+      }
+      rA *= rr;
+      rB *= rr;
+    }
+    JA = rA - rl * lA;
+    JB = rB - rl * lB;
+  }
+  const T JA_ = (T)JA, dJ = (T)(JB - JA);
   // zeroth and first moments (in the left element's edge parameter s) of the
   // weighted correction flux: they are all the test modes of degree <= 1 see
   T M0[3] = {0, 0, 0}, M1[3] = {0, 0, 0};
-  T Ffull[3][N];
+  T Ffull[3][N], FJ[N];
   sfor<0, N>([&](auto q) {
     const T hb = hA + cES[GI][q] * (hB - hA);
     const Tr& x = a[q];
     const Tr& y = b[q];
-    // base flux (P1 parts)
+    // base flux (P1 parts, which the base modes take from the base edge
+    // kernel): for the higher modes g h_b J replaces its g xi_lin h_b terms
     const T wxb = x.ub * nx + x.vb * ny, wyb = y.ub * nx + y.vb * ny;
-    const T pxb = g * x.xb * ((T)0.5 * x.xb + hb), pyb = g * y.xb * ((T)0.5 * y.xb + hb);
+    const T pxb = g * x.xb * ((T)0.5 * x.xb), pyb = g * y.xb * ((T)0.5 * y.xb);
     const T Fb0 = (x.Ub + y.Ub) * nx + (x.Vb + y.Vb) * ny + lam * (x.xb - y.xb);
     const T Fb1 = x.Ub * wxb + y.Ub * wyb + (pxb + pyb) * nx + lam * (x.Ub - y.Ub);
     const T Fb2 = x.Vb * wxb + y.Vb * wyb + (pxb + pyb) * ny + lam * (x.Vb - y.Vb);
@@ -499,27 +546,33 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
     Ffull[0][q] = wgt * (Fb0 + Fh0);
     Ffull[1][q] = wgt * (Fb1 + Fh1);
     Ffull[2][q] = wgt * (Fb2 + Fh2);
+    FJ[q] = wgt * g * hb * (JA_ + cES[GI][q] * dJ);
   });
   // the full flux projected onto the higher test modes of each side once here,
-  //   P[k][f][q] = -+ (1/s) sum_g F_f(s_g) phihat_q(gamma_k(s_g)),
-  // (left: minus, points in its own direction; right: plus, points reversed),
-  // stored in the element's own slot of its order group (local edge k), so
-  // that the element kernel reads one value per edge, field and mode,
-  // consecutive elements contiguous
+  //   P[k][f][q] = -+ (1/s) sum_g (F_f(s_g) +- n_f FJ(s_g)) phihat_q(gamma_k(s_g)),
+  // (left: minus, points in its own direction, +J; right: plus, points
+  // reversed, -J), stored in the element's own slot of its order group (local
+  // edge k), so that the element kernel reads one value per edge, field and
+  // mode, consecutive elements contiguous
   auto project = [&](int side, int64_t el, int k, int pside, T sg) {
     const int Kside = Kof(pside), KH = Kside - 3;
     const int64_t s0 = pside == 2 ? G.start[2] : pside == 3 ? G.start[3] : G.start[4];
     const int64_t ns = (pside == 2 ? G.start[3] : pside == 3 ? G.start[4] : G.start[5]) - s0;
     T* P = (T*)(pside == 2 ? Pf[2] : pside == 3 ? Pf[3] : Pf[4]) + (el - s0);
+    const T jx = side ? -nx : nx, jy = side ? -ny : ny;
     sfor<3, Kof(PM)>([&](auto q) {
       if (q < Kside) {
-        sfor<0, 3>([&](auto f) {
-          T acc = 0;
-          sfor<0, N>([&](auto g) {
-            acc += Ffull[f][g] * (side ? cEB[GI][k][q][N - 1 - g] : cEB[GI][k][q][g]);
-          });
-          P[((k * 3 + f) * KH + (q - 3)) * ns] = sg * acc;
+        T acc[3] = {0, 0, 0}, aj = 0;
+        sfor<0, N>([&](auto g) {
+          const T bq = side ? cEB[GI][k][q][N - 1 - g] : cEB[GI][k][q][g];
+          acc[0] += Ffull[0][g] * bq;
+          acc[1] += Ffull[1][g] * bq;
+          acc[2] += Ffull[2][g] * bq;
+          aj += FJ[g] * bq;
         });
+        P[((k * 3 + 0) * KH + (q - 3)) * ns] = sg * acc[0];
+        P[((k * 3 + 1) * KH + (q - 3)) * ns] = sg * (acc[1] + jx * aj);
+        P[((k * 3 + 2) * KH + (q - 3)) * ns] = sg * (acc[2] + jy * aj);
       }
     });
   };
@@ -631,18 +684,18 @@ __global__ void __launch_bounds__(128, kF32 ? 4 : 2) k_elem_corr(DevMesh m, Corr
     load_modes<K>(V, cbS, ne, e, chS, n, l, 2);
     load_modes<K>(uu, ub, ne, e, uh, n, l, 0);
     load_modes<K>(vv, ub, ne, e, uh, n, l, 1);
+    const T hb[3] = {geo[G_HB0 * ne + e], geo[G_HB1 * ne + e], geo[G_HB2 * ne + e]};
     sfor<0, K>([&](auto j) {
       uc[j] = J0 * uu[j] + J1 * vv[j];
       vc[j] = J2 * uu[j] + J3 * vv[j];
-      if constexpr (j < 3) pp[j] = (T)0.5 * xi[j] + geo[(G_HB0 + j) * ne + e];
-      else pp[j] = (T)0.5 * xi[j];
+      pp[j] = (T)0.5 * xi[j];
       if constexpr (j < KL) {
         Uc[j] = J0 * U[j] + J1 * V[j];
         Vc[j] = J2 * U[j] + J3 * V[j];
       }
     });
     sfor<1, K>([&](auto Q) {
-      if (q == Q) volume_q<K, Q, KL>(r, xi, U, V, uc, vc, pp, Uc, Vc, rs, J0, J1, J2, J3, g);
+      if (q == Q) volume_q<K, Q, KL>(r, xi, U, V, uc, vc, pp, hb, Uc, Vc, rs, J0, J1, J2, J3, g);
     });
     sfor<3, K>([&](auto Q) {
       if (q == Q) { xq = xi[Q]; Uq = U[Q]; Vq = V[Q]; }

@@ -10,7 +10,7 @@
 //   r_U[q] = (1/s) sum_{k,i,j} G_k[q][i][j] (U_i w^k_j + xi_i px^k_j)
 //   r_V[q] = (1/s) sum_{k,i,j} G_k[q][i][j] (V_i w^k_j + xi_i py^k_j)
 // with w = (uc, vc) the contravariant velocity coefficients (J^-1 u) and
-// px^k = g J^-1_{k,x} pp, py^k = g J^-1_{k,y} pp, pp = xi/2 + h_b, is done in
+// px^k = g J^-1_{k,x} pp, py^k = g J^-1_{k,y} pp, pp = xi/2, is done in
 // two stages.  Stage one contracts over (k, j) for every (i, q) at once,
 //   W[i][q]  = sum_{k,j} G_k[q][i][j] w^k_j
 //   ZU[i][q] = sum_{k,j} G_k[q][i][j] px^k_j,   ZV[i][q] = ... py^k_j,
@@ -31,9 +31,11 @@
 // to within 2^-22 |x|, with h = tf32(x) and t = tf32(x - h) (tf32 = round to
 // the nearest value with 10 mantissa bits), and each GEMM runs as the three
 // products hh + ht + th into one FP32 accumulator.  The B parts come from the
-// FP64 values of G.  The mean depth (kilometres, against metres of elevation)
-// would be the largest part of pp; it stays out of the GEMMs and enters as
-// g h_b0 sum_i xi_i sum_k J^-1_k G_k[q][i][0], added on the CUDA cores.
+// FP64 values of G.  The bottom term g xi h_b keeps only the products with a
+// higher elevation mode (i >= 3; the correction edge kernel carries the rest
+// as g h_b times the FP64 jump of the degree-1 elevation), which the GEMM's
+// shared operand cannot single out: it is added on the CUDA cores after the
+// GEMMs, g sum_{i >= 3, j < 3} xi_i h_b_j sum_k J^-1_k G_k[q][i][j].
 //
 // Schedule: one persistent CTA per SM (128 threads, thread t = element row t
 // of the tile) loads both parts of B once (bulk TMA copies on an mbarrier),
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(TC_M, 1) k_vol_tc(DevMesh m, int64_t g0, int64
     const bool live = l < n;
     const int64_t e = g0 + (live ? l : 0);
     float xi[K], U[K], V[K], pp[K];
-    float J0 = 0.f, J1 = 0.f, J2 = 0.f, J3 = 0.f, rs = 0.f, hb0 = 0.f;
+    float J0 = 0.f, J1 = 0.f, J2 = 0.f, J3 = 0.f, rs = 0.f, hb[3] = {0.f, 0.f, 0.f};
     float aw[TC_KD], ax[TC_KD];
 #pragma unroll
     for (int c = 0; c < TC_KD; ++c) aw[c] = ax[c] = 0.0f;
@@ -313,7 +315,9 @@ __global__ void __launch_bounds__(TC_M, 1) k_vol_tc(DevMesh m, int64_t g0, int64
       J0 = geo[G_JI0 * ne + e]; J1 = geo[G_JI1 * ne + e];
       J2 = geo[G_JI2 * ne + e]; J3 = geo[G_JI3 * ne + e];
       rs = geo[G_RS * ne + e];
-      hb0 = geo[G_HB0 * ne + e];
+      hb[0] = geo[G_HB0 * ne + e];
+      hb[1] = geo[G_HB1 * ne + e];
+      hb[2] = geo[G_HB2 * ne + e];
       float uu[K], vv[K];
       load_modes<K>(xi, cb, ne, e, ch, n, l, 0);
       load_modes<K>(U, cb, ne, e, ch, n, l, 1);
@@ -323,9 +327,7 @@ __global__ void __launch_bounds__(TC_M, 1) k_vol_tc(DevMesh m, int64_t g0, int64
       sfor<0, K>([&](auto j) {
         aw[j] = J0 * uu[j] + J1 * vv[j];       // uc
         aw[K + j] = J2 * uu[j] + J3 * vv[j];   // vc
-        // h_b's mean mode stays out of the GEMM (see the epilogue)
-        if constexpr (j == 1 || j == 2) pp[j] = 0.5f * xi[j] + geo[(G_HB0 + j) * ne + e];
-        else pp[j] = 0.5f * xi[j];
+        pp[j] = 0.5f * xi[j];  // h_b stays out of the GEMM (see the epilogue)
         ax[j] = g * J0 * pp[j];                // px (U equation)
         ax[K + j] = g * J2 * pp[j];
       });
@@ -403,17 +405,22 @@ __global__ void __launch_bounds__(TC_M, 1) k_vol_tc(DevMesh m, int64_t g0, int64
         });
       }
     }
-    // the pressure's mean-depth part, g hb0 sum_i xi_i sum_k J^-1_k G_k[q][i][0], in FP32 here
+    // the bottom term's products with the higher elevation modes,
+    // g sum_{i >= 3, j < 3} xi_i h_b_j sum_k J^-1_k G_k[q][i][j], in FP32 here
+    float xh[K][3];
+    sfor<3, K>([&](auto i) { sfor<0, 3>([&](auto j) { xh[i][j] = xi[i] * hb[j]; }); });
     sfor<1, K>([&](auto Q) {
       float ex = 0.f, ey = 0.f;
-      sfor<0, K>([&](auto i) {
-        if constexpr (gnz(Q, i, 0) && !base3(Q, i, 0)) {
-          ex = fmaf(xi[i], cG[0][Q][pk(i, 0)], ex);
-          ey = fmaf(xi[i], cG[1][Q][pk(i, 0)], ey);
-        }
+      sfor<3, K>([&](auto i) {
+        sfor<0, 3>([&](auto j) {
+          if constexpr (gnz(Q, i, j)) {
+            ex = fmaf(xh[i][j], cG[0][Q][pk(i, j)], ex);
+            ey = fmaf(xh[i][j], cG[1][Q][pk(i, j)], ey);
+          }
+        });
       });
-      rU[Q] = fmaf(g * hb0, J0 * ex + J2 * ey, rU[Q]);
-      rV[Q] = fmaf(g * hb0, J1 * ex + J3 * ey, rV[Q]);
+      rU[Q] = fmaf(g, J0 * ex + J2 * ey, rU[Q]);
+      rV[Q] = fmaf(g, J1 * ex + J3 * ey, rV[Q]);
     });
     if (live && ok) {
 #pragma unroll

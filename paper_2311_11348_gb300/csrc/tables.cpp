@@ -153,6 +153,13 @@ void build_tables(RefTables* R) {
         for (int i = 0; i < KMAX; ++i) R->EB[np][k][i][g] = ph[i];
       }
   }
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 2; ++a) {
+      double x, y;
+      edge_point(k, (double)a, &x, &y);
+      dubiner(x, y, ph, nullptr, nullptr);
+      for (int i = 0; i < 3; ++i) R->EV[k][a][i] = ph[i];
+    }
 }
 
 const RefTables& tables() {

@@ -14,6 +14,7 @@ struct RefTables {
   double Lv[3][3];                  // int lambda_v phihat_i, i < 3
   double es[9][8], ew[9][8];        // Gauss-Legendre rules on [0,1], 1..8 points
   double EB[9][3][KMAX][8];         // EB[n][k][i][g] = phihat_i(gamma_k(s_g)) with the n-point rule
+  double EV[3][2][3];               // EV[k][a][i] = phihat_i(gamma_k(a)), a = 0, 1: degree-1 modes at the edge ends
 };
 
 void dubiner(double x, double y, double* v, double* vx, double* vy);

@@ -88,7 +88,7 @@ def usolve_flops(K, rc=False):
 
 
 def setup_flops(K, tc=False):
-    """contravariant coefficients (J^-1 applied to u, v and to U, V of degree < p) and xi/2 + h_b"""
+    """contravariant coefficients (J^-1 applied to u, v and to U, V of degree < p) and xi/2"""
     KL = KP[DEG[K - 1] - 1]
     return KL * 6 if tc else K * 6 + KL * 6
 
@@ -102,7 +102,9 @@ def volume_flops(K, q, tc=False):
         if tc:
             continue
         inner = sum(1 for j in range(K) if gnz(q, i, j) and not (q < 3 and i < 3 and j < 3))
-        f += 8 * inner + (8 if inner else 0)
+        # the bottom term's h_b_j (j < 3) joins the products of the higher elevation modes
+        hb = sum(1 for j in range(3) if gnz(q, i, j)) if i >= 3 else 0
+        f += 8 * inner + hb + (8 if inner else 0)
     return f + (0 if tc else 10)
 
 
@@ -126,13 +128,14 @@ def vol_tc_flops(K):
 
 
 def edge_corr_flops(KL, KR, pm):
-    """traces of both sides (5 fields), lambda, the flux at npts(pm) points and
-    its two moments, the projections onto the higher test modes of each side"""
+    """traces of both sides (5 fields), lambda, the FP64 elevation jump at the
+    edge ends, the flux and the jump term at npts(pm) points and the flux's two
+    moments, the projections onto the higher test modes of each side"""
     N = npts(pm)
-    f = 12 + N * (2 * 10 * (KL + KR) + (KL + KR) + 95)
+    f = 12 + 30 + N * (2 * 10 * (KL + KR) + (KL + KR) + 99)
     for K in (KL, KR):
         if K >= 6:
-            f += (K - 3) * 3 * (2 * N + 1)
+            f += (K - 3) * (8 * N + 7)
     return f
 
 

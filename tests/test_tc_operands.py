@@ -77,9 +77,9 @@ def test_operand_images_hold_G_split_into_tf32_head_and_tail(lib, K):
 @pytest.mark.parametrize("K", [6, 10, 15])
 def test_gemm_decomposition_reproduces_the_volume_contraction(lib, K):
     """the kernel's two stages: GEMMs of per-element rows (2 K values: the
-    contravariant velocities, or g J^-1 times the pressure products without
-    h_b's mean) against the image, giving W, ZU, ZV [i][q]; then the sums over
-    i with the element's U, V, xi, and the mean-depth part added apart"""
+    contravariant velocities, or g J^-1 xi / 2) against the image, giving W,
+    ZU, ZV [i][q]; then the sums over i with the element's U, V, xi, and the
+    bottom term's products with the higher elevation modes added apart"""
     rng = np.random.default_rng(K)
     n = 7
     xi, U, V, u, v = (rng.standard_normal((n, K)) for _ in range(5))
@@ -91,13 +91,13 @@ def test_gemm_decomposition_reproduces_the_volume_contraction(lib, K):
     Gm = B[:, :K]
     mask = np.array([[[used(q, i, j) for j in range(K)] for i in range(K)] for q in range(K)])
     assert not np.any(Gm[:, ~mask])
-    # direct contraction (non-base triples only), physical gradients through J^-1
+    # direct contraction (non-base triples only), physical gradients through J^-1;
+    # the bottom term xi_i h_b_j only with a higher elevation mode i >= 3
     pp = 0.5 * xi
-    pp[:, :3] += hb
     uc = J[:, [0]] * u + J[:, [1]] * v
     vc = J[:, [2]] * u + J[:, [3]] * v
-    Px = np.einsum("qij,ei,ej->eq", Gm[0], xi, pp)
-    Py = np.einsum("qij,ei,ej->eq", Gm[1], xi, pp)
+    Px, Py = (np.array([sum(xi[e, i] * (pp[e, j] + (hb[e, j] if i >= 3 and j < 3 else 0.0)) * Gm[k][:, i, j]
+                            for i in range(K) for j in range(K)) for e in range(n)]) for k in range(2))
     rU = rs[:, None] * (np.einsum("qij,ei,ej->eq", Gm[0], U, uc) + np.einsum("qij,ei,ej->eq", Gm[1], U, vc)
                         + g * (J[:, [0]] * Px + J[:, [2]] * Py))
     rV = rs[:, None] * (np.einsum("qij,ei,ej->eq", Gm[0], V, uc) + np.einsum("qij,ei,ej->eq", Gm[1], V, vc)
@@ -108,18 +108,16 @@ def test_gemm_decomposition_reproduces_the_volume_contraction(lib, K):
         for q in range(16):
             Bop[16 * i + q, :K] = B[0, q, i, :]
             Bop[16 * i + q, K:] = B[1, q, i, :]
-    pq = pp.copy()
-    pq[:, 0] -= hb[:, 0]  # h_b's mean mode stays out of the GEMM
     Aw = np.hstack([uc, vc])
-    Au = g * np.hstack([J[:, [0]] * pq, J[:, [2]] * pq])
-    Av = g * np.hstack([J[:, [1]] * pq, J[:, [3]] * pq])
+    Au = g * np.hstack([J[:, [0]] * pp, J[:, [2]] * pp])
+    Av = g * np.hstack([J[:, [1]] * pp, J[:, [3]] * pp])
     W, ZU, ZV = ((A @ Bop.T).reshape(n, K, 16) for A in (Aw, Au, Av))
-    ex = np.einsum("qi,ei->eq", Gm[0, :, :, 0], xi)
-    ey = np.einsum("qi,ei->eq", Gm[1, :, :, 0], xi)
+    ex = np.einsum("qij,ei,ej->eq", Gm[0, :, 3:, :3], xi[:, 3:], hb)
+    ey = np.einsum("qij,ei,ej->eq", Gm[1, :, 3:, :3], xi[:, 3:], hb)
     gU = np.einsum("ei,eiq->eq", U, W) + np.einsum("ei,eiq->eq", xi, ZU)
     gV = np.einsum("ei,eiq->eq", V, W) + np.einsum("ei,eiq->eq", xi, ZV)
-    gU = rs[:, None] * (gU[:, :K] + g * hb[:, [0]] * (J[:, [0]] * ex + J[:, [2]] * ey))
-    gV = rs[:, None] * (gV[:, :K] + g * hb[:, [0]] * (J[:, [1]] * ex + J[:, [3]] * ey))
+    gU = rs[:, None] * (gU[:, :K] + g * (J[:, [0]] * ex + J[:, [2]] * ey))
+    gV = rs[:, None] * (gV[:, :K] + g * (J[:, [1]] * ex + J[:, [3]] * ey))
     tol = 1e-9 * max(np.abs(rU).max(), np.abs(rV).max())
     assert np.abs(gU - rU).max() <= tol
     assert np.abs(gV - rV).max() <= tol
