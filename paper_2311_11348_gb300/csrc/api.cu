@@ -283,32 +283,54 @@ struct ProfScope {
 
 // ------------------------------------------------------------------ mesh
 static int build_topology(swe_ctx* ctx) {
-  const int64_t ne = ctx->ne;
+  // Edge k of triangle e joins vertices a, b (the two other than vertex k).
+  // Every edge is filed under its lower vertex (a counting sort over vertex
+  // ids: linear in the mesh size), and the two sides of an interior edge are
+  // the two entries of one vertex's bucket with the same upper vertex.
+  const int64_t ne = ctx->ne, nv = ctx->nv;
   ctx->nb.assign(3 * ne, -1);
   ctx->nbk.assign(3 * ne, -1);
-  struct Key { int64_t a, b; int64_t e; int k; };
-  std::vector<Key> keys(3 * ne);
-  for (int64_t e = 0; e < ne; ++e)
-    for (int k = 0; k < 3; ++k) {
-      int64_t a = ctx->tri[3 * e + (k + 1) % 3], b = ctx->tri[3 * e + (k + 2) % 3];
-      keys[3 * e + k] = {std::min(a, b), std::max(a, b), e, k};
-    }
-  std::sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
-    return x.a != y.a ? x.a < y.a : x.b != y.b ? x.b < y.b : x.e != y.e ? x.e < y.e : x.k < y.k;
-  });
-  for (size_t r = 0; r < keys.size();) {
-    size_t s = r;
-    while (s < keys.size() && keys[s].a == keys[r].a && keys[s].b == keys[r].b) ++s;
-    if (s - r > 2) return fail(ctx, SWE_EMESH, "edge (%lld,%lld) is shared by %zu triangles", (long long)keys[r].a,
-                               (long long)keys[r].b, s - r);
-    if (s - r == 2) {
-      const Key &A = keys[r], &B = keys[r + 1];
-      if (A.e == B.e) return fail(ctx, SWE_EMESH, "triangle %lld repeats a vertex", (long long)A.e);
-      ctx->nb[3 * A.e + A.k] = B.e; ctx->nbk[3 * A.e + A.k] = (int8_t)B.k;
-      ctx->nb[3 * B.e + B.k] = A.e; ctx->nbk[3 * B.e + B.k] = (int8_t)A.k;
-    }
-    r = s;
+  const int32_t* tri = ctx->tri.data();
+  auto ends = [&](int64_t x, int32_t& lo, int32_t& hi) {
+    const int64_t e = x / 3;
+    const int k = (int)(x % 3);
+    const int32_t a = tri[3 * e + (k + 1) % 3], b = tri[3 * e + (k + 2) % 3];
+    lo = std::min(a, b);
+    hi = std::max(a, b);
+  };
+  std::vector<int64_t> start(nv + 1, 0), ent(3 * ne);
+  int32_t lo, hi;
+  for (int64_t x = 0; x < 3 * ne; ++x) { ends(x, lo, hi); ++start[lo + 1]; }
+  for (int64_t v = 0; v < nv; ++v) start[v + 1] += start[v];
+  {
+    std::vector<int64_t> cur(start.begin(), start.end() - 1);
+    for (int64_t x = 0; x < 3 * ne; ++x) { ends(x, lo, hi); ent[cur[lo]++] = x; }
   }
+  for (int64_t v = 0; v < nv; ++v)
+    for (int64_t i = start[v]; i < start[v + 1]; ++i) {
+      const int64_t x = ent[i];
+      if (x < 0) continue;  // the second side of an edge already paired
+      int32_t hx;
+      ends(x, lo, hx);
+      int64_t match = -1;
+      for (int64_t j = i + 1; j < start[v + 1]; ++j) {
+        const int64_t y = ent[j];
+        if (y < 0) continue;
+        ends(y, lo, hi);
+        if (hi != hx) continue;
+        if (match >= 0)
+          return fail(ctx, SWE_EMESH, "edge (%lld,%lld) is shared by more than 2 triangles", (long long)v,
+                      (long long)hx);
+        match = j;
+      }
+      if (match < 0) continue;  // boundary edge
+      const int64_t y = ent[match];
+      const int64_t A = x / 3, B = y / 3;
+      if (A == B) return fail(ctx, SWE_EMESH, "triangle %lld repeats a vertex", (long long)A);
+      ctx->nb[x] = B; ctx->nbk[x] = (int8_t)(y % 3);
+      ctx->nb[y] = A; ctx->nbk[y] = (int8_t)(x % 3);
+      ent[match] = -1;
+    }
   return 0;
 }
 
@@ -466,11 +488,9 @@ static int build_device(swe_ctx* ctx) {
       x.hA = ctx->hv[a]; x.hB = ctx->hv[b];
       ed.push_back(x);
     }
-  std::stable_sort(ed.begin(), ed.end(), [](const E& a, const E& b) {
-    const bool ia = a.R >= 0, ib = b.R >= 0;
-    if (ia != ib) return ia;
-    return a.L < b.L;
-  });
+  // built in increasing left element: a stable partition puts the interior
+  // edges first and keeps each part sorted by the left element
+  std::stable_partition(ed.begin(), ed.end(), [](const E& a) { return a.R >= 0; });
   const int64_t nE = (int64_t)ed.size();
   ctx->nedge = nE;
   if (nE >= (1ll << 27) || ne >= (1ll << 30)) return fail(ctx, SWE_EINVAL, "mesh too large for 27-bit edge slots");

@@ -275,6 +275,36 @@ def test_errors_are_reported_not_faulted():
     assert ei.value.code in (-3, -4)
 
 
+def test_non_manifold_mesh_is_rejected():
+    """three triangles on the edge (1, 2): the adjacency build reports it"""
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0], [0.5, -1.0]])
+    tri = np.array([[0, 1, 2], [1, 3, 2], [1, 2, 4]], np.int32)
+    s = swedg.Solver(g=9.81, cfl=0.2, rk_order=3)
+    with pytest.raises(swedg.SweError) as ei:
+        s.set_mesh(xy, tri)
+    assert ei.value.code == -2 and "more than 2" in str(ei.value)
+    s.set_mesh(xy, tri[:2])
+    s.close()
+
+
+def test_renumbered_mesh_matches_the_oracle():
+    """vertex ids and triangles in random order (no locality in the edge
+    buckets): the right-hand side still equals the oracle's on that mesh"""
+    w = mixed_workload(n=20, seed=3)
+    rng = np.random.default_rng(5)
+    pv = rng.permutation(len(w["xy"]))
+    inv = np.argsort(pv)
+    pt = rng.permutation(len(w["tri"]))
+    w = dict(w, xy=w["xy"][pv], hv=w["hv"][pv], tri=inv[w["tri"][pt]].astype(np.int32), orders=w["orders"][pt],
+             bc_tag=w["bc_tag"][pt])
+    m, P, s = make_pair(w)
+    c = m.project_state(w["ic"])
+    r_o = m.rhs(P, c)
+    r_g = s.rhs(c)
+    assert np.abs(r_g - r_o).max() <= 1e-12 * np.abs(r_o).max()
+    s.close()
+
+
 def test_device_wait_timeout_is_reported_and_the_context_survives():
     """The failure path of the bounded device waits, without a GPU fault: a
     wait that nothing completes runs out, the call returns SWE_ETIMEOUT, and
