@@ -567,13 +567,13 @@ def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, c
                 span += b - a
         return acc / span if span > 0 else None
     occ_a, occ_b = occupancy(0.0, duration / 2), occupancy(duration / 2, duration)
-    # stable: every request of the window done within the drain time and no
-    # growth of the queue over the window (the second half's time-averaged
-    # number of requests in the system at most 1.5 times the first half's,
-    # plus 2).  The p99 of a half is its slowest request or two at these
-    # counts, and request sizes span three decades, so p99 is reported, not
-    # used for the decision.
-    stable = backlog == 0 and occ_a is not None and occ_b is not None and occ_b <= 1.5 * occ_a + 2.0
+    # stable: the server keeps up with the arrivals -- every request of the
+    # window done, within a tenth of the window after the last arrival.  The
+    # request sizes span three decades (the largest take ~20 s alone), so the
+    # p99 of a half window is its slowest request or two and the number of
+    # requests in the system follows when the largest ones arrive: both are
+    # reported, not used for the decision.
+    stable = backlog == 0 and makespan - duration <= 0.1 * duration
     return dict(value=work / makespan, requests=len(prepared), completed=len(srv.done), backlog=backlog,
                 failed=len(srv.failed), makespan_s=makespan, rate=rate,
                 p50_s=pct(lat, 50), p99_s=pct(lat, 99), mean_s=float(lat.mean()) if len(lat) else None,

@@ -14,7 +14,9 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -177,19 +179,56 @@ static const char* g_create_err = "";
 static std::string g_create_err_s;
 
 // ------------------------------------------------------------------ memory
+// Device buffers come from one stream-ordered memory pool per device, shared
+// by the contexts of the process, that keeps freed memory for reuse: building
+// and dropping contexts (ensemble cohorts of a server) then neither maps new
+// memory nor synchronises the device, as cudaMalloc / cudaFree would while
+// other contexts' kernels run.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static int device_pool(int dev, cudaMemPool_t* out) {
+  if (dev < 0 || dev >= 64) return cuda_fail(cudaErrorInvalidDevice, "device_pool", __FILE__, __LINE__);
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps pr{};
+    pr.allocType = cudaMemAllocationTypePinned;
+    pr.location.type = cudaMemLocationTypeDevice;
+    pr.location.id = dev;
+    cudaError_t e = cudaMemPoolCreate(&g_pool[dev], &pr);
+    if (e != cudaSuccess) { g_pool[dev] = nullptr; return cuda_fail(e, "cudaMemPoolCreate", __FILE__, __LINE__); }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  *out = g_pool[dev];
+  return 0;
+}
+
+// every stream of the context idle (before buffers are returned to the pool)
+static void sync_streams(swe_ctx* ctx) {
+  for (cudaStream_t s : {ctx->stream, ctx->stream2, ctx->sg[0], ctx->sg[1], ctx->cin, ctx->cout})
+    if (s) cudaStreamSynchronize(s);
+}
+
 static void free_all(swe_ctx* ctx) {
   if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
-  for (auto& a : ctx->allocs) cudaFree(a.first);
+  if (!ctx->allocs.empty()) sync_streams(ctx);
+  for (auto& a : ctx->allocs) cudaFreeAsync(a.first, ctx->stream);
   ctx->allocs.clear();
   ctx->dev_bytes = 0;
 }
 
+// a buffer in stream order on the context stream; work on the context's other
+// streams is ordered after it by the events that fork them from that stream
 template <typename P>
 static int dalloc(swe_ctx* ctx, P** out, size_t bytes) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&p, bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc", __FILE__, __LINE__);
+  cudaMemPool_t pool;
+  int rc = device_pool(ctx->device, &pool);
+  if (rc) return rc;
+  cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync", __FILE__, __LINE__);
   ctx->allocs.push_back({p, bytes});
   ctx->dev_bytes += (int64_t)bytes;
   *out = (P*)p;
@@ -199,7 +238,8 @@ static int dalloc(swe_ctx* ctx, P** out, size_t bytes) {
 static void dfree(swe_ctx* ctx, void* p) {
   for (size_t i = 0; i < ctx->allocs.size(); ++i)
     if (ctx->allocs[i].first == p) {
-      cudaFree(p);
+      sync_streams(ctx);
+      cudaFreeAsync(p, ctx->stream);
       ctx->dev_bytes -= (int64_t)ctx->allocs[i].second;
       ctx->allocs.erase(ctx->allocs.begin() + (long)i);
       return;
@@ -226,9 +266,9 @@ template <typename V>
 static int upload(swe_ctx* ctx, V** out, const std::vector<V>& h) {
   int rc = dalloc(ctx, out, h.size() * sizeof(V));
   if (rc) return rc;
-  if (!h.empty()) {
-    cudaError_t e = cudaMemcpy(*out, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy", __FILE__, __LINE__);
+  if (!h.empty()) {  // from pageable memory: the call returns once the source has been staged
+    cudaError_t e = cudaMemcpyAsync(*out, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync", __FILE__, __LINE__);
   }
   return 0;
 }
@@ -282,6 +322,28 @@ struct ProfScope {
 };
 
 // ------------------------------------------------------------------ mesh
+// f(a, b) over [0, n) in contiguous chunks on up to 16 host threads: the
+// mesh setup loops, independent per element, edge or vertex (each chunk
+// writes its own range), so the result does not depend on the split.
+template <typename F>
+static void host_parallel(int64_t n, F&& f) {
+  const int64_t min_chunk = 1 << 15;
+  int64_t nt = std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
+  nt = std::min<int64_t>(nt, (n + min_chunk - 1) / min_chunk);
+  if (nt <= 1) {
+    if (n > 0) f((int64_t)0, n);
+    return;
+  }
+  const int64_t per = (n + nt - 1) / nt;
+  std::vector<std::thread> th;
+  for (int64_t t = 1; t < nt; ++t) {
+    const int64_t a = t * per, b = std::min(n, a + per);
+    if (a < b) th.emplace_back([&f, a, b] { f(a, b); });
+  }
+  f((int64_t)0, std::min(n, per));
+  for (auto& x : th) x.join();
+}
+
 static int build_topology(swe_ctx* ctx) {
   // Edge k of triangle e joins vertices a, b (the two other than vertex k).
   // Every edge is filed under its lower vertex (a counting sort over vertex
@@ -306,31 +368,51 @@ static int build_topology(swe_ctx* ctx) {
     std::vector<int64_t> cur(start.begin(), start.end() - 1);
     for (int64_t x = 0; x < 3 * ne; ++x) { ends(x, lo, hi); ent[cur[lo]++] = x; }
   }
-  for (int64_t v = 0; v < nv; ++v)
-    for (int64_t i = start[v]; i < start[v + 1]; ++i) {
-      const int64_t x = ent[i];
-      if (x < 0) continue;  // the second side of an edge already paired
-      int32_t hx;
-      ends(x, lo, hx);
-      int64_t match = -1;
-      for (int64_t j = i + 1; j < start[v + 1]; ++j) {
-        const int64_t y = ent[j];
-        if (y < 0) continue;
-        ends(y, lo, hi);
-        if (hi != hx) continue;
-        if (match >= 0)
-          return fail(ctx, SWE_EMESH, "edge (%lld,%lld) is shared by more than 2 triangles", (long long)v,
-                      (long long)hx);
-        match = j;
+  // pair within each bucket (a vertex's bucket is touched by its chunk only);
+  // a chunk stops at its first bad vertex, and the lowest one is reported
+  struct Bad { int64_t v, what; int kind; };  // kind 1: third triangle on (v, what); 2: triangle `what`
+  std::vector<Bad> bad;
+  std::mutex mu;
+  host_parallel(nv, [&](int64_t v0, int64_t v1) {
+    int32_t lo_, hi_, hx;
+    for (int64_t v = v0; v < v1; ++v)
+      for (int64_t i = start[v]; i < start[v + 1]; ++i) {
+        const int64_t x = ent[i];
+        if (x < 0) continue;  // the second side of an edge already paired
+        ends(x, lo_, hx);
+        int64_t match = -1;
+        for (int64_t j = i + 1; j < start[v + 1]; ++j) {
+          const int64_t y = ent[j];
+          if (y < 0) continue;
+          ends(y, lo_, hi_);
+          if (hi_ != hx) continue;
+          if (match >= 0) {
+            std::lock_guard<std::mutex> g(mu);
+            bad.push_back({v, hx, 1});
+            return;
+          }
+          match = j;
+        }
+        if (match < 0) continue;  // boundary edge
+        const int64_t y = ent[match];
+        const int64_t A = x / 3, B = y / 3;
+        if (A == B) {
+          std::lock_guard<std::mutex> g(mu);
+          bad.push_back({v, A, 2});
+          return;
+        }
+        ctx->nb[x] = B; ctx->nbk[x] = (int8_t)(y % 3);
+        ctx->nb[y] = A; ctx->nbk[y] = (int8_t)(x % 3);
+        ent[match] = -1;
       }
-      if (match < 0) continue;  // boundary edge
-      const int64_t y = ent[match];
-      const int64_t A = x / 3, B = y / 3;
-      if (A == B) return fail(ctx, SWE_EMESH, "triangle %lld repeats a vertex", (long long)A);
-      ctx->nb[x] = B; ctx->nbk[x] = (int8_t)(y % 3);
-      ctx->nb[y] = A; ctx->nbk[y] = (int8_t)(x % 3);
-      ent[match] = -1;
-    }
+  });
+  if (!bad.empty()) {
+    const Bad b = *std::min_element(bad.begin(), bad.end(), [](const Bad& p, const Bad& q) { return p.v < q.v; });
+    if (b.kind == 1)
+      return fail(ctx, SWE_EMESH, "edge (%lld,%lld) is shared by more than 2 triangles", (long long)b.v,
+                  (long long)b.what);
+    return fail(ctx, SWE_EMESH, "triangle %lld repeats a vertex", (long long)b.what);
+  }
   return 0;
 }
 
@@ -417,7 +499,8 @@ static int build_device(swe_ctx* ctx) {
   const RefTables& R = tables();
   // geometry, caller order
   std::vector<double> geo((size_t)NGEO * ne);
-  for (int64_t u = 0; u < ne; ++u) {
+  host_parallel(ne, [&](int64_t u0, int64_t u1) {
+  for (int64_t u = u0; u < u1; ++u) {
     const int32_t* v = &ctx->tri[3 * u];
     const double x0 = ctx->xy[2 * v[0]], y0 = ctx->xy[2 * v[0] + 1];
     const double J00 = ctx->xy[2 * v[1]] - x0, J01 = ctx->xy[2 * v[2]] - x0;
@@ -454,50 +537,70 @@ static int build_device(swe_ctx* ctx) {
     G_(G_SQA) = std::sqrt(0.5 * det);
     G_(G_M0) = R.phi0 * rs;
   }
+  });
   std::vector<double> etb((size_t)12 * ne);
-  for (int64_t u = 0; u < ne; ++u)
-    for (int k = 0; k < 3; ++k) {
-      const double rs = geo[(size_t)G_RS * ne + u];
-      double* t = &etb[(size_t)(3 * u + k) * 4];
-      t[0] = rs * R.EB[2][k][1][0]; t[1] = rs * R.EB[2][k][2][0];
-      t[2] = rs * R.EB[2][k][1][1]; t[3] = rs * R.EB[2][k][2][1];
-    }
-  // edges: left element = the lower caller index, interior edges first, then
-  // sorted by the left element
-  struct E { int32_t L, R, info; double len, nx, ny, hA, hB; };
-  std::vector<E> ed;
-  ed.reserve(3 * ne / 2 + 16);
-  for (int64_t u = 0; u < ne; ++u)
-    for (int k = 0; k < 3; ++k) {
-      const int64_t n = ctx->nb[3 * u + k];
-      if (n >= 0 && n < u) continue;  // created from the other side
-      E x;
-      int32_t Rr = -1, kR = 0, bc;
-      if (n >= 0) {
-        bc = 0;
-        Rr = (int32_t)n; kR = ctx->nbk[3 * u + k];
-      } else {
-        bc = ctx->tag[3 * u + k] == 2 ? 2 : 1;
+  host_parallel(ne, [&](int64_t u0, int64_t u1) {
+    for (int64_t u = u0; u < u1; ++u)
+      for (int k = 0; k < 3; ++k) {
+        const double rs = geo[(size_t)G_RS * ne + u];
+        double* t = &etb[(size_t)(3 * u + k) * 4];
+        t[0] = rs * R.EB[2][k][1][0]; t[1] = rs * R.EB[2][k][2][0];
+        t[2] = rs * R.EB[2][k][1][1]; t[3] = rs * R.EB[2][k][2][1];
       }
-      x.L = (int32_t)u; x.R = Rr;
-      x.info = k | (kR << 2) | (bc << 4);
-      const int32_t a = ctx->tri[3 * u + (k + 1) % 3], b = ctx->tri[3 * u + (k + 2) % 3];
-      const double dx = ctx->xy[2 * b] - ctx->xy[2 * a], dy = ctx->xy[2 * b + 1] - ctx->xy[2 * a + 1];
-      x.len = std::hypot(dx, dy);
-      x.nx = dy / x.len; x.ny = -dx / x.len;
-      x.hA = ctx->hv[a]; x.hB = ctx->hv[b];
-      ed.push_back(x);
+  });
+  // edges: left element = the lower caller index, interior edges first, then
+  // the boundary edges, each part sorted by the left element (an edge is made
+  // by its lower element; counts per element place it without a sort)
+  struct E { int32_t L, R, info; double len, nx, ny, hA, hB; };
+  std::vector<int64_t> offI(ne + 1, 0), offB(ne + 1, 0);
+  host_parallel(ne, [&](int64_t u0, int64_t u1) {
+    for (int64_t u = u0; u < u1; ++u) {
+      int ci = 0, cb = 0;
+      for (int k = 0; k < 3; ++k) {
+        const int64_t n = ctx->nb[3 * u + k];
+        if (n < 0) ++cb;
+        else if (n > u) ++ci;
+      }
+      offI[u + 1] = ci;
+      offB[u + 1] = cb;
     }
-  // built in increasing left element: a stable partition puts the interior
-  // edges first and keeps each part sorted by the left element
-  std::stable_partition(ed.begin(), ed.end(), [](const E& a) { return a.R >= 0; });
+  });
+  for (int64_t u = 0; u < ne; ++u) { offI[u + 1] += offI[u]; offB[u + 1] += offB[u]; }
+  const int64_t nI = offI[ne];
+  std::vector<E> ed((size_t)(nI + offB[ne]));
+  host_parallel(ne, [&](int64_t u0, int64_t u1) {
+    for (int64_t u = u0; u < u1; ++u) {
+      int64_t pi = offI[u], pb = nI + offB[u];
+      for (int k = 0; k < 3; ++k) {
+        const int64_t n = ctx->nb[3 * u + k];
+        if (n >= 0 && n < u) continue;  // made by the other side
+        E x;
+        int32_t Rr = -1, kR = 0, bc;
+        if (n >= 0) {
+          bc = 0;
+          Rr = (int32_t)n; kR = ctx->nbk[3 * u + k];
+        } else {
+          bc = ctx->tag[3 * u + k] == 2 ? 2 : 1;
+        }
+        x.L = (int32_t)u; x.R = Rr;
+        x.info = k | (kR << 2) | (bc << 4);
+        const int32_t a = ctx->tri[3 * u + (k + 1) % 3], b = ctx->tri[3 * u + (k + 2) % 3];
+        const double dx = ctx->xy[2 * b] - ctx->xy[2 * a], dy = ctx->xy[2 * b + 1] - ctx->xy[2 * a + 1];
+        x.len = std::hypot(dx, dy);
+        x.nx = dy / x.len; x.ny = -dx / x.len;
+        x.hA = ctx->hv[a]; x.hB = ctx->hv[b];
+        ed[(size_t)(n >= 0 ? pi++ : pb++)] = x;
+      }
+    }
+  });
   const int64_t nE = (int64_t)ed.size();
   ctx->nedge = nE;
   if (nE >= (1ll << 27) || ne >= (1ll << 30)) return fail(ctx, SWE_EINVAL, "mesh too large for 27-bit edge slots");
   std::vector<int32_t> eLu(nE), eRu(nE), einfo(nE), eedge_u(3 * ne, -1), emem(nE);
   std::vector<double> egeo((size_t)NEGEO * nE);
-  int64_t nint = 0;
-  for (int64_t i = 0; i < nE; ++i) {
+  const int64_t nint = nI;
+  host_parallel(nE, [&](int64_t i0, int64_t i1) {
+  for (int64_t i = i0; i < i1; ++i) {
     eLu[i] = ed[i].L; eRu[i] = ed[i].R; einfo[i] = ed[i].info;
     emem[i] = ctx->member_user[ed[i].L];
     auto E_ = [&](int row) -> double& { return egeo[(size_t)row * nE + i]; };
@@ -509,10 +612,10 @@ static int build_device(swe_ctx* ctx) {
     E_(E_WLEN) = 0.5 * ed[i].len * R.ew[2][0];  // the two weights of the base rule are equal
     E_(E_NXW) = E_(E_WLEN) * ed[i].nx;
     E_(E_NYW) = E_(E_WLEN) * ed[i].ny;
-    if (ed[i].R >= 0) ++nint;
     eedge_u[(size_t)(ed[i].info & 3) * ne + ed[i].L] = (int32_t)(i << 1);
     if (ed[i].R >= 0) eedge_u[(size_t)((ed[i].info >> 2) & 3) * ne + ed[i].R] = (int32_t)((i << 1) | 1);
   }
+  });
   int rc = 0;
   // the mesh in caller order (read by every regrouping) and the fixed edge data
   double *d_geo_u, *d_etb_u, *d_egeo;
@@ -543,7 +646,7 @@ static int build_device(swe_ctx* ctx) {
         (rc = dalloc(ctx, &W.psum, 8 * (size_t)be)) || (rc = dalloc(ctx, &W.poff, 8 * (size_t)(be + 1))) ||
         (rc = dalloc(ctx, &W.info, 8 * 16)))
       return cuda_err(ctx, rc);
-    cudaMemset(W.info, 0, 8 * 16);
+    cudaMemsetAsync(W.info, 0, 8 * 16, ctx->stream);
   }
   ctx->d_perm = D.perm;
   ctx->d_off = D.off;
@@ -554,11 +657,11 @@ static int build_device(swe_ctx* ctx) {
   // base state, velocity and fluxes (sized by the mesh)
   for (int s = 0; s < 3; ++s) {
     if ((rc = dalloc(ctx, &ctx->st[s].cb, sizeof(double) * 9 * ne))) return cuda_err(ctx, rc);
-    cudaMemset(ctx->st[s].cb, 0, sizeof(double) * 9 * ne);
+    cudaMemsetAsync(ctx->st[s].cb, 0, sizeof(double) * 9 * ne, ctx->stream);
     ctx->st[s].cb32 = nullptr;
     if (ctx->corr32) {
       if ((rc = dalloc(ctx, &ctx->st[s].cb32, sizeof(float) * 9 * ne))) return cuda_err(ctx, rc);
-      cudaMemset(ctx->st[s].cb32, 0, sizeof(float) * 9 * ne);
+      cudaMemsetAsync(ctx->st[s].cb32, 0, sizeof(float) * 9 * ne, ctx->stream);
     }
   }
   if ((rc = dalloc(ctx, &ctx->vel.ub, sizeof(double) * 6 * ne))) return cuda_err(ctx, rc);
@@ -576,24 +679,22 @@ static int build_device(swe_ctx* ctx) {
       (rc = dalloc(ctx, &ctx->d_status, sizeof(unsigned))) ||
       (rc = dalloc(ctx, &ctx->d_mstatus, sizeof(unsigned) * nm)))
     return cuda_err(ctx, rc);
-  cudaMemset(ctx->d_mstatus, 0, sizeof(unsigned) * nm);
-  cudaMemset(ctx->d_dt, 0, sizeof(double) * nm);
+  cudaMemsetAsync(ctx->d_mstatus, 0, sizeof(unsigned) * nm, ctx->stream);
+  cudaMemsetAsync(ctx->d_dt, 0, sizeof(double) * nm, ctx->stream);
   if ((rc = launch_reset_min(ctx->stream, ctx->d_dmin, ctx->nmem))) return cuda_err(ctx, rc);
   ctx->nred = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (ne + 255) / 256));
   if ((rc = dalloc(ctx, &ctx->d_partial, sizeof(double) * ctx->nred)) || (rc = dalloc(ctx, &ctx->d_red, sizeof(double) * 2)))
     return cuda_err(ctx, rc);
-  cudaMemset(ctx->d_t, 0, sizeof(double) * nm);
-  cudaMemset(ctx->d_status, 0, sizeof(unsigned));
+  cudaMemsetAsync(ctx->d_t, 0, sizeof(double) * nm, ctx->stream);
+  cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream);
   ctx->dm.mstatus = ctx->d_mstatus;
   if ((rc = dalloc(ctx, &ctx->d_work, sizeof(unsigned) * 4))) return cuda_err(ctx, rc);
-  cudaMemset(ctx->d_work, 0, sizeof(unsigned) * 4);
-  cudaError_t e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) return cuda_err(ctx, cuda_fail(e, "build_device", __FILE__, __LINE__));
+  cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned) * 4, ctx->stream);
   // the order-dependent part
-  CU(cudaMemcpy(ctx->d_newp, ctx->p_user.data(), (size_t)ne, cudaMemcpyHostToDevice));
+  CU(cudaMemcpyAsync(ctx->d_newp, ctx->p_user.data(), (size_t)ne, cudaMemcpyHostToDevice, ctx->stream));
   ctx->packed_n = -1;
   CK(regroup(ctx, false));
-  e = cudaDeviceSynchronize();
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_err(ctx, cuda_fail(e, "build_device", __FILE__, __LINE__));
   return 0;
 }
@@ -883,20 +984,35 @@ int swe_create(swe_ctx** out, const swe_params* params) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     set_sm_count(nsm);
   }
-  upload_base_tables();
-  corr64::upload_tables();
-  corr32::upload_tables();
-  corrtc::upload_tables();
-  if (corrtc::upload_tc_tables() != 0) {
-    g_create_err = "tensor-core operand upload failed";
-    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
-    delete ctx;
-    return SWE_ECUDA;
+  // the reference tables go to the device's constant memory once per process
+  // (a later write would race with the kernels of contexts already running)
+  {
+    static std::mutex mu;
+    static bool done[64] = {};
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64) {
+      g_create_err = "device ordinal out of range";
+      e = cudaErrorInvalidDevice;
+    } else if (!done[dev]) {
+      upload_base_tables();
+      corr64::upload_tables();
+      corr32::upload_tables();
+      corrtc::upload_tables();
+      if (corrtc::upload_tc_tables() != 0) {
+        g_create_err = "tensor-core operand upload failed";
+        e = cudaErrorUnknown;
+      } else {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+          g_create_err_s = std::string("table upload failed: ") + cudaGetErrorString(e);
+          g_create_err = g_create_err_s.c_str();
+        } else {
+          done[dev] = true;
+        }
+      }
+    }
   }
-  e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
-    g_create_err_s = std::string("table upload failed: ") + cudaGetErrorString(e);
-    g_create_err = g_create_err_s.c_str();
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return SWE_ECUDA;
@@ -907,8 +1023,9 @@ int swe_create(swe_ctx** out, const swe_params* params) {
 
 void swe_destroy(swe_ctx* ctx) {
   if (!ctx) return;
-  cudaStreamSynchronize(ctx->stream);
+  sync_streams(ctx);
   free_all(ctx);
+  cudaStreamSynchronize(ctx->stream);  // the frees are done before the stream goes
   for (auto& ev : ctx->evs) { cudaEventDestroy(ev.a); cudaEventDestroy(ev.b); }
   for (auto ev : ctx->pool) cudaEventDestroy(ev);
   for (cudaEvent_t ev : {ctx->ev_fork, ctx->ev_u1, ctx->ev_u2, ctx->ev_c, ctx->ev_dt, ctx->ev_c2, ctx->ev_gf,
@@ -936,19 +1053,40 @@ int swe_set_mesh(swe_ctx* ctx, int64_t nv, const double* xy, int64_t ne, const i
   ctx->hv.assign(nv, 0.0);
   ctx->tri.resize(3 * ne);
   ctx->tag.assign(3 * ne, 0);
-  for (int64_t e = 0; e < ne; ++e) {
-    int32_t v[3] = {tri[3 * e], tri[3 * e + 1], tri[3 * e + 2]};
-    int8_t t[3] = {0, 0, 0};
-    if (bc_tag) for (int k = 0; k < 3; ++k) t[k] = bc_tag[3 * e + k];
-    for (int k = 0; k < 3; ++k)
-      if (v[k] < 0 || v[k] >= nv) { ctx->have_mesh = false; return fail(ctx, SWE_EMESH, "triangle %lld: vertex id out of range", (long long)e); }
-    for (int k = 0; k < 3; ++k)
-      if (t[k] < 0 || t[k] > 2) { ctx->have_mesh = false; return fail(ctx, SWE_EINVAL, "triangle %lld: boundary tag must be 0, 1 or 2", (long long)e); }
-    const double cr = (xy[2 * v[1]] - xy[2 * v[0]]) * (xy[2 * v[2] + 1] - xy[2 * v[0] + 1]) -
-                      (xy[2 * v[2]] - xy[2 * v[0]]) * (xy[2 * v[1] + 1] - xy[2 * v[0] + 1]);
-    if (!(cr != 0.0) || !std::isfinite(cr)) { ctx->have_mesh = false; return fail(ctx, SWE_EMESH, "triangle %lld is degenerate", (long long)e); }
-    if (cr < 0.0) { std::swap(v[1], v[2]); std::swap(t[1], t[2]); }
-    for (int k = 0; k < 3; ++k) { ctx->tri[3 * e + k] = v[k]; ctx->tag[3 * e + k] = t[k]; }
+  // per chunk the first bad triangle (1: vertex id, 2: boundary tag, 3: degenerate); the lowest is reported
+  std::vector<std::pair<int64_t, int>> bad;
+  std::mutex mu;
+  host_parallel(ne, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e) {
+      int32_t v[3] = {tri[3 * e], tri[3 * e + 1], tri[3 * e + 2]};
+      int8_t t[3] = {0, 0, 0};
+      if (bc_tag) for (int k = 0; k < 3; ++k) t[k] = bc_tag[3 * e + k];
+      int why = 0;
+      for (int k = 0; k < 3; ++k)
+        if (v[k] < 0 || v[k] >= nv) why = 1;
+      for (int k = 0; k < 3 && !why; ++k)
+        if (t[k] < 0 || t[k] > 2) why = 2;
+      double cr = 0.0;
+      if (!why) {
+        cr = (xy[2 * v[1]] - xy[2 * v[0]]) * (xy[2 * v[2] + 1] - xy[2 * v[0] + 1]) -
+             (xy[2 * v[2]] - xy[2 * v[0]]) * (xy[2 * v[1] + 1] - xy[2 * v[0] + 1]);
+        if (!(cr != 0.0) || !std::isfinite(cr)) why = 3;
+      }
+      if (why) {
+        std::lock_guard<std::mutex> g(mu);
+        bad.push_back({e, why});
+        return;
+      }
+      if (cr < 0.0) { std::swap(v[1], v[2]); std::swap(t[1], t[2]); }
+      for (int k = 0; k < 3; ++k) { ctx->tri[3 * e + k] = v[k]; ctx->tag[3 * e + k] = t[k]; }
+    }
+  });
+  if (!bad.empty()) {
+    const auto b = *std::min_element(bad.begin(), bad.end());
+    ctx->have_mesh = false;
+    if (b.second == 1) return fail(ctx, SWE_EMESH, "triangle %lld: vertex id out of range", (long long)b.first);
+    if (b.second == 2) return fail(ctx, SWE_EINVAL, "triangle %lld: boundary tag must be 0, 1 or 2", (long long)b.first);
+    return fail(ctx, SWE_EMESH, "triangle %lld is degenerate", (long long)b.first);
   }
   ctx->p_user.assign(ne, 1);
   ctx->member_user.assign(ne, 0);
@@ -1206,13 +1344,16 @@ static int ensure_async(swe_ctx* ctx) {
         CU(cudaEventRecord(*ev, ctx->stream));  // every slot starts free
       }
   }
+  bool fresh = false;
   for (int k = 0; k < 2; ++k) {
     if (!ctx->d_stage_in[k]) {
       int rc = dalloc(ctx, &ctx->d_stage_in[k], sizeof(double) * (size_t)std::max<int64_t>(ctx->packed_n, 1));
       if (!rc) rc = dalloc(ctx, &ctx->d_stage_out[k], sizeof(double) * (size_t)std::max<int64_t>(ctx->packed_n, 1));
       if (rc) return cuda_err(ctx, rc);
+      fresh = true;
     }
   }
+  if (fresh) CU(cudaStreamSynchronize(ctx->stream));  // the copy streams use them next
   return 0;
 }
 

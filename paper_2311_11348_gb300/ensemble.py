@@ -49,7 +49,9 @@ class Ensemble:
         if all(hasattr(s, "is_cuda") and s.is_cuda for s in states):
             import torch
             c = torch.cat([s.to(torch.float64) for s in states], dim=2).contiguous()
-            torch.cuda.synchronize()  # the library reads on its own stream
+            # the library reads on its own stream: wait for torch's stream only
+            # (a device-wide sync would also wait for other contexts' steps)
+            torch.cuda.current_stream().synchronize()
         else:
             c = np.zeros((3, KMAX, int(self.e0[-1])))
             for i, s in enumerate(states):
@@ -62,8 +64,8 @@ class Ensemble:
         if device:
             import torch
             c = torch.empty((3, KMAX, int(self.e0[-1])), dtype=torch.float64, device="cuda")
-            torch.cuda.synchronize()
-            self.solver.get_state(c)
+            torch.cuda.current_stream().synchronize()  # the memory is free on torch's stream
+            self.solver.get_state(c)  # written on the library's stream, complete on return
             return [c[:, :, self.e0[i]:self.e0[i + 1]].clone() for i in range(self.n)]
         c, _ = self.solver.get_state()
         return [c[:, :, self.e0[i]:self.e0[i + 1]].copy() for i in range(self.n)]
