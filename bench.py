@@ -529,16 +529,16 @@ def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, c
     busy = 0.0
     stop = None if drain_s is None else duration + drain_s
     occ = []  # (time, requests in the system: admitted or waiting) at every scheduling point
-    while pending or srv.waiting or srv.active:
+    while pending or srv.waiting or srv.in_flight:
         now = time.perf_counter() - t0
-        occ.append((now, len(srv.waiting) + len(srv.active)))
+        occ.append((now, len(srv.waiting) + len(srv.in_flight)))
         if stop is not None and now >= stop:
             break
         while pending and pending[0][0] <= now:
             t_arr, r = pending.pop(0)
             r.arrival = t0 + t_arr
             srv.submit(r)
-        if not srv.waiting and not srv.active:
+        if not srv.waiting and not srv.in_flight:
             time.sleep(max(0.0, min(0.05, pending[0][0] - now)))
             continue
         tb = time.perf_counter()
@@ -546,7 +546,7 @@ def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, c
         busy += time.perf_counter() - tb
     makespan = time.perf_counter() - t0
     clk = clocks.stop()
-    backlog = len(pending) + len(srv.waiting) + len(srv.active)
+    backlog = len(pending) + len(srv.waiting) + len(srv.in_flight)
     srv.close()
     lat = srv.latencies()
     arr = np.array([r.arrival - t0 for r in srv.done])
@@ -650,7 +650,7 @@ def bench_serving(args, world):
         return r
     r = one(args.rate)
     sweep = [one(x) for x in args.rates] if args.rates else []
-    stable = [x["rate"] for x in sweep if x["stable"]]
+    stable = [x["rate"] for x in [r] + sweep if x["stable"]]
     pool = f", meshes drawn from a pool of {args.pool} seeded members" if args.pool else ""
     drain = (f"; the loop stops {args.drain_s} s after the last arrival (unfinished requests: backlog)"
              if args.drain_s is not None else "; every request runs to completion")
@@ -677,11 +677,11 @@ def bench_serving(args, world):
         "roofline": None,
     }
     if sweep:
-        line["rate_sweep"] = [{k: x[k] for k in ("rate", "requests", "completed", "backlog", "p50_s", "p99_s",
-                                                "p99_first_half_s", "p99_second_half_s", "in_system_first_half",
-                                                "in_system_second_half", "stable", "value",
-                                                "offered_dof_stage_per_s", "makespan_s", "rebuild_s")}
-                              for x in sweep]
+        line["rate_sweep"] = sorted(({k: x[k] for k in ("rate", "requests", "completed", "backlog", "p50_s", "p99_s",
+                                                       "p99_first_half_s", "p99_second_half_s", "in_system_first_half",
+                                                       "in_system_second_half", "stable", "value",
+                                                       "offered_dof_stage_per_s", "makespan_s", "rebuild_s")}
+                                     for x in [r] + sweep), key=lambda x: x["rate"])
         line["highest_stable_rate_per_s"] = max(stable) if stable else None
     return line
 

@@ -11,9 +11,12 @@ GPU.  A finished request's state is copied out at once; its cohort is
 compacted (rebuilt with the continuing requests, states moved device to
 device) when requests wait for memory or less than half of it is still live,
 and the two smallest cohorts are merged when there are more than max_cohorts.
-Admitting a request therefore costs one context build of its own cohort, not
-of everything on the GPU, and that build runs on the host while the running
-cohorts take their next chunk (the new cohort joins at the following one).
+Every context build runs on the host thread pool while the other cohorts
+take their next chunk: a new cohort joins at the end of the round that
+admitted it, a compacted or merged one (whose requests pause meanwhile) at
+the end of the following round.  So admitting a request costs one context
+build of its own cohort, not of everything on the GPU, and no build holds up
+the cohorts already running.
 
 This module is host-side scheduling only; every step runs in the CUDA library.
 """
@@ -21,6 +24,7 @@ from __future__ import annotations
 
 import concurrent.futures
 import dataclasses
+import threading
 import time
 
 import numpy as np
@@ -141,25 +145,33 @@ class Server:
         self.clock = clock
         self.waiting: list[Request] = []
         self.cohorts: list[Cohort] = []
+        self.pending: list = []  # [future of a Cohort, its bytes, the round it joins at the end of, its requests]
         self.done: list[Request] = []
         self.failed: list[Request] = []
         self.h_min = h_min
         self.dof_stage_updates = 0
         self.rebuilds = 0
-        self.rebuild_s = 0.0    # host time spent building cohort contexts
+        self.rebuild_s = 0.0    # host time spent building cohort contexts (mostly beside the GPU work)
         self.launches = 0       # kernels launched by closed cohort contexts
-        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=max_cohorts + 2)
+        self.round = 0
+        self._lock = threading.Lock()
+        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=max_cohorts + 4)
 
     @property
     def active(self):
         return [r for c in self.cohorts for r, l in zip(c.reqs, c.live) if l]
+
+    @property
+    def in_flight(self):
+        """admitted and unfinished: running, or in a cohort being built"""
+        return self.active + [r for p in self.pending for r in p[3]]
 
     def submit(self, req: Request):
         req.arrival = self.clock() if req.arrival <= 0.0 else req.arrival
         self.waiting.append(req)
 
     def _used(self):
-        return sum(c.nbytes for c in self.cohorts)
+        return sum(c.nbytes for c in self.cohorts) + sum(p[1] for p in self.pending)
 
     def _close(self, c):
         prof = getattr(c.ens.solver, "profile_read", None) if hasattr(c.ens, "solver") else None
@@ -170,12 +182,18 @@ class Server:
     def _build(self, reqs, keep):
         t0 = self.clock()
         c = Cohort(reqs, self.kw, self.precision, self.device_resident, keep)
-        self.rebuilds += 1
-        self.rebuild_s += self.clock() - t0
+        with self._lock:
+            self.rebuilds += 1
+            self.rebuild_s += self.clock() - t0
         return c
 
-    def _rebuild(self, cohorts):
-        """one cohort holding the live requests of `cohorts` (states and times kept on the device)"""
+    def _build_later(self, reqs, keep, due):
+        nbytes = sum(footprint(r, self.precision) for r in reqs)
+        self.pending.append([self.pool.submit(self._build, reqs, keep), nbytes, due, list(reqs)])
+
+    def _rebuild_later(self, cohorts, due):
+        """the live requests of `cohorts` into one new cohort, built on the pool
+        (states and times taken now, on the device); the old contexts close"""
         keep, reqs = {}, []
         for c in cohorts:
             states = c.ens.states(device=self.device_resident)
@@ -186,7 +204,18 @@ class Server:
                     keep[("t", r.rid)] = t[i]
                     reqs.append(r)
             self._close(c)
-        return self._build(reqs, keep) if reqs else None
+        if reqs:
+            self._build_later(reqs, keep, due)
+
+    def _join(self, upto=None):
+        """cohorts whose build is due by round `upto` (all when None) join the running ones"""
+        keep = []
+        for p in self.pending:
+            if upto is None or p[2] <= upto:
+                self.cohorts.append(p[0].result())
+            else:
+                keep.append(p)
+        self.pending = keep
 
     @staticmethod
     def _run_cohort(c, chunk):
@@ -217,28 +246,28 @@ class Server:
 
     def step(self):
         """One scheduling round: admit, run a chunk on every cohort, retire.  Returns False when idle."""
+        rnd = self.round
+        self.round += 1
         admitted = []
         used = self._used()
         while self.waiting:
             r = self.waiting[0]
             f = footprint(r, self.precision)
-            if (self.cohorts or admitted) and used + f > self.budget:
+            if (self.cohorts or self.pending or admitted) and used + f > self.budget:
                 break
             self.waiting.pop(0)
             r.admitted = self.clock()
             admitted.append(r)
             used += f
-        pending = None
         if admitted:
-            if self.cohorts:  # build the new cohort on the host while the running ones take their chunk
-                pending = self.pool.submit(self._build, admitted, {})
+            if self.cohorts:  # built on the host while the running cohorts take their chunk
+                self._build_later(admitted, {}, rnd)
             else:
                 self.cohorts.append(self._build(admitted, {}))
         active = self.active
         if not active:
-            if pending is not None:
-                self.cohorts.append(pending.result())
-            return bool(self.cohorts)
+            self._join()
+            return bool(self.cohorts or self.waiting)
         chunk = min(self.max_chunk, min(r.steps - r.done_steps for r in active))
         errors = list(self.pool.map(lambda c: self._run_cohort(c, chunk), self.cohorts))
         failed = set()
@@ -251,7 +280,7 @@ class Server:
             r.done_steps += chunk
             K = np.array(KP)[np.asarray(r.mesh["orders"], np.int64)]
             self.dof_stage_updates += chunk * self.kw["rk_order"] * 3 * int(K.sum())
-        # retire
+        # retire; compactions are built on the pool and join at the end of the next round
         now = None
         keep_cohorts = []
         for c in self.cohorts:
@@ -270,16 +299,15 @@ class Server:
             if not any(c.live):
                 self._close(c)
             elif id(c) in failed or (fin and (self.waiting or c.live_fraction() < 0.5)):  # evicted: always compact
-                keep_cohorts.append(self._rebuild([c]))
+                self._rebuild_later([c], rnd + 1)
             else:
                 keep_cohorts.append(c)
         self.cohorts = keep_cohorts
-        if pending is not None:  # the new cohort joins for the next chunk
-            self.cohorts.append(pending.result())
-        while len(self.cohorts) > self.max_cohorts:
+        self._join(upto=rnd)
+        while len(self.cohorts) + len(self.pending) > self.max_cohorts and len(self.cohorts) >= 2:
             a, b = sorted(self.cohorts, key=lambda c: c.nbytes)[:2]
             self.cohorts = [c for c in self.cohorts if c is not a and c is not b]
-            self.cohorts.append(self._rebuild([a, b]))
+            self._rebuild_later([a, b], rnd + 1)
         return True
 
     def run_until_idle(self):
@@ -290,6 +318,7 @@ class Server:
         return np.array([r.finished - r.arrival for r in self.done])
 
     def close(self):
+        self._join()
         for c in self.cohorts:
             self._close(c)
         self.cohorts = []

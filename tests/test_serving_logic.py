@@ -59,10 +59,11 @@ def test_admission_chunking_and_results(monkeypatch):
     runs = [e for e in FakeUnion.log if e[0] == "run"]
     builds = [e for e in FakeUnion.log if e[0] == "build"]
     # 0 and 1 fit the budget together and form one cohort; the chunk stops at 0's end;
-    # 1's cohort is compacted because 2 waits; 2's cohort is built while 1 runs its
-    # next chunk (to its end) and runs after that
+    # 1's cohort is compacted because 2 waits, built on the pool during the next
+    # round, in which 2's cohort (built at once: nothing else runs) takes its 20
+    # steps; 1 rejoins at the end of that round and runs to its end
     assert runs[0] == ("run", 30, 2)
-    assert runs[1:] == [("run", 40, 1), ("run", 20, 1)]
+    assert runs[1:] == [("run", 20, 1), ("run", 40, 1)]
     assert builds == [("build", 2), ("build", 1), ("build", 1)]
     assert srv.latencies().shape == (3,)
 
