@@ -20,26 +20,13 @@
 
 namespace swedg {
 
-__constant__ double cB2[3][3][2];   // phihat_i(gamma_k(s_g)), i < 3, 2-point rule
-__constant__ double cW2[2];         // weights of the 2-point rule on [0,1]
-__constant__ double cS2[2];         // its points
-__constant__ double cT1[3][3][3];   // T[n][i][j] for n, i, j < 3
-__constant__ double cPhi0;          // phihat_1 = sqrt 2
+__constant__ double cTs[6];  // T[1][1][1], T[2][1][1], T[1][1][2], T[2][1][2], T[1][2][2], T[2][2][2] over phihat_1
 
 void upload_base_tables() {
   const RefTables& R = tables();
-  double B[3][3][2], T1[3][3][3];
-  for (int k = 0; k < 3; ++k)
-    for (int i = 0; i < 3; ++i)
-      for (int g = 0; g < 2; ++g) B[k][i][g] = R.EB[2][k][i][g];
-  for (int n = 0; n < 3; ++n)
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) T1[n][i][j] = R.T[n][i][j];
-  cudaMemcpyToSymbol(cB2, B, sizeof B);
-  cudaMemcpyToSymbol(cW2, R.ew[2], sizeof(double) * 2);
-  cudaMemcpyToSymbol(cS2, R.es[2], sizeof(double) * 2);
-  cudaMemcpyToSymbol(cT1, T1, sizeof T1);
-  cudaMemcpyToSymbol(cPhi0, &R.phi0, sizeof(double));
+  const double Ts[6] = {R.T[1][1][1] / R.phi0, R.T[2][1][1] / R.phi0, R.T[1][1][2] / R.phi0,
+                        R.T[2][1][2] / R.phi0, R.T[1][2][2] / R.phi0, R.T[2][2][2] / R.phi0};
+  cudaMemcpyToSymbol(cTs, Ts, sizeof Ts);
 }
 
 static inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
@@ -204,6 +191,10 @@ int launch_to_user(cudaStream_t s, const DevMesh& m, const Groups& G, const int3
 // auxiliary system for p <= 1 (Sect. 3):  M_H u = U, M_H v = V with
 //   M_H[i][j] = (1/s) sum_{n < K(i,j)} H_n T[n][i][j],  K(1,1) = 1, else 3.
 // The 3 x 3 symmetric system is solved with its adjugate (one division).
+// The basis is orthonormal with the constant phihat_1, so T[0][i][j] =
+// T[i][0][j] = phihat_1 delta_ij: over phihat_1 the first row and column are
+// H_0, H_1, H_2 and the other entries need the six T[n][i][j] with n, i, j
+// >= 1 only (the factor comes back in the final scale).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_usolve_base(DevMesh m, int64_t n_end, Phys ph, const double* __restrict__ cb,
                                                      double* __restrict__ ub, float* __restrict__ ub32,
@@ -216,13 +207,13 @@ __global__ void __launch_bounds__(256) k_usolve_base(DevMesh m, int64_t n_end, P
     const double rs = m.geo[G_RS * ne + e];
     const double H0 = cb[0 * ne + e] + m.geo[G_HB0 * ne + e];
     const double U0 = cb[3 * ne + e], V0 = cb[6 * ne + e];
-    if (!(H0 * cPhi0 * rs > ph.h_min)) {
+    if (!(H0 * m.geo[G_M0 * ne + e] > ph.h_min)) {  // mean depth: mode 0 times phi_{e,1} = phihat_1 / s_e
       atomicOr(status, (unsigned)ST_DEPTH);
       atomicOr(m.mstatus + m.mem[e], (unsigned)ST_DEPTH);
     }
     double v[6];
     if (m.p[e] == 0) {
-      const double r = 1.0 / (H0 * cT1[0][0][0] * rs);
+      const double r = 1.0 / (H0 * m.geo[G_M0 * ne + e]);
       v[0] = U0 * r; v[1] = 0.0; v[2] = 0.0;
       v[3] = V0 * r; v[4] = 0.0; v[5] = 0.0;
     } else {
@@ -230,18 +221,17 @@ __global__ void __launch_bounds__(256) k_usolve_base(DevMesh m, int64_t n_end, P
       const double H2 = cb[2 * ne + e] + m.geo[G_HB2 * ne + e];
       const double U1 = cb[4 * ne + e], U2 = cb[5 * ne + e];
       const double V1 = cb[7 * ne + e], V2 = cb[8 * ne + e];
-      // entries (scaled by s: the 1/s factor cancels in the adjugate solve up to a final scale)
-      const double a = H0 * cT1[0][0][0];
-      const double b = H0 * cT1[0][0][1] + H1 * cT1[1][0][1] + H2 * cT1[2][0][1];
-      const double c = H0 * cT1[0][0][2] + H1 * cT1[1][0][2] + H2 * cT1[2][0][2];
-      const double d = H0 * cT1[0][1][1] + H1 * cT1[1][1][1] + H2 * cT1[2][1][1];
-      const double f = H0 * cT1[0][1][2] + H1 * cT1[1][1][2] + H2 * cT1[2][1][2];
-      const double h = H0 * cT1[0][2][2] + H1 * cT1[1][2][2] + H2 * cT1[2][2][2];
-      // M = (1/s) [[a b c][b d f][c f h]];  u = s * adj(S) U / det(S), S = s M
+      // entries of S / phihat_1 with S = s M (the 1/s factor cancels in the
+      // adjugate solve up to a final scale)
+      const double a = H0, b = H1, c = H2;
+      const double d = H0 + H1 * cTs[0] + H2 * cTs[1];
+      const double f = H1 * cTs[2] + H2 * cTs[3];
+      const double h = H0 + H1 * cTs[4] + H2 * cTs[5];
+      // M = (phihat_1 / s) [[a b c][b d f][c f h]];  u = s adj(S') U / (phihat_1 det(S'))
       const double C00 = d * h - f * f, C01 = c * f - b * h, C02 = b * f - c * d;
       const double C11 = a * h - c * c, C12 = b * c - a * f, C22 = a * d - b * b;
       const double det = a * C00 + b * C01 + c * C02;
-      const double r = 1.0 / (det * rs);
+      const double r = 1.0 / (det * m.geo[G_M0 * ne + e]);
       v[0] = (C00 * U0 + C01 * U1 + C02 * U2) * r; v[1] = (C01 * U0 + C11 * U1 + C12 * U2) * r;
       v[2] = (C02 * U0 + C12 * U1 + C22 * U2) * r; v[3] = (C00 * V0 + C01 * V1 + C02 * V2) * r;
       v[4] = (C01 * V0 + C11 * V1 + C12 * V2) * r; v[5] = (C02 * V0 + C12 * V1 + C22 * V2) * r;

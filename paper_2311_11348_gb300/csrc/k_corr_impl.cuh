@@ -171,27 +171,36 @@ __device__ __forceinline__ void load_modes(T (&out)[K], const T* __restrict__ ba
 // the two O(g |xi| h_b) integrals otherwise cancel to a residual several
 // orders of magnitude smaller and carry their rounding error into it.
 // ---------------------------------------------------------------------------
-template <int K, int Q, int KL>
-__device__ __forceinline__ void volume_q(T (&r)[3], const T (&xi)[K], const T (&U)[K], const T (&V)[K],
+// The structural zeros depend on the degrees of q, i, j only, so one body
+// serves every test mode of degree DQ (q a run-time value: the tensors are
+// read with a block-uniform index, and K = 15 needs 4 code bodies instead of
+// 14, which the instruction cache holds); QR stands for the degree class in
+// the compile-time predicates.
+template <int DQ>
+__host__ __device__ constexpr int qrep() { return DQ <= 1 ? DQ : Kof(DQ - 1); }
+
+template <int K, int DQ, int KL>
+__device__ __forceinline__ void volume_c(T (&r)[3], int q, const T (&xi)[K], const T (&U)[K], const T (&V)[K],
                                          const T (&uc)[K], const T (&vc)[K], const T (&pp)[K], const T (&hb)[3],
                                          const T (&Uc)[KL], const T (&Vc)[KL], T rs, T J0, T J1, T J2, T J3,
                                          T g) {
+  constexpr int QR = qrep<DQ>();
   T am = 0;
   sfor<0, KL>([&](auto i) {
-    if constexpr (dnz(Q, i) && !base2(Q, i)) am += Uc[i] * cD[0][Q][i] + Vc[i] * cD[1][Q][i];
+    if constexpr (dnz(QR, i) && !base2(QR, i)) am += Uc[i] * cD[0][q][i] + Vc[i] * cD[1][q][i];
   });
   T aU = 0, aV = 0, Px = 0, Py = 0;
   sfor<0, K>([&](auto i) {
     constexpr bool any = [] {
       for (int j = 0; j < K; ++j)
-        if (gnz(Q, decltype(i)::value, j) && !base3(Q, decltype(i)::value, j)) return true;
+        if (gnz(QR, decltype(i)::value, j) && !base3(QR, decltype(i)::value, j)) return true;
       return false;
     }();
     if constexpr (any) {
       T w = 0, px = 0, py = 0;
       sfor<0, K>([&](auto j) {
-        if constexpr (gnz(Q, i, j) && !base3(Q, i, j)) {
-          const T gx = cG[0][Q][pk(i, j)], gy = cG[1][Q][pk(i, j)];
+        if constexpr (gnz(QR, i, j) && !base3(QR, i, j)) {
+          const T gx = cG[0][q][pk(i, j)], gy = cG[1][q][pk(i, j)];
           w += uc[j] * gx + vc[j] * gy;
           T pj = pp[j];
           if constexpr (i >= 3 && j < 3) pj += hb[j];
@@ -208,12 +217,22 @@ __device__ __forceinline__ void volume_q(T (&r)[3], const T (&xi)[K], const T (&
   r[2] = rs * (aV + g * (J1 * Px + J3 * Py));
 }
 
-// the elevation row of volume_q alone
+// one test mode Q known at compile time
 template <int K, int Q, int KL>
-__device__ __forceinline__ T volume_xi(const T (&Uc)[KL], const T (&Vc)[KL]) {
+__device__ __forceinline__ void volume_q(T (&r)[3], const T (&xi)[K], const T (&U)[K], const T (&V)[K],
+                                         const T (&uc)[K], const T (&vc)[K], const T (&pp)[K], const T (&hb)[3],
+                                         const T (&Uc)[KL], const T (&Vc)[KL], T rs, T J0, T J1, T J2, T J3,
+                                         T g) {
+  volume_c<K, deg_of(Q), KL>(r, Q, xi, U, V, uc, vc, pp, hb, Uc, Vc, rs, J0, J1, J2, J3, g);
+}
+
+// the elevation row of volume_c alone
+template <int K, int DQ, int KL>
+__device__ __forceinline__ T volume_xi(int q, const T (&Uc)[KL], const T (&Vc)[KL]) {
+  constexpr int QR = qrep<DQ>();
   T am = 0;
   sfor<0, KL>([&](auto i) {
-    if constexpr (dnz(Q, i) && !base2(Q, i)) am += Uc[i] * cD[0][Q][i] + Vc[i] * cD[1][Q][i];
+    if constexpr (dnz(QR, i) && !base2(QR, i)) am += Uc[i] * cD[0][q][i] + Vc[i] * cD[1][q][i];
   });
   return am;
 }
@@ -615,10 +634,10 @@ int launch_edge_corr(GroupStreams gs, const DevMesh& m, const CorrEdges& ce, con
 // correction element update of one order group (K = K(p), p >= 2).
 // Block = 128 elements of one test mode q: the grid is ordered q-major
 // (blocks 0..nb-1 compute q = 1, the next nb q = 2, ...), so the blocks that
-// run at the same time on an SM mostly share one branch of the
-// compile-time-specialised code -- one branch per test mode does not fit the
-// instruction cache all at once (ncu: no_instruction stalls when the K - 1
-// warps of a block each ran a different q).  q = 1, 2: the correction of the base
+// run at the same time on an SM mostly share one branch of the specialised
+// code, and there is one branch per degree of q (volume_c), not per test
+// mode: the branches of all test modes do not fit the instruction cache
+// (ncu: no_instruction stalls).  q = 1, 2: the correction of the base
 // modes (volume terms with a higher coefficient index) -> rc;  q >= 3: the
 // full volume term, the source g grad h_b xi_q, the projections of the full
 // edge fluxes, and the SSP-RK combination of that higher mode.  One launch
@@ -664,8 +683,8 @@ __global__ void __launch_bounds__(128, kF32 ? 4 : 2) k_elem_corr(DevMesh m, Corr
       Uc[j] = J0 * Uj + J1 * Vj;
       Vc[j] = J2 * Uj + J3 * Vj;
     });
-    sfor<1, K>([&](auto Q) {
-      if (q == Q) r[0] = volume_xi<K, Q, KL>(Uc, Vc);
+    sfor<1, deg_of(K - 1) + 1>([&](auto DQ) {
+      if (deg_of(q) == DQ) r[0] = volume_xi<K, DQ, KL>(q, Uc, Vc);
     });
     r[1] = (T)vol[q * nrc + rc_off + l];
     r[2] = (T)vol[(16 + q) * nrc + rc_off + l];
@@ -694,8 +713,8 @@ __global__ void __launch_bounds__(128, kF32 ? 4 : 2) k_elem_corr(DevMesh m, Corr
         Vc[j] = J2 * U[j] + J3 * V[j];
       }
     });
-    sfor<1, K>([&](auto Q) {
-      if (q == Q) volume_q<K, Q, KL>(r, xi, U, V, uc, vc, pp, hb, Uc, Vc, rs, J0, J1, J2, J3, g);
+    sfor<1, deg_of(K - 1) + 1>([&](auto DQ) {
+      if (deg_of(q) == DQ) volume_c<K, DQ, KL>(r, q, xi, U, V, uc, vc, pp, hb, Uc, Vc, rs, J0, J1, J2, J3, g);
     });
     sfor<3, K>([&](auto Q) {
       if (q == Q) { xq = xi[Q]; Uq = U[Q]; Vq = V[Q]; }

@@ -1,5 +1,6 @@
 """The C ABI library builds, loads and exports every declared symbol; its own
 reference tables agree with the oracle's (host-only calls, no GPU)."""
+import math
 import os
 import re
 
@@ -37,6 +38,16 @@ def test_library_tensors_match_oracle(lib):
     t = O.tensors()
     for a, b in ((D, t["D"]), (G, t["G"]), (T, t["T"])):
         assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
+
+
+def test_p1_mass_tensor_structure_the_velocity_solve_uses(lib):
+    """the P1 velocity solve drops T[0][i][j] = T[i][0][j] = phihat_1 delta_ij
+    (orthonormal basis, constant phihat_1 = sqrt 2) from its arithmetic"""
+    _, _, T = swedg.reference_tensors()
+    for i in range(3):
+        for j in range(3):
+            assert abs(T[0, i, j] - math.sqrt(2.0) * (i == j)) < 1e-14
+            assert abs(T[i, 0, j] - math.sqrt(2.0) * (i == j)) < 1e-14
 
 
 @pytest.mark.parametrize("npts,pmax", [(2, 1), (4, 2), (5, 3), (7, 4)])
