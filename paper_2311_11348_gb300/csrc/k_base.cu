@@ -400,13 +400,16 @@ __global__ void __launch_bounds__(128) k_edge_base(DevMesh m, Phys ph, Stage stg
   // lambda of Eq. (10) from the means (Sect. 3); max sqrt = sqrt max; times wl
   const double wl = m.egeo[E_WLEN * nE + ed];
   const double lam = fmax(fabs(unL), fabs(unR)) + wl * sqrt(ph.g * fmax(HL, HR));
+  // momentum rows as U (w + lambda) + U+ (w+ - lambda) + P n: the two
+  // factors are shared by both rows
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
     const double hb = m.egeo[(E_HG0 + g) * nE + ed];
     const double P = ph.g * (a.xi[g] * (0.5 * a.xi[g] + hb) + b.xi[g] * (0.5 * b.xi[g] + hb));
+    const double wa = a.w[g] + lam, wb = b.w[g] - lam;
     Fb[(0 * 2 + g) * nE + ed] = (a.U[g] + b.U[g]) * nxw + (a.V[g] + b.V[g]) * nyw + lam * (a.xi[g] - b.xi[g]);
-    Fb[(1 * 2 + g) * nE + ed] = a.U[g] * a.w[g] + b.U[g] * b.w[g] + P * nxw + lam * (a.U[g] - b.U[g]);
-    Fb[(2 * 2 + g) * nE + ed] = a.V[g] * a.w[g] + b.V[g] * b.w[g] + P * nyw + lam * (a.V[g] - b.V[g]);
+    Fb[(1 * 2 + g) * nE + ed] = a.U[g] * wa + b.U[g] * wb + P * nxw;
+    Fb[(2 * 2 + g) * nE + ed] = a.V[g] * wa + b.V[g] * wb + P * nyw;
   }
   });
 }
@@ -535,6 +538,7 @@ __global__ void __launch_bounds__(128, 3) k_elem_base(DevMesh m, Phys ph, Stage 
   }
   const int K = m.p[e] == 0 ? 1 : 3;
   const double dt = stage_dt(stg, m.mem[e]), a = stg.a, bb = stg.b;
+  const bool euler = a == 0.0 && bb == 1.0;  // the first stage: c + dt r
 #pragma unroll
   for (int f = 0; f < 3; ++f)
 #pragma unroll
@@ -543,6 +547,7 @@ __global__ void __launch_bounds__(128, 3) k_elem_base(DevMesh m, Phys ph, Stage 
       double v = 0.0;
       if (q < K) {
         if (stg.rhs_only) v = r[f][q];
+        else if (euler) v = c[f][q] + dt * r[f][q];
         else v = (a != 0.0 ? a * cbN[ix] : 0.0) + bb * (c[f][q] + dt * r[f][q]);
       }
       cbO[ix] = v;
