@@ -9,7 +9,7 @@ unit" of the roofline that bench.py reports:
   family      unit                         arithmetic       count per unit
   usolve      element (p<=1 / p>=2)        FP64 / corr      USOLVE_P1 / usolve_flops(K, rc)
   edge_base   edge                         FP64             EDGE_BASE
-  elem_base   element                      FP64             ELEM_BASE
+  elem_base   element                      FP64             ELEM_BASE (first stage ELEM_BASE_EULER)
   edge_corr   edge with max(p_L,p_R) >= 2  corr type        edge_corr_flops(K_L, K_R, pmax)
   elem_corr   element p >= 2               corr type        elem_corr_flops(K, tc, rc)
   vol_tc      element p >= 2               TF32 tensor      vol_tc_flops(K)
@@ -40,9 +40,10 @@ FP32_PEAK_TFLOPS = SM_COUNT * 256 * SM_MAX_GHZ / 1e3
 # dense TF32 : BF16 tensor rate of the part (1.1 : 2.25 PFLOP/s nominal)
 TF32_OVER_BF16 = 1.1 / 2.25
 
-USOLVE_P1 = 92
-EDGE_BASE = 160
-ELEM_BASE = 226
+USOLVE_P1 = 76   # the 3 x 3 solve with the entries the orthonormal basis fixes left out
+EDGE_BASE = 152
+ELEM_BASE = 226  # a stage with the full SSP-RK combination
+ELEM_BASE_EULER = 199  # the first stage (c + dt r)
 DT = 12
 
 
@@ -147,7 +148,7 @@ def family_flops(orders, fam, nedge=None, mode="mixed"):
     nedge = nedge or int(round(1.5 * ne))
     st = 3
     if fam == "elem_base":
-        return st * ELEM_BASE * ne
+        return ((st - 1) * ELEM_BASE + ELEM_BASE_EULER) * ne
     if fam == "edge_base":
         return st * EDGE_BASE * nedge
     if fam == "dt":
