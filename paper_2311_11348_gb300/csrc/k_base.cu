@@ -439,7 +439,12 @@ int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Sta
 // f_c U_q with bottom friction and Coriolis), and the edge terms are
 // -sum_g F_g phi_q(x_g) over the three edges (sign flipped for the right side).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 3) k_elem_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cbS,
+// MINB: blocks per SM the register allocation must allow -- 4 (128 registers)
+// for uncapped grids, where the kernel's own occupancy is what counts; 3 for
+// grids capped at a few blocks per SM beside the correction kernels, where
+// the measured step is faster with the unrestricted allocation
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_elem_base(DevMesh m, Phys ph, Stage stg, const double* __restrict__ cbS,
                                                    const double* __restrict__ cbN, double* __restrict__ cbO,
                                                    float* __restrict__ cbO32, const double* __restrict__ ub,
                                                    const double* __restrict__ Fb, const double* __restrict__ Fbc,
@@ -563,8 +568,13 @@ int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Ph
   if (m.ne == 0) return 0;
   (void)corr_fp32;
   const LaunchShape& L = launch_shape();
-  k_elem_base<<<capped_blocks(m.ne, L.base_threads, L.base_bpsm), L.base_threads, 0, s>>>(
-      m, ph, stg, cbS, cbN, cbO, cbO32, ub, fx.Fb, fx.Fbc, (const double*)rc, G.start[2], base_chunk(L), work);
+  const int nb = capped_blocks(m.ne, L.base_threads, L.base_bpsm);
+  if (L.base_bpsm == 0 || L.base_bpsm >= 4)
+    k_elem_base<4><<<nb, L.base_threads, 0, s>>>(m, ph, stg, cbS, cbN, cbO, cbO32, ub, fx.Fb, fx.Fbc,
+                                                 (const double*)rc, G.start[2], base_chunk(L), work);
+  else
+    k_elem_base<3><<<nb, L.base_threads, 0, s>>>(m, ph, stg, cbS, cbN, cbO, cbO32, ub, fx.Fb, fx.Fbc,
+                                                 (const double*)rc, G.start[2], base_chunk(L), work);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
