@@ -589,8 +589,9 @@ def serving_run(rate, duration, tri_lo, tri_hi, steps_lo, steps_hi, budget_gb, c
 def bench_sweep(args, world):
     """The paper's statically adaptive p1-2 study (Sect. 5, radial dam break on
     a perturbed uniform mesh of 2,097,152 triangles): every nth element at p = 2,
-    fractions 0, 1/64, 1/32, 1/16, 1/8, 1; mixed and FP64 modes with the default
-    launch shape, W warm-up and K timed steps each (CUDA events, L2 flushed)."""
+    fractions 0, 1/64, 1/32, 1/16, 1/8, 1; mixed and FP64 modes, each with the
+    autotuned launch shape (--shape: that one; --no-autotune: the default), W
+    warm-up and K timed steps each (CUDA events, L2 flushed)."""
     import torch
     from paper_2311_11348_gb300 import swedg
     stream = torch.cuda.Stream()
@@ -604,9 +605,13 @@ def bench_sweep(args, world):
         row = {"fraction_p2": frac, "triangles": len(w["tri"]), "dof_stage_per_step": dps}
         for name, prec in (("mixed", swedg.PREC_MIXED_FP32), ("fp64", swedg.PREC_FP64)):
             s = make_solver(w, prec, stream.cuda_stream)
+            c0 = initial_state(s, w)
+            s.set_state(c0, 0.0)
             if args.shape:
                 s.set_launch_shape(args.shape)
-            c0 = initial_state(s, w)
+            elif args.autotune:
+                s.autotune(steps=2)
+            row[name + "_launch_shape"] = list(s.launch_shape())
             s.set_state(c0, 0.0)
             s.run(args.warmup)
             torch.cuda.synchronize()
@@ -635,7 +640,8 @@ def bench_sweep(args, world):
             "config": {"workload": f"dam break p1-2 sweep: {n}x{n} perturbed split squares ({2 * n * n} triangles), "
                                    "flat 10 m bottom, radial dam, walls, every nth element at p = 2; value = the mixed "
                                    "mode at 1/32", "l2": "flushed between timed steps (256 MB write)", "replicas": world,
-                       "launch_shape": list(args.shape) if args.shape else "default"},
+                       "launch_shape": list(args.shape) if args.shape else ("autotuned per fraction and mode"
+                                                                             if args.autotune else "default")},
             "sweep": rows, "clocks": clk}
 
 
