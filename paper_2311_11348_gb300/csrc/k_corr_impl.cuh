@@ -406,9 +406,11 @@ int launch_usolve_corr(GroupStreams gs, const DevMesh& m, const Groups& G, const
 //                         U_h w + U_b w_h + g nx xi_h (xi_b + xi_h/2 + h_b),
 //                         V_h w + V_b w_h + g ny xi_h (xi_b + xi_h/2 + h_b) )
 // so the correction flux  F_h = 1/2 (A_h(L) + A_h(R) + lambda (c_h(L) - c_h(R)))
-// carries no cancellation against the base flux.  F_f = F_b + F_h is the full
-// LF flux for the test modes of degree >= 2.  Both are stored pre-weighted by
-// |E| w_g at the points of the left element's direction.
+// carries no cancellation against the base flux.  F_f = F_b + F_h is the LF
+// flux the test modes of degree >= 2 see, except that the g xi_lin h_b terms
+// of F_b give way to g h_b times the jump of xi_lin (the volume term's share,
+// see volume_q).  Both are stored pre-weighted by |E| w_g at the points of
+// the left element's direction.
 // ---------------------------------------------------------------------------
 struct Tr { T xb, Ub, Vb, ub, vb, xh, Uh, Vh, uh, vh; };
 
