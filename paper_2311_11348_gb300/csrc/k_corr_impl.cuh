@@ -456,9 +456,9 @@ __device__ __forceinline__ void side_traces(const DevMesh& m, const Groups& G, S
 }
 
 template <int PM>
-__global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __restrict__ list, int64_t nl, Groups G,
-                                                   Phys ph, Stage stg, StateDev c, VelDev u,
-                                                   double* __restrict__ Fbc, EdgeFlux fx) {
+__device__ __forceinline__ void edge_corr_body(const DevMesh& m, const int32_t* __restrict__ list, int64_t nl,
+                                               const Groups& G, const Phys& ph, const Stage& stg, const StateDev& c,
+                                               const VelDev& u, double* __restrict__ Fbc, const EdgeFlux& fx) {
   constexpr int N = npts_for(PM), GI = PM - 2;
   void* const* Pf = fx.Pf;
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -611,13 +611,34 @@ __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __r
   });
 }
 
+// Register budgets: the compiler's allocation (FP32: 124, 168, 210 registers
+// for pmax = 2, 3, 4), and for pmax = 3 in FP32 a second build in 128
+// registers (4 blocks per SM) for launch shapes that cap the base grids --
+// where the correction kernels share the SMs with a few base blocks, the
+// extra warps pay (measured on the p 1-4 shelf: -1.2 % per step); beside
+// uncapped base grids the smaller register file share does not.
+template <int PM>
+__global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __restrict__ list, int64_t nl, Groups G,
+                                                   Phys ph, Stage stg, StateDev c, VelDev u,
+                                                   double* __restrict__ Fbc, EdgeFlux fx) {
+  edge_corr_body<PM>(m, list, nl, G, ph, stg, c, u, Fbc, fx);
+}
+__global__ void __launch_bounds__(128, 4) k_edge_corr3(DevMesh m, const int32_t* __restrict__ list, int64_t nl,
+                                                       Groups G, Phys ph, Stage stg, StateDev c, VelDev u,
+                                                       double* __restrict__ Fbc, EdgeFlux fx) {
+  edge_corr_body<3>(m, list, nl, G, ph, stg, c, u, Fbc, fx);
+}
+
 template <int PM>
 static int edge_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, const Groups& G, const Phys& ph,
                       const Stage& stg, StateDev c, VelDev u, EdgeFlux fx) {
   const int64_t nl = ce.n[PM];
   if (nl == 0) return 0;
   const int ct = launch_shape().corr_threads;
-  k_edge_corr<PM><<<nblocks(nl, ct), ct, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc, fx);
+  if (PM == 3 && kF32 && launch_shape().base_bpsm > 0)
+    k_edge_corr3<<<nblocks(nl, ct), ct, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc, fx);
+  else
+    k_edge_corr<PM><<<nblocks(nl, ct), ct, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc, fx);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
