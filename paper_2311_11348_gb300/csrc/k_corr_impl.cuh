@@ -260,12 +260,12 @@ __host__ __device__ constexpr bool tc_vol(int K) { return false; }
 // kernel can take it without waiting for the correction element kernel.
 // ---------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int64_t n, Phys ph, StateDev c,
-                                                     const T* __restrict__ ch, double* __restrict__ ub,
-                                                     float* __restrict__ ub32, T* __restrict__ uh,
-                                                     T* __restrict__ tr, T* __restrict__ trv,
-                                                     unsigned* status, unsigned long long* dmin,
-                                                     double* __restrict__ rc, int64_t rc_off, int64_t nrc) {
+__device__ __forceinline__ void usolve_corr_body(const DevMesh& m, int64_t g0, int64_t n, const Phys& ph,
+                                                 const StateDev& c, const T* __restrict__ ch, double* __restrict__ ub,
+                                                 float* __restrict__ ub32, T* __restrict__ uh,
+                                                 T* __restrict__ tr, T* __restrict__ trv,
+                                                 unsigned* status, unsigned long long* dmin,
+                                                 double* __restrict__ rc, int64_t rc_off, int64_t nrc) {
   const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double dcfl = DBL_MAX;
   int mem = 0;
@@ -376,6 +376,27 @@ __global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int6
   if (dmin) cfl_min_store(dmin, mem, dcfl);  // uniform over the grid: every lane of the warp is here
 }
 
+// The compiler's register allocation (FP32: 80, 127, 255 registers for K =
+// 6, 10, 15), and for K = 15 in FP32 a second build in 168 registers (3
+// blocks per SM) for launch shapes that cap the base grids (see k_edge_corr).
+template <int K>
+__global__ void __launch_bounds__(128) k_usolve_corr(DevMesh m, int64_t g0, int64_t n, Phys ph, StateDev c,
+                                                     const T* __restrict__ ch, double* __restrict__ ub,
+                                                     float* __restrict__ ub32, T* __restrict__ uh,
+                                                     T* __restrict__ tr, T* __restrict__ trv,
+                                                     unsigned* status, unsigned long long* dmin,
+                                                     double* __restrict__ rc, int64_t rc_off, int64_t nrc) {
+  usolve_corr_body<K>(m, g0, n, ph, c, ch, ub, ub32, uh, tr, trv, status, dmin, rc, rc_off, nrc);
+}
+__global__ void __launch_bounds__(128, 3) k_usolve_corr15(DevMesh m, int64_t g0, int64_t n, Phys ph, StateDev c,
+                                                         const T* __restrict__ ch, double* __restrict__ ub,
+                                                         float* __restrict__ ub32, T* __restrict__ uh,
+                                                         T* __restrict__ tr, T* __restrict__ trv,
+                                                         unsigned* status, unsigned long long* dmin,
+                                                         double* __restrict__ rc, int64_t rc_off, int64_t nrc) {
+  usolve_corr_body<15>(m, g0, n, ph, c, ch, ub, ub32, uh, tr, trv, status, dmin, rc, rc_off, nrc);
+}
+
 template <int K>
 static int usolve_group(cudaStream_t st, const DevMesh& m, const Groups& G, int p, const Phys& ph, StateDev c,
                         VelDev u, unsigned* status, unsigned long long* dmin, void* rc) {
@@ -383,9 +404,14 @@ static int usolve_group(cudaStream_t st, const DevMesh& m, const Groups& G, int 
   if (n == 0) return 0;
   const int64_t nrc = G.start[5] - G.start[2], rc_off = g0 - G.start[2];
   const int ct = launch_shape().corr_threads;
-  k_usolve_corr<K><<<nblocks(n, ct), ct, 0, st>>>(m, g0, n, ph, c, (const T*)c.ch[p], u.ub, u.ub32,
-                                                    (T*)u.uh[p], (T*)u.tr[p], (T*)u.trv[p], status, dmin,
-                                                    (double*)rc, rc_off, nrc);
+  if (K == 15 && kF32 && launch_shape().base_bpsm > 0)
+    k_usolve_corr15<<<nblocks(n, ct), ct, 0, st>>>(m, g0, n, ph, c, (const T*)c.ch[p], u.ub, u.ub32,
+                                                   (T*)u.uh[p], (T*)u.tr[p], (T*)u.trv[p], status, dmin,
+                                                   (double*)rc, rc_off, nrc);
+  else
+    k_usolve_corr<K><<<nblocks(n, ct), ct, 0, st>>>(m, g0, n, ph, c, (const T*)c.ch[p], u.ub, u.ub32,
+                                                      (T*)u.uh[p], (T*)u.tr[p], (T*)u.trv[p], status, dmin,
+                                                      (double*)rc, rc_off, nrc);
   count_launch();
   SWE_CUDA_OK(cudaGetLastError());
   return 0;
@@ -612,16 +638,22 @@ __device__ __forceinline__ void edge_corr_body(const DevMesh& m, const int32_t* 
 }
 
 // Register budgets: the compiler's allocation (FP32: 124, 168, 210 registers
-// for pmax = 2, 3, 4), and for pmax = 3 in FP32 a second build in 128
-// registers (4 blocks per SM) for launch shapes that cap the base grids --
-// where the correction kernels share the SMs with a few base blocks, the
-// extra warps pay (measured on the p 1-4 shelf: -1.2 % per step); beside
-// uncapped base grids the smaller register file share does not.
+// for pmax = 2, 3, 4), and in FP32 second builds for pmax = 3 in 128 and for
+// pmax = 4 in 168 registers (4 and 3 blocks per SM) for launch shapes that
+// cap the base grids: where the correction kernels share the SMs with a few
+// base blocks, the extra warps pay (with the K = 15 velocity solve in 168
+// registers, measured on the p 1-4 shelf: -2.6 % per step); beside uncapped
+// base grids they do not.
 template <int PM>
 __global__ void __launch_bounds__(128) k_edge_corr(DevMesh m, const int32_t* __restrict__ list, int64_t nl, Groups G,
                                                    Phys ph, Stage stg, StateDev c, VelDev u,
                                                    double* __restrict__ Fbc, EdgeFlux fx) {
   edge_corr_body<PM>(m, list, nl, G, ph, stg, c, u, Fbc, fx);
+}
+__global__ void __launch_bounds__(128, 3) k_edge_corr4(DevMesh m, const int32_t* __restrict__ list, int64_t nl,
+                                                       Groups G, Phys ph, Stage stg, StateDev c, VelDev u,
+                                                       double* __restrict__ Fbc, EdgeFlux fx) {
+  edge_corr_body<4>(m, list, nl, G, ph, stg, c, u, Fbc, fx);
 }
 __global__ void __launch_bounds__(128, 4) k_edge_corr3(DevMesh m, const int32_t* __restrict__ list, int64_t nl,
                                                        Groups G, Phys ph, Stage stg, StateDev c, VelDev u,
@@ -637,6 +669,8 @@ static int edge_group(cudaStream_t st, const DevMesh& m, const CorrEdges& ce, co
   const int ct = launch_shape().corr_threads;
   if (PM == 3 && kF32 && launch_shape().base_bpsm > 0)
     k_edge_corr3<<<nblocks(nl, ct), ct, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc, fx);
+  else if (PM == 4 && kF32 && launch_shape().base_bpsm > 0)
+    k_edge_corr4<<<nblocks(nl, ct), ct, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc, fx);
   else
     k_edge_corr<PM><<<nblocks(nl, ct), ct, 0, st>>>(m, ce.list[PM], nl, G, ph, stg, c, u, fx.Fbc, fx);
   count_launch();
