@@ -86,7 +86,11 @@ void swe_default_params(swe_params* p);
 /* Create a context on the current CUDA device.  *out is set on success. */
 int swe_create(swe_ctx** out, const swe_params* params);
 
-/* Release every resource of the context (NULL is accepted). */
+/* Release every resource of the context (NULL is accepted).  Device buffers
+ * come from one stream-ordered memory pool per device that the library keeps
+ * for the process: a destroyed context's memory goes back to that pool (for
+ * the next context to reuse, without mapping new memory or synchronising the
+ * device), not to the driver. */
 void swe_destroy(swe_ctx* ctx);
 
 /* Text of the last error of the context (or of swe_create when ctx is NULL). */
@@ -218,8 +222,8 @@ int swe_get_member_times(swe_ctx* ctx, double* t_out, double* dt_out);
 #define SWE_STATUS_NONFINITE 2u
 int swe_member_status(swe_ctx* ctx, uint32_t* status_out);
 
-/* Device memory held by the context (bytes); a serving loop admits requests
- * by this footprint. */
+/* Device memory held by the context (bytes; its buffers in the library's
+ * pool); a serving loop admits requests by this footprint. */
 int swe_memory_bytes(swe_ctx* ctx, int64_t* bytes);
 
 /* Dynamic p-adaptivity (Sect. 2, end, and Sect. 3: with a hierarchical basis
