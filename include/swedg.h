@@ -90,7 +90,7 @@ int swe_create(swe_ctx** out, const swe_params* params);
  * come from one stream-ordered memory pool per device that the library keeps
  * for the process: a destroyed context's memory goes back to that pool (for
  * the next context to reuse, without mapping new memory or synchronising the
- * device), not to the driver. */
+ * device), not released to the CUDA driver. */
 void swe_destroy(swe_ctx* ctx);
 
 /* Text of the last error of the context (or of swe_create when ctx is NULL). */
