@@ -863,7 +863,7 @@ def main():
 # triangle ocean workload (default launch shape), from one ncu capture of the
 # current kernels (cold cache): TRAFFIC_CAPTURE below, run after the same
 # command exited 0 without ncu.  None for other workloads and kernels.
-MEASURED_TRAFFIC = {"edge_base": 41.235968e6 + 0.469248e6, "elem_base": 62.576128e6 + 2.774528e6}
+MEASURED_TRAFFIC = {"edge_base": 41.235200e6 + 0.472576e6, "elem_base": 62.594304e6 + 2.891776e6}
 TRAFFIC_CAPTURE = ("ncu --set full --clock-control none -k regex:'k_edge_base|k_elem_base|k_elem_corr|k_edge_corr|"
                    "k_usolve' -s 27 -c 9 python bench.py --steps 2 --warmup 3 --no-oracle --no-serving --no-adaptive "
                    "--no-autotune (dram__bytes_read.sum + dram__bytes_write.sum of the launch)")
