@@ -860,13 +860,17 @@ def main():
 
 
 # DRAM bytes (read + write) per launch of the base kernels on the 131,072-
-# triangle ocean workload (default launch shape), from one ncu capture of the
-# current kernels (cold cache): TRAFFIC_CAPTURE below, run after the same
-# command exited 0 without ncu.  None for other workloads and kernels.
-MEASURED_TRAFFIC = {"edge_base": 41.235200e6 + 0.472576e6, "elem_base": 62.594304e6 + 2.891776e6}
-TRAFFIC_CAPTURE = ("ncu --set full --clock-control none -k regex:'k_edge_base|k_elem_base|k_elem_corr|k_edge_corr|"
-                   "k_usolve' -s 27 -c 9 python bench.py --steps 2 --warmup 3 --no-oracle --no-serving --no-adaptive "
-                   "--no-autotune (dram__bytes_read.sum + dram__bytes_write.sum of the launch)")
+# triangle ocean workload with the autotuned ocean shape (uncapped base grids:
+# the 128-register element kernel), from one ncu capture of the current
+# kernels (cold cache), TRAFFIC_CAPTURE below, run after the same command
+# exited 0 without ncu: the mean over an SSP-RK3 step's launches (the element
+# kernel reads the step's start state in two of the three stages).  None for
+# other workloads and kernels.
+MEASURED_TRAFFIC = {"edge_base": (41.240832e6 + 0.227584e6 + 41.236480e6 + 0.071680e6) / 2.0,
+                    "elem_base": ((62.336256e6 + 0.406528e6) + 2.0 * (71.815936e6 + 0.165376e6)) / 3.0}
+TRAFFIC_CAPTURE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control "
+                   "none -k regex:'k_edge_base|k_elem_base' -s 6 -c 4 python bench.py --steps 2 --warmup 3 --no-oracle "
+                   "--no-serving --no-adaptive --shape 0,128,128,64,1,2")
 
 
 def roofline(w, r, dom, steps, pk, head):
