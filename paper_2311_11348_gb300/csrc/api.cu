@@ -706,10 +706,16 @@ static Phys phys(const swe_ctx* ctx) {
               (p.fric_lin != 0.0 || p.fric_quad != 0.0 || p.f_c != 0.0) ? 1 : 0};
 }
 
+// The FP32 copies of the base state and velocity serve the correction kernels
+// only: with no element of order >= 2 they are not written (an order change
+// rewrites them from the caller layout before a correction kernel reads them).
+static float* cb32_out(const swe_ctx* ctx, const StateDev& s) { return ctx->G.start[2] < ctx->ne ? s.cb32 : nullptr; }
+static float* ub32_out(const swe_ctx* ctx) { return ctx->G.start[2] < ctx->ne ? ctx->vel.ub32 : nullptr; }
+
 static int usolve_all(swe_ctx* ctx, StateDev in) {
   ProfScope ps(ctx, F_USOLVE);
   const Phys ph = phys(ctx);
-  CK(launch_usolve_base(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status, nullptr));
+  CK(launch_usolve_base(ctx->stream, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ub32_out(ctx), ctx->d_status, nullptr));
   if (ctx->tc)
     CK(corrtc::launch_usolve_corr(GroupStreams{{ctx->stream, ctx->stream, ctx->stream}}, ctx->dm, ctx->G, ph, in, ctx->vel,
                                   ctx->d_status, nullptr, nullptr));
@@ -769,7 +775,7 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
     // the first stage of a CFL step folds the elements' CFL bounds into d_dmin
     ProfScope ps(ctx, F_USOLVE);
     unsigned long long* dmin = cfl_dt ? ctx->d_dmin : nullptr;
-    CK(launch_usolve_base(A, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ctx->vel.ub32, ctx->d_status, dmin));
+    CK(launch_usolve_base(A, ctx->dm, ctx->G, ph, in.cb, ctx->vel.ub, ub32_out(ctx), ctx->d_status, dmin));
     CK(fork_groups());
     // the CUDA-core modes form rc in the velocity solve; the tensor-core mode in elem_corr (from vol)
     if (ctx->tc) CK(corrtc::launch_usolve_corr(gs, ctx->dm, ctx->G, ph, in, ctx->vel, ctx->d_status, dmin, nullptr));
@@ -837,7 +843,7 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
   if (split) CK(elem_corr(1));  // the higher test modes, beside elem_base
   {
     ProfScope ps(ctx, F_ELEMB);
-    CK(launch_elem_base(A, ctx->dm, ctx->G, ph, stg, ctx->corr32, in.cb, nst.cb, out.cb, out.cb32, ctx->vel.ub,
+    CK(launch_elem_base(A, ctx->dm, ctx->G, ph, stg, ctx->corr32, in.cb, nst.cb, out.cb, cb32_out(ctx, out), ctx->vel.ub,
                         ctx->fx, ctx->rc, ctx->prm.cfl, ctx->d_work + 2));
   }
   if (conc && split) {
