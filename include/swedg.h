@@ -104,9 +104,12 @@ const char* swe_last_error(const swe_ctx* ctx);
  *               vertex k: 0 = interior, or land if no neighbour matches;
  *               1 = land (q.n = 0); 2 = open sea (xi = xi_hat).  NULL = every
  *               edge without a neighbour is land.
- * Errors: SWE_EMESH for a zero-area triangle, an out-of-range vertex index or
- * an edge shared by more than two triangles.  Resets orders to p = 1, the
- * bathymetry to zero and the state to zero. */
+ * Errors: SWE_EINVAL for nv < 3, ne < 1, a NULL xy or tri, or a boundary tag
+ * outside 0..2; SWE_EMESH for a zero-area triangle, an out-of-range vertex
+ * index or an edge shared by more than two triangles.  After an error the
+ * context holds no mesh (calls that need one return SWE_EINVAL) until a
+ * successful swe_set_mesh.  Resets orders to p = 1, the bathymetry to zero and
+ * the state to zero. */
 int swe_set_mesh(swe_ctx* ctx, int64_t nv, const double* xy, int64_t ne, const int32_t* tri,
                  const int8_t* bc_tag);
 

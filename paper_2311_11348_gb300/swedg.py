@@ -235,9 +235,9 @@ class Solver:
         pxy, kx = _ptr(xy)
         pt, kt = _ptr(tri, np.int32)
         pb, kb = _ptr(bc_tag, np.int8)
-        self.nv = int(xy.shape[0])
-        self.ne = int(tri.shape[0])
-        self._ck(self._lib.swe_set_mesh(self.h, self.nv, pxy, self.ne, pt, pb))
+        nv, ne = int(xy.shape[0]), int(tri.shape[0])
+        self._ck(self._lib.swe_set_mesh(self.h, nv, pxy, ne, pt, pb))
+        self.nv, self.ne = nv, ne
 
     def set_bathymetry(self, hv):
         p, k = _ptr(hv)

@@ -293,6 +293,19 @@ def test_errors_are_reported_not_faulted():
     with pytest.raises(swedg.SweError) as ei:
         s.set_mesh(w["xy"], bad)
     assert ei.value.code == -2
+    # an empty mesh and a boundary tag outside 0..2 are invalid arguments;
+    # after a failed set_mesh the context holds no mesh
+    with pytest.raises(swedg.SweError) as ei:
+        s.set_mesh(w["xy"], np.zeros((0, 3), np.int32))
+    assert ei.value.code == -1
+    tags = np.zeros((len(w["tri"]), 3), np.int8)
+    tags[len(tags) // 2, 1] = 3
+    with pytest.raises(swedg.SweError) as ei:
+        s.set_mesh(w["xy"], w["tri"], tags)
+    assert ei.value.code == -1 and "boundary tag" in str(ei.value)
+    with pytest.raises(swedg.SweError) as ei:
+        s.set_state(np.zeros((3, 15, len(w["tri"]))), 0.0)
+    assert ei.value.code == -1
     s.set_mesh(w["xy"], w["tri"])
     s.set_bathymetry(np.full(len(w["xy"]), 1.0))
     c = np.zeros((3, 15, len(w["tri"])))
