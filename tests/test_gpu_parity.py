@@ -136,6 +136,28 @@ def test_mixed_fp32_correction_accuracy():
     assert abs(s.mass() - m0) <= 1e-13 * math.sqrt(n) * abs(m0)
 
 
+@pytest.mark.parametrize("p", [0, 2, 4])
+@pytest.mark.parametrize("precision", [swedg.PREC_FP64, swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32])
+def test_uniform_order_meshes(precision, p):
+    """one order everywhere (288 triangles, a ragged tail of every 128-wide
+    launch): p = 0 leaves the correction branch without elements, p = 4 the
+    base branch without base-only elements; 20 CFL steps of SSP-RK3 with the
+    tide on the open western side against the oracle (relative L2 1e-11 in
+    FP64, 1e-6 with the FP32 or tensor-core correction)"""
+    w = mixed_workload(n=12, seed=7, pmin=p, pmax=p)
+    tide = (0.2, 1800.0, 0.3)
+    m, P, s = make_pair(w, precision=precision, tide=tide)
+    c = m.project_state(w["ic"])
+    s.set_state(c, 0.0)
+    t_g = s.run(20)
+    c_g, _ = s.get_state()
+    c_o, t_o = m.run(P, c, 0.0, 20)
+    tol = 1e-11 if precision == swedg.PREC_FP64 else 1e-6
+    assert rel_l2(c_g, c_o) < tol, rel_l2(c_g, c_o)
+    assert abs(t_g - t_o) <= tol * t_o
+    s.close()
+
+
 @pytest.mark.parametrize("precision", [swedg.PREC_MIXED_FP32, swedg.PREC_MIXED_TF32])
 def test_mixed_rhs_of_the_higher_modes_over_deep_water(precision):
     """The bottom term g xi h_b of the higher test modes (h_b of 50..4000 m
