@@ -843,8 +843,8 @@ static int run_stage(swe_ctx* ctx, StateDev in, StateDev nst, StateDev out, cons
   if (split) CK(elem_corr(1));  // the higher test modes, beside elem_base
   {
     ProfScope ps(ctx, F_ELEMB);
-    CK(launch_elem_base(A, ctx->dm, ctx->G, ph, stg, ctx->corr32, in.cb, nst.cb, out.cb, cb32_out(ctx, out), ctx->vel.ub,
-                        ctx->fx, ctx->rc, ctx->prm.cfl, ctx->d_work + 2));
+    CK(launch_elem_base(A, ctx->dm, ctx->G, ph, stg, in.cb, nst.cb, out.cb, cb32_out(ctx, out), ctx->vel.ub, ctx->fx,
+                        ctx->rc, ctx->d_work + 2));
   }
   if (conc && split) {
     CU(cudaEventRecord(ctx->ev_c2, B));

@@ -562,11 +562,9 @@ __global__ void __launch_bounds__(128, MINB) k_elem_base(DevMesh m, Phys ph, Sta
 }
 
 int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
-                     int corr_fp32, const double* cbS, const double* cbN, double* cbO, float* cbO32, const double* ub,
-                     EdgeFlux fx, const void* rc, double cfl, unsigned* work) {
-  (void)cfl;
+                     const double* cbS, const double* cbN, double* cbO, float* cbO32, const double* ub, EdgeFlux fx,
+                     const void* rc, unsigned* work) {
   if (m.ne == 0) return 0;
-  (void)corr_fp32;
   const LaunchShape& L = launch_shape();
   const int nb = capped_blocks(m.ne, L.base_threads, L.base_bpsm);
   if (L.base_bpsm == 0 || L.base_bpsm >= 4)

@@ -124,8 +124,8 @@ int launch_usolve_base(cudaStream_t s, const DevMesh& m, const Groups& G, const 
 int launch_edge_base(cudaStream_t s, const DevMesh& m, const Phys& ph, const Stage& stg, const double* cb,
                      const double* ub, EdgeFlux fx, unsigned* work);
 int launch_elem_base(cudaStream_t s, const DevMesh& m, const Groups& G, const Phys& ph, const Stage& stg,
-                     int corr_fp32, const double* cbS, const double* cbN, double* cbO, float* cbO32,
-                     const double* ub, EdgeFlux fx, const void* rc, double cfl, unsigned* work);
+                     const double* cbS, const double* cbN, double* cbO, float* cbO32, const double* ub, EdgeFlux fx,
+                     const void* rc, unsigned* work);
 int launch_advance_time(cudaStream_t s, double* t_dev, unsigned long long* dmin, double cfl,
                         double dt_fixed, double* dt_dev, int nmem);
 int launch_reset_min(cudaStream_t s, unsigned long long* dmin, int nmem);
