@@ -2,22 +2,22 @@
 oracle's source, compiled, and must fail a pin that the unmodified copy
 passes: the brute-force pin of the right-hand side (quadrature of the
 pointwise weak form of Eq. 8 with the Lax-Friedrichs flux and lambda of
-Eq. 10, and the truncated auxiliary system of Sect. 3), the closed-form
-integral of the mass diagnostic, or the temporal order of the SSP-RK schemes
-under a time-dependent open-sea boundary (which sees the stage times).  The
-oracle itself is never modified: the copies live in pytest's temporary
-directory."""
+Eq. 10, land and open-sea edges, and the truncated auxiliary system of
+Sect. 3), the same pin with bottom friction and Coriolis (Eq. 5), the
+closed-form integral of the mass diagnostic, the temporal order of the SSP-RK
+schemes under a time-dependent open-sea boundary (which sees the stage
+times), the closed-form CFL step, or the hand-computed decisions of the
+adaptivity indicator.  The oracle itself is never modified: the copies live
+in pytest's temporary directory."""
 import importlib.util
 import os
 import shutil
 
-import numpy as np
 import pytest
 
-import dgref
 import oracle as O_REAL
-from test_oracle_scheme import (MASS_TOL, mass_errors, random_state, scale_state_means, tide_order_rate,
-                                tiny_meshes)
+from test_oracle_scheme import (MASS_TOL, cfl_pin_error, indicator_pin_failures, mass_errors, rhs_pin_errors,
+                                source_pin_errors, tide_order_rate)
 
 SRC_DIR = os.path.dirname(os.path.abspath(O_REAL.__file__))
 
@@ -36,6 +36,11 @@ MUTANTS = {
     # xi^2 / 2 of the volume pressure with a wrong factor
     "volume_pressure_factor": ("double pres = g * (0.5 * xi[i] * xi[j] + xi[i] * hb[j]);",
                                "double pres = g * (0.45 * xi[i] * xi[j] + xi[i] * hb[j]);"),
+    # the land boundary's ghost state without the mirrored normal momentum
+    "wall_not_mirrored": ("Uo[i] = U[i] - 2.0 * nx * qn; Vo[i] = V[i] - 2.0 * ny * qn;",
+                          "Uo[i] = U[i]; Vo[i] = V[i];"),
+    # the open-sea ghost state with zero momentum instead of q+ = q
+    "open_sea_momentum_zero": ("xo[i] = 0.0; Uo[i] = U[i]; Vo[i] = V[i];", "xo[i] = 0.0; Uo[i] = 0.0; Vo[i] = 0.0;"),
 }
 
 # mistakes that the right-hand side cannot see, each with the pin that must catch it
@@ -46,12 +51,29 @@ OTHER_MUTANTS = {
     "rk3_third_stage_time": (("tau3[3] = {0.0, 1.0, 0.5}", "tau3[3] = {0.0, 1.0, 1.0}"), "rk3"),
     # the second stage of SSP-RK2 evaluated at t instead of t + dt
     "rk2_second_stage_time": (("tau2[2] = {0.0, 1.0}", "tau2[2] = {0.0, 0.0}"), "rk2"),
+    # Coriolis with the wrong sense of rotation
+    "coriolis_sign": (("- tau * uu[q] + P->f_c * V[q];", "- tau * uu[q] - P->f_c * V[q];"), "source"),
+    # the quadratic friction law with |u|^2 instead of |u|
+    "friction_quadratic_law": (("P->fric_quad * sqrt(um * um + vm * vm);", "P->fric_quad * (um * um + vm * vm);"),
+                               "source"),
+    # the CFL step without the order factor 1 / (2p + 1)
+    "cfl_without_order_factor": (("(sp * (2.0 * m->p[e] + 1.0))", "(sp * (m->p[e] + 1.0))"), "cfl"),
+    # the indicator's energy fraction with the mean mode in the denominator
+    "indicator_counts_the_mean": (("for (int i = 1; i < K; ++i) {\n      double x = C_(c, 0, i, e, ne);",
+                                   "for (int i = 0; i < K; ++i) {\n      double x = C_(c, 0, i, e, ne);"),
+                                  "indicator"),
 }
 
 
 def other_pin_passes(O, pin):
     if pin == "mass":
         return all(max(mass_errors(O, f)) <= MASS_TOL[f] for f in ("poly", "sine"))
+    if pin == "source":
+        return all(source_pin_errors(O, case)[0] <= 1e-12 for case in range(3))
+    if pin == "cfl":
+        return cfl_pin_error(O) <= 1e-15
+    if pin == "indicator":
+        return indicator_pin_failures(O) == []
     rk = 3 if pin == "rk3" else 2
     return abs(tide_order_rate(O, rk) - rk) < 0.3
 
@@ -77,21 +99,8 @@ def brute_force_pin_passes(O):
     """the checks of test_rhs_equals_brute_force_weak_form with the given oracle copy"""
     for case in range(3):
         for seed in (0, 1):
-            xy, tri = tiny_meshes()[case]
-            rng = np.random.default_rng(100 * case + seed)
-            ne = len(tri)
-            orders = rng.integers(0, 5, size=ne).astype(np.int8)
-            hv = 1.0 + 0.3 * rng.uniform(size=len(xy))
-            g = 9.81
-            m = O.Mesh(xy, tri, hv, orders)
-            c = scale_state_means(random_state(ne, orders, rng), m.geometry()["area"])
-            r, u = m.rhs(O.Params(g=g), c, t=0.0, with_u=True)
-            msh = dgref.Tri(xy, tri)
-            u_ref = dgref.solve_u(msh, hv, orders, c)
-            if np.abs(u - u_ref).max() > 1e-13 * max(1.0, np.abs(u_ref).max()):
-                return False
-            rb = dgref.brute_force_rhs(msh, hv, orders, c, u, g)
-            if np.abs(r - rb).max() > 1e-12 * max(1.0, np.abs(rb).max()):
+            eu, er = rhs_pin_errors(O, case, seed)
+            if eu > 1e-13 or er > 1e-12:
                 return False
     return True
 
@@ -107,7 +116,7 @@ def test_planted_mistake_fails_the_pin(tmp_path, name):
 
 def test_unmodified_copy_passes_the_other_pins(tmp_path):
     O = load_copy(tmp_path, "unmodified_other", None)
-    assert all(other_pin_passes(O, pin) for pin in ("mass", "rk2", "rk3"))
+    assert all(other_pin_passes(O, pin) for pin in ("mass", "rk2", "rk3", "source", "cfl", "indicator"))
 
 
 @pytest.mark.parametrize("name", sorted(OTHER_MUTANTS))
