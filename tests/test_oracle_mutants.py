@@ -6,8 +6,10 @@ Eq. 10, land and open-sea edges, and the truncated auxiliary system of
 Sect. 3), the same pin with bottom friction and Coriolis (Eq. 5), the
 closed-form integral of the mass diagnostic, the temporal order of the SSP-RK
 schemes under a time-dependent open-sea boundary (which sees the stage
-times), the closed-form CFL step, or the hand-computed decisions of the
-adaptivity indicator.  The oracle itself is never modified: the copies live
+times), the closed-form CFL step, the hand-computed decisions of the
+adaptivity indicator, the open-sea elevation against the tide formula, or the
+base part of the separated form against the
+brute-force weak form of the degree-1 truncation.  The oracle itself is never modified: the copies live
 in pytest's temporary directory."""
 import importlib.util
 import os
@@ -16,7 +18,7 @@ import shutil
 import pytest
 
 import oracle as O_REAL
-from test_oracle_scheme import (MASS_TOL, cfl_pin_error, indicator_pin_failures, mass_errors, rhs_pin_errors,
+from test_oracle_scheme import (MASS_TOL, base_part_pin_error, cfl_pin_error, indicator_pin_failures, mass_errors, rhs_pin_errors, tide_pin_error,
                                 source_pin_errors, tide_order_rate)
 
 SRC_DIR = os.path.dirname(os.path.abspath(O_REAL.__file__))
@@ -58,6 +60,14 @@ OTHER_MUTANTS = {
                                "source"),
     # the CFL step without the order factor 1 / (2p + 1)
     "cfl_without_order_factor": (("(sp * (2.0 * m->p[e] + 1.0))", "(sp * (m->p[e] + 1.0))"), "cfl"),
+    # the base part with the own side's edge products whose second coefficient
+    # index is of degree >= 2 (the sum of the two parts, and so the whole rhs,
+    # unchanged; in the volume terms the same products vanish by orthogonality)
+    "base_part_with_higher_products": (("if (i < Kx && j < Kx && use_term(part, q < 3 && i < 3 && j < 3)) {",
+                                        "if (i < Kx && j < Kx && use_term(part, q < 3 && i < 3)) {"), "base"),
+    # the tide's phase with the wrong sign
+    "tide_phase_sign": (("sin(2.0 * M_PI * t / P->tide_period + P->tide_phase)",
+                         "sin(2.0 * M_PI * t / P->tide_period - P->tide_phase)"), "tide"),
     # the indicator's energy fraction with the mean mode in the denominator
     "indicator_counts_the_mean": (("for (int i = 1; i < K; ++i) {\n      double x = C_(c, 0, i, e, ne);",
                                    "for (int i = 0; i < K; ++i) {\n      double x = C_(c, 0, i, e, ne);"),
@@ -70,6 +80,10 @@ def other_pin_passes(O, pin):
         return all(max(mass_errors(O, f)) <= MASS_TOL[f] for f in ("poly", "sine"))
     if pin == "source":
         return all(source_pin_errors(O, case)[0] <= 1e-12 for case in range(3))
+    if pin == "tide":
+        return tide_pin_error(O) <= 1e-13
+    if pin == "base":
+        return base_part_pin_error(O) <= 1e-12
     if pin == "cfl":
         return cfl_pin_error(O) <= 1e-15
     if pin == "indicator":
@@ -116,7 +130,7 @@ def test_planted_mistake_fails_the_pin(tmp_path, name):
 
 def test_unmodified_copy_passes_the_other_pins(tmp_path):
     O = load_copy(tmp_path, "unmodified_other", None)
-    assert all(other_pin_passes(O, pin) for pin in ("mass", "rk2", "rk3", "source", "cfl", "indicator"))
+    assert all(other_pin_passes(O, pin) for pin in ("mass", "rk2", "rk3", "source", "cfl", "indicator", "base", "tide"))
 
 
 @pytest.mark.parametrize("name", sorted(OTHER_MUTANTS))

@@ -288,6 +288,69 @@ def test_separation_identity():
     assert np.all(base[:, 3:, :] == 0.0)
 
 
+def base_part_pin_error(Om):
+    """relative error of the oracle's base part (Sect. 3: the terms whose test
+    index and coefficient indices are all modes of degree <= 1) against its
+    plain definition: the brute-force weak form of the state and of the
+    scheme's own u with every mode of degree >= 2 set to zero, rows of degree
+    <= 1, on tiny meshes with orders 0..4, an open-sea edge, friction and
+    Coriolis; also the rows of degree >= 2, which the base part must leave zero"""
+    worst = 0.0
+    for case in range(3):
+        xy, tri = tiny_meshes()[case]
+        rng = np.random.default_rng(70 + case)
+        ne = len(tri)
+        orders = rng.integers(0, 5, size=ne).astype(np.int8)
+        hv = 1.0 + 0.3 * rng.uniform(size=len(xy))
+        bc, opened = None, []
+        if case == 1:
+            bc = np.zeros((ne, 3), np.int8)
+            bc[0, 2] = 2
+            opened = [(0, 2)]
+        m = Om.Mesh(xy, tri, hv, orders, bc_tag=bc)
+        geo = m.geometry()
+        c = scale_state_means(random_state(ne, orders, rng), geo["area"])
+        fr = dict(fric_lin=0.3, fric_quad=0.5, f_c=0.4)
+        P = Om.Params(g=9.81, tide_amp=0.05, tide_period=0.0, **fr)
+        _, u = m.rhs(P, c, t=0.0, with_u=True)
+        base = m.rhs(P, c, t=0.0, part=1)
+        ct, ut = c.copy(), u.copy()
+        ct[:, 3:] = 0.0
+        ut[:, 3:] = 0.0
+        rb = dgref.brute_force_rhs(dgref.Tri(xy, tri), hv, orders, ct, ut, 9.81, bc_open=opened, xi_hat=0.05, **fr)
+        scale = max(1.0, np.abs(rb[:, :3]).max())
+        worst = max(worst, np.abs(base[:, :3] - rb[:, :3]).max() / scale, np.abs(base[:, 3:]).max() / scale)
+    return worst
+
+
+def tide_pin_error(Om):
+    """relative difference between the oracle's rhs with the periodic open-sea
+    elevation xi_hat(t) = amp sin(2 pi t / period + phase) at three times and
+    its rhs with the constant elevation of that value (period 0), on a mesh
+    with an open western side"""
+    xy, tri, hv, orders = jittered_mixed(seed=12)
+    bc = inputs.boundary_tags(xy, tri, "west")
+    m = Om.Mesh(xy, tri, hv, orders, bc_tag=bc)
+    rng = np.random.default_rng(12)
+    c = scale_state_means(random_state(len(tri), orders, rng), m.geometry()["area"])
+    amp, period, phase = 0.2, 700.0, 0.9
+    worst = 0.0
+    for t in (0.0, 130.0, 1234.5):
+        r = m.rhs(Om.Params(g=9.81, tide_amp=amp, tide_period=period, tide_phase=phase), c, t=t)
+        xh = amp * math.sin(2.0 * math.pi * t / period + phase)
+        r0 = m.rhs(Om.Params(g=9.81, tide_amp=xh, tide_period=0.0), c, t=t)
+        worst = max(worst, np.abs(r - r0).max() / np.abs(r0).max())
+    return worst
+
+
+def test_open_sea_elevation_is_the_tide_formula():
+    assert tide_pin_error(O) <= 1e-13
+
+
+def test_base_part_is_the_degree_one_truncation():
+    assert base_part_pin_error(O) <= 1e-12
+
+
 def test_rotation_equivariance():
     xy, tri, hv, orders = jittered_mixed(seed=9)
     rng = np.random.default_rng(4)
