@@ -53,6 +53,9 @@ OTHER_MUTANTS = {
     "rk3_third_stage_time": (("tau3[3] = {0.0, 1.0, 0.5}", "tau3[3] = {0.0, 1.0, 1.0}"), "rk3"),
     # the second stage of SSP-RK2 evaluated at t instead of t + dt
     "rk2_second_stage_time": (("tau2[2] = {0.0, 1.0}", "tau2[2] = {0.0, 0.0}"), "rk2"),
+    # the second stage of SSP-RK3 combined half and half (still consistent)
+    "rk3_second_stage_weights": (("a3[3] = {0.0, 0.75, 1.0 / 3.0}, b3[3] = {1.0, 0.25, 2.0 / 3.0}",
+                                  "a3[3] = {0.0, 0.5, 1.0 / 3.0}, b3[3] = {1.0, 0.5, 2.0 / 3.0}"), "rk3"),
     # Coriolis with the wrong sense of rotation
     "coriolis_sign": (("- tau * uu[q] + P->f_c * V[q];", "- tau * uu[q] - P->f_c * V[q];"), "source"),
     # the quadratic friction law with |u|^2 instead of |u|
