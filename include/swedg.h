@@ -93,7 +93,8 @@ int swe_create(swe_ctx** out, const swe_params* params);
  * device), not released to the CUDA driver. */
 void swe_destroy(swe_ctx* ctx);
 
-/* Text of the last error of the context (or of swe_create when ctx is NULL). */
+/* Text of the last error of the context; with ctx NULL, of the calling
+ * thread's last failed swe_create or swe_mesh_adjacency. */
 const char* swe_last_error(const swe_ctx* ctx);
 
 /* Triangulation (Sect. 2: Omega = union of triangles Omega_e).
@@ -112,6 +113,19 @@ const char* swe_last_error(const swe_ctx* ctx);
  * the state to zero. */
 int swe_set_mesh(swe_ctx* ctx, int64_t nv, const double* xy, int64_t ne, const int32_t* tri,
                  const int8_t* bc_tag);
+
+/* The adjacency swe_set_mesh builds, on the host alone (no context, no
+ * device): the same validation of xy[nv][2] and tri[ne][3], then
+ *   nbr_out[ne][3]  the triangle across the edge opposite vertex k, -1 on the
+ *                   boundary (host, required)
+ *   nbk_out[ne][3]  that triangle's own local index of the shared edge, -1 on
+ *                   the boundary (host, may be NULL)
+ * in the caller's triangle and vertex numbering (a clockwise triangle keeps
+ * its vertex order here).  ne < 2^31.  Errors as swe_set_mesh (SWE_EINVAL
+ * also for a NULL nbr_out); the text is swe_last_error(NULL) on the calling
+ * thread. */
+int swe_mesh_adjacency(int64_t nv, const double* xy, int64_t ne, const int32_t* tri, int32_t* nbr_out,
+                       int8_t* nbk_out);
 
 /* Bathymetry h_b (Eq. 2: H = h_b + xi), depths > 0 below the datum, given at
  * the vertices (host [nv]); the library uses its continuous piecewise-linear

@@ -175,8 +175,9 @@ static int cuda_err(swe_ctx* c, int rc) {
     if (e__ != cudaSuccess) return cuda_err(ctx, cuda_fail(e__, #call, __FILE__, __LINE__)); \
   } while (0)
 
-static const char* g_create_err = "";
-static std::string g_create_err_s;
+// errors of the calls without a context (swe_create, swe_mesh_adjacency), per thread
+static thread_local const char* g_create_err = "";
+static thread_local std::string g_create_err_s;
 
 // ------------------------------------------------------------------ memory
 // Device buffers come from one stream-ordered memory pool per device, shared
@@ -1103,6 +1104,32 @@ int swe_set_mesh(swe_ctx* ctx, int64_t nv, const double* xy, int64_t ne, const i
   ctx->dirty = true;
   ctx->keep_valid = false;
   std::vector<double>().swap(ctx->keep_c);
+  return 0;
+}
+
+int swe_mesh_adjacency(int64_t nv, const double* xy, int64_t ne, const int32_t* tri, int32_t* nbr_out,
+                       int8_t* nbk_out) {
+  if (!nbr_out || ne > (int64_t)INT32_MAX) {
+    g_create_err = "swe_mesh_adjacency: NULL nbr_out or ne >= 2^31";
+    return SWE_EINVAL;
+  }
+  swe_ctx tmp;  // the host description only: swe_set_mesh touches no device
+  const int rc = swe_set_mesh(&tmp, nv, xy, ne, tri, nullptr);
+  if (rc) {
+    g_create_err_s = tmp.err;
+    g_create_err = g_create_err_s.c_str();
+    return rc;
+  }
+  // swe_set_mesh re-orients a clockwise triangle by swapping its vertices 1
+  // and 2, which swaps its local edges 1 and 2 (a swap is its own inverse)
+  auto local = [&](int64_t e, int k) { return tmp.tri[3 * e + 1] != tri[3 * e + 1] && k ? 3 - k : k; };
+  for (int64_t e = 0; e < ne; ++e)
+    for (int k = 0; k < 3; ++k) {
+      const int ki = local(e, k);
+      const int64_t n = tmp.nb[3 * e + ki];
+      nbr_out[3 * e + k] = (int32_t)n;
+      if (nbk_out) nbk_out[3 * e + k] = n < 0 ? (int8_t)-1 : (int8_t)local(n, tmp.nbk[3 * e + ki]);
+    }
   return 0;
 }
 

@@ -48,7 +48,7 @@ SYMBOLS = ("swe_default_params", "swe_create", "swe_destroy", "swe_last_error", 
            "swe_memory_bytes", "swe_tc_operand_image", "swe_get_launch_shape", "swe_set_launch_shape",
            "swe_autotune", "swe_selftest_wait", "swe_packed_size", "swe_set_state_packed",
            "swe_get_state_packed", "swe_set_state_packed_async", "swe_run_async", "swe_get_state_packed_async",
-           "swe_sync", "swe_member_status")
+           "swe_sync", "swe_member_status", "swe_mesh_adjacency")
 
 
 def library_path() -> str:
@@ -73,6 +73,7 @@ def load():
     lib.swe_last_error.argtypes = [P]
     lib.swe_last_error.restype = C.c_char_p
     lib.swe_set_mesh.argtypes = [P, i64, P, i64, P, P]
+    lib.swe_mesh_adjacency.argtypes = [i64, P, i64, P, P, P]
     lib.swe_set_bathymetry.argtypes = [P, P]
     lib.swe_set_orders.argtypes = [P, P]
     lib.swe_set_state.argtypes = [P, P, d]
@@ -140,6 +141,23 @@ def tc_operand_image(K: int):
     out = np.zeros(n, np.float32)
     lib.swe_tc_operand_image(int(K), out.ctypes.data_as(C.c_void_p), C.c_int64(n))
     return out
+
+
+def mesh_adjacency(xy, tri):
+    """(nbr [ne,3] int32, nbk [ne,3] int8) of the library's adjacency build
+    (host only, no device): the triangle across the edge opposite vertex k and
+    its local index of that edge, -1 on the boundary"""
+    lib = load()
+    pxy, kx = _ptr(xy)
+    pt, kt = _ptr(tri, np.int32)
+    ne = int(np.shape(tri)[0])
+    nbr = np.zeros((ne, 3), np.int32)
+    nbk = np.zeros((ne, 3), np.int8)
+    rc = lib.swe_mesh_adjacency(int(np.shape(xy)[0]), pxy, ne, pt, nbr.ctypes.data_as(C.c_void_p),
+                                nbk.ctypes.data_as(C.c_void_p))
+    if rc:
+        raise SweError(rc, lib.swe_last_error(None).decode())
+    return nbr, nbk
 
 
 def edge_table(npts: int):
