@@ -10,7 +10,9 @@
  *
  * What is followed, passage by passage:
  *   Sect. 2, Eqs. (1)-(5)  : conservative SWE, flux A(c,u), source r(c,u),
- *                            H = h_b + xi; friction, Coriolis and F are zero.
+ *                            H = h_b + xi; bottom friction (linear and
+ *                            quadratic law) and Coriolis as parameters, zero
+ *                            by default; the body force F is zero.
  *   Sect. 2, Eqs. (8)-(9)  : semi-discrete weak form, orthonormal basis so the
  *                            mass matrix is the identity.
  *   Sect. 2, LF flux       : A_hat = 1/2((A(c)+A(c+)).n + lambda (c - c+)).
