@@ -17,6 +17,28 @@ DEG = np.array([0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4])
 MODES = [(d - b, b) for d in range(5) for b in range(d + 1)]  # (a, b), ordered by degree then b
 
 
+def brute_force_adjacency(tri):
+    """(nbr, nbk) [ne,3]: edge k of triangle e joins the two vertices other
+    than vertex k; two triangles are neighbours across an edge with the same
+    two vertices, nbk the neighbour's local index of it; -1 on the boundary.
+    Raises on an edge of more than two triangles."""
+    ne = len(tri)
+    nbr = np.full((ne, 3), -1, np.int64)
+    nbk = np.full((ne, 3), -1, np.int64)
+    sides = {}
+    for e in range(ne):
+        for k in range(3):
+            key = tuple(sorted((int(tri[e][(k + 1) % 3]), int(tri[e][(k + 2) % 3]))))
+            sides.setdefault(key, []).append((e, k))
+    for s in sides.values():
+        if len(s) > 2:
+            raise ValueError("non-manifold edge")
+        if len(s) == 2:
+            (a, ka), (b, kb) = s
+            nbr[a, ka], nbk[a, ka], nbr[b, kb], nbk[b, kb] = b, kb, a, ka
+    return nbr, nbk
+
+
 def _dleg(n, x):
     # d/dx P_n = n (x P_n - P_{n-1}) / (x^2 - 1), via the Jacobi derivative identity instead:
     # d/dx P_n^{(0,0)} = (n+1)/2 P_{n-1}^{(1,1)}

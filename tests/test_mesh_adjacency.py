@@ -5,6 +5,7 @@ rejection of invalid meshes."""
 import numpy as np
 import pytest
 
+from dgref import brute_force_adjacency
 from paper_2311_11348_gb300 import build, inputs, swedg
 
 
@@ -12,25 +13,6 @@ from paper_2311_11348_gb300 import build, inputs, swedg
 def lib():
     build.build()
     swedg.load()
-
-
-def brute_force_adjacency(tri):
-    """edge k of triangle e joins the two vertices other than vertex k; two
-    triangles are neighbours across an edge with the same two vertices"""
-    ne = len(tri)
-    nbr = np.full((ne, 3), -1, np.int64)
-    nbk = np.full((ne, 3), -1, np.int64)
-    sides = {}
-    for e in range(ne):
-        for k in range(3):
-            key = tuple(sorted((int(tri[e][(k + 1) % 3]), int(tri[e][(k + 2) % 3]))))
-            sides.setdefault(key, []).append((e, k))
-    for s in sides.values():
-        assert len(s) <= 2
-        if len(s) == 2:
-            (a, ka), (b, kb) = s
-            nbr[a, ka], nbk[a, ka], nbr[b, kb], nbk[b, kb] = b, kb, a, ka
-    return nbr, nbk
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])

@@ -194,6 +194,37 @@ def fv_rhs(xy, tri, hv, means, g):
     return d / area
 
 
+def test_neighbour_map_equals_brute_force_pairing():
+    """the oracle's mesh set-up: clockwise triangles re-oriented (a permutation
+    of the given vertices with positive area), the neighbour map and local
+    edge indices of the re-oriented triangles equal a brute-force pairing of
+    their edges, boundary edges land unless tagged open sea"""
+    rng = np.random.default_rng(21)
+    xy, tri = inputs.split_square_mesh(6, 1.0, jitter=0.2, seed=21)
+    tri = tri[rng.permutation(len(tri))].astype(np.int32)
+    flip = rng.uniform(size=len(tri)) < 0.4
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    bc = inputs.boundary_tags(xy, tri, "west")
+    m = O.Mesh(xy, tri, np.ones(len(xy)), np.ones(len(tri), np.int8), bc_tag=bc)
+    nb = m.neighbours()
+    t = nb["tri"]
+    assert np.array_equal(np.sort(t, axis=1), np.sort(tri, axis=1))
+    a, b, c = xy[t[:, 0]], xy[t[:, 1]], xy[t[:, 2]]
+    assert np.all((b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (c[:, 0] - a[:, 0]) * (b[:, 1] - a[:, 1]) > 0)
+    rb, rk = dgref.brute_force_adjacency(t)
+    assert np.array_equal(nb["nb"], rb) and np.array_equal(nb["nbk"], rk)
+    boundary = rb < 0
+    assert np.all(nb["bc"][~boundary] == 0)
+    # tags follow the caller's local edge numbering: edge k opposite vertex k of the given triangle
+    open_edges = set()
+    for e, k in zip(*np.nonzero(bc == 2)):
+        open_edges.add((e, frozenset((int(tri[e][(k + 1) % 3]), int(tri[e][(k + 2) % 3])))))
+    assert len(open_edges) == 6
+    for e, k in zip(*np.nonzero(boundary)):
+        key = (e, frozenset((int(t[e][(k + 1) % 3]), int(t[e][(k + 2) % 3]))))
+        assert nb["bc"][e, k] == (2 if key in open_edges else 1)
+
+
 def test_p0_is_first_order_finite_volumes():
     xy, tri = inputs.split_square_mesh(6, 2.0, jitter=0.2, seed=3)
     ne = len(tri)
