@@ -17,8 +17,8 @@
  *    text of the last failure is available from swe_last_error().
  *  - The library owns all device memory.  Buffers passed in are copied before
  *    the call returns and not retained, except by the asynchronous transfers
- *    (swe_*_async: until swe_sync returns) and the caller's CUDA stream of
- *    swe_params (for the context's lifetime).
+ *    (swe_*_async: until swe_sync returns) and the caller's CUDA stream in
+ *    the parameters, which the context uses for its lifetime.
  *  - Pointers marked "host or device" may point to host memory or to device
  *    memory of the context's device (detected with cudaPointerGetAttributes).
  *  - State arrays use the layout c[3][15][ne]: field (0 = xi, 1 = U, 2 = V),
