@@ -194,6 +194,31 @@ def fv_rhs(xy, tri, hv, means, g):
     return d / area
 
 
+def test_mesh_geometry_closed_forms():
+    """per element: |Omega_e| = the shoelace area, s_e = sqrt(2 |Omega_e|)
+    (sqrt |det J_e|), the gradient of a linear bathymetry a + b x + c y is
+    (b, c) exactly, and its three P1 modes are those of that plane: the
+    element mean times sqrt|Omega_e| in mode 0"""
+    rng = np.random.default_rng(31)
+    xy, tri = inputs.split_square_mesh(5, 3.0, jitter=0.25, seed=31)
+    tri = tri.astype(np.int32)
+    flip = rng.uniform(size=len(tri)) < 0.5
+    tri[flip] = tri[flip][:, [0, 2, 1]]
+    a0, b0, c0 = 40.0, -3.0, 5.5
+    hv = a0 + b0 * xy[:, 0] + c0 * xy[:, 1]
+    m = O.Mesh(xy, tri, hv, np.ones(len(tri), np.int8))
+    geo = m.geometry()
+    P = xy[tri]
+    area = 0.5 * np.abs((P[:, 1, 0] - P[:, 0, 0]) * (P[:, 2, 1] - P[:, 0, 1])
+                        - (P[:, 2, 0] - P[:, 0, 0]) * (P[:, 1, 1] - P[:, 0, 1]))
+    assert np.allclose(geo["area"], area, rtol=1e-14, atol=0)
+    assert np.allclose(geo["s"], np.sqrt(2.0 * area), rtol=1e-14, atol=0)
+    assert np.allclose(geo["dhb"], np.tile([b0, c0], (len(tri), 1)), rtol=0, atol=1e-12)
+    centroid = P.mean(axis=1)
+    mean = a0 + b0 * centroid[:, 0] + c0 * centroid[:, 1]
+    assert np.allclose(geo["hb"][:, 0], mean * np.sqrt(area), rtol=1e-13, atol=0)
+
+
 def test_neighbour_map_equals_brute_force_pairing():
     """the oracle's mesh set-up: clockwise triangles re-oriented (a permutation
     of the given vertices with positive area), the neighbour map and local
