@@ -1,5 +1,5 @@
 // libswedg host side: the C ABI of include/swedg.h, mesh processing (the
-// "buffered geometric information" of Sect. 4), grouping of the elements by
+// per-element and per-edge geometry kept between steps, Sect. 4), grouping of the elements by
 // polynomial order, device buffers and the SSP Runge-Kutta driver.
 //
 // One RK stage (Sect. 2 time stepping, Sect. 3 order separation):
